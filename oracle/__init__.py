@@ -1,0 +1,316 @@
+"""FP64 CPU oracle for the data-parallel volume rendering path.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+benchmark's CPU-baseline leg, never by the product package.  The C source
+(`dpv_oracle.c`) is compiled with gcc into `liboracle.so` next to it on first
+use (or by `build()`); it shares no code with the CUDA path.
+
+Each wrapper states the passage or reading it follows; the arithmetic itself
+is in the C file.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dpv_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+F32, F16, BF16, FP8 = 0, 1, 2, 3
+DTYPE_NAMES = {"f32": F32, "f16": F16, "bf16": BF16, "fp8": FP8}
+NP_STORAGE = {F32: np.float32, F16: np.uint16, BF16: np.uint16, FP8: np.uint8}
+KEY_EMPTY = 2 ** 31 - 1
+FLAG_HIT, FLAG_EXIT_AMBIG, FLAG_OWNER_AMBIG, FLAG_ERT_AMBIG = 1, 2, 4, 8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, -O2, OpenMP) if missing or stale."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-fPIC", "-shared",
+                               "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Grid(C.Structure):
+    _fields_ = [("dims", C.c_int * 3), ("origin", C.c_double * 3), ("spacing", C.c_double)]
+
+
+class _Camera(C.Structure):
+    _fields_ = [("eye", C.c_double * 3), ("center", C.c_double * 3), ("up", C.c_double * 3),
+                ("fovy_deg", C.c_double)]
+
+
+class _Frame(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("step_voxels", C.c_double),
+                ("sigma_max", C.c_double), ("ert", C.c_double), ("amb_samples", C.c_double),
+                ("amb_alpha", C.c_double)]
+
+
+class _Brick(C.Structure):
+    _fields_ = [("owned_lo", C.c_int * 3), ("owned_hi", C.c_int * 3), ("dtype", C.c_int),
+                ("scale", C.c_double), ("data", C.c_void_p)]
+
+
+class _TF(C.Structure):
+    _fields_ = [("rgba", C.c_void_p), ("n", C.c_int), ("vmin", C.c_double), ("vmax", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.c_void_p
+        _lib.orc_render_full.argtypes = [P, P, P, P, P, C.c_int, P, P, P, P]
+        _lib.orc_render_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P, P, P, P, P]
+        _lib.orc_grad_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P]
+        _lib.orc_composite.argtypes = [C.c_int, C.c_int, P, P, P, P]
+        _lib.orc_kd_order.argtypes = [C.c_int, P, P, P, P, P, P]
+        _lib.orc_kd_order.restype = C.c_int
+        _lib.orc_camera_ray.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
+        _lib.orc_brick_scale.argtypes = [P, C.c_int64, C.c_int]
+        _lib.orc_brick_scale.restype = C.c_float
+        _lib.orc_quantize.argtypes = [P, C.c_int64, C.c_int, C.c_float, P]
+        _lib.orc_dequantize.argtypes = [P, C.c_int64, C.c_int, C.c_double, P]
+        _lib.orc_stored_box.argtypes = [P, P, P, P, P]
+        _lib.orc_extract_brick.argtypes = [P, P, P, P, P]
+        _lib.orc_max_threads.restype = C.c_int
+        _lib.orc_set_threads.argtypes = [C.c_int]
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
+
+
+@dataclass
+class Frame:
+    """Frame parameters (R2, R4, R6): image size, step in voxels, sigma_max,
+    per-fragment early-termination threshold (0 = off) and the ambiguity
+    bands used for flags."""
+    width: int
+    height: int
+    step_voxels: float = 0.5
+    sigma_max: float = 8.0
+    ert: float = 0.0
+    amb_samples: float = 1e-2
+    amb_alpha: float = 1e-4
+
+    def c(self) -> _Frame:
+        return _Frame(self.width, self.height, self.step_voxels, self.sigma_max, self.ert,
+                      self.amb_samples, self.amb_alpha)
+
+
+def _grid(dims, origin=(0.0, 0.0, 0.0), spacing=None) -> _Grid:
+    sp = 1.0 / (max(dims) - 1) if spacing is None else spacing
+    return _Grid((C.c_int * 3)(*dims), (C.c_double * 3)(*origin), sp)
+
+
+def _camera(cam) -> _Camera:
+    return _Camera((C.c_double * 3)(*cam.eye), (C.c_double * 3)(*cam.center), (C.c_double * 3)(*cam.up),
+                   float(cam.fovy_deg))
+
+
+def _tf(tab: np.ndarray, vmin: float, vmax: float):
+    tab = np.ascontiguousarray(tab, dtype=np.float32)
+    return _TF(tab.ctypes.data, tab.shape[0], vmin, vmax), tab
+
+
+def _pix(pix, frame: Frame):
+    if pix is None:
+        return frame.width * frame.height, None, None
+    arr = np.ascontiguousarray(pix, dtype=np.int32)
+    return int(arr.size), _p(arr), arr
+
+
+# ---------------------------------------------------------------------------
+# number formats and bricks (R1, a0)
+# ---------------------------------------------------------------------------
+
+def brick_scale(values: np.ndarray, dtype: int) -> np.float32:
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    return np.float32(lib().orc_brick_scale(_p(v), v.size, dtype))
+
+
+def quantize(values: np.ndarray, dtype: int, scale: float = 1.0) -> np.ndarray:
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    out = np.empty(v.shape, dtype=NP_STORAGE[dtype])
+    lib().orc_quantize(_p(v), v.size, dtype, float(np.float32(scale)), _p(out))
+    return out
+
+
+def dequantize(stored: np.ndarray, dtype: int, scale: float = 1.0) -> np.ndarray:
+    s = np.ascontiguousarray(stored)
+    out = np.empty(s.shape, dtype=np.float64)
+    lib().orc_dequantize(_p(s), s.size, dtype, float(scale), _p(out))
+    return out
+
+
+def stored_box(dims, lo, hi):
+    """(first node, node count) per axis of the nodes a rank stores."""
+    d = np.array(dims, np.int32)
+    l = np.array(lo, np.int32)
+    h = np.array(hi, np.int32)
+    s_lo = np.zeros(3, np.int32)
+    s_n = np.zeros(3, np.int32)
+    lib().orc_stored_box(_p(d), _p(l), _p(h), _p(s_lo), _p(s_n))
+    return s_lo, s_n
+
+
+def extract_brick(field: np.ndarray, lo, hi) -> np.ndarray:
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    dims = np.array([f.shape[2], f.shape[1], f.shape[0]], np.int32)
+    _, s_n = stored_box(dims, lo, hi)
+    out = np.empty((s_n[2], s_n[1], s_n[0]), np.float32)
+    l = np.array(lo, np.int32)
+    h = np.array(hi, np.int32)
+    lib().orc_extract_brick(_p(f), _p(dims), _p(l), _p(h), _p(out))
+    return out
+
+
+@dataclass
+class Brick:
+    lo: Sequence[int]
+    hi: Sequence[int]
+    dtype: int
+    scale: float
+    data: np.ndarray          # stored nodes in the storage format
+
+
+def make_bricks(field: np.ndarray, partition, dtype: int = F32) -> List[Brick]:
+    """The oracle's own brick commit: extract stored nodes (owned + 1 ghost),
+    choose the per-brick scale and quantise."""
+    out = []
+    for k in range(partition.num_ranks):
+        lo, hi = [int(x) for x in partition.lo[k]], [int(x) for x in partition.hi[k]]
+        v = extract_brick(field, lo, hi)
+        sc = brick_scale(v, dtype)
+        out.append(Brick(lo, hi, dtype, float(sc), quantize(v, dtype, sc)))
+    return out
+
+
+def _bricks_c(bricks: List[Brick]):
+    arr = (_Brick * len(bricks))()
+    keep = []
+    for i, b in enumerate(bricks):
+        d = np.ascontiguousarray(b.data)
+        keep.append(d)
+        arr[i] = _Brick((C.c_int * 3)(*b.lo), (C.c_int * 3)(*b.hi), b.dtype, float(b.scale), d.ctypes.data)
+    return arr, keep
+
+
+# ---------------------------------------------------------------------------
+# rendering
+# ---------------------------------------------------------------------------
+
+def camera_ray(cam, width: int, height: int, px: int, py: int):
+    """Eye and unit direction of the ray through pixel (px, py) (R5)."""
+    o = np.zeros(3)
+    d = np.zeros(3)
+    c = _camera(cam)
+    lib().orc_camera_ray(C.byref(c), width, height, px, py, _p(o), _p(d))
+    return o, d
+
+
+def render_full(field: np.ndarray, tf: np.ndarray, cam, frame: Frame, pix=None, vmin=0.0, vmax=1.0,
+                origin=(0.0, 0.0, 0.0), spacing=None):
+    """Unpartitioned FP64 render of the global float32 field (no early
+    termination): the plain definition the partitioned path reproduces."""
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    dims = (f.shape[2], f.shape[1], f.shape[0])
+    g = _grid(dims, origin, spacing)
+    t, tab = _tf(tf, vmin, vmax)
+    cam_c = _camera(cam)
+    fr = frame.c()
+    n, pp, keep = _pix(pix, frame)
+    rgba = np.zeros((n, 4))
+    ns = np.zeros(n, np.int64)
+    fl = np.zeros(n, np.uint8)
+    lib().orc_render_full(C.byref(g), _p(f), C.byref(t), C.byref(cam_c), C.byref(fr), n, pp, _p(rgba), _p(ns), _p(fl))
+    return {"rgba": rgba, "nsamples": ns, "flags": fl}
+
+
+def render_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, pix=None, vmin=0.0, vmax=1.0,
+                  origin=(0.0, 0.0, 0.0), spacing=None):
+    """Partitioned FP64 render: per-brick fragments (with per-fragment early
+    termination when frame.ert is set), sort by key, front-to-back over."""
+    g = _grid(dims, origin, spacing)
+    t, tab = _tf(tf, vmin, vmax)
+    cam_c = _camera(cam)
+    fr = frame.c()
+    K = len(bricks)
+    barr, keep_b = _bricks_c(bricks)
+    n, pp, keep = _pix(pix, frame)
+    res = {
+        "rgba": np.zeros((n, 4)), "depth": np.zeros(n), "order": np.zeros((n, K), np.uint8),
+        "frag_rgba": np.zeros((n, K, 4)), "frag_key": np.zeros((n, K), np.int32),
+        "frag_nsamp": np.zeros((n, K), np.int32), "frag_margin": np.zeros((n, K)),
+        "nsamples": np.zeros(n, np.int64), "flags": np.zeros(n, np.uint8),
+    }
+    lib().orc_render_bricks(C.byref(g), K, barr, C.byref(t), C.byref(cam_c), C.byref(fr), n, pp,
+                            _p(res["rgba"]), _p(res["depth"]), _p(res["order"]), _p(res["frag_rgba"]),
+                            _p(res["frag_key"]), _p(res["frag_nsamp"]), _p(res["frag_margin"]),
+                            _p(res["nsamples"]), _p(res["flags"]))
+    return res
+
+
+def grad_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, grad_rgba: np.ndarray, pix=None,
+                vmin=0.0, vmax=1.0, want_volume=True, origin=(0.0, 0.0, 0.0), spacing=None):
+    """FP64 reverse-mode gradient of sum(grad_rgba * image) with respect to the
+    TF table (n x 4) and the global field (nz, ny, nx)."""
+    g = _grid(dims, origin, spacing)
+    t, tab = _tf(tf, vmin, vmax)
+    cam_c = _camera(cam)
+    fr = frame.c()
+    K = len(bricks)
+    barr, keep_b = _bricks_c(bricks)
+    n, pp, keep = _pix(pix, frame)
+    gr = np.ascontiguousarray(grad_rgba, dtype=np.float64).reshape(n, 4)
+    dtf = np.zeros((tab.shape[0], 4))
+    dvol = np.zeros((dims[2], dims[1], dims[0])) if want_volume else None
+    lib().orc_grad_bricks(C.byref(g), K, barr, C.byref(t), C.byref(cam_c), C.byref(fr), n, pp, _p(gr), _p(dtf),
+                          _p(dvol) if dvol is not None else None)
+    return dtf, dvol
+
+
+def composite(frag_rgba: np.ndarray, frag_key: np.ndarray):
+    """Sort-last composite of given fragments (npix, K, 4) / (npix, K)."""
+    fr = np.ascontiguousarray(frag_rgba, dtype=np.float64)
+    fk = np.ascontiguousarray(frag_key, dtype=np.int32)
+    n, K = fk.shape
+    rgba = np.zeros((n, 4))
+    order = np.zeros((n, K), np.uint8)
+    lib().orc_composite(n, K, _p(fr), _p(fk), _p(rgba), _p(order))
+    return rgba, order
+
+
+def kd_order(partition, eye_node) -> np.ndarray:
+    """Front-to-back leaf order of the partition's k-d tree from a point given
+    in node coordinates (R7)."""
+    K = partition.num_ranks
+    out = np.zeros(K, np.uint8)
+    ax = np.ascontiguousarray(partition.axis, np.int32)
+    sp = np.ascontiguousarray(partition.split, np.int32)
+    le = np.ascontiguousarray(partition.left, np.int32)
+    ri = np.ascontiguousarray(partition.right, np.int32)
+    e = np.ascontiguousarray(eye_node, np.float64)
+    m = lib().orc_kd_order(int(ax.size), _p(ax), _p(sp), _p(le), _p(ri), _p(e), _p(out))
+    return out[:m]

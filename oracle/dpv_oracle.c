@@ -1,0 +1,860 @@
+/*
+ * dpv_oracle.c -- plain, slow, FP64 CPU oracle for the data-parallel volume
+ * rendering path (sort-last compositing of per-brick ray-march fragments).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link,
+ * load or call this file: only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg use it.  It shares no code, header, table or
+ * constant with the CUDA path.
+ *
+ * What it follows (arXiv 2407.00179, "Standardized Data-Parallel Rendering
+ * Using ANARI"):
+ *   - each rank owns one spatial part of a jointly defined world (§1, §3.1.2);
+ *   - ghost layers make local effects correct across part borders (§1);
+ *   - each rank reduces its render to one fragment (colour, opacity, depth)
+ *     per pixel, which is correct for convex parts (§2.1);
+ *   - fragments carry RGBA and depth and are sorted per pixel, then blended
+ *     front to back (§5.1.1, "Compositing");
+ *   - the final frame exists on rank 0 (§3.1.3).
+ * The paper gives no rendering equations.  The emission-absorption model,
+ * the sampling rule and everything numeric are the readings listed in the
+ * design notes (R1..R12), restated here where they are used.
+ *
+ * Everything is FP64.  Stored brick values (f32, f16, bf16, fp8 e4m3) are
+ * decoded per access and never copied into an FP64 array.
+ *
+ * Parity status: every function below is pinned by a CPU test against a
+ * closed form, an invariant, a library routine or brute force, except the
+ * camera convention (R5) which is pinned only by geometric properties.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_F32 0
+#define ORC_F16 1
+#define ORC_BF16 2
+#define ORC_FP8 3
+
+#define ORC_KEY_EMPTY 2147483647
+
+#define ORC_FLAG_HIT 1
+#define ORC_FLAG_EXIT_AMBIG 2
+#define ORC_FLAG_OWNER_AMBIG 4
+#define ORC_FLAG_ERT_AMBIG 8
+
+typedef struct {
+    int dims[3];          /* nodes per axis */
+    double origin[3];     /* world position of node (0,0,0) */
+    double spacing;       /* world distance between nodes */
+} orc_grid;
+
+typedef struct {
+    double eye[3], center[3], up[3];
+    double fovy_deg;
+} orc_camera;
+
+typedef struct {
+    int width, height;
+    double step_voxels;   /* dt = step_voxels * spacing (world units) */
+    double sigma_max;     /* extinction per world unit at TF alpha 1 */
+    double ert;           /* per-fragment early termination; <=0 or >=1: off */
+    double amb_samples;   /* ambiguity band, in samples, for flags */
+    double amb_alpha;     /* ambiguity band on opacity, for ERT flags */
+} orc_frame;
+
+typedef struct {
+    int owned_lo[3], owned_hi[3];   /* half-open node range owned */
+    int dtype;                      /* ORC_F32 .. ORC_FP8 */
+    double scale;                   /* value = scale * stored */
+    const void* data;               /* stored nodes (see orc_stored_box), x fastest */
+} orc_brick;
+
+typedef struct {
+    const float* rgba;    /* n x 4 */
+    int n;
+    double vmin, vmax;
+} orc_tf;
+
+/* ------------------------------------------------------------------------ */
+/* number formats                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* IEEE binary16 -> double. */
+static double dec_f16(uint16_t h) {
+    int s = (h >> 15) & 1, e = (h >> 10) & 31, m = h & 1023;
+    double v;
+    if (e == 0) v = ldexp((double)m, -24);
+    else if (e == 31) v = m ? NAN : INFINITY;
+    else v = ldexp(1.0 + m / 1024.0, e - 15);
+    return s ? -v : v;
+}
+
+/* bfloat16 (upper half of a binary32) -> double. */
+static double dec_bf16(uint16_t h) {
+    uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* OCP FP8 E4M3 ("fn": no infinities, S.1111.111 is NaN, max 448) -> double. */
+static double dec_fp8(uint8_t b) {
+    int s = (b >> 7) & 1, e = (b >> 3) & 15, m = b & 7;
+    double v;
+    if (e == 0) v = ldexp((double)m, -9);
+    else if (e == 15 && m == 7) v = NAN;
+    else v = ldexp(1.0 + m / 8.0, e - 7);
+    return s ? -v : v;
+}
+
+static double decode(const void* data, int dtype, int64_t i) {
+    switch (dtype) {
+        case ORC_F32: return (double)((const float*)data)[i];
+        case ORC_F16: return dec_f16(((const uint16_t*)data)[i]);
+        case ORC_BF16: return dec_bf16(((const uint16_t*)data)[i]);
+        default: return dec_fp8(((const uint8_t*)data)[i]);
+    }
+}
+
+/* Round x to the nearest value with `mbits` fraction bits, exponent >= emin
+ * (subnormals below), ties to even.  Overflow beyond maxv gives +-inf, or
+ * +-maxv when `sat`. */
+static double round_format(double x, int mbits, int emin, double maxv, int sat) {
+    if (x == 0.0 || isnan(x)) return x;
+    double a = fabs(x);
+    int E;
+    frexp(a, &E);                      /* a = f * 2^E, f in [0.5, 1) */
+    int e = E - 1;                     /* exponent of the leading bit */
+    if (e < emin) e = emin;
+    double q = ldexp(1.0, e - mbits);  /* spacing of representable values */
+    double r = nearbyint(a / q) * q;   /* a / q is exact; nearbyint ties to even */
+    if (r > maxv) r = sat ? maxv : INFINITY;
+    return copysign(r, x);
+}
+
+static uint16_t enc_f16(float f) {
+    double r = round_format((double)f, 10, -14, 65504.0, 0);
+    uint16_t s = signbit(r) ? 0x8000 : 0;
+    double a = fabs(r);
+    if (isinf(a)) return s | 0x7C00;
+    if (a == 0.0) return s;
+    int E;
+    frexp(a, &E);
+    int e = E - 1;
+    if (e < -14) return s | (uint16_t)(a / ldexp(1.0, -24));        /* subnormal */
+    return s | (uint16_t)((e + 15) << 10) | (uint16_t)((a / ldexp(1.0, e) - 1.0) * 1024.0);
+}
+
+static uint16_t enc_bf16(float f) {
+    double r = round_format((double)f, 7, -126, 3.3895313892515355e38, 0);
+    float g = (float)r;
+    uint32_t u;
+    memcpy(&u, &g, 4);
+    return (uint16_t)(u >> 16);
+}
+
+static uint8_t enc_fp8(float f) {
+    double r = round_format((double)f, 3, -6, 448.0, 1);   /* saturating */
+    uint8_t s = signbit(r) ? 0x80 : 0;
+    double a = fabs(r);
+    if (a == 0.0) return s;
+    int E;
+    frexp(a, &E);
+    int e = E - 1;
+    if (e < -6) return s | (uint8_t)(a / ldexp(1.0, -9));
+    return s | (uint8_t)((e + 7) << 3) | (uint8_t)((a / ldexp(1.0, e) - 1.0) * 8.0);
+}
+
+/* Per-brick scale for a storage format: fp8 maps max|v| of the brick's stored
+ * nodes onto 448 (computed in float32: max|v| / 448); the others use 1. */
+float orc_brick_scale(const float* v, int64_t n, int dtype) {
+    if (dtype != ORC_FP8) return 1.0f;
+    float m = 0.0f;
+    for (int64_t i = 0; i < n; ++i) {
+        float a = fabsf(v[i]);
+        if (a > m) m = a;
+    }
+    return m > 0.0f ? m / 448.0f : 1.0f;
+}
+
+/* Quantise float32 values to a storage format: stored = round(v / scale),
+ * the division in float32, rounding to nearest even (fp8 saturates). */
+void orc_quantize(const float* v, int64_t n, int dtype, float scale, void* out) {
+    for (int64_t i = 0; i < n; ++i) {
+        float q = v[i] / scale;
+        switch (dtype) {
+            case ORC_F32: ((float*)out)[i] = q; break;
+            case ORC_F16: ((uint16_t*)out)[i] = enc_f16(q); break;
+            case ORC_BF16: ((uint16_t*)out)[i] = enc_bf16(q); break;
+            default: ((uint8_t*)out)[i] = enc_fp8(q); break;
+        }
+    }
+}
+
+void orc_dequantize(const void* data, int64_t n, int dtype, double scale, double* out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = scale * decode(data, dtype, i);
+}
+
+/* ------------------------------------------------------------------------ */
+/* bricks (R1)                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Nodes a rank stores: its owned nodes [lo, hi) plus one ghost node on each
+ * side, clipped to the volume.  Writes first node and node count per axis. */
+void orc_stored_box(const int dims[3], const int lo[3], const int hi[3], int s_lo[3], int s_n[3]) {
+    for (int a = 0; a < 3; ++a) {
+        int l = lo[a] - 1 < 0 ? 0 : lo[a] - 1;
+        int h = hi[a] > dims[a] - 1 ? dims[a] - 1 : hi[a];
+        s_lo[a] = l;
+        s_n[a] = h - l + 1;
+    }
+}
+
+/* Copy a brick's stored nodes out of the global float32 field (x fastest). */
+void orc_extract_brick(const float* field, const int dims[3], const int lo[3], const int hi[3], float* out) {
+    int s_lo[3], s_n[3];
+    orc_stored_box(dims, lo, hi, s_lo, s_n);
+    int64_t k = 0;
+    for (int z = 0; z < s_n[2]; ++z)
+        for (int y = 0; y < s_n[1]; ++y)
+            for (int x = 0; x < s_n[0]; ++x)
+                out[k++] = field[((int64_t)(z + s_lo[2]) * dims[1] + (y + s_lo[1])) * dims[0] + (x + s_lo[0])];
+}
+
+/* Owned region of a brick in node coordinates: [lo - 1/2, hi - 1/2] per axis,
+ * clipped to the volume box [0, n - 1]. */
+static void owned_region(const orc_grid* g, const orc_brick* b, double r0[3], double r1[3]) {
+    for (int a = 0; a < 3; ++a) {
+        double l = b->owned_lo[a] - 0.5, h = b->owned_hi[a] - 0.5;
+        r0[a] = l < 0.0 ? 0.0 : l;
+        r1[a] = h > g->dims[a] - 1 ? g->dims[a] - 1 : h;
+    }
+}
+
+/* Does node-space point q lie in the brick's owned region?  Half-open
+ * [r0, r1) per axis, except that the volume's upper face is closed. */
+static int owns(const orc_grid* g, const orc_brick* b, const double q[3]) {
+    double r0[3], r1[3];
+    owned_region(g, b, r0, r1);
+    for (int a = 0; a < 3; ++a) {
+        if (q[a] < r0[a]) return 0;
+        if (b->owned_hi[a] >= g->dims[a]) {
+            if (q[a] > r1[a]) return 0;
+        } else if (q[a] >= r1[a]) return 0;
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* trilinear interpolation (R1)                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Trilinear value at node-space point q from a box of nodes [b_lo, b_lo+b_n)
+ * stored x fastest.  Cell index i = clamp(floor(q), b_lo, b_lo + b_n - 2),
+ * weights f = q - i, then lerp in x, y, z.  Corner values are decoded (and
+ * scaled) before interpolation.  Optionally returns the 8 corner indices
+ * (into the box) and weights, corner c = dx + 2 dy + 4 dz. */
+static double trilinear(const void* data, int dtype, double scale, const int b_lo[3], const int b_n[3],
+                        const double q[3], int64_t idx[8], double w[8]) {
+    int i[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        int c = (int)floor(q[a]);
+        if (c < b_lo[a]) c = b_lo[a];
+        if (c > b_lo[a] + b_n[a] - 2) c = b_lo[a] + b_n[a] - 2;
+        i[a] = c - b_lo[a];
+        f[a] = q[a] - c;
+    }
+    double v[8];
+    for (int c = 0; c < 8; ++c) {
+        int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+        int64_t k = ((int64_t)(i[2] + dz) * b_n[1] + (i[1] + dy)) * b_n[0] + (i[0] + dx);
+        v[c] = scale * decode(data, dtype, k);
+        if (idx) idx[c] = k;
+        if (w) w[c] = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+    }
+    double x00 = v[0] + f[0] * (v[1] - v[0]);
+    double x10 = v[2] + f[0] * (v[3] - v[2]);
+    double x01 = v[4] + f[0] * (v[5] - v[4]);
+    double x11 = v[6] + f[0] * (v[7] - v[6]);
+    double y0 = x00 + f[1] * (x10 - x00);
+    double y1 = x01 + f[1] * (x11 - x01);
+    return y0 + f[2] * (y1 - y0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* transfer function (R3)                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Piecewise-linear RGBA lookup: u = clamp((s - vmin) / (vmax - vmin), 0, 1) *
+ * (N - 1), i0 = min(floor(u), N - 2), w = u - i0, value = (1 - w) Tab[i0] +
+ * w Tab[i0 + 1].  Also returns i0, w and du/ds (0 where clamped). */
+static void tf_lookup(const orc_tf* tf, double s, double out[4], int* i0_out, double* w_out, double* duds) {
+    double x = (s - tf->vmin) / (tf->vmax - tf->vmin);
+    double d = (double)(tf->n - 1) / (tf->vmax - tf->vmin);
+    if (x < 0.0) { x = 0.0; d = 0.0; }
+    if (x > 1.0) { x = 1.0; d = 0.0; }
+    double u = x * (tf->n - 1);
+    int i0 = (int)floor(u);
+    if (i0 > tf->n - 2) i0 = tf->n - 2;
+    double w = u - i0;
+    for (int c = 0; c < 4; ++c)
+        out[c] = (1.0 - w) * tf->rgba[4 * i0 + c] + w * tf->rgba[4 * (i0 + 1) + c];
+    if (i0_out) *i0_out = i0;
+    if (w_out) *w_out = w;
+    if (duds) *duds = d;
+}
+
+/* ------------------------------------------------------------------------ */
+/* camera (R5)                                                               */
+/* ------------------------------------------------------------------------ */
+
+static void normalize3(double v[3]) {
+    double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= n; v[1] /= n; v[2] /= n;
+}
+
+static void cross3(const double a[3], const double b[3], double o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Pinhole camera, right-handed look-at: forward f = normalize(center - eye),
+ * right r = normalize(f x up), true up u = r x f.  Pixel (px, py), row 0 at
+ * the bottom, is hit through its centre: ndc = ((px + 1/2) / W * 2 - 1) * W/H
+ * horizontally and (py + 1/2) / H * 2 - 1 vertically; the direction is
+ * normalize(f + ndc_x tan(fovy/2) r + ndc_y tan(fovy/2) u), origin the eye. */
+void orc_camera_ray(const orc_camera* c, int W, int H, int px, int py, double o[3], double d[3]) {
+    double f[3] = {c->center[0] - c->eye[0], c->center[1] - c->eye[1], c->center[2] - c->eye[2]};
+    normalize3(f);
+    double r[3], u[3];
+    cross3(f, c->up, r);
+    normalize3(r);
+    cross3(r, f, u);
+    double th = tan(c->fovy_deg * M_PI / 360.0);
+    double nx = (((px + 0.5) / W) * 2.0 - 1.0) * ((double)W / H);
+    double ny = ((py + 0.5) / H) * 2.0 - 1.0;
+    for (int a = 0; a < 3; ++a) {
+        d[a] = f[a] + nx * th * r[a] + ny * th * u[a];
+        o[a] = c->eye[a];
+    }
+    normalize3(d);
+}
+
+/* Ray against the axis-aligned world box [lo, hi]: parametric interval,
+ * clipped to t >= 0.  Returns 1 when non-empty. */
+static int ray_box(const double o[3], const double d[3], const double lo[3], const double hi[3],
+                   double* t0, double* t1) {
+    double a = 0.0, b = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        if (d[k] == 0.0) {
+            if (o[k] < lo[k] || o[k] > hi[k]) return 0;
+            continue;
+        }
+        double ta = (lo[k] - o[k]) / d[k], tb = (hi[k] - o[k]) / d[k];
+        if (ta > tb) { double s = ta; ta = tb; tb = s; }
+        if (ta > a) a = ta;
+        if (tb < b) b = tb;
+    }
+    *t0 = a;
+    *t1 = b;
+    return a < b;
+}
+
+/* ------------------------------------------------------------------------ */
+/* samples along a ray (R2)                                                  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double o[3], d[3];
+    double t_enter, t_exit, dt;
+    int64_t n;            /* number of samples */
+    int flags;
+} orc_rayinfo;
+
+/* Ray of pixel (px, py) against the whole volume box; samples sit at
+ * t_j = t_enter + (j + 1/2) dt for every j >= 0 with t_j < t_exit. */
+static void ray_samples(const orc_grid* g, const orc_camera* cam, const orc_frame* fr, int px, int py,
+                        orc_rayinfo* ri) {
+    orc_camera_ray(cam, fr->width, fr->height, px, py, ri->o, ri->d);
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = g->origin[a];
+        hi[a] = g->origin[a] + (g->dims[a] - 1) * g->spacing;
+    }
+    ri->dt = fr->step_voxels * g->spacing;
+    ri->n = 0;
+    ri->flags = 0;
+    if (!ray_box(ri->o, ri->d, lo, hi, &ri->t_enter, &ri->t_exit)) return;
+    ri->flags |= ORC_FLAG_HIT;
+    double x = (ri->t_exit - ri->t_enter) / ri->dt - 0.5;
+    int64_t n = (int64_t)ceil(x);
+    if (n < 0) n = 0;
+    while (n > 0 && ri->t_enter + (n - 0.5) * ri->dt >= ri->t_exit) --n;
+    while (ri->t_enter + (n + 0.5) * ri->dt < ri->t_exit) ++n;
+    ri->n = n;
+    if (fabs(x - nearbyint(x)) < fr->amb_samples) ri->flags |= ORC_FLAG_EXIT_AMBIG;
+}
+
+static void sample_point(const orc_grid* g, const orc_rayinfo* ri, int64_t j, double q[3], double* t) {
+    double tj = ri->t_enter + (j + 0.5) * ri->dt;
+    for (int a = 0; a < 3; ++a) {
+        double p = ri->o[a] + tj * ri->d[a];
+        q[a] = (p - g->origin[a]) / g->spacing;
+        if (q[a] < 0.0) q[a] = 0.0;                       /* rounding at the box */
+        if (q[a] > g->dims[a] - 1) q[a] = g->dims[a] - 1;
+    }
+    if (t) *t = tj;
+}
+
+/* ------------------------------------------------------------------------ */
+/* emission-absorption (R4)                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Classify one sample: TF colour c and opacity alpha = 1 - exp(-sigma dt)
+ * with sigma = sigma_max * a. */
+static void classify(const orc_tf* tf, const orc_frame* fr, double dt, double s, double c[3], double* alpha) {
+    double v[4];
+    tf_lookup(tf, s, v, NULL, NULL, NULL);
+    c[0] = v[0]; c[1] = v[1]; c[2] = v[2];
+    *alpha = 1.0 - exp(-fr->sigma_max * v[3] * dt);
+}
+
+/* Unpartitioned render of the global float32 field: front-to-back
+ * C += T alpha c, T *= (1 - alpha), A = 1 - T over every sample of the ray,
+ * no early termination.  This is the plain definition every partitioned
+ * result must reproduce.  Outputs per listed pixel: rgba (premultiplied),
+ * sample count, flags. */
+void orc_render_full(const orc_grid* g, const float* field, const orc_tf* tf, const orc_camera* cam,
+                     const orc_frame* fr, int npix, const int32_t* pix,
+                     double* rgba, int64_t* nsamples, uint8_t* flags) {
+    int all_lo[3] = {0, 0, 0};
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < npix; ++k) {
+        int p = pix ? pix[k] : k;
+        orc_rayinfo ri;
+        ray_samples(g, cam, fr, p % fr->width, p / fr->width, &ri);
+        double C[3] = {0, 0, 0}, T = 1.0;
+        for (int64_t j = 0; j < ri.n; ++j) {
+            double q[3];
+            sample_point(g, &ri, j, q, NULL);
+            double s = trilinear(field, ORC_F32, 1.0, all_lo, g->dims, q, NULL, NULL);
+            double c[3], al;
+            classify(tf, fr, ri.dt, s, c, &al);
+            for (int a = 0; a < 3; ++a) C[a] += T * al * c[a];
+            T *= 1.0 - al;
+        }
+        rgba[4 * k + 0] = C[0];
+        rgba[4 * k + 1] = C[1];
+        rgba[4 * k + 2] = C[2];
+        rgba[4 * k + 3] = 1.0 - T;
+        if (nsamples) nsamples[k] = ri.n;
+        if (flags) flags[k] = (uint8_t)ri.flags;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* per-brick fragments and sort-last compositing                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double C[3], T;
+    int64_t key;          /* first global sample index, or EMPTY */
+    int32_t nsamp;        /* samples evaluated */
+    int done;             /* early-terminated */
+    double margin;        /* distance of opacity to the ERT threshold at stop */
+} frag_state;
+
+static int find_owner(const orc_grid* g, int K, const orc_brick* b, const double q[3], int hint) {
+    if (hint >= 0 && owns(g, &b[hint], q)) return hint;
+    for (int k = 0; k < K; ++k)
+        if (owns(g, &b[k], q)) return k;
+    return -1;
+}
+
+/* Is the sample within `band` samples of an internal face of its owner? */
+static int near_internal_face(const orc_grid* g, const orc_brick* b, const orc_rayinfo* ri, double tj,
+                              double band) {
+    double r0[3], r1[3];
+    owned_region(g, b, r0, r1);
+    for (int a = 0; a < 3; ++a) {
+        if (ri->d[a] == 0.0) continue;
+        double faces[2] = {r0[a], r1[a]};
+        int internal[2] = {b->owned_lo[a] > 0, b->owned_hi[a] < g->dims[a]};
+        for (int s = 0; s < 2; ++s) {
+            if (!internal[s]) continue;
+            double pw = g->origin[a] + faces[s] * g->spacing;
+            double tf = (pw - ri->o[a]) / ri->d[a];
+            if (fabs(tj - tf) < band * ri->dt) return 1;
+        }
+    }
+    return 0;
+}
+
+/* Fragments of one pixel: every sample goes to the brick owning its
+ * position; each brick front-to-back accumulates its own samples (with
+ * per-fragment early termination when enabled).  Fragment = premultiplied
+ * RGBA, key = global index of its first sample. */
+static void pixel_fragments(const orc_grid* g, int K, const orc_brick* b, const orc_tf* tf,
+                            const orc_frame* fr, const orc_rayinfo* ri, frag_state* fs, int* flags) {
+    int bl[3], bn[3];
+    for (int k = 0; k < K; ++k) {
+        fs[k].C[0] = fs[k].C[1] = fs[k].C[2] = 0.0;
+        fs[k].T = 1.0;
+        fs[k].key = ORC_KEY_EMPTY;
+        fs[k].nsamp = 0;
+        fs[k].done = 0;
+        fs[k].margin = INFINITY;
+    }
+    int ert_on = fr->ert > 0.0 && fr->ert < 1.0;
+    int owner = -1;
+    for (int64_t j = 0; j < ri->n; ++j) {
+        double q[3], tj;
+        sample_point(g, ri, j, q, &tj);
+        owner = find_owner(g, K, b, q, owner);
+        if (owner < 0) continue;     /* unreachable for a valid partition */
+        frag_state* f = &fs[owner];
+        if (near_internal_face(g, &b[owner], ri, tj, fr->amb_samples)) *flags |= ORC_FLAG_OWNER_AMBIG;
+        if (f->key == ORC_KEY_EMPTY) f->key = j;
+        if (f->done) continue;
+        orc_stored_box(g->dims, b[owner].owned_lo, b[owner].owned_hi, bl, bn);
+        double s = trilinear(b[owner].data, b[owner].dtype, b[owner].scale, bl, bn, q, NULL, NULL);
+        double c[3], al;
+        classify(tf, fr, ri->dt, s, c, &al);
+        double A_before = 1.0 - f->T;
+        for (int a = 0; a < 3; ++a) f->C[a] += f->T * al * c[a];
+        f->T *= 1.0 - al;
+        f->nsamp++;
+        if (ert_on && 1.0 - f->T > fr->ert) {
+            f->done = 1;
+            double m1 = (1.0 - f->T) - fr->ert, m0 = fr->ert - A_before;
+            f->margin = m1 < m0 ? m1 : m0;
+            if (f->margin < fr->amb_alpha) *flags |= ORC_FLAG_ERT_AMBIG;
+        }
+    }
+}
+
+/* Order of a pixel's fragments: non-empty fragments by ascending key (keys
+ * of non-empty fragments are distinct), written as brick ids, then 0xFF. */
+static int fragment_order(int K, const frag_state* fs, uint8_t* order) {
+    int m = 0;
+    for (int k = 0; k < K; ++k)
+        if (fs[k].key != ORC_KEY_EMPTY) order[m++] = (uint8_t)k;
+    for (int i = 1; i < m; ++i) {          /* insertion sort by key */
+        uint8_t v = order[i];
+        int j = i - 1;
+        while (j >= 0 && fs[order[j]].key > fs[v].key) {
+            order[j + 1] = order[j];
+            --j;
+        }
+        order[j + 1] = v;
+    }
+    for (int k = m; k < K; ++k) order[k] = 0xFF;
+    return m;
+}
+
+/* Sort-last composite of one pixel: front-to-back "over" on premultiplied
+ * RGBA, C += (1 - A) C_k, A += (1 - A) A_k, in key order.  Depth = t of the
+ * first sample of the first fragment with A_k > 0, +inf if none. */
+static void composite_pixel(int K, const frag_state* fs, const orc_rayinfo* ri, const uint8_t* order, int m,
+                            double out[4], double* depth) {
+    double C[3] = {0, 0, 0}, A = 0.0;
+    *depth = INFINITY;
+    for (int i = 0; i < m; ++i) {
+        const frag_state* f = &fs[order[i]];
+        double Ak = 1.0 - f->T;
+        for (int a = 0; a < 3; ++a) C[a] += (1.0 - A) * f->C[a];
+        A += (1.0 - A) * Ak;
+        if (Ak > 0.0 && isinf(*depth)) *depth = ri->t_enter + (f->key + 0.5) * ri->dt;
+    }
+    (void)K;
+    out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = A;
+}
+
+/* Partitioned render: fragments per brick, then sort-last composite.
+ * Outputs per listed pixel k (any pointer may be NULL):
+ *   rgba[4k..], depth[k]           composited frame
+ *   order[K k ..]                  brick ids front to back, 0xFF padded
+ *   frag_rgba[4 (K k + b) ..]      fragment of brick b (premultiplied)
+ *   frag_key[K k + b]              first sample index or 2^31 - 1
+ *   frag_nsamp[K k + b]            samples evaluated
+ *   frag_margin[K k + b]           ERT margin (+inf if no stop)
+ *   nsamples[k]                    samples evaluated, all bricks
+ *   flags[k]                       ORC_FLAG_* bits */
+void orc_render_bricks(const orc_grid* g, int K, const orc_brick* bricks, const orc_tf* tf,
+                       const orc_camera* cam, const orc_frame* fr, int npix, const int32_t* pix,
+                       double* rgba, double* depth, uint8_t* order, double* frag_rgba, int32_t* frag_key,
+                       int32_t* frag_nsamp, double* frag_margin, int64_t* nsamples, uint8_t* flags) {
+#pragma omp parallel
+    {
+        frag_state* fs = (frag_state*)malloc(sizeof(frag_state) * K);
+        uint8_t* ord = (uint8_t*)malloc(K);
+#pragma omp for schedule(dynamic, 16)
+        for (int k = 0; k < npix; ++k) {
+            int p = pix ? pix[k] : k;
+            orc_rayinfo ri;
+            ray_samples(g, cam, fr, p % fr->width, p / fr->width, &ri);
+            int fl = ri.flags;
+            pixel_fragments(g, K, bricks, tf, fr, &ri, fs, &fl);
+            int m = fragment_order(K, fs, ord);
+            double out[4], dep;
+            composite_pixel(K, fs, &ri, ord, m, out, &dep);
+            if (rgba) for (int c = 0; c < 4; ++c) rgba[4 * k + c] = out[c];
+            if (depth) depth[k] = dep;
+            if (order) memcpy(order + (int64_t)K * k, ord, K);
+            int64_t ns = 0;
+            for (int b = 0; b < K; ++b) {
+                int64_t o = (int64_t)K * k + b;
+                if (frag_rgba) {
+                    frag_rgba[4 * o + 0] = fs[b].C[0];
+                    frag_rgba[4 * o + 1] = fs[b].C[1];
+                    frag_rgba[4 * o + 2] = fs[b].C[2];
+                    frag_rgba[4 * o + 3] = 1.0 - fs[b].T;
+                }
+                if (frag_key) frag_key[o] = (int32_t)fs[b].key;
+                if (frag_nsamp) frag_nsamp[o] = fs[b].nsamp;
+                if (frag_margin) frag_margin[o] = fs[b].margin;
+                ns += fs[b].nsamp;
+            }
+            if (nsamples) nsamples[k] = ns;
+            if (flags) flags[k] = (uint8_t)fl;
+        }
+        free(fs);
+        free(ord);
+    }
+}
+
+/* Composite arbitrary fragments: per pixel K fragments (premultiplied RGBA
+ * and key), non-empty ones in ascending key order, front-to-back over. */
+void orc_composite(int npix, int K, const double* frag_rgba, const int32_t* frag_key, double* rgba,
+                   uint8_t* order) {
+    frag_state* fs = (frag_state*)malloc(sizeof(frag_state) * K);
+    uint8_t* ord = (uint8_t*)malloc(K);
+    for (int k = 0; k < npix; ++k) {
+        for (int b = 0; b < K; ++b) {
+            int64_t o = (int64_t)K * k + b;
+            for (int a = 0; a < 3; ++a) fs[b].C[a] = frag_rgba[4 * o + a];
+            fs[b].T = 1.0 - frag_rgba[4 * o + 3];
+            fs[b].key = frag_key[o];
+        }
+        int m = fragment_order(K, fs, ord);
+        orc_rayinfo ri;
+        memset(&ri, 0, sizeof ri);
+        double out[4], dep;
+        composite_pixel(K, fs, &ri, ord, m, out, &dep);
+        for (int c = 0; c < 4; ++c) rgba[4 * k + c] = out[c];
+        if (order) memcpy(order + (int64_t)K * k, ord, K);
+    }
+    free(fs);
+    free(ord);
+}
+
+/* ------------------------------------------------------------------------ */
+/* k-d visibility order (R7)                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Front-to-back order of the leaves of a k-d tree seen from a point: at each
+ * node visit first the child on the eye's side of the split plane (node-space
+ * coordinate split - 1/2), the lower child when the eye lies on the plane.
+ * A child < 0 is leaf -(rank + 1).  Empty tree: the single rank 0. */
+static int kd_visit(int node, const int* axis, const int* split, const int* left, const int* right,
+                    const double eye_q[3], uint8_t* out, int m) {
+    if (node < 0) {
+        out[m] = (uint8_t)(-node - 1);
+        return m + 1;
+    }
+    double plane = split[node] - 0.5;
+    int first = eye_q[axis[node]] > plane ? right[node] : left[node];
+    int second = first == right[node] ? left[node] : right[node];
+    m = kd_visit(first, axis, split, left, right, eye_q, out, m);
+    return kd_visit(second, axis, split, left, right, eye_q, out, m);
+}
+
+int orc_kd_order(int nnodes, const int* axis, const int* split, const int* left, const int* right,
+                 const double eye_q[3], uint8_t* out) {
+    if (nnodes == 0) {
+        out[0] = 0;
+        return 1;
+    }
+    return kd_visit(0, axis, split, left, right, eye_q, out, 0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* gradients: reverse mode with a per-sample tape                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int brick;
+    double s, alpha, c[3];
+    int i0;
+    double w, duds;
+    int64_t idx[8];
+    double wt[8];
+} tape_entry;
+
+/* Reverse-mode gradient of sum_k <g_k, I_k> over listed pixels, where I_k is
+ * the partitioned render (fragments + composite, ERT as in the forward).
+ * Differentiates with respect to the TF table (dtf: n x 4, accumulated) and
+ * the global field values (dvol: global nodes, accumulated; a ghost copy's
+ * gradient goes to its global node).  The field enters through each brick's
+ * stored values times its scale.  Reverse sweep of the recurrences, no
+ * closed-form adjoint:
+ *   over:  C' = C + (1 - A) C_k,  A' = A + (1 - A) A_k
+ *   EA:    C' = C + T alpha c,    T' = T (1 - alpha),  A_k = 1 - T_end
+ *   alpha = 1 - exp(-sigma_max a dt);  TF lerp;  trilinear. */
+void orc_grad_bricks(const orc_grid* g, int K, const orc_brick* bricks, const orc_tf* tf, const orc_camera* cam,
+                     const orc_frame* fr, int npix, const int32_t* pix, const double* grad_rgba, double* dtf,
+                     double* dvol) {
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = omp_get_max_threads();
+#endif
+    double* dtf_priv = (double*)calloc((size_t)nthreads * tf->n * 4, sizeof(double));
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* my_dtf = dtf_priv + (size_t)tid * tf->n * 4;
+        frag_state* fs = (frag_state*)malloc(sizeof(frag_state) * K);
+        uint8_t* ord = (uint8_t*)malloc(K);
+        size_t cap = 1024;
+        tape_entry* tape = (tape_entry*)malloc(cap * sizeof(tape_entry));
+        int64_t* perm = (int64_t*)malloc(cap * sizeof(int64_t));
+        int64_t* first = (int64_t*)malloc(sizeof(int64_t) * K);
+        int64_t* count = (int64_t*)malloc(sizeof(int64_t) * K);
+        int* bl = (int*)malloc(sizeof(int) * 3 * K);
+        int* bn = (int*)malloc(sizeof(int) * 3 * K);
+        for (int b = 0; b < K; ++b) orc_stored_box(g->dims, bricks[b].owned_lo, bricks[b].owned_hi, bl + 3 * b, bn + 3 * b);
+#pragma omp for schedule(dynamic, 16)
+        for (int k = 0; k < npix; ++k) {
+            int p = pix ? pix[k] : k;
+            orc_rayinfo ri;
+            ray_samples(g, cam, fr, p % fr->width, p / fr->width, &ri);
+            /* forward with a tape: record evaluated samples grouped per brick */
+            if ((size_t)ri.n > cap) {
+                cap = (size_t)ri.n;
+                tape = (tape_entry*)realloc(tape, cap * sizeof(tape_entry));
+                perm = (int64_t*)realloc(perm, cap * sizeof(int64_t));
+            }
+            int fl = 0;
+            pixel_fragments(g, K, bricks, tf, fr, &ri, fs, &fl);
+            /* re-walk the ray and tape the samples each brick evaluated, in ray order */
+            int64_t nt = 0;
+            for (int b = 0; b < K; ++b) count[b] = 0;
+            int owner = -1;
+            for (int64_t j = 0; j < ri.n; ++j) {
+                double q[3];
+                sample_point(g, &ri, j, q, NULL);
+                owner = find_owner(g, K, bricks, q, owner);
+                if (owner < 0) continue;
+                if (count[owner] >= fs[owner].nsamp) continue;   /* after early termination */
+                tape_entry* e = &tape[nt++];
+                e->brick = owner;
+                e->s = trilinear(bricks[owner].data, bricks[owner].dtype, bricks[owner].scale, bl + 3 * owner,
+                                 bn + 3 * owner, q, e->idx, e->wt);
+                double v[4];
+                tf_lookup(tf, e->s, v, &e->i0, &e->w, &e->duds);
+                e->c[0] = v[0]; e->c[1] = v[1]; e->c[2] = v[2];
+                e->alpha = 1.0 - exp(-fr->sigma_max * v[3] * ri.dt);
+                count[owner]++;
+            }
+            /* group the tape by brick, keeping ray order within a brick */
+            int64_t acc = 0;
+            for (int b = 0; b < K; ++b) { first[b] = acc; acc += count[b]; count[b] = 0; }
+            for (int64_t i = 0; i < nt; ++i) {
+                int b = tape[i].brick;
+                perm[first[b] + count[b]++] = i;
+            }
+            int m = fragment_order(K, fs, ord);
+            /* composite forward states A before each fragment */
+            double gr[4];
+            for (int c = 0; c < 4; ++c) gr[c] = grad_rgba[4 * k + c];
+            double Aprev[256];
+            double A = 0.0;
+            for (int i = 0; i < m; ++i) {
+                Aprev[i] = A;
+                A += (1.0 - A) * (1.0 - fs[ord[i]].T);
+            }
+            /* reverse through the over operator */
+            double gC[3] = {gr[0], gr[1], gr[2]}, gA = gr[3];
+            for (int i = m - 1; i >= 0; --i) {
+                const frag_state* f = &fs[ord[i]];
+                double Ak = 1.0 - f->T, Ain = Aprev[i];
+                double gCk[3], gAk;
+                for (int a = 0; a < 3; ++a) gCk[a] = (1.0 - Ain) * gC[a];
+                gAk = (1.0 - Ain) * gA;
+                double gAin = gA * (1.0 - Ak) - (gC[0] * f->C[0] + gC[1] * f->C[1] + gC[2] * f->C[2]);
+                gA = gAin;
+                /* reverse through the fragment's EA recurrence */
+                int b = ord[i];
+                int64_t n0 = first[b], nb = count[b];
+                if (nb == 0) continue;
+                /* forward transmittances */
+                double* Ts = (double*)malloc(sizeof(double) * (nb + 1));
+                Ts[0] = 1.0;
+                for (int64_t s = 0; s < nb; ++s) Ts[s + 1] = Ts[s] * (1.0 - tape[perm[n0 + s]].alpha);
+                double gT = -gAk;   /* A_k = 1 - T_end */
+                for (int64_t s = nb - 1; s >= 0; --s) {
+                    tape_entry* e = &tape[perm[n0 + s]];
+                    double T = Ts[s];
+                    double galpha = (gCk[0] * e->c[0] + gCk[1] * e->c[1] + gCk[2] * e->c[2]) * T - gT * T;
+                    double gc[3];
+                    for (int a = 0; a < 3; ++a) gc[a] = gCk[a] * T * e->alpha;
+                    gT = (gCk[0] * e->c[0] + gCk[1] * e->c[1] + gCk[2] * e->c[2]) * e->alpha + gT * (1.0 - e->alpha);
+                    /* alpha = 1 - exp(-sigma_max a dt) */
+                    double ga = galpha * fr->sigma_max * ri.dt * (1.0 - e->alpha);
+                    double gv[4] = {gc[0], gc[1], gc[2], ga};
+                    double gw = 0.0;
+                    for (int c = 0; c < 4; ++c) {
+                        my_dtf[4 * e->i0 + c] += (1.0 - e->w) * gv[c];
+                        my_dtf[4 * (e->i0 + 1) + c] += e->w * gv[c];
+                        gw += gv[c] * (tf->rgba[4 * (e->i0 + 1) + c] - tf->rgba[4 * e->i0 + c]);
+                    }
+                    double gs = gw * e->duds;
+                    if (dvol && gs != 0.0) {
+                        const int* lo = bl + 3 * e->brick;
+                        const int* nn = bn + 3 * e->brick;
+                        for (int c = 0; c < 8; ++c) {
+                            int64_t li = e->idx[c];
+                            int x = (int)(li % nn[0]), y = (int)((li / nn[0]) % nn[1]), z = (int)(li / ((int64_t)nn[0] * nn[1]));
+                            int64_t gi = ((int64_t)(z + lo[2]) * g->dims[1] + (y + lo[1])) * g->dims[0] + (x + lo[0]);
+                            double contrib = gs * e->wt[c] * bricks[e->brick].scale;
+#pragma omp atomic
+                            dvol[gi] += contrib;
+                        }
+                    }
+                }
+                free(Ts);
+            }
+        }
+        free(fs); free(ord); free(tape); free(perm); free(first); free(count); free(bl); free(bn);
+    }
+    for (int t = 0; t < nthreads; ++t)
+        for (int i = 0; i < tf->n * 4; ++i) dtf[i] += dtf_priv[(size_t)t * tf->n * 4 + i];
+    free(dtf_priv);
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
