@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of the data-parallel brick ray-march + sort-last compositing
+path on B300 (one JSON line on stdout).
+
+A step is one pass of the whole hot path over one batch: cull and work list,
+brick ray-march, sort-last composite (the forward frame of every camera),
+then the adjoint (compositor backward, ray-march replay with TF and volume
+gradients) for a fixed upstream image gradient.  The scene (bricks, TF,
+cameras, upstream gradient) is resident in HBM before timing; the 512 MiB
+volume is larger than L2, so no flush is needed between steps.
+
+`value` is the forward sample rate (samples the ray-march evaluated per
+second of forward device time); frames/s and the backward sample rate are
+reported beside it, and `ms_per_step` covers the whole step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config mid]
+  python bench.py --impl reference      # the FP64 CPU oracle, bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2407_00179_b300 import build as _build  # noqa: E402
+from paper_2407_00179_b300 import inputs  # noqa: E402
+
+METRIC = "Gsamples/s and composited frames/s at 1 B300 (% HBM roofline); backward Gsamples/s"
+BYTES_PER_VOXEL = {"f32": 4, "f16": 2, "bf16": 2, "fp8": 1}
+
+CONFIGS = {
+    # 512^3 f32, 64 blobs + 3-octave noise, 2x2x2 bricks, 1920x1080, ERT 0.99
+    "mid": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
+                storage="f32", cams="direction"),
+    "mid_f16": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
+                    storage="f16", cams="direction"),
+    # 64^3 f32, 8 blobs, 2x1x1 bricks, 256x256, no ERT
+    "small": dict(dims=(64, 64, 64), field="small", splits=(2, 1, 1), ncam=1, width=256, height=256, ert=0.0,
+                  storage="f32", cams="direction"),
+    # 1024x1024x512 f16 turbulence, k-d 37 bricks, 16 orbit cameras at 1024^2
+    "batched": dict(dims=(1024, 1024, 512), field="turbulent", kd=37, ncam=16, width=1024, height=1024, ert=0.0,
+                    storage="f16", cams="orbit"),
+    # 256^3 f32, 16 blobs, 2x2x2, 32 sphere cameras at 512^2
+    "diff": dict(dims=(256, 256, 256), field="diff", splits=(2, 2, 2), ncam=32, width=512, height=512, ert=0.0,
+                 storage="f32", cams="sphere"),
+}
+
+
+def _field(cfg, device):
+    fn = {"mid": inputs.field_mid, "small": inputs.field_small, "turbulent": inputs.field_turbulent,
+          "diff": inputs.field_diff}[cfg["field"]]
+    return fn(0, cfg["dims"], device=device)
+
+
+def _partition(cfg):
+    if cfg.get("kd"):
+        return inputs.kd_partition(cfg["dims"], cfg["kd"], seed=0)
+    return inputs.regular_partition(cfg["dims"], cfg["splits"])
+
+
+def _cameras(cfg, rank=0):
+    dims = cfg["dims"]
+    if cfg["cams"] == "direction":
+        return [inputs.camera_from_direction(dims, (1.0, 0.7, 0.5))] * cfg["ncam"]
+    if cfg["cams"] == "orbit":
+        return inputs.orbit_cameras(dims, cfg["ncam"], seed=rank)
+    return inputs.sphere_cameras(dims, cfg["ncam"], seed=rank)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_mod=None):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded pixel
+    sample of the same workload: whole pixel rows spread over the image."""
+    import oracle
+    oracle.build()
+    ncores = len(os.sched_getaffinity(0))
+    oracle.set_threads(ncores)
+    bricks = oracle.make_bricks(field_np, part, oracle.DTYPE_NAMES[cfg["storage"]])
+    fr = oracle.Frame(cfg["width"], cfg["height"], step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"])
+    W, H = cfg["width"], cfg["height"]
+    cam = cams[0]
+
+    def run(rows):
+        pix = np.concatenate([np.arange(W, dtype=np.int32) + W * int(r) for r in rows])
+        t = time.perf_counter()
+        out = oracle.render_bricks(cfg["dims"], bricks, tf, cam, fr, pix=pix)
+        return time.perf_counter() - t, int(out["nsamples"].sum()), len(pix)
+
+    # calibrate on the middle rows, then size the sample for the budget
+    dt, ns, npx = run([H // 2])
+    rate = max(ns, 1) / max(dt, 1e-6)
+    per_row = max(ns, 1)
+    nrows = int(min(H, max(1, budget_s * rate / per_row)))
+    rows = np.linspace(0, H - 1, nrows).astype(int)
+    dt, ns, npx = run(rows)
+    return {"value": ns / dt / 1e9, "unit": "Gsamples/s", "cores": ncores, "kind": "oracle",
+            "sample": "%d of %d pixel rows (%d pixels, %d samples) of camera 0, FP64, %.1f s" % (
+                len(rows), H, npx, ns, dt),
+            "seconds": dt, "samples": ns, "rows": rows}
+
+
+def run_reference(args, cfg_name, cfg):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    dev = "cpu"
+    f = _field(cfg, "cuda" if torch.cuda.is_available() else "cpu").cpu().numpy()
+    part = _partition(cfg)
+    tf = inputs.make_tf(1234)
+    cams = _cameras(cfg)
+    steps = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(cfg_name, cfg, f, part, tf, cams, budget_s=args.ref_budget)
+        if i >= args.warmup:
+            steps.append(r)
+        base = r
+    tot_s = sum(r["seconds"] for r in steps)
+    tot_n = sum(r["samples"] for r in steps)
+    val = tot_n / tot_s / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gsamples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_s / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": cfg_name, "dims": list(cfg["dims"]), "bricks": part.num_ranks,
+                       "cameras": cfg["ncam"], "image": [cfg["width"], cfg["height"]], "storage": cfg["storage"],
+                       "ert": cfg["ert"]},
+            "cpu_baseline": {"value": val, "unit": "Gsamples/s", "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": val, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, cfg_name, cfg):
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    from paper_2407_00179_b300 import dpv
+    _build.build()
+    dpv.load()
+    device = torch.device("cuda", local)
+    field = _field(cfg, device)
+    part = _partition(cfg)
+    tf_np = inputs.make_tf(1234)
+    cams = _cameras(cfg, rank)
+    W, H = cfg["width"], cfg["height"]
+    ncam = len(cams)
+
+    dev = dpv.Device(part.num_ranks, local)
+    dev.set_geometry(cfg["dims"])
+    dev.commit_partition(field, part, cfg["storage"])
+    tf = torch.from_numpy(tf_np).to(device)
+    dev.set_tf(tf)
+    dev.set_cameras(cams)
+    dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=(args.tile_w, args.tile_h))
+    # fixed upstream gradient: d/dI of mean (I - I*)^2 with I* from a perturbed TF
+    dev.set_tf(torch.from_numpy(inputs.perturb_tf(tf_np, 0)).to(device))
+    dev.render()
+    target = dev.frames()[0].clone()
+    dev.set_tf(tf)
+    dev.render()
+    grad = (2.0 / target.numel()) * (dev.frames()[0] - target)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(device)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        dev.render()
+        if ev:
+            ev[1].record(stream)
+        dev.backward(grad, volume_grad=True)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dev.set_profiling(True)
+    dev.reset_stats()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    st = dev.stats()
+    dev.set_profiling(False)
+    total_ms = t0.elapsed_time(t1)
+    fwd_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+    bwd_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
+    n_fwd = st["samples_forward"] * args.steps          # per step counts are deterministic
+    n_bwd = st["samples_backward"] * args.steps
+    launches = st["kernel_launches"]
+    if pg:
+        t = torch.tensor([total_ms, fwd_ms, bwd_ms], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms, fwd_ms, bwd_ms = t.tolist()
+    # roofline of the dominant kernel (forward ray-march): stencil bytes
+    bpv = BYTES_PER_VOXEL[cfg["storage"]]
+    march_ms = st["stage_ms"]["march"] / max(1, st["stage_calls"]["march"])
+    march_bwd_ms = st["stage_ms"]["march_bwd"] / max(1, st["stage_calls"]["march_bwd"])
+    bytes_per_launch = st["samples_forward"] * 8 * bpv
+    achieved = bytes_per_launch / (march_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+
+    # end to end through the public API: TF from pinned host memory in, the
+    # composited frames to pinned host memory out, every step
+    tf_host = torch.from_numpy(tf_np).pin_memory()
+    frame_host = torch.empty((ncam, H, W, 4), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        dev.set_tf(tf_host.numpy())
+        dev.render()
+        dev.copy_frame(0, frame_host[0])
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps)
+    if pg:
+        pg.barrier()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dev.set_tf(tf_host.numpy())
+        dev.render()
+        for c in range(ncam):
+            dev.copy_frame(c, frame_host[c])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+    e2e_val = st["samples_forward"] * e2e_steps / e2e_s / 1e9
+    ws_factor = ws
+    value = n_fwd / (fwd_ms * 1e-3) / 1e9 * ws_factor
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "Gsamples/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if cfg["storage"] == "f32" else "f32 math, %s storage" % cfg["storage"],
+        "data": "synthetic (seeded field, TF, cameras; no paper dataset)",
+        "config": {"workload": cfg_name, "dims": list(cfg["dims"]), "bricks": part.num_ranks,
+                   "cameras_per_gpu": ncam, "image": [W, H], "storage": cfg["storage"], "ert": cfg["ert"],
+                   "step_voxels": 0.5, "sigma_max": 8.0, "tile": [dev.width and args.tile_w or 16,
+                                                                 args.tile_h or 16],
+                   "l2": "inputs larger than L2 (%d MiB volume), no flush" % (
+                       np.prod(cfg["dims"]) * bpv // 2 ** 20),
+                   "parallelism": "weak: each GPU renders its own cameras over its own copy of the bricks"},
+        "frames_per_s": ncam * args.steps / (fwd_ms * 1e-3) * ws_factor,
+        "forward_ms_per_step": fwd_ms / args.steps,
+        "backward": {"value": n_bwd / (bwd_ms * 1e-3) / 1e9 * ws_factor, "unit": "Gsamples/s",
+                     "ms_per_step": bwd_ms / args.steps},
+        "samples_per_step": {"forward": st["samples_forward"], "backward": st["samples_backward"]},
+        "stage_ms_per_step": {k: v / max(1, args.steps) for k, v in st["stage_ms"].items()},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_march_fwd<%s>" % cfg["storage"],
+                     "model": "stencil bytes: 8 corners x %d B per evaluated sample" % bpv,
+                     "peak_kind": peak_kind,
+                     "backward_frac": st["samples_backward"] * 8 * bpv / (march_bwd_ms * 1e-3) / 1e9 / peak},
+        "e2e": {"value": e2e_val * ws_factor, "unit": "Gsamples/s", "h2d_bytes_per_step": int(tf_np.nbytes),
+                "d2h_bytes_per_step": int(ncam * H * W * 16), "what": "set TF from pinned host, render, copy frames"
+                " to pinned host, per step (forward)"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "error_flags": st["error_flags"],
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cb = cpu_baseline(cfg_name, cfg, field.cpu().numpy(), part, tf_np, cams, budget_s=args.ref_budget)
+            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        except Exception as e:  # the oracle is a reported baseline, never the product
+            line["cpu_baseline"] = {"value": None, "unit": "Gsamples/s", "cores": None, "kind": "oracle",
+                                    "sample": "failed: %s" % e}
+    dev.release()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="mid", choices=sorted(CONFIGS))
+    ap.add_argument("--tile-w", type=int, default=0)
+    ap.add_argument("--tile-h", type=int, default=0)
+    ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of oracle work per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        if args.steps * args.ref_budget > 240:
+            args.ref_budget = max(2.0, 240.0 / max(1, args.steps + args.warmup))
+        run_reference(args, args.config, cfg)
+    else:
+        run_ours(args, args.config, cfg)
+
+
+if __name__ == "__main__":
+    main()

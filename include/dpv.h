@@ -1,0 +1,250 @@
+/*
+ * dpv.h -- C ABI of the data-parallel volume renderer (B300, sm_103a).
+ *
+ * The call shape follows the data-parallel use of ANARI described in
+ * "Standardized Data-Parallel Rendering Using ANARI" (arXiv 2407.00179):
+ *   - a device is created collaboratively (§3.3);
+ *   - each rank defines its own local part of a jointly defined world and
+ *     commits it independently (§1, §3.1.2; commit semantics §2.3);
+ *   - frame, renderer and camera parameters are globally consistent (§3.1.1);
+ *   - rendering is a collaborative, asynchronous call (§3.2, §2.3);
+ *   - completion can be waited for or polled (ANARI_WAIT / NO_WAIT, §3.2);
+ *   - the final frame is mapped on rank 0 only (§3.1.3);
+ *   - the device is released in lock step (§3.2);
+ *   - the application tells the device how the data is partitioned (§8.2:
+ *     "boundingBox"-style meta parameters): here every rank commits the node
+ *     range it owns.
+ * All ranks are logical: they are emulated as partitions of one volume on
+ * one GPU.  Rank k owns one axis-aligned brick of a structured scalar field
+ * and keeps a one-node ghost layer around it.  Rendering ray-marches every
+ * brick into one RGBA+key fragment per pixel (emission-absorption, front to
+ * back, trilinear samples, 1D RGBA transfer function) and composites the
+ * fragments sort-last in per-pixel key order (§2.1, §5.1.1).  An adjoint
+ * pass gives gradients of an image loss with respect to the transfer
+ * function and the field.
+ *
+ * Conventions (readings of the paper, which gives no rendering equations):
+ *   - nodes: node (i,j,k) sits at world origin + (i,j,k) * spacing; the
+ *     volume box is [0, dims-1] in node coordinates;
+ *   - a rank owning nodes [lo, hi) per axis owns the region [lo-1/2, hi-1/2]
+ *     (clipped to the volume) and stores nodes [lo-1, hi] (clipped);
+ *   - samples along a ray sit at t_j = t_enter + (j + 1/2) dt, dt =
+ *     step_voxels * spacing, for t_j < t_exit, where [t_enter, t_exit) is the
+ *     ray's interval in the volume box clipped to t >= 0; sample j belongs to
+ *     the brick whose owned region contains it;
+ *   - TF: n RGBA entries at s_i = vmin + i (vmax - vmin)/(n-1), linear
+ *     interpolation, clamped outside [vmin, vmax];
+ *   - extinction sigma = sigma_max * alpha_TF per world unit, sample opacity
+ *     1 - exp(-sigma dt), premultiplied colour accumulation front to back;
+ *   - a fragment is (premultiplied RGBA, key = global index of its first
+ *     sample); fragments are composited in ascending key order;
+ *   - early ray termination, when enabled, is per fragment: a brick stops
+ *     once its own opacity exceeds the threshold;
+ *   - pinhole cameras, right-handed look-at, rays through pixel centres,
+ *     image row 0 at the bottom.
+ *
+ * Threading and ownership: a device handle must not be used from two host
+ * threads at once.  All GPU work is issued asynchronously on the stream
+ * given at creation.  Every call returns a status; on failure
+ * dpvGetLastError() returns a message for the calling thread.  After a CUDA
+ * error the device is poisoned: every later call except dpvRelease returns
+ * DPV_ERR_CUDA.
+ */
+#ifndef DPV_H
+#define DPV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dpv_device_t* dpv_device;
+
+typedef enum {
+    DPV_OK = 0,
+    DPV_ERR_INVALID_ARG = 1,   /* bad pointer, size, index or parameter */
+    DPV_ERR_STATE = 2,         /* call not valid in the current state */
+    DPV_ERR_OUT_OF_MEMORY = 3, /* a device or host allocation failed */
+    DPV_ERR_CUDA = 4,          /* a CUDA call failed; the device is poisoned */
+    DPV_ERR_TIMEOUT = 5,       /* a bounded wait expired */
+    DPV_ERR_UNSUPPORTED = 6    /* valid request this build does not handle */
+} dpv_status;
+
+typedef enum {
+    DPV_F32 = 0,
+    DPV_F16 = 1,
+    DPV_BF16 = 2,
+    DPV_FP8_E4M3 = 3           /* OCP E4M3 (max 448, no infinities) */
+} dpv_dtype;
+
+/* One rank's brick.  `data` holds a box of nodes [data_lo, data_lo +
+ * data_dims) of the global field, x fastest, in `src_dtype`; it must contain
+ * every node the rank stores (owned range plus one ghost node per side,
+ * clipped to the volume).  Passing the whole global field (data_lo = 0,
+ * data_dims = dims) is allowed: the device extracts what it needs.  The
+ * device copies the data (ANARI commit semantics); the caller may free it
+ * when dpvCommitBrick returns.  src_dtype must be DPV_F32 (converted to
+ * `storage` on the GPU, rounding to nearest even, fp8 saturating) or equal
+ * to `storage` (copied).  Stored values are decoded as scale * stored.
+ * scale <= 0 selects the default: max|v| / 448 over the stored nodes for
+ * DPV_FP8_E4M3 (computed in float32; 1 if all are zero), 1 otherwise. */
+typedef struct {
+    int owned_lo[3], owned_hi[3];
+    dpv_dtype storage;
+    float scale;
+    dpv_dtype src_dtype;
+    const void* data;
+    int data_lo[3], data_dims[3];
+    int data_on_device;           /* 1: data is a device pointer, 0: host */
+} dpv_brick_desc;
+
+/* Pinhole camera: right-handed look-at, vertical field of view in degrees. */
+typedef struct {
+    float eye[3], center[3], up[3];
+    float fovy_deg;
+} dpv_camera;
+
+#define DPV_FRAME_ORDER 1          /* also produce the per-pixel order (debug) */
+
+/* Frame parameters, identical on all ranks (§3.1.1).  Every camera renders
+ * a width x height image.  tile_w/tile_h: pixels per work item (multiples
+ * of 8 and 4; 0 = autotuned default).  ert_threshold <= 0 or >= 1 disables
+ * early termination. */
+typedef struct {
+    int width, height;
+    float step_voxels;
+    float sigma_max;
+    float ert_threshold;
+    int tile_w, tile_h;
+    int flags;
+} dpv_frame_desc;
+
+/* Pipeline stages timed when profiling is on (dpvSetProfiling). */
+typedef enum {
+    DPV_STAGE_CULL = 0,           /* camera setup, culling, work list */
+    DPV_STAGE_MARCH = 1,          /* brick ray-march (forward) */
+    DPV_STAGE_COMPOSITE = 2,      /* sort-last compositor (forward) */
+    DPV_STAGE_COMPOSITE_BWD = 3,  /* compositor adjoint */
+    DPV_STAGE_MARCH_BWD = 4,      /* ray-march adjoint */
+    DPV_NUM_STAGES = 5
+} dpv_stage;
+
+/* Counters.  samples_* and error_flags are those of the most recent
+ * dpvRenderFrame / dpvBackward.  stage_ms / stage_calls: device time of each
+ * stage, measured with CUDA events on the device stream around its kernels,
+ * summed over all renders since the last dpvResetStats while profiling was
+ * on.  kernel_launches: kernels this device launched since the last reset. */
+typedef struct {
+    uint64_t samples_forward;     /* samples evaluated by the ray-march */
+    uint64_t samples_backward;    /* samples replayed by the adjoint march */
+    uint64_t work_items;          /* (camera, brick, tile) items marched */
+    uint64_t fragment_bytes;      /* device bytes held by the fragment pool */
+    uint32_t error_flags;         /* device-side error bits (0 = none) */
+    uint32_t max_fragments;       /* most fragments listed for one tile */
+    double stage_ms[DPV_NUM_STAGES];
+    uint32_t stage_calls[DPV_NUM_STAGES];
+    uint64_t kernel_launches;
+} dpv_stats;
+
+/* Create a device for `num_ranks` logical ranks (1..255) on CUDA device
+ * `cuda_device`, issuing all work on `cuda_stream` (a cudaStream_t; NULL =
+ * the legacy default stream).  The stream must outlive the device. */
+dpv_status dpvCreateDevice(int num_ranks, int cuda_device, void* cuda_stream, dpv_device* out);
+
+/* Global node grid: dims[a] >= 2 nodes per axis, world origin of node 0 and
+ * isotropic spacing > 0.  Must be set before bricks are committed; setting
+ * it again discards all bricks. */
+dpv_status dpvSetVolumeGeometry(dpv_device dev, const int dims[3], const float origin[3], float spacing);
+
+/* Commit rank `rank`'s brick (copies, see dpv_brick_desc).  Ranks commit
+ * independently, in any order (§3.1.2).  A brick may hold at most 2^31 - 1
+ * stored nodes.  All ranks of a device must use the same storage dtype.
+ * Blocks the host until the copy has been issued; with host data it returns
+ * after the host buffer has been read. */
+dpv_status dpvCommitBrick(dpv_device dev, int rank, const dpv_brick_desc* desc);
+
+/* Transfer function: n (2..4096) RGBA float entries, x fastest, on the host
+ * (on_device = 0) or the device; values over [vmin, vmax], vmax > vmin.
+ * Copied; visible to the next render. */
+dpv_status dpvSetTransferFunction(dpv_device dev, const float* rgba, int n, float vmin, float vmax, int on_device);
+
+/* Cameras (host array of n >= 1).  Every render produces one image each. */
+dpv_status dpvSetCameras(dpv_device dev, const dpv_camera* cams, int n);
+
+/* Frame parameters (host struct). */
+dpv_status dpvSetFrame(dpv_device dev, const dpv_frame_desc* desc);
+
+/* Render one frame for every camera: cull, brick ray-march and sort-last
+ * composite, asynchronously on the device stream (§3.2: collaborative).
+ * Every rank must have committed a brick, and the owned ranges must tile
+ * the volume exactly, else DPV_ERR_STATE / DPV_ERR_INVALID_ARG.  The first
+ * render after a change of geometry, bricks, cameras or frame size blocks
+ * while it sizes the fragment pool. */
+dpv_status dpvRenderFrame(dpv_device dev);
+
+/* Frame completion: wait = 1 blocks until the last render has finished
+ * (ANARI_WAIT); wait = 0 only polls (ANARI_NO_WAIT).  *ready = 1 when done. */
+dpv_status dpvFrameReady(dpv_device dev, int wait, int* ready);
+
+/* Device pointers to camera `camera`'s composited frame: rgba = height x
+ * width x 4 floats (premultiplied, row 0 at the bottom), depth = height x
+ * width floats (t of the first sample of the first fragment with non-zero
+ * opacity, +inf if none).  Device-owned, valid until the next render or
+ * release; read them on the device stream or after dpvFrameReady. */
+dpv_status dpvMapFrame(dpv_device dev, int camera, const float** rgba, const float** depth);
+dpv_status dpvUnmapFrame(dpv_device dev, int camera);
+
+/* Copy camera `camera`'s frame into caller buffers (device or host
+ * pointers; either may be NULL), ordered on the device stream.  Returns
+ * after the copy has been issued (host destinations: after it completed). */
+dpv_status dpvCopyFrame(dpv_device dev, int camera, float* rgba, float* depth);
+
+/* Debug/test: write rank `rank`'s fragments for camera `camera` into caller
+ * device buffers rgba (height x width x 4, premultiplied) and key (height x
+ * width int32; 2^31 - 1 = empty, also for pixels the rank was culled from). */
+dpv_status dpvReadFragments(dpv_device dev, int camera, int rank, float* rgba, int32_t* key);
+
+/* Debug/test: copy rank `rank`'s stored nodes (owned + ghost box, x
+ * fastest, in the storage format) to the caller's device buffer `dst` (NULL
+ * to skip) and return the box and the rank's decode scale (synchronises the
+ * device stream).  stored_lo/stored_dims/scale may be NULL. */
+dpv_status dpvReadBrick(dpv_device dev, int rank, void* dst, int stored_lo[3], int stored_dims[3], float* scale);
+
+/* Debug/test (needs DPV_FRAME_ORDER): device pointer to camera `camera`'s
+ * order image: height x width x stride bytes, the ranks of the pixel's
+ * non-empty fragments front to back, then 0xFF. */
+dpv_status dpvMapOrder(dpv_device dev, int camera, const uint8_t** order, int* stride);
+
+/* Adjoint of the last render.  dL_drgba: device array cameras x height x
+ * width x 4 floats (gradient of the loss with respect to the composited
+ * premultiplied RGBA).  dL_dtf: device array n x 4 doubles, overwritten with
+ * the gradient with respect to the TF entries.  dL_dvol: device array of the
+ * global field's size (x fastest) of floats, overwritten with the gradient
+ * with respect to the field values (a ghost copy's share goes to its global
+ * node), or NULL.  Both outputs are zeroed by the call.  Uses the fragments
+ * of the last render: call it before the next render.  Asynchronous on the
+ * device stream. */
+dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, float* dL_dvol);
+
+/* Counters (synchronises the device stream). */
+dpv_status dpvGetStats(dpv_device dev, dpv_stats* out);
+
+/* Clear the accumulated stage times and the launch count. */
+dpv_status dpvResetStats(dpv_device dev);
+
+/* Turn per-stage CUDA-event timing on (1) or off (0). */
+dpv_status dpvSetProfiling(dpv_device dev, int enable);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* dpvGetLastError(void);
+
+/* Release the device and all its memory (§3.2: lock step).  NULL is OK. */
+dpv_status dpvRelease(dpv_device dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPV_H */

@@ -1,0 +1,836 @@
+// device.cu -- C-ABI implementation of include/dpv.h: device state, the
+// rank-commit state machine, scheduling (work list and fragment pool
+// sizing) and kernel launches on the caller's stream.
+//
+// Collaborative semantics (arXiv 2407.00179 §3.2) are modelled on one
+// process: dpvRenderFrame requires every logical rank to have committed its
+// brick (the implicit barrier of anariRenderFrame), and the final frame is
+// the one mapped "on rank 0" (§3.1.3).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/dpv.h"
+#include "dpv_internal.cuh"
+#include "launch.h"
+
+using namespace dpv;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+dpv_status fail(dpv_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+struct HostBrick {
+    bool committed = false;
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int s_lo[3] = {0, 0, 0}, s_n[3] = {0, 0, 0};
+    int dtype = 0;
+    void* data = nullptr;       // device storage
+    size_t bytes = 0;
+};
+
+const int kElemSize[4] = {4, 2, 2, 1};
+
+}  // namespace
+
+struct dpv_device_t {
+    int nranks = 0;
+    int cuda_device = 0;
+    cudaStream_t stream = nullptr;
+    bool poisoned = false;
+
+    bool has_geom = false;
+    int dims[3] = {0, 0, 0};
+    float origin[3] = {0, 0, 0};
+    float spacing = 1.0f;
+
+    std::vector<HostBrick> bricks;
+    float* d_scales = nullptr;          // per-rank scale (written by commit)
+    unsigned int* d_tmp = nullptr;      // commit scratch (max |v|)
+    BrickDev* d_bricks = nullptr;
+
+    float4* d_tf = nullptr;
+    int ntf = 0;
+    float vmin = 0.f, vmax = 1.f;
+
+    std::vector<CamIn> cams;
+    CamIn* d_cam_in = nullptr;
+    CamBasis* d_cams = nullptr;
+    int cam_cap = 0;
+
+    bool has_frame = false;
+    dpv_frame_desc frame{};
+
+    // schedule and buffers (rebuilt when dirty)
+    bool dirty = true;
+    FrameParams P{};
+    int4* d_rects = nullptr;
+    int* d_tile_count = nullptr;
+    int* d_tile_first = nullptr;
+    Item* d_items = nullptr;
+    int items_cap = 0;
+    int n_items = 0;
+    float4* d_frag_rgba = nullptr;
+    int* d_frag_key = nullptr;
+    float4* d_frag_grad = nullptr;
+    size_t frag_cap = 0;                // items the fragment pool holds
+    float4* d_out_rgba = nullptr;
+    float* d_out_depth = nullptr;
+    unsigned char* d_order = nullptr;
+    size_t out_cap = 0;                 // pixels the frame buffers hold
+    size_t order_cap = 0;
+    Counters* d_counters = nullptr;
+    cudaEvent_t ev_done = nullptr;
+    bool rendered = false;
+
+    // profiling: event pairs around stages, resolved by dpvGetStats
+    struct Timer {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    bool profiling = false;
+    std::vector<Timer> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double stage_ms[DPV_NUM_STAGES] = {0};
+    uint32_t stage_calls[DPV_NUM_STAGES] = {0};
+    uint64_t launches = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+dpv_status cuda_fail(dpv_device dev, cudaError_t e, const char* what) {
+    if (dev) dev->poisoned = true;
+    return fail(DPV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(dev, e_, what); \
+    } while (0)
+
+dpv_status dev_alloc(dpv_device dev, void** p, size_t bytes, const char* what) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(DPV_ERR_OUT_OF_MEMORY, "%s: cannot allocate %zu bytes", what, bytes);
+    }
+    if (e != cudaSuccess) return cuda_fail(dev, e, what);
+    return DPV_OK;
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+cudaEvent_t take_event(dpv_device dev) {
+    if (!dev->event_pool.empty()) {
+        cudaEvent_t e = dev->event_pool.back();
+        dev->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Record the start of a timed stage on the device stream (no-op when off).
+cudaEvent_t stage_start(dpv_device dev) {
+    if (!dev->profiling) return nullptr;
+    cudaEvent_t e = take_event(dev);
+    if (e) cudaEventRecord(e, dev->stream);
+    return e;
+}
+
+void stage_stop(dpv_device dev, int stage, cudaEvent_t a) {
+    if (!dev->profiling || !a) return;
+    cudaEvent_t b = take_event(dev);
+    if (!b) return;
+    cudaEventRecord(b, dev->stream);
+    dev->pending.push_back({stage, a, b});
+}
+
+// Wait for and accumulate all pending stage timers.
+void resolve_timers(dpv_device dev) {
+    for (auto& t : dev->pending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(t.b) == cudaSuccess && cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            dev->stage_ms[t.stage] += ms;
+            dev->stage_calls[t.stage] += 1;
+        }
+        cudaGetLastError();
+        dev->event_pool.push_back(t.a);
+        dev->event_pool.push_back(t.b);
+    }
+    dev->pending.clear();
+}
+
+dpv_status check_dev(dpv_device dev) {
+    if (!dev) return fail(DPV_ERR_INVALID_ARG, "null device");
+    if (dev->poisoned) return fail(DPV_ERR_CUDA, "device is poisoned by an earlier CUDA error");
+    return DPV_OK;
+}
+
+void free_schedule(dpv_device dev) {
+    dev_free(dev->d_rects);
+    dev_free(dev->d_tile_count);
+    dev_free(dev->d_tile_first);
+    dev_free(dev->d_items);
+    dev->d_rects = nullptr;
+    dev->d_tile_count = dev->d_tile_first = nullptr;
+    dev->d_items = nullptr;
+    dev->items_cap = 0;
+}
+
+void free_frags(dpv_device dev) {
+    dev_free(dev->d_frag_rgba);
+    dev_free(dev->d_frag_key);
+    dev_free(dev->d_frag_grad);
+    dev->d_frag_rgba = nullptr;
+    dev->d_frag_key = nullptr;
+    dev->d_frag_grad = nullptr;
+    dev->frag_cap = 0;
+}
+
+// Owned ranges must tile [0, dims) exactly: every range non-empty and inside
+// the volume, volumes summing to the total, and no two overlapping.
+dpv_status check_partition(dpv_device dev) {
+    long long total = 0;
+    for (int k = 0; k < dev->nranks; ++k) {
+        const HostBrick& b = dev->bricks[k];
+        long long v = 1;
+        for (int a = 0; a < 3; ++a) v *= (long long)(b.hi[a] - b.lo[a]);
+        total += v;
+        for (int m = k + 1; m < dev->nranks; ++m) {
+            const HostBrick& c = dev->bricks[m];
+            bool overlap = true;
+            for (int a = 0; a < 3; ++a) overlap = overlap && b.lo[a] < c.hi[a] && c.lo[a] < b.hi[a];
+            if (overlap) return fail(DPV_ERR_INVALID_ARG, "owned ranges of ranks %d and %d overlap", k, m);
+        }
+    }
+    long long want = (long long)dev->dims[0] * dev->dims[1] * dev->dims[2];
+    if (total != want)
+        return fail(DPV_ERR_INVALID_ARG, "owned ranges cover %lld nodes, the volume has %lld", total, want);
+    return DPV_OK;
+}
+
+// Build FrameParams, upload the brick table, run the cull once to size the
+// work list and fragment pool, and (re)allocate buffers.
+dpv_status prepare(dpv_device dev) {
+    const dpv_frame_desc& F = dev->frame;
+    FrameParams& P = dev->P;
+    P.W = F.width;
+    P.H = F.height;
+    P.tw = F.tile_w > 0 ? F.tile_w : 16;
+    P.th = F.tile_h > 0 ? F.tile_h : 16;
+    P.ntx = (P.W + P.tw - 1) / P.tw;
+    P.nty = (P.H + P.th - 1) / P.th;
+    P.ncam = (int)dev->cams.size();
+    P.tp = P.tw * P.th;
+    P.dt = F.step_voxels * dev->spacing;
+    P.inv_dt = 1.0f / P.dt;
+    P.sigma_max = F.sigma_max;
+    P.ert = F.ert_threshold;
+    P.ert_on = (F.ert_threshold > 0.0f && F.ert_threshold < 1.0f) ? 1 : 0;
+    P.vmin = dev->vmin;
+    P.tf_scale = (float)(dev->ntf - 1) / (dev->vmax - dev->vmin);
+    P.ntf = dev->ntf;
+    for (int a = 0; a < 3; ++a) P.dims[a] = dev->dims[a];
+    P.nbricks = dev->nranks;
+    P.order_stride = (F.flags & DPV_FRAME_ORDER) ? dev->nranks : 0;
+    P.items_cap = 0;
+
+    // brick table
+    std::vector<BrickDev> table(dev->nranks);
+    int dtype = dev->bricks[0].dtype;
+    for (int k = 0; k < dev->nranks; ++k) {
+        const HostBrick& h = dev->bricks[k];
+        if (h.dtype != dtype) return fail(DPV_ERR_UNSUPPORTED, "all ranks must use the same storage dtype");
+        BrickDev& b = table[k];
+        b.data = h.data;
+        for (int a = 0; a < 3; ++a) {
+            b.s_lo[a] = h.s_lo[a];
+            b.s_n[a] = h.s_n[a];
+            float lo = (float)h.lo[a] - 0.5f, hi = (float)h.hi[a] - 0.5f;
+            b.r0[a] = lo < 0.0f ? 0.0f : lo;
+            b.r1[a] = hi > (float)(dev->dims[a] - 1) ? (float)(dev->dims[a] - 1) : hi;
+            b.closed[a] = h.hi[a] >= dev->dims[a] ? 1 : 0;
+        }
+        b.sx = h.s_n[0];
+        b.sxy = h.s_n[0] * h.s_n[1];
+        b.scale_idx = k;
+        b.pad = 0;
+    }
+    if (!dev->d_bricks) {
+        dpv_status s = dev_alloc(dev, (void**)&dev->d_bricks, sizeof(BrickDev) * MAX_RANKS, "brick table");
+        if (s) return s;
+    }
+    CK(cudaMemcpyAsync(dev->d_bricks, table.data(), sizeof(BrickDev) * dev->nranks, cudaMemcpyHostToDevice,
+                       dev->stream), "upload brick table");
+
+    // cameras
+    if ((int)dev->cams.size() > dev->cam_cap) {
+        dev_free(dev->d_cam_in);
+        dev_free(dev->d_cams);
+        dev->d_cam_in = nullptr;
+        dev->d_cams = nullptr;
+        dev->cam_cap = 0;
+        dpv_status s = dev_alloc(dev, (void**)&dev->d_cam_in, sizeof(CamIn) * dev->cams.size(), "cameras");
+        if (s) return s;
+        s = dev_alloc(dev, (void**)&dev->d_cams, sizeof(CamBasis) * dev->cams.size(), "cameras");
+        if (s) return s;
+        dev->cam_cap = (int)dev->cams.size();
+    }
+    CK(cudaMemcpyAsync(dev->d_cam_in, dev->cams.data(), sizeof(CamIn) * dev->cams.size(), cudaMemcpyHostToDevice,
+                       dev->stream), "upload cameras");
+
+    // schedule: count pass
+    free_schedule(dev);
+    size_t nct = (size_t)P.ncam * P.ntx * P.nty;
+    dpv_status s;
+    if ((s = dev_alloc(dev, (void**)&dev->d_rects, sizeof(int4) * (size_t)P.ncam * P.nbricks, "cull rects"))) return s;
+    if ((s = dev_alloc(dev, (void**)&dev->d_tile_count, sizeof(int) * nct, "tile counts"))) return s;
+    if ((s = dev_alloc(dev, (void**)&dev->d_tile_first, sizeof(int) * nct, "tile offsets"))) return s;
+    if (!dev->d_counters) {
+        if ((s = dev_alloc(dev, (void**)&dev->d_counters, sizeof(Counters), "counters"))) return s;
+    }
+    CK(cudaMemsetAsync(dev->d_counters, 0, sizeof(Counters), dev->stream), "reset counters");
+    float3 og = make_float3(dev->origin[0], dev->origin[1], dev->origin[2]);
+    CK(launch_cull(P, dev->d_cam_in, og, 1.0f / dev->spacing, dev->d_cams, dev->d_bricks, dev->d_rects,
+                   dev->d_tile_count, dev->d_tile_first, nullptr, 0, dev->d_counters, false, dev->stream),
+       "cull (sizing)");
+    dev->launches += 4;
+    Counters hc;
+    CK(cudaMemcpyAsync(&hc, dev->d_counters, sizeof(Counters), cudaMemcpyDeviceToHost, dev->stream), "read counts");
+    CK(cudaStreamSynchronize(dev->stream), "cull (sizing)");
+    if (hc.n_items > (unsigned long long)0x7fffffff / (unsigned long long)P.tp)
+        return fail(DPV_ERR_UNSUPPORTED, "work list too large (%llu items)", hc.n_items);
+    dev->n_items = (int)hc.n_items;
+    dev->items_cap = dev->n_items;
+    P.items_cap = dev->items_cap;
+    if ((s = dev_alloc(dev, (void**)&dev->d_items, sizeof(Item) * (size_t)std::max(1, dev->items_cap), "work list")))
+        return s;
+    // an invalid item (all bits set) until the first fill writes the list
+    CK(cudaMemsetAsync(dev->d_items, 0xFF, sizeof(Item) * (size_t)std::max(1, dev->items_cap), dev->stream),
+       "clear work list");
+
+    // fragment pool
+    if ((size_t)dev->n_items > dev->frag_cap) {
+        free_frags(dev);
+        size_t slots = (size_t)dev->n_items * P.tp;
+        if ((s = dev_alloc(dev, (void**)&dev->d_frag_rgba, sizeof(float4) * slots, "fragment pool"))) return s;
+        if ((s = dev_alloc(dev, (void**)&dev->d_frag_key, sizeof(int) * slots, "fragment pool"))) return s;
+        dev->frag_cap = (size_t)dev->n_items;
+    }
+    // frame buffers
+    size_t npix = (size_t)P.ncam * P.W * P.H;
+    if (npix > dev->out_cap) {
+        dev_free(dev->d_out_rgba);
+        dev_free(dev->d_out_depth);
+        dev->d_out_rgba = nullptr;
+        dev->d_out_depth = nullptr;
+        dev->out_cap = 0;
+        if ((s = dev_alloc(dev, (void**)&dev->d_out_rgba, sizeof(float4) * npix, "frame"))) return s;
+        if ((s = dev_alloc(dev, (void**)&dev->d_out_depth, sizeof(float) * npix, "frame"))) return s;
+        dev->out_cap = npix;
+    }
+    size_t nord = npix * (size_t)P.order_stride;
+    if (nord > dev->order_cap) {
+        dev_free(dev->d_order);
+        dev->d_order = nullptr;
+        dev->order_cap = 0;
+        if ((s = dev_alloc(dev, (void**)&dev->d_order, nord, "order image"))) return s;
+        dev->order_cap = nord;
+    }
+    dev->dirty = false;
+    return DPV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dpvGetLastError(void) { return g_last_error.c_str(); }
+
+dpv_status dpvCreateDevice(int num_ranks, int cuda_device, void* cuda_stream, dpv_device* out) {
+    g_last_error.clear();
+    if (!out) return fail(DPV_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (num_ranks < 1 || num_ranks > MAX_RANKS) return fail(DPV_ERR_INVALID_ARG, "num_ranks must be 1..%d", MAX_RANKS);
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(DPV_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    if (cuda_device < 0 || cuda_device >= ndev) return fail(DPV_ERR_INVALID_ARG, "cuda_device %d out of range", cuda_device);
+    dpv_device dev = new (std::nothrow) dpv_device_t();
+    if (!dev) return fail(DPV_ERR_OUT_OF_MEMORY, "host allocation failed");
+    dev->nranks = num_ranks;
+    dev->cuda_device = cuda_device;
+    dev->stream = (cudaStream_t)cuda_stream;
+    dev->bricks.resize(num_ranks);
+    DeviceGuard g(cuda_device);
+    dpv_status s;
+    if ((s = dev_alloc(dev, (void**)&dev->d_scales, sizeof(float) * MAX_RANKS, "scales")) ||
+        (s = dev_alloc(dev, (void**)&dev->d_tmp, sizeof(unsigned int) * 4, "scratch"))) {
+        dpvRelease(dev);
+        return s;
+    }
+    e = cudaEventCreateWithFlags(&dev->ev_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        dpvRelease(dev);
+        return fail(DPV_ERR_CUDA, "event: %s", cudaGetErrorString(e));
+    }
+    *out = dev;
+    return DPV_OK;
+}
+
+dpv_status dpvSetVolumeGeometry(dpv_device dev, const int dims[3], const float origin[3], float spacing) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!dims || !origin) return fail(DPV_ERR_INVALID_ARG, "dims/origin NULL");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 2) return fail(DPV_ERR_INVALID_ARG, "dims[%d] = %d < 2", a, dims[a]);
+    if (!(spacing > 0.0f) || !isfinite(spacing)) return fail(DPV_ERR_INVALID_ARG, "spacing must be > 0");
+    DeviceGuard g(dev->cuda_device);
+    for (auto& b : dev->bricks) {
+        dev_free(b.data);
+        b = HostBrick();
+    }
+    for (int a = 0; a < 3; ++a) {
+        dev->dims[a] = dims[a];
+        dev->origin[a] = origin[a];
+    }
+    dev->spacing = spacing;
+    dev->has_geom = true;
+    dev->dirty = true;
+    return DPV_OK;
+}
+
+dpv_status dpvCommitBrick(dpv_device dev, int rank, const dpv_brick_desc* d) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!dev->has_geom) return fail(DPV_ERR_STATE, "set the volume geometry before committing bricks");
+    if (rank < 0 || rank >= dev->nranks) return fail(DPV_ERR_INVALID_ARG, "rank %d out of range", rank);
+    if (!d || !d->data) return fail(DPV_ERR_INVALID_ARG, "brick descriptor or data is NULL");
+    if ((int)d->storage < 0 || (int)d->storage > 3 || (int)d->src_dtype < 0 || (int)d->src_dtype > 3)
+        return fail(DPV_ERR_INVALID_ARG, "bad dtype");
+    if (d->src_dtype != DPV_F32 && d->src_dtype != d->storage)
+        return fail(DPV_ERR_UNSUPPORTED, "source data must be float32 or already in the storage format");
+    HostBrick nb;
+    long long nodes = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (d->owned_lo[a] < 0 || d->owned_hi[a] > dev->dims[a] || d->owned_lo[a] >= d->owned_hi[a])
+            return fail(DPV_ERR_INVALID_ARG, "owned range on axis %d is [%d, %d) in a volume of %d nodes", a,
+                        d->owned_lo[a], d->owned_hi[a], dev->dims[a]);
+        nb.lo[a] = d->owned_lo[a];
+        nb.hi[a] = d->owned_hi[a];
+        nb.s_lo[a] = std::max(d->owned_lo[a] - 1, 0);
+        int s_hi = std::min(d->owned_hi[a], dev->dims[a] - 1);
+        nb.s_n[a] = s_hi - nb.s_lo[a] + 1;
+        nodes *= nb.s_n[a];
+        if (d->data_dims[a] < 1 || d->data_lo[a] > nb.s_lo[a] || d->data_lo[a] + d->data_dims[a] < nb.s_lo[a] + nb.s_n[a])
+            return fail(DPV_ERR_INVALID_ARG, "data box on axis %d does not contain the stored nodes [%d, %d)", a,
+                        nb.s_lo[a], nb.s_lo[a] + nb.s_n[a]);
+    }
+    if (nodes > 0x7fffffffLL) return fail(DPV_ERR_UNSUPPORTED, "brick stores %lld nodes (max 2^31 - 1)", nodes);
+    nb.dtype = (int)d->storage;
+    nb.bytes = (size_t)nodes * kElemSize[nb.dtype];
+    DeviceGuard g(dev->cuda_device);
+    HostBrick& hb = dev->bricks[rank];
+    if (hb.data && hb.bytes == nb.bytes) {
+        nb.data = hb.data;
+        hb.data = nullptr;
+    } else {
+        dev_free(hb.data);
+        hb.data = nullptr;
+        if ((s = dev_alloc(dev, &nb.data, nb.bytes, "brick storage"))) return s;
+    }
+    CommitArgs a;
+    void* staging = nullptr;
+    if (d->data_on_device) {
+        a.src = d->data;
+        for (int k = 0; k < 3; ++k) {
+            a.d_lo[k] = d->data_lo[k];
+            a.d_n[k] = d->data_dims[k];
+        }
+    } else {
+        // copy just the stored box from the host into a staging buffer
+        size_t es = kElemSize[d->src_dtype];
+        if ((s = dev_alloc(dev, &staging, (size_t)nodes * es, "staging"))) {
+            dev_free(nb.data);
+            return s;
+        }
+        cudaMemcpy3DParms p;
+        memset(&p, 0, sizeof p);
+        p.srcPtr = make_cudaPitchedPtr((void*)d->data, (size_t)d->data_dims[0] * es, (size_t)d->data_dims[0],
+                                       (size_t)d->data_dims[1]);
+        p.srcPos = make_cudaPos((size_t)(nb.s_lo[0] - d->data_lo[0]) * es, (size_t)(nb.s_lo[1] - d->data_lo[1]),
+                                (size_t)(nb.s_lo[2] - d->data_lo[2]));
+        p.dstPtr = make_cudaPitchedPtr(staging, (size_t)nb.s_n[0] * es, (size_t)nb.s_n[0], (size_t)nb.s_n[1]);
+        p.extent = make_cudaExtent((size_t)nb.s_n[0] * es, (size_t)nb.s_n[1], (size_t)nb.s_n[2]);
+        p.kind = cudaMemcpyHostToDevice;
+        CK(cudaMemcpy3DAsync(&p, dev->stream), "copy brick from host");
+        a.src = staging;
+        for (int k = 0; k < 3; ++k) {
+            a.d_lo[k] = nb.s_lo[k];
+            a.d_n[k] = nb.s_n[k];
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        a.s_lo[k] = nb.s_lo[k];
+        a.s_n[k] = nb.s_n[k];
+    }
+    cudaError_t e = launch_commit(a, nb.dtype, d->src_dtype == DPV_F32, d->scale, dev->d_tmp, dev->d_scales + rank,
+                                  nb.data, dev->stream);
+    if (staging) {
+        cudaError_t e2 = cudaStreamSynchronize(dev->stream);
+        dev_free(staging);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) return cuda_fail(dev, e, "brick commit");
+    nb.committed = true;
+    hb = nb;
+    dev->dirty = true;
+    return DPV_OK;
+}
+
+dpv_status dpvSetTransferFunction(dpv_device dev, const float* rgba, int n, float vmin, float vmax, int on_device) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!rgba) return fail(DPV_ERR_INVALID_ARG, "rgba is NULL");
+    if (n < 2 || n > MAX_TF) return fail(DPV_ERR_INVALID_ARG, "TF size %d not in 2..%d", n, MAX_TF);
+    if (!(vmax > vmin)) return fail(DPV_ERR_INVALID_ARG, "need vmax > vmin");
+    DeviceGuard g(dev->cuda_device);
+    if (n > dev->ntf || !dev->d_tf) {
+        dev_free(dev->d_tf);
+        dev->d_tf = nullptr;
+        if ((s = dev_alloc(dev, (void**)&dev->d_tf, sizeof(float4) * n, "TF"))) return s;
+    }
+    CK(cudaMemcpyAsync(dev->d_tf, rgba, sizeof(float4) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       dev->stream), "upload TF");
+    if (!on_device) CK(cudaStreamSynchronize(dev->stream), "upload TF");
+    if (n != dev->ntf || vmin != dev->vmin || vmax != dev->vmax) dev->dirty = true;
+    dev->ntf = n;
+    dev->vmin = vmin;
+    dev->vmax = vmax;
+    return DPV_OK;
+}
+
+dpv_status dpvSetCameras(dpv_device dev, const dpv_camera* cams, int n) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!cams || n < 1) return fail(DPV_ERR_INVALID_ARG, "need at least one camera");
+    std::vector<CamIn> v(n);
+    for (int i = 0; i < n; ++i) {
+        const dpv_camera& c = cams[i];
+        float fx = c.center[0] - c.eye[0], fy = c.center[1] - c.eye[1], fz = c.center[2] - c.eye[2];
+        float cx = fy * c.up[2] - fz * c.up[1], cy = fz * c.up[0] - fx * c.up[2], cz = fx * c.up[1] - fy * c.up[0];
+        if (fx * fx + fy * fy + fz * fz == 0.0f) return fail(DPV_ERR_INVALID_ARG, "camera %d: eye == center", i);
+        if (cx * cx + cy * cy + cz * cz == 0.0f) return fail(DPV_ERR_INVALID_ARG, "camera %d: up parallel to view", i);
+        if (!(c.fovy_deg > 0.0f && c.fovy_deg < 180.0f)) return fail(DPV_ERR_INVALID_ARG, "camera %d: fovy", i);
+        memcpy(&v[i], &c, sizeof(CamIn));
+    }
+    dev->cams.swap(v);
+    dev->dirty = true;
+    return DPV_OK;
+}
+
+dpv_status dpvSetFrame(dpv_device dev, const dpv_frame_desc* f) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!f) return fail(DPV_ERR_INVALID_ARG, "frame descriptor is NULL");
+    if (f->width < 1 || f->height < 1) return fail(DPV_ERR_INVALID_ARG, "frame size %dx%d", f->width, f->height);
+    if (!(f->step_voxels > 0.0f)) return fail(DPV_ERR_INVALID_ARG, "step_voxels must be > 0");
+    if (!(f->sigma_max >= 0.0f)) return fail(DPV_ERR_INVALID_ARG, "sigma_max must be >= 0");
+    int tw = f->tile_w > 0 ? f->tile_w : 16, th = f->tile_h > 0 ? f->tile_h : 16;
+    if (tw % 8 || th % 4 || tw * th > 256)
+        return fail(DPV_ERR_INVALID_ARG, "tile %dx%d: width a multiple of 8, height of 4, at most 256 pixels", tw, th);
+    dev->frame = *f;
+    dev->has_frame = true;
+    dev->dirty = true;
+    return DPV_OK;
+}
+
+dpv_status dpvRenderFrame(dpv_device dev) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!dev->has_geom) return fail(DPV_ERR_STATE, "no volume geometry");
+    for (int k = 0; k < dev->nranks; ++k)
+        if (!dev->bricks[k].committed) return fail(DPV_ERR_STATE, "rank %d has not committed its brick", k);
+    if (!dev->d_tf) return fail(DPV_ERR_STATE, "no transfer function");
+    if (dev->cams.empty()) return fail(DPV_ERR_STATE, "no cameras");
+    if (!dev->has_frame) return fail(DPV_ERR_STATE, "no frame parameters");
+    DeviceGuard g(dev->cuda_device);
+    if (dev->dirty) {
+        if ((s = check_partition(dev))) return s;
+        if ((s = prepare(dev))) return s;
+    }
+    const FrameParams& P = dev->P;
+    float inv_sp = 1.0f / dev->spacing;
+    float3 og = make_float3(dev->origin[0], dev->origin[1], dev->origin[2]);
+    CK(cudaMemsetAsync(dev->d_counters, 0, sizeof(Counters), dev->stream), "reset counters");
+    cudaEvent_t t0 = stage_start(dev);
+    CK(launch_cull(P, dev->d_cam_in, og, inv_sp, dev->d_cams, dev->d_bricks, dev->d_rects, dev->d_tile_count,
+                   dev->d_tile_first, dev->d_items, dev->items_cap, dev->d_counters, true, dev->stream),
+       "cull");
+    stage_stop(dev, DPV_STAGE_CULL, t0);
+    t0 = stage_start(dev);
+    CK(launch_march_fwd(dev->bricks[0].dtype, P, inv_sp, dev->d_cams, dev->d_bricks, dev->d_scales, dev->d_items,
+                        dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters, dev->stream),
+       "march");
+    stage_stop(dev, DPV_STAGE_MARCH, t0);
+    t0 = stage_start(dev);
+    CK(launch_composite_fwd(P, inv_sp, dev->d_cams, dev->d_tile_first, dev->d_tile_count, dev->d_items,
+                            dev->d_frag_rgba, dev->d_frag_key, dev->d_out_rgba, dev->d_out_depth,
+                            P.order_stride ? dev->d_order : nullptr, dev->stream),
+       "composite");
+    stage_stop(dev, DPV_STAGE_COMPOSITE, t0);
+    dev->launches += 5 + (dev->n_items > 0 ? 1 : 0) + 1;
+    CK(cudaEventRecord(dev->ev_done, dev->stream), "record");
+    dev->rendered = true;
+    return DPV_OK;
+}
+
+dpv_status dpvFrameReady(dpv_device dev, int wait, int* ready) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!ready) return fail(DPV_ERR_INVALID_ARG, "ready is NULL");
+    if (!dev->rendered) {
+        *ready = 1;
+        return DPV_OK;
+    }
+    DeviceGuard g(dev->cuda_device);
+    cudaError_t e = wait ? cudaEventSynchronize(dev->ev_done) : cudaEventQuery(dev->ev_done);
+    if (e == cudaErrorNotReady) {
+        *ready = 0;
+        return DPV_OK;
+    }
+    if (e != cudaSuccess) return cuda_fail(dev, e, "frame completion");
+    *ready = 1;
+    return DPV_OK;
+}
+
+dpv_status dpvMapFrame(dpv_device dev, int camera, const float** rgba, const float** depth) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!dev->rendered) return fail(DPV_ERR_STATE, "no frame rendered yet");
+    if (camera < 0 || camera >= dev->P.ncam) return fail(DPV_ERR_INVALID_ARG, "camera %d out of range", camera);
+    size_t off = (size_t)camera * dev->P.W * dev->P.H;
+    if (rgba) *rgba = (const float*)(dev->d_out_rgba + off);
+    if (depth) *depth = dev->d_out_depth + off;
+    return DPV_OK;
+}
+
+dpv_status dpvUnmapFrame(dpv_device dev, int camera) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (camera < 0 || camera >= dev->P.ncam) return fail(DPV_ERR_INVALID_ARG, "camera %d out of range", camera);
+    return DPV_OK;
+}
+
+dpv_status dpvCopyFrame(dpv_device dev, int camera, float* rgba, float* depth) {
+    const float *r = nullptr, *d = nullptr;
+    dpv_status s = dpvMapFrame(dev, camera, &r, &d);
+    if (s) return s;
+    DeviceGuard g(dev->cuda_device);
+    size_t n = (size_t)dev->P.W * dev->P.H;
+    if (rgba) CK(cudaMemcpyAsync(rgba, r, n * sizeof(float4), cudaMemcpyDefault, dev->stream), "copy frame");
+    if (depth) CK(cudaMemcpyAsync(depth, d, n * sizeof(float), cudaMemcpyDefault, dev->stream), "copy frame");
+    cudaPointerAttributes at;
+    bool host = false;
+    if (rgba && cudaPointerGetAttributes(&at, rgba) == cudaSuccess && at.type != cudaMemoryTypeDevice &&
+        at.type != cudaMemoryTypeManaged)
+        host = true;
+    if (depth && cudaPointerGetAttributes(&at, depth) == cudaSuccess && at.type != cudaMemoryTypeDevice &&
+        at.type != cudaMemoryTypeManaged)
+        host = true;
+    cudaGetLastError();
+    if (host) CK(cudaStreamSynchronize(dev->stream), "copy frame");
+    return DPV_OK;
+}
+
+dpv_status dpvReadFragments(dpv_device dev, int camera, int rank, float* rgba, int32_t* key) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!dev->rendered) return fail(DPV_ERR_STATE, "no frame rendered yet");
+    if (camera < 0 || camera >= dev->P.ncam) return fail(DPV_ERR_INVALID_ARG, "camera %d out of range", camera);
+    if (rank < 0 || rank >= dev->nranks) return fail(DPV_ERR_INVALID_ARG, "rank %d out of range", rank);
+    if (!rgba || !key) return fail(DPV_ERR_INVALID_ARG, "output NULL");
+    DeviceGuard g(dev->cuda_device);
+    CK(launch_read_frags(dev->P, dev->d_items, dev->n_items, camera, rank, dev->d_frag_rgba, dev->d_frag_key,
+                         (float4*)rgba, key, dev->stream),
+       "read fragments");
+    return DPV_OK;
+}
+
+dpv_status dpvReadBrick(dpv_device dev, int rank, void* dst, int stored_lo[3], int stored_dims[3], float* scale) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (rank < 0 || rank >= dev->nranks) return fail(DPV_ERR_INVALID_ARG, "rank %d out of range", rank);
+    const HostBrick& b = dev->bricks[rank];
+    if (!b.committed) return fail(DPV_ERR_STATE, "rank %d has not committed its brick", rank);
+    DeviceGuard g(dev->cuda_device);
+    if (dst) CK(cudaMemcpyAsync(dst, b.data, b.bytes, cudaMemcpyDeviceToDevice, dev->stream), "read brick");
+    float sc = 1.0f;
+    CK(cudaMemcpyAsync(&sc, dev->d_scales + rank, sizeof(float), cudaMemcpyDeviceToHost, dev->stream), "read scale");
+    CK(cudaStreamSynchronize(dev->stream), "read brick");
+    for (int a = 0; a < 3; ++a) {
+        if (stored_lo) stored_lo[a] = b.s_lo[a];
+        if (stored_dims) stored_dims[a] = b.s_n[a];
+    }
+    if (scale) *scale = sc;
+    return DPV_OK;
+}
+
+dpv_status dpvMapOrder(dpv_device dev, int camera, const uint8_t** order, int* stride) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!dev->rendered) return fail(DPV_ERR_STATE, "no frame rendered yet");
+    if (!dev->P.order_stride) return fail(DPV_ERR_STATE, "frame was rendered without DPV_FRAME_ORDER");
+    if (camera < 0 || camera >= dev->P.ncam) return fail(DPV_ERR_INVALID_ARG, "camera %d out of range", camera);
+    if (!order || !stride) return fail(DPV_ERR_INVALID_ARG, "output NULL");
+    *order = dev->d_order + (size_t)camera * dev->P.W * dev->P.H * dev->P.order_stride;
+    *stride = dev->P.order_stride;
+    return DPV_OK;
+}
+
+dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, float* dL_dvol) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!dev->rendered || dev->dirty) return fail(DPV_ERR_STATE, "backward needs the fragments of a render");
+    if (!dL_drgba || !dL_dtf) return fail(DPV_ERR_INVALID_ARG, "gradient pointers NULL");
+    DeviceGuard g(dev->cuda_device);
+    const FrameParams& P = dev->P;
+    if (!dev->d_frag_grad) {
+        if ((s = dev_alloc(dev, (void**)&dev->d_frag_grad, sizeof(float4) * dev->frag_cap * P.tp, "fragment grads")))
+            return s;
+    }
+    CK(cudaMemsetAsync(dL_dtf, 0, sizeof(double) * 4 * dev->ntf, dev->stream), "zero dtf");
+    if (dL_dvol)
+        CK(cudaMemsetAsync(dL_dvol, 0, sizeof(float) * (size_t)dev->dims[0] * dev->dims[1] * dev->dims[2], dev->stream),
+           "zero dvol");
+    CK(cudaMemsetAsync(&dev->d_counters->samples_bwd, 0, sizeof(unsigned long long), dev->stream), "reset counter");
+    cudaEvent_t t0 = stage_start(dev);
+    CK(launch_composite_bwd(P, dev->d_tile_first, dev->d_tile_count, dev->d_frag_rgba, dev->d_frag_key,
+                            (const float4*)dL_drgba, dev->d_frag_grad, dev->stream),
+       "composite backward");
+    stage_stop(dev, DPV_STAGE_COMPOSITE_BWD, t0);
+    t0 = stage_start(dev);
+    CK(launch_march_bwd(dev->bricks[0].dtype, P, 1.0f / dev->spacing, dev->d_cams, dev->d_bricks, dev->d_scales,
+                        dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_frag_grad,
+                        dL_dtf, dL_dvol, dev->d_counters, dev->stream),
+       "march backward");
+    stage_stop(dev, DPV_STAGE_MARCH_BWD, t0);
+    dev->launches += 1 + (dev->n_items > 0 ? 1 : 0);
+    return DPV_OK;
+}
+
+dpv_status dpvGetStats(dpv_device dev, dpv_stats* out) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!out) return fail(DPV_ERR_INVALID_ARG, "out NULL");
+    memset(out, 0, sizeof *out);
+    if (!dev->d_counters) return DPV_OK;
+    DeviceGuard g(dev->cuda_device);
+    Counters c;
+    CK(cudaMemcpyAsync(&c, dev->d_counters, sizeof c, cudaMemcpyDeviceToHost, dev->stream), "read counters");
+    CK(cudaStreamSynchronize(dev->stream), "read counters");
+    out->samples_forward = c.samples_fwd;
+    out->samples_backward = c.samples_bwd;
+    out->work_items = (uint64_t)dev->n_items;
+    out->fragment_bytes = (uint64_t)dev->frag_cap * dev->P.tp * (sizeof(float4) + sizeof(int) +
+                                                                  (dev->d_frag_grad ? sizeof(float4) : 0));
+    out->error_flags = c.err;
+    out->max_fragments = c.max_frag;
+    resolve_timers(dev);
+    for (int i = 0; i < DPV_NUM_STAGES; ++i) {
+        out->stage_ms[i] = dev->stage_ms[i];
+        out->stage_calls[i] = dev->stage_calls[i];
+    }
+    out->kernel_launches = dev->launches;
+    return DPV_OK;
+}
+
+dpv_status dpvResetStats(dpv_device dev) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    DeviceGuard g(dev->cuda_device);
+    resolve_timers(dev);
+    for (int i = 0; i < DPV_NUM_STAGES; ++i) {
+        dev->stage_ms[i] = 0.0;
+        dev->stage_calls[i] = 0;
+    }
+    dev->launches = 0;
+    return DPV_OK;
+}
+
+dpv_status dpvSetProfiling(dpv_device dev, int enable) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    dev->profiling = enable != 0;
+    return DPV_OK;
+}
+
+dpv_status dpvRelease(dpv_device dev) {
+    if (!dev) return DPV_OK;
+    {
+        DeviceGuard g(dev->cuda_device);
+        if (!dev->poisoned && dev->stream) cudaStreamSynchronize(dev->stream);
+        for (auto& b : dev->bricks) dev_free(b.data);
+        free_schedule(dev);
+        free_frags(dev);
+        dev_free(dev->d_scales);
+        dev_free(dev->d_tmp);
+        dev_free(dev->d_bricks);
+        dev_free(dev->d_tf);
+        dev_free(dev->d_cam_in);
+        dev_free(dev->d_cams);
+        dev_free(dev->d_out_rgba);
+        dev_free(dev->d_out_depth);
+        dev_free(dev->d_order);
+        dev_free(dev->d_counters);
+        if (dev->ev_done) cudaEventDestroy(dev->ev_done);
+        for (auto& t : dev->pending) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+        for (auto e : dev->event_pool) cudaEventDestroy(e);
+        cudaGetLastError();
+    }
+    delete dev;
+    return DPV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+// dpv_internal.cuh -- device-side data layout and per-sample arithmetic of
+// the brick ray-march and the sort-last compositor (sm_103a).
+//
+// Conventions are the ones stated in include/dpv.h.  Everything here is
+// FP32 with integer sample indices; nothing is shared with the FP64 oracle.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dpv {
+
+constexpr int KEY_EMPTY = 0x7fffffff;
+constexpr int MAX_RANKS = 255;
+constexpr int MAX_TF = 4096;
+constexpr int KR = 16;                   // fragments a pixel sorts in registers
+
+// device error bits (Counters::err)
+constexpr unsigned ERR_ITEM_OVERFLOW = 1u;   // culling listed more items than sized for
+
+// One camera, prepared on the device: eye in node coordinates and the
+// orthonormal look-at basis (world directions are node directions up to the
+// uniform scale 1/spacing).
+struct CamBasis {
+    float o[3];
+    float f[3], r[3], u[3];
+    float th;          // tan(fovy / 2)
+    float pad;
+};
+
+// One rank's brick as the kernels see it.
+struct BrickDev {
+    const void* data;  // stored nodes, x fastest
+    int s_lo[3];       // first stored node (global node index)
+    int s_n[3];        // stored nodes per axis (>= 2)
+    float r0[3], r1[3];// owned region, node coordinates, clipped to the volume
+    int closed[3];     // 1 where r1 is the volume's upper face (closed end)
+    int sx, sxy;       // strides of y and z in nodes
+    int scale_idx;     // index into the device scale array
+    int pad;
+};
+
+// A work item: one brick seen through one screen tile of one camera.
+struct Item {
+    int cam;
+    int tile;          // tile index within the camera's image
+    int brick;
+    int pad;
+};
+
+struct Counters {
+    unsigned long long samples_fwd;
+    unsigned long long samples_bwd;
+    unsigned long long n_items;
+    unsigned int err;
+    unsigned int max_frag;
+};
+
+// Per-frame constants, passed by value.
+struct FrameParams {
+    int W, H;          // image size
+    int tw, th;        // tile size (tw % 8 == 0, th % 4 == 0)
+    int ntx, nty;      // tiles per row / column
+    int ncam, tp;      // cameras, pixels per tile
+    float dt;          // world step
+    float inv_dt;
+    float sigma_max;
+    float ert;         // local opacity threshold
+    int ert_on;
+    float vmin;        // TF domain start
+    float tf_scale;    // (n - 1) / (vmax - vmin)
+    int ntf;           // TF entries
+    int dims[3];       // global nodes per axis
+    int nbricks;
+    int order_stride;  // bytes per pixel of the order image (0 = off)
+    int items_cap;     // work items the list and fragment pool hold
+};
+
+// A work item read back from the list is used only if it names a valid
+// camera, tile and brick (the list is rebuilt every frame; an overflowed
+// tile leaves its entries unwritten).
+__device__ __forceinline__ bool item_ok(const Item& it, const FrameParams& P) {
+    return (unsigned)it.cam < (unsigned)P.ncam && (unsigned)it.brick < (unsigned)P.nbricks &&
+           (unsigned)it.tile < (unsigned)(P.ntx * P.nty);
+}
+
+// ---------------------------------------------------------------------------
+// tiles: warps cover 8 x 4 pixel blocks, laid row-major inside the tile, so
+// a warp's rays are spatially compact.  The fragment of tile thread t is
+// stored at slot t of its item (thread order).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tile_pixel(int t, int tw, int& lx, int& ly) {
+    int w = t >> 5, l = t & 31;
+    int wpr = tw >> 3;
+    lx = (w % wpr) * 8 + (l & 7);
+    ly = (w / wpr) * 4 + (l >> 3);
+}
+
+// ---------------------------------------------------------------------------
+// rays: pinhole camera, pixel centres, row 0 at the bottom.  Ray origin and
+// direction are returned in node coordinates, with t in world units.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pixel_ray(const CamBasis& c, const FrameParams& P, float inv_spacing, int px,
+                                          int py, float o[3], float d[3]) {
+    float nx = (((px + 0.5f) / P.W) * 2.0f - 1.0f) * ((float)P.W / (float)P.H);
+    float ny = ((py + 0.5f) / P.H) * 2.0f - 1.0f;
+    float a = nx * c.th, b = ny * c.th;
+    float dx = c.f[0] + a * c.r[0] + b * c.u[0];
+    float dy = c.f[1] + a * c.r[1] + b * c.u[1];
+    float dz = c.f[2] + a * c.r[2] + b * c.u[2];
+    float n = inv_spacing / sqrtf(dx * dx + dy * dy + dz * dz);
+    d[0] = dx * n;
+    d[1] = dy * n;
+    d[2] = dz * n;
+    o[0] = c.o[0];
+    o[1] = c.o[1];
+    o[2] = c.o[2];
+}
+
+// Parametric interval of a ray in the node-space box [lo, hi] per axis.  An
+// axis the ray is parallel to constrains nothing if the origin lies in
+// [lo, hi) (or [lo, hi] where `closed`), else empties the interval.  Every
+// face plane's t is (plane - o) / d computed one way, so boxes that share a
+// plane get bit-identical boundaries and their sample ranges tile the ray.
+__device__ __forceinline__ void ray_box(const float o[3], const float d[3], const float lo[3], const float hi[3],
+                                        const int closed[3], float& t0, float& t1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.0f) {
+            float ta = (lo[a] - o[a]) / d[a];
+            float tb = (hi[a] - o[a]) / d[a];
+            t0 = fmaxf(t0, fminf(ta, tb));
+            t1 = fminf(t1, fmaxf(ta, tb));
+        } else {
+            bool in = o[a] >= lo[a] && (closed[a] ? o[a] <= hi[a] : o[a] < hi[a]);
+            if (!in) t0 = __int_as_float(0x7f800000);
+        }
+    }
+}
+
+// Interval of the ray in the whole volume, clipped to t >= 0.
+__device__ __forceinline__ bool volume_interval(const FrameParams& P, const float o[3], const float d[3], float& te,
+                                                float& tx) {
+    const float lo[3] = {0.0f, 0.0f, 0.0f};
+    const float hi[3] = {(float)(P.dims[0] - 1), (float)(P.dims[1] - 1), (float)(P.dims[2] - 1)};
+    const int closed[3] = {1, 1, 1};
+    te = 0.0f;
+    tx = __int_as_float(0x7f800000);
+    ray_box(o, d, lo, hi, closed, te, tx);
+    return te < tx;
+}
+
+// Sample index of the first sample at or after t: samples sit at
+// t_enter + (j + 1/2) dt.
+__device__ __forceinline__ int first_sample_at(float t, float te, const FrameParams& P) {
+    return (int)ceilf((t - te) * P.inv_dt - 0.5f);
+}
+
+// ---------------------------------------------------------------------------
+// stored values
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Storage;
+
+template <>
+struct Storage<float> {
+    static __device__ __forceinline__ float load(const float* p, int i) { return __ldg(p + i); }
+    static constexpr bool unit_scale = true;
+};
+template <>
+struct Storage<__half> {
+    static __device__ __forceinline__ float load(const __half* p, int i) {
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p) + i)));
+    }
+    static constexpr bool unit_scale = false;
+};
+template <>
+struct Storage<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16* p, int i) {
+        return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p) + i)));
+    }
+    static constexpr bool unit_scale = false;
+};
+template <>
+struct Storage<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ float load(const __nv_fp8_e4m3* p, int i) {
+        unsigned char b = __ldg(reinterpret_cast<const unsigned char*>(p) + i);
+        return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3)));
+    }
+    static constexpr bool unit_scale = false;
+};
+
+// Trilinear value at brick-local node coordinates q (x fastest): cell
+// i = clamp(floor(q), 0, n - 2), weights q - i, lerp in x, then y, then z.
+// The per-brick scale multiplies the interpolated value (equal to scaling
+// each corner, up to rounding).  Returns the cell base index and weights for
+// the adjoint.
+template <typename T>
+__device__ __forceinline__ float trilinear(const BrickDev& b, const T* data, float scale, float qx, float qy,
+                                           float qz, int& base, float& fx, float& fy, float& fz) {
+    int ix = min(max(__float2int_rd(qx), 0), b.s_n[0] - 2);
+    int iy = min(max(__float2int_rd(qy), 0), b.s_n[1] - 2);
+    int iz = min(max(__float2int_rd(qz), 0), b.s_n[2] - 2);
+    fx = qx - (float)ix;
+    fy = qy - (float)iy;
+    fz = qz - (float)iz;
+    base = ix + iy * b.sx + iz * b.sxy;
+    const T* p = data + base;
+    float v000 = Storage<T>::load(p, 0);
+    float v100 = Storage<T>::load(p, 1);
+    float v010 = Storage<T>::load(p, b.sx);
+    float v110 = Storage<T>::load(p, b.sx + 1);
+    float v001 = Storage<T>::load(p, b.sxy);
+    float v101 = Storage<T>::load(p, b.sxy + 1);
+    float v011 = Storage<T>::load(p, b.sxy + b.sx);
+    float v111 = Storage<T>::load(p, b.sxy + b.sx + 1);
+    float x00 = fmaf(fx, v100 - v000, v000);
+    float x10 = fmaf(fx, v110 - v010, v010);
+    float x01 = fmaf(fx, v101 - v001, v001);
+    float x11 = fmaf(fx, v111 - v011, v011);
+    float y0 = fmaf(fy, x10 - x00, x00);
+    float y1 = fmaf(fy, x11 - x01, x01);
+    float v = fmaf(fz, y1 - y0, y0);
+    return Storage<T>::unit_scale ? v : v * scale;
+}
+
+// ---------------------------------------------------------------------------
+// transfer function and emission-absorption
+// ---------------------------------------------------------------------------
+struct TFSample {
+    float4 v;          // interpolated RGBA
+    int i0;            // left entry
+    float w;           // weight of the right entry
+    float duds;        // du/ds (0 where clamped)
+};
+
+__device__ __forceinline__ TFSample tf_lookup(const float4* tab, const FrameParams& P, float s) {
+    TFSample r;
+    float u = (s - P.vmin) * P.tf_scale;
+    float hi = (float)(P.ntf - 1);
+    r.duds = (u >= 0.0f && u <= hi) ? P.tf_scale : 0.0f;
+    u = fminf(fmaxf(u, 0.0f), hi);
+    r.i0 = min(__float2int_rd(u), P.ntf - 2);
+    r.w = u - (float)r.i0;
+    float4 a = tab[r.i0], b = tab[r.i0 + 1];
+    r.v.x = fmaf(r.w, b.x - a.x, a.x);
+    r.v.y = fmaf(r.w, b.y - a.y, a.y);
+    r.v.z = fmaf(r.w, b.z - a.z, a.z);
+    r.v.w = fmaf(r.w, b.w - a.w, a.w);
+    return r;
+}
+
+// Opacity of one sample: 1 - exp(-sigma_max * a * dt).
+__device__ __forceinline__ float sample_alpha(const FrameParams& P, float a) {
+    return -expm1f(-P.sigma_max * a * P.dt);
+}
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace dpv

@@ -1,0 +1,820 @@
+// kernels.cu -- the GPU path: brick commit, culling / work list, brick
+// ray-march, sort-last compositor, and their adjoints (sm_103a).
+//
+// Paper structure followed (arXiv 2407.00179): every rank owns one spatial
+// part of the volume (§1, §3.1.2) with a ghost layer (§1); each rank reduces
+// its part to one RGBA fragment per pixel, which is exact for convex parts
+// (§2.1); fragments carry a depth key and are sorted per pixel and blended
+// front to back in one kernel (§5.1.1, "Compositing").  The paper's parallel
+// direct send is replaced by the compositor reading every logical rank's
+// fragments straight from HBM.
+#include "dpv_internal.cuh"
+#include "launch.h"
+
+namespace dpv {
+
+// ===========================================================================
+// brick commit (ghost extraction + storage conversion)
+// ===========================================================================
+
+template <typename T>
+__device__ __forceinline__ float src_value(const T* p, long long i);
+template <>
+__device__ __forceinline__ float src_value<float>(const float* p, long long i) { return p[i]; }
+
+template <typename T>
+__device__ __forceinline__ T to_storage(float v);
+template <>
+__device__ __forceinline__ float to_storage<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half to_storage<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __nv_fp8_e4m3 to_storage<__nv_fp8_e4m3>(float v) {
+    __nv_fp8_e4m3 r;
+    r.__x = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    return r;
+}
+
+// Linear index in the source box of stored node k of a brick.
+__device__ __forceinline__ long long src_index(long long k, const CommitArgs& a) {
+    long long nx = a.s_n[0], nxy = (long long)a.s_n[0] * a.s_n[1];
+    long long z = k / nxy, y = (k - z * nxy) / nx, x = k - z * nxy - y * nx;
+    long long gx = x + a.s_lo[0] - a.d_lo[0], gy = y + a.s_lo[1] - a.d_lo[1], gz = z + a.s_lo[2] - a.d_lo[2];
+    return (gz * a.d_n[1] + gy) * (long long)a.d_n[0] + gx;
+}
+
+// max |v| over the stored nodes (non-negative floats order like their bits)
+__global__ void k_brick_maxabs(CommitArgs a, unsigned int* out) {
+    long long n = (long long)a.s_n[0] * a.s_n[1] * a.s_n[2];
+    float m = 0.0f;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(src_value<float>((const float*)a.src, src_index(k, a))));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// scale = given, or max|v| / 448 for fp8 (1 if zero), or 1
+__global__ void k_brick_scale(const unsigned int* maxabs, float given, int fp8, float* scale_out) {
+    float s = given;
+    if (!(given > 0.0f)) {
+        s = 1.0f;
+        if (fp8) {
+            float m = __uint_as_float(*maxabs);
+            if (m > 0.0f) s = m / 448.0f;
+        }
+    }
+    *scale_out = s;
+}
+
+template <typename T>
+__global__ void k_brick_convert(CommitArgs a, const float* scale, T* dst) {
+    long long n = (long long)a.s_n[0] * a.s_n[1] * a.s_n[2];
+    float sc = *scale;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        float v = src_value<float>((const float*)a.src, src_index(k, a));
+        dst[k] = to_storage<T>(v / sc);
+    }
+}
+
+// same-format copy (no conversion), element size es
+__global__ void k_brick_copy(CommitArgs a, int es, unsigned char* dst) {
+    long long n = (long long)a.s_n[0] * a.s_n[1] * a.s_n[2];
+    const unsigned char* s = (const unsigned char*)a.src;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        long long si = src_index(k, a);
+        for (int b = 0; b < es; ++b) dst[k * es + b] = s[si * es + b];
+    }
+}
+
+cudaError_t launch_commit(const CommitArgs& a, int storage, int src_is_f32, float given_scale, unsigned int* d_tmp,
+                          float* d_scale, void* dst, cudaStream_t st) {
+    long long n = (long long)a.s_n[0] * a.s_n[1] * a.s_n[2];
+    long long nb = (n + 255) / 256;
+    int blocks = (int)(nb < 148LL * 16 ? nb : 148LL * 16);
+    if (!src_is_f32) {
+        // data already in the storage format: copy, scale as given (default 1)
+        k_brick_scale<<<1, 1, 0, st>>>(d_tmp, given_scale, 0, d_scale);
+        static const int es[4] = {4, 2, 2, 1};
+        k_brick_copy<<<blocks, 256, 0, st>>>(a, es[storage], (unsigned char*)dst);
+        return cudaGetLastError();
+    }
+    cudaMemsetAsync(d_tmp, 0, sizeof(unsigned int), st);
+    if (storage == 3 && !(given_scale > 0.0f)) k_brick_maxabs<<<blocks, 256, 0, st>>>(a, d_tmp);
+    k_brick_scale<<<1, 1, 0, st>>>(d_tmp, given_scale, storage == 3, d_scale);
+    switch (storage) {
+        case 0: k_brick_convert<float><<<blocks, 256, 0, st>>>(a, d_scale, (float*)dst); break;
+        case 1: k_brick_convert<__half><<<blocks, 256, 0, st>>>(a, d_scale, (__half*)dst); break;
+        case 2: k_brick_convert<__nv_bfloat16><<<blocks, 256, 0, st>>>(a, d_scale, (__nv_bfloat16*)dst); break;
+        default: k_brick_convert<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>(a, d_scale, (__nv_fp8_e4m3*)dst); break;
+    }
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// cameras and culling (work list)
+// ===========================================================================
+
+__global__ void k_cam_setup(const CamIn* cams, int n, float3 origin, float inv_spacing, CamBasis* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    CamIn c = cams[i];
+    float f[3] = {c.center[0] - c.eye[0], c.center[1] - c.eye[1], c.center[2] - c.eye[2]};
+    float fn = 1.0f / sqrtf(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (int a = 0; a < 3; ++a) f[a] *= fn;
+    float r[3] = {f[1] * c.up[2] - f[2] * c.up[1], f[2] * c.up[0] - f[0] * c.up[2], f[0] * c.up[1] - f[1] * c.up[0]};
+    float rn = 1.0f / sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (int a = 0; a < 3; ++a) r[a] *= rn;
+    float u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+    CamBasis b;
+    const float og[3] = {origin.x, origin.y, origin.z};
+    for (int a = 0; a < 3; ++a) {
+        b.o[a] = (c.eye[a] - og[a]) * inv_spacing;
+        b.f[a] = f[a];
+        b.r[a] = r[a];
+        b.u[a] = u[a];
+    }
+    b.th = tanf(c.fovy_deg * 0.008726646259971648f);   // pi / 360
+    b.pad = 0.0f;
+    out[i] = b;
+}
+
+// Screen tile rectangle [x0, x1] x [y0, y1] (inclusive) that may see brick b
+// from camera c: the bounding box of the projected corners of its owned
+// region, one pixel wider on each side.  Corners at or behind the eye plane
+// make the rectangle the whole screen; a brick wholly behind is culled.
+__global__ void k_cull_rects(FrameParams P, const CamBasis* cams, const BrickDev* bricks, int4* rects) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.ncam * P.nbricks) return;
+    int c = i / P.nbricks, k = i % P.nbricks;
+    CamBasis cb = cams[c];
+    BrickDev b = bricks[k];
+    float aspect = (float)P.W / (float)P.H;
+    float xmin = 1e30f, xmax = -1e30f, ymin = 1e30f, ymax = -1e30f;
+    int behind = 0, front = 0;
+    for (int m = 0; m < 8; ++m) {
+        float p[3] = {(m & 1) ? b.r1[0] : b.r0[0], (m & 2) ? b.r1[1] : b.r0[1], (m & 4) ? b.r1[2] : b.r0[2]};
+        float v[3] = {p[0] - cb.o[0], p[1] - cb.o[1], p[2] - cb.o[2]};
+        float z = v[0] * cb.f[0] + v[1] * cb.f[1] + v[2] * cb.f[2];
+        float len = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (z <= 1e-3f * len) {
+            ++behind;
+            continue;
+        }
+        ++front;
+        float x = (v[0] * cb.r[0] + v[1] * cb.r[1] + v[2] * cb.r[2]) / (z * cb.th * aspect);
+        float y = (v[0] * cb.u[0] + v[1] * cb.u[1] + v[2] * cb.u[2]) / (z * cb.th);
+        float px = (x + 1.0f) * 0.5f * P.W - 0.5f, py = (y + 1.0f) * 0.5f * P.H - 0.5f;
+        xmin = fminf(xmin, px);
+        xmax = fmaxf(xmax, px);
+        ymin = fminf(ymin, py);
+        ymax = fmaxf(ymax, py);
+    }
+    int4 r;
+    if (front == 0) {
+        r = make_int4(1, 1, 0, 0);   // empty
+    } else if (behind > 0) {
+        r = make_int4(0, 0, P.ntx - 1, P.nty - 1);
+    } else {
+        xmin -= 1.0f;
+        ymin -= 1.0f;
+        xmax += 1.0f;
+        ymax += 1.0f;
+        if (xmax < 0.0f || ymax < 0.0f || xmin > (float)(P.W - 1) || ymin > (float)(P.H - 1)) {
+            r = make_int4(1, 1, 0, 0);
+        } else {
+            int x0 = max(0, (int)floorf(fmaxf(xmin, 0.0f)) / P.tw), x1 = min(P.ntx - 1, (int)floorf(fminf(xmax, (float)P.W)) / P.tw);
+            int y0 = max(0, (int)floorf(fmaxf(ymin, 0.0f)) / P.th), y1 = min(P.nty - 1, (int)floorf(fminf(ymax, (float)P.H)) / P.th);
+            r = make_int4(x0, y0, x1, y1);
+        }
+    }
+    rects[i] = r;
+}
+
+__device__ __forceinline__ bool rect_has(int4 r, int tx, int ty) {
+    return tx >= r.x && tx <= r.z && ty >= r.y && ty <= r.w;
+}
+
+__global__ void k_cull_count(FrameParams P, const int4* rects, int* tile_count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int ntiles = P.ntx * P.nty;
+    if (i >= P.ncam * ntiles) return;
+    int c = i / ntiles, t = i % ntiles, tx = t % P.ntx, ty = t / P.ntx;
+    int n = 0;
+    for (int k = 0; k < P.nbricks; ++k) n += rect_has(rects[c * P.nbricks + k], tx, ty);
+    tile_count[i] = n;
+}
+
+// Exclusive scan of n ints by one block; writes the total to *total.
+__global__ void k_scan(const int* in, int* out, int n, unsigned long long* total, unsigned int* max_out) {
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    __shared__ unsigned int mx;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        mx = 0;
+    }
+    __syncthreads();
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int base = 0; base < n; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = i < n ? in[i] : 0;
+        if (v > 0) atomicMax(&mx, (unsigned)v);
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < nw) warp_sums[lane] = w;
+        }
+        __syncthreads();
+        int excl = x - v + (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
+        if (i < n) out[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *total = (unsigned long long)carry;
+        if (max_out) *max_out = mx;
+    }
+}
+
+__global__ void k_cull_fill(FrameParams P, const int4* rects, const int* tile_first, const int* tile_count,
+                            Item* items, int cap, unsigned int* err) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int ntiles = P.ntx * P.nty;
+    if (i >= P.ncam * ntiles) return;
+    int c = i / ntiles, t = i % ntiles, tx = t % P.ntx, ty = t / P.ntx;
+    int f = tile_first[i];
+    if (f + tile_count[i] > cap) {
+        atomicOr(err, ERR_ITEM_OVERFLOW);
+        return;
+    }
+    for (int k = 0; k < P.nbricks; ++k)
+        if (rect_has(rects[c * P.nbricks + k], tx, ty)) {
+            Item it;
+            it.cam = c;
+            it.tile = t;
+            it.brick = k;
+            it.pad = 0;
+            items[f++] = it;
+        }
+}
+
+cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 origin, float inv_spacing,
+                        CamBasis* d_cams, const BrickDev* d_bricks, int4* d_rects, int* d_tile_count,
+                        int* d_tile_first, Item* d_items, int cap, Counters* d_counters, bool fill,
+                        cudaStream_t st) {
+    k_cam_setup<<<(P.ncam + 63) / 64, 64, 0, st>>>(d_cam_in, P.ncam, origin, inv_spacing, d_cams);
+    int ncb = P.ncam * P.nbricks;
+    k_cull_rects<<<(ncb + 127) / 128, 128, 0, st>>>(P, d_cams, d_bricks, d_rects);
+    int nct = P.ncam * P.ntx * P.nty;
+    k_cull_count<<<(nct + 127) / 128, 128, 0, st>>>(P, d_rects, d_tile_count);
+    k_scan<<<1, 1024, 0, st>>>(d_tile_count, d_tile_first, nct, &d_counters->n_items, &d_counters->max_frag);
+    if (fill)
+        k_cull_fill<<<(nct + 127) / 128, 128, 0, st>>>(P, d_rects, d_tile_first, d_tile_count, d_items, cap,
+                                                       &d_counters->err);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// brick ray-march (forward)
+// ===========================================================================
+//
+// One CTA per work item (camera, brick, tile); one thread per pixel; warps
+// cover 8 x 4 pixel blocks.  Each thread finds its ray's sample range in the
+// brick, marches it front to back and writes one fragment (premultiplied
+// RGBA, key = first sample index, or key = EMPTY).  The TF table is staged
+// in shared memory.
+
+struct MarchState {
+    int j0, j1;        // sample range [j0, j1)
+    float te;          // t_enter of the ray in the volume
+    float q0[3];       // brick-local node position of sample j0
+    float st[3];       // brick-local step per sample
+};
+
+// Ray of pixel (px, py) against brick b: its sample range and the local
+// frame.  Returns false when the brick holds no sample of the ray.
+__device__ __forceinline__ bool brick_samples(const FrameParams& P, const CamBasis& cam, const BrickDev& b,
+                                              float inv_spacing, int px, int py, MarchState& m) {
+    float o[3], d[3];
+    pixel_ray(cam, P, inv_spacing, px, py, o, d);
+    float te, tx;
+    if (!volume_interval(P, o, d, te, tx)) return false;
+    float t0 = te, t1 = tx;
+    ray_box(o, d, b.r0, b.r1, b.closed, t0, t1);
+    if (!(t0 < t1)) return false;
+    m.j0 = first_sample_at(t0, te, P);
+    m.j1 = first_sample_at(t1, te, P);
+    if (m.j0 >= m.j1) return false;
+    m.te = te;
+    float tj = te + ((float)m.j0 + 0.5f) * P.dt;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float ol = o[a] - (float)b.s_lo[a];
+        m.q0[a] = fmaf(tj, d[a], ol);
+        m.st[a] = P.dt * d[a];
+    }
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, float inv_spacing, const CamBasis* cams,
+                                                   const BrickDev* bricks, const float* scales, const Item* items,
+                                                   const float4* tf, float4* frag_rgba, int* frag_key,
+                                                   Counters* counters) {
+    extern __shared__ float4 s_tf[];
+    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
+    __syncthreads();
+
+    const Item it = items[blockIdx.x];
+    if (!item_ok(it, P)) return;
+    const BrickDev b = bricks[it.brick];
+    const CamBasis cam = cams[it.cam];
+    const float scale = scales[b.scale_idx];
+    const T* data = (const T*)b.data;
+    int lx, ly;
+    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
+    long long slot = (long long)blockIdx.x * P.tp + threadIdx.x;
+    unsigned long long nsamp = 0;
+    if (px < P.W && py < P.H) {
+        MarchState m;
+        if (brick_samples(P, cam, b, inv_spacing, px, py, m)) {
+            float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.0f;
+            int n = m.j1 - m.j0;
+            int k = 0;
+            for (; k < n; ++k) {
+                float fk = (float)k;
+                int base;
+                float fx, fy, fz;
+                float s = trilinear<T>(b, data, scale, fmaf(fk, m.st[0], m.q0[0]), fmaf(fk, m.st[1], m.q0[1]),
+                                       fmaf(fk, m.st[2], m.q0[2]), base, fx, fy, fz);
+                TFSample c = tf_lookup(s_tf, P, s);
+                float al = sample_alpha(P, c.v.w);
+                float ta = Tr * al;
+                C0 = fmaf(ta, c.v.x, C0);
+                C1 = fmaf(ta, c.v.y, C1);
+                C2 = fmaf(ta, c.v.z, C2);
+                Tr = Tr * (1.0f - al);
+                if (P.ert_on && 1.0f - Tr > P.ert) {
+                    ++k;
+                    break;
+                }
+            }
+            nsamp = (unsigned long long)k;
+            frag_rgba[slot] = make_float4(C0, C1, C2, 1.0f - Tr);
+            frag_key[slot] = m.j0;
+        } else {
+            frag_key[slot] = KEY_EMPTY;
+        }
+    }
+    nsamp = warp_sum_u64(nsamp);
+    if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
+}
+
+cudaError_t launch_march_fwd(int dtype, const FrameParams& P, float inv_spacing, const CamBasis* cams,
+                             const BrickDev* bricks, const float* scales, const Item* items, int n_items,
+                             const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
+                             cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    size_t smem = sizeof(float4) * P.ntf;
+    if (smem > 48 * 1024) {
+        cudaFuncSetAttribute(k_march_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_march_fwd<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_march_fwd<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_march_fwd<__nv_fp8_e4m3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    switch (dtype) {
+        case 0: k_march_fwd<float><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, counters); break;
+        case 1: k_march_fwd<__half><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, counters); break;
+        case 2: k_march_fwd<__nv_bfloat16><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, counters); break;
+        default: k_march_fwd<__nv_fp8_e4m3><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, counters); break;
+    }
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// sort-last compositor (forward)
+// ===========================================================================
+
+// The pixel's non-empty fragments in ascending key order.  Up to KR are kept
+// sorted in registers (insertion with compile-time indices); `n` may exceed
+// KR, in which case the caller falls back to selection from memory.
+struct SortedFrags {
+    int key[KR];
+    int slot[KR];
+    int n;
+};
+
+__device__ __forceinline__ void collect_sorted(const int* frag_key, long long first, int cnt, int tp, int t,
+                                               SortedFrags& s) {
+#pragma unroll
+    for (int i = 0; i < KR; ++i) {
+        s.key[i] = KEY_EMPTY;
+        s.slot[i] = -1;
+    }
+    s.n = 0;
+    for (int q = 0; q < cnt; ++q) {
+        int k = frag_key[(first + q) * tp + t];
+        if (k == KEY_EMPTY) continue;
+        int ck = k, cs = q;
+#pragma unroll
+        for (int i = 0; i < KR; ++i) {
+            if (ck < s.key[i]) {
+                int tk = s.key[i], ts = s.slot[i];
+                s.key[i] = ck;
+                s.slot[i] = cs;
+                ck = tk;
+                cs = ts;
+            }
+        }
+        ++s.n;
+    }
+}
+
+// Fallback for more than KR fragments: the slot of the smallest key > last.
+__device__ __forceinline__ int next_slot(const int* frag_key, long long first, int cnt, int tp, int t, int last) {
+    int best = KEY_EMPTY, bs = -1;
+    for (int q = 0; q < cnt; ++q) {
+        int k = frag_key[(first + q) * tp + t];
+        if (k != KEY_EMPTY && k > last && k < best) {
+            best = k;
+            bs = q;
+        }
+    }
+    return bs;
+}
+
+__device__ __forceinline__ float pixel_t_enter(const FrameParams& P, const CamBasis& cam, float inv_spacing, int px,
+                                               int py) {
+    float o[3], d[3], te, tx;
+    pixel_ray(cam, P, inv_spacing, px, py, o, d);
+    volume_interval(P, o, d, te, tx);
+    return te;
+}
+
+__global__ void __launch_bounds__(256) k_composite_fwd(FrameParams P, float inv_spacing, const CamBasis* cams,
+                                                       const int* tile_first, const int* tile_count,
+                                                       const Item* items, const float4* frag_rgba,
+                                                       const int* frag_key, float4* out_rgba, float* out_depth,
+                                                       unsigned char* order) {
+    int ct = blockIdx.x;
+    int ntiles = P.ntx * P.nty;
+    int c = ct / ntiles, tile = ct % ntiles;
+    int lx, ly;
+    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    int px = (tile % P.ntx) * P.tw + lx, py = (tile / P.ntx) * P.th + ly;
+    if (px >= P.W || py >= P.H) return;
+    long long first = tile_first[ct];
+    int cnt = tile_count[ct];
+    if (first < 0 || first + cnt > P.items_cap) cnt = 0;    // list overflowed: error bit already set
+    int t = threadIdx.x;
+    SortedFrags s;
+    collect_sorted(frag_key, first, cnt, P.tp, t, s);
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+    int depth_key = KEY_EMPTY;
+    long long pix = ((long long)c * P.H + py) * P.W + px;
+    unsigned char* ord = order ? order + pix * P.order_stride : nullptr;
+    if (s.n <= KR) {
+#pragma unroll
+        for (int i = 0; i < KR; ++i) {
+            if (i < s.n) {
+                float4 f = frag_rgba[(first + s.slot[i]) * P.tp + t];
+                float w = 1.0f - A;
+                C0 = fmaf(w, f.x, C0);
+                C1 = fmaf(w, f.y, C1);
+                C2 = fmaf(w, f.z, C2);
+                A = fmaf(w, f.w, A);
+                if (f.w > 0.0f && depth_key == KEY_EMPTY) depth_key = s.key[i];
+                if (ord) ord[i] = (unsigned char)items[first + s.slot[i]].brick;
+            }
+        }
+    } else {
+        int last = -1;
+        for (int i = 0; i < s.n; ++i) {
+            int q = next_slot(frag_key, first, cnt, P.tp, t, last);
+            int k = frag_key[(first + q) * P.tp + t];
+            last = k;
+            float4 f = frag_rgba[(first + q) * P.tp + t];
+            float w = 1.0f - A;
+            C0 = fmaf(w, f.x, C0);
+            C1 = fmaf(w, f.y, C1);
+            C2 = fmaf(w, f.z, C2);
+            A = fmaf(w, f.w, A);
+            if (f.w > 0.0f && depth_key == KEY_EMPTY) depth_key = k;
+            if (ord && i < P.order_stride) ord[i] = (unsigned char)items[first + q].brick;
+        }
+    }
+    if (ord)
+        for (int i = s.n; i < P.order_stride; ++i) ord[i] = 0xFF;
+    out_rgba[pix] = make_float4(C0, C1, C2, A);
+    float depth = __int_as_float(0x7f800000);
+    if (depth_key != KEY_EMPTY) {
+        float te = pixel_t_enter(P, cams[c], inv_spacing, px, py);
+        depth = te + ((float)depth_key + 0.5f) * P.dt;
+    }
+    out_depth[pix] = depth;
+}
+
+cudaError_t launch_composite_fwd(const FrameParams& P, float inv_spacing, const CamBasis* cams,
+                                 const int* tile_first, const int* tile_count, const Item* items,
+                                 const float4* frag_rgba, const int* frag_key, float4* out_rgba, float* out_depth,
+                                 unsigned char* order, cudaStream_t st) {
+    int nct = P.ncam * P.ntx * P.nty;
+    k_composite_fwd<<<nct, P.tp, 0, st>>>(P, inv_spacing, cams, tile_first, tile_count, items, frag_rgba, frag_key,
+                                          out_rgba, out_depth, order);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// compositor adjoint
+// ===========================================================================
+//
+// For the ordered fragments k = 0..n-1 of a pixel with loss gradient g:
+//   T_k   = prod_{m<k} (1 - A_m)                       (transmittance in front)
+//   Cb_k, Ab_k = composite of the fragments behind k
+//   dL/dC_k = T_k g_rgb
+//   dL/dA_k = T_k (g_a (1 - Ab_k) - g_rgb . Cb_k)
+__global__ void __launch_bounds__(256) k_composite_bwd(FrameParams P, const int* tile_first, const int* tile_count,
+                                                       const float4* frag_rgba, const int* frag_key,
+                                                       const float4* grad_img, float4* frag_grad) {
+    int ct = blockIdx.x;
+    int ntiles = P.ntx * P.nty;
+    int c = ct / ntiles, tile = ct % ntiles;
+    int lx, ly;
+    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    int px = (tile % P.ntx) * P.tw + lx, py = (tile / P.ntx) * P.th + ly;
+    if (px >= P.W || py >= P.H) return;
+    long long first = tile_first[ct];
+    int cnt = tile_count[ct];
+    if (first < 0 || first + cnt > P.items_cap) cnt = 0;
+    int t = threadIdx.x;
+    long long pix = ((long long)c * P.H + py) * P.W + px;
+    float4 g = grad_img[pix];
+    SortedFrags s;
+    collect_sorted(frag_key, first, cnt, P.tp, t, s);
+    if (s.n <= KR) {
+        float Tf[KR];
+        float T = 1.0f;
+#pragma unroll
+        for (int i = 0; i < KR; ++i) {
+            Tf[i] = T;
+            if (i < s.n) T *= 1.0f - frag_rgba[(first + s.slot[i]) * P.tp + t].w;
+        }
+        float Cb0 = 0.f, Cb1 = 0.f, Cb2 = 0.f, Ab = 0.f;
+#pragma unroll
+        for (int i = KR - 1; i >= 0; --i) {
+            if (i < s.n) {
+                long long o = (first + s.slot[i]) * P.tp + t;
+                float4 f = frag_rgba[o];
+                float gA = Tf[i] * (g.w * (1.0f - Ab) - (g.x * Cb0 + g.y * Cb1 + g.z * Cb2));
+                frag_grad[o] = make_float4(Tf[i] * g.x, Tf[i] * g.y, Tf[i] * g.z, gA);
+                float w = 1.0f - f.w;
+                Cb0 = fmaf(w, Cb0, f.x);
+                Cb1 = fmaf(w, Cb1, f.y);
+                Cb2 = fmaf(w, Cb2, f.z);
+                Ab = fmaf(w, Ab, f.w);
+            }
+        }
+    } else {
+        // more than KR fragments: walk the order from memory twice
+        float T = 1.0f;
+        int last = -1;
+        for (int i = 0; i < s.n; ++i) {          // front to back: store T_k in the grad slot
+            int q = next_slot(frag_key, first, cnt, P.tp, t, last);
+            long long o = (first + q) * P.tp + t;
+            last = frag_key[o];
+            frag_grad[o] = make_float4(T, 0.f, 0.f, 0.f);
+            T *= 1.0f - frag_rgba[o].w;
+        }
+        float Cb0 = 0.f, Cb1 = 0.f, Cb2 = 0.f, Ab = 0.f;
+        int prev = KEY_EMPTY;
+        for (int i = 0; i < s.n; ++i) {          // back to front
+            int best = -1, bq = -1;
+            for (int q = 0; q < cnt; ++q) {
+                int k = frag_key[(first + q) * P.tp + t];
+                if (k != KEY_EMPTY && k < prev && k > best) {
+                    best = k;
+                    bq = q;
+                }
+            }
+            long long o = (first + bq) * P.tp + t;
+            prev = best;
+            float Tk = frag_grad[o].x;
+            float4 f = frag_rgba[o];
+            float gA = Tk * (g.w * (1.0f - Ab) - (g.x * Cb0 + g.y * Cb1 + g.z * Cb2));
+            frag_grad[o] = make_float4(Tk * g.x, Tk * g.y, Tk * g.z, gA);
+            float w = 1.0f - f.w;
+            Cb0 = fmaf(w, Cb0, f.x);
+            Cb1 = fmaf(w, Cb1, f.y);
+            Cb2 = fmaf(w, Cb2, f.z);
+            Ab = fmaf(w, Ab, f.w);
+        }
+    }
+}
+
+cudaError_t launch_composite_bwd(const FrameParams& P, const int* tile_first, const int* tile_count,
+                                 const float4* frag_rgba, const int* frag_key, const float4* grad_img,
+                                 float4* frag_grad, cudaStream_t st) {
+    int nct = P.ncam * P.ntx * P.nty;
+    k_composite_bwd<<<nct, P.tp, 0, st>>>(P, tile_first, tile_count, frag_rgba, frag_key, grad_img, frag_grad);
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// ray-march adjoint
+// ===========================================================================
+//
+// Replays the fragment's samples front to back with the forward's exact
+// arithmetic (same early-termination decisions), recomputing transmittance
+// instead of storing it.  For fragment (C, A) with gradient (gC, gA) and
+// sample i (opacity a_i, colour c_i, transmittance T_i):
+//   S_i       = C - C_{<=i}                  (what the samples behind add)
+//   dC/dc_i   = T_i a_i
+//   dC/da_i   = T_i c_i - S_i / (1 - a_i)
+//   dA/da_i   = (1 - A) / (1 - a_i)
+//   da_i/dsig = dt (1 - a_i),  sigma = sigma_max * alpha_TF
+// then the TF lerp (weights 1-w, w on entries i0, i0+1), ds from the lerp
+// slope, and the eight trilinear weights scatter into the global field.
+// TF gradients go to a shared-memory table per CTA (FP32), flushed to the
+// global FP64 table with one atomic per touched entry.
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spacing, const CamBasis* cams,
+                                                   const BrickDev* bricks, const float* scales, const Item* items,
+                                                   const float4* tf, const float4* frag_rgba, const int* frag_key,
+                                                   const float4* frag_grad, double* dtf, float* dvol,
+                                                   Counters* counters) {
+    extern __shared__ float4 s_mem[];
+    float4* s_tf = s_mem;
+    float* s_g = (float*)(s_mem + P.ntf);
+    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) {
+        s_tf[i] = tf[i];
+        s_g[4 * i + 0] = 0.f;
+        s_g[4 * i + 1] = 0.f;
+        s_g[4 * i + 2] = 0.f;
+        s_g[4 * i + 3] = 0.f;
+    }
+    __syncthreads();
+
+    Item it = items[blockIdx.x];
+    const bool valid = item_ok(it, P);
+    if (!valid) it.cam = it.brick = it.tile = 0;
+    const BrickDev b = bricks[it.brick];
+    const CamBasis cam = cams[it.cam];
+    const float scale = scales[b.scale_idx];
+    const T* data = (const T*)b.data;
+    int lx, ly;
+    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
+    long long slot = (long long)blockIdx.x * P.tp + threadIdx.x;
+    unsigned long long nsamp = 0;
+    const float gscale = Storage<T>::unit_scale ? 1.0f : scale;
+    if (valid && px < P.W && py < P.H && frag_key[slot] != KEY_EMPTY) {
+        MarchState m;
+        float4 F = frag_rgba[slot];
+        float4 G = frag_grad[slot];
+        if (brick_samples(P, cam, b, inv_spacing, px, py, m) && (G.x != 0.f || G.y != 0.f || G.z != 0.f || G.w != 0.f)) {
+            float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.0f;
+            float Tend = 1.0f - F.w;
+            int n = m.j1 - m.j0;
+            for (int k = 0; k < n; ++k) {
+                float fk = (float)k;
+                int base;
+                float fx, fy, fz;
+                float s = trilinear<T>(b, data, scale, fmaf(fk, m.st[0], m.q0[0]), fmaf(fk, m.st[1], m.q0[1]),
+                                       fmaf(fk, m.st[2], m.q0[2]), base, fx, fy, fz);
+                TFSample c = tf_lookup(s_tf, P, s);
+                float al = sample_alpha(P, c.v.w);
+                float ta = Tr * al;
+                float n0 = fmaf(ta, c.v.x, C0), n1 = fmaf(ta, c.v.y, C1), n2 = fmaf(ta, c.v.z, C2);
+                float om = 1.0f - al;
+                float inv1ma = om > 0.0f ? 1.0f / om : 0.0f;
+                float S0 = F.x - n0, S1 = F.y - n1, S2 = F.z - n2;
+                float gal = G.x * (Tr * c.v.x - S0 * inv1ma) + G.y * (Tr * c.v.y - S1 * inv1ma) +
+                            G.z * (Tr * c.v.z - S2 * inv1ma) + G.w * Tend * inv1ma;
+                float g_r = G.x * ta, g_g = G.y * ta, g_b = G.z * ta;
+                float g_a = gal * P.sigma_max * P.dt * (1.0f - al);
+                float w1 = c.w, w0 = 1.0f - c.w;
+                float* e0 = s_g + 4 * c.i0;
+                atomicAdd(e0 + 0, w0 * g_r);
+                atomicAdd(e0 + 1, w0 * g_g);
+                atomicAdd(e0 + 2, w0 * g_b);
+                atomicAdd(e0 + 3, w0 * g_a);
+                atomicAdd(e0 + 4, w1 * g_r);
+                atomicAdd(e0 + 5, w1 * g_g);
+                atomicAdd(e0 + 6, w1 * g_b);
+                atomicAdd(e0 + 7, w1 * g_a);
+                if (dvol && c.duds != 0.0f) {
+                    float4 ta0 = s_tf[c.i0], ta1 = s_tf[c.i0 + 1];
+                    float gs = (g_r * (ta1.x - ta0.x) + g_g * (ta1.y - ta0.y) + g_b * (ta1.z - ta0.z) +
+                                g_a * (ta1.w - ta0.w)) * c.duds * gscale;
+                    if (gs != 0.0f) {
+                        // brick-local cell -> global node index
+                        int ix = base % b.sx, iz = base / b.sxy, iy = (base - iz * b.sxy) / b.sx;
+                        long long gx = ix + b.s_lo[0], gy = iy + b.s_lo[1], gz = iz + b.s_lo[2];
+                        long long sy = P.dims[0], sz = (long long)P.dims[0] * P.dims[1];
+                        float* v = dvol + gz * sz + gy * sy + gx;
+                        float ax = 1.0f - fx, ay = 1.0f - fy, az = 1.0f - fz;
+                        atomicAdd(v, gs * ax * ay * az);
+                        atomicAdd(v + 1, gs * fx * ay * az);
+                        atomicAdd(v + sy, gs * ax * fy * az);
+                        atomicAdd(v + sy + 1, gs * fx * fy * az);
+                        atomicAdd(v + sz, gs * ax * ay * fz);
+                        atomicAdd(v + sz + 1, gs * fx * ay * fz);
+                        atomicAdd(v + sz + sy, gs * ax * fy * fz);
+                        atomicAdd(v + sz + sy + 1, gs * fx * fy * fz);
+                    }
+                }
+                C0 = n0;
+                C1 = n1;
+                C2 = n2;
+                Tr = Tr * (1.0f - al);
+                ++nsamp;
+                if (P.ert_on && 1.0f - Tr > P.ert) break;
+            }
+        }
+    }
+    nsamp = warp_sum_u64(nsamp);
+    if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) {
+        float v = s_g[i];
+        if (v != 0.0f) atomicAdd(dtf + i, (double)v);
+    }
+}
+
+cudaError_t launch_march_bwd(int dtype, const FrameParams& P, float inv_spacing, const CamBasis* cams,
+                             const BrickDev* bricks, const float* scales, const Item* items, int n_items,
+                             const float4* tf, const float4* frag_rgba, const int* frag_key,
+                             const float4* frag_grad, double* dtf, float* dvol, Counters* counters,
+                             cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    size_t smem = sizeof(float4) * P.ntf * 2;
+    if (smem > 48 * 1024) {
+        cudaFuncSetAttribute(k_march_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_march_bwd<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_march_bwd<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_march_bwd<__nv_fp8_e4m3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    switch (dtype) {
+        case 0: k_march_bwd<float><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol, counters); break;
+        case 1: k_march_bwd<__half><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol, counters); break;
+        case 2: k_march_bwd<__nv_bfloat16><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol, counters); break;
+        default: k_march_bwd<__nv_fp8_e4m3><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol, counters); break;
+    }
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// debug: scatter one rank's fragments into a full frame
+// ===========================================================================
+
+__global__ void k_fill_key(int* key, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) key[i] = KEY_EMPTY;
+}
+
+__global__ void k_read_frags(FrameParams P, const Item* items, int n_items, int cam, int rank,
+                             const float4* frag_rgba, const int* frag_key, float4* out_rgba, int* out_key) {
+    int i = blockIdx.x;
+    if (i >= n_items) return;
+    Item it = items[i];
+    if (!item_ok(it, P) || it.cam != cam || it.brick != rank) return;
+    int lx, ly;
+    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
+    if (px >= P.W || py >= P.H) return;
+    long long slot = (long long)i * P.tp + threadIdx.x;
+    long long pix = (long long)py * P.W + px;
+    int k = frag_key[slot];
+    out_key[pix] = k;
+    out_rgba[pix] = k == KEY_EMPTY ? make_float4(0.f, 0.f, 0.f, 0.f) : frag_rgba[slot];
+}
+
+cudaError_t launch_read_frags(const FrameParams& P, const Item* items, int n_items, int cam, int rank,
+                              const float4* frag_rgba, const int* frag_key, float4* out_rgba, int* out_key,
+                              cudaStream_t st) {
+    long long n = (long long)P.W * P.H;
+    cudaMemsetAsync(out_rgba, 0, sizeof(float4) * n, st);
+    k_fill_key<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out_key, n);
+    if (n_items) k_read_frags<<<n_items, P.tp, 0, st>>>(P, items, n_items, cam, rank, frag_rgba, frag_key, out_rgba, out_key);
+    return cudaGetLastError();
+}
+
+}  // namespace dpv

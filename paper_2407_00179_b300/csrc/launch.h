@@ -1,0 +1,57 @@
+// launch.h -- host-side launchers of the kernels in kernels.cu, used by the
+// C-ABI implementation in device.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dpv_internal.cuh"
+
+namespace dpv {
+
+// Raw camera as given by the caller (mirrors dpv_camera).
+struct CamIn {
+    float eye[3], center[3], up[3];
+    float fovy_deg;
+};
+
+// Source box of a brick commit: `src` (device) holds nodes [d_lo, d_lo + d_n)
+// x fastest; the brick stores nodes [s_lo, s_lo + s_n).
+struct CommitArgs {
+    const void* src;
+    int d_lo[3], d_n[3];
+    int s_lo[3], s_n[3];
+};
+
+cudaError_t launch_commit(const CommitArgs& a, int storage, int src_is_f32, float given_scale, unsigned int* d_tmp,
+                          float* d_scale, void* dst, cudaStream_t st);
+
+cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 origin, float inv_spacing,
+                        CamBasis* d_cams, const BrickDev* d_bricks, int4* d_rects, int* d_tile_count,
+                        int* d_tile_first, Item* d_items, int cap, Counters* d_counters, bool fill,
+                        cudaStream_t st);
+
+cudaError_t launch_march_fwd(int dtype, const FrameParams& P, float inv_spacing, const CamBasis* cams,
+                             const BrickDev* bricks, const float* scales, const Item* items, int n_items,
+                             const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
+                             cudaStream_t st);
+
+cudaError_t launch_composite_fwd(const FrameParams& P, float inv_spacing, const CamBasis* cams,
+                                 const int* tile_first, const int* tile_count, const Item* items,
+                                 const float4* frag_rgba, const int* frag_key, float4* out_rgba, float* out_depth,
+                                 unsigned char* order, cudaStream_t st);
+
+cudaError_t launch_composite_bwd(const FrameParams& P, const int* tile_first, const int* tile_count,
+                                 const float4* frag_rgba, const int* frag_key, const float4* grad_img,
+                                 float4* frag_grad, cudaStream_t st);
+
+cudaError_t launch_march_bwd(int dtype, const FrameParams& P, float inv_spacing, const CamBasis* cams,
+                             const BrickDev* bricks, const float* scales, const Item* items, int n_items,
+                             const float4* tf, const float4* frag_rgba, const int* frag_key,
+                             const float4* frag_grad, double* dtf, float* dvol, Counters* counters,
+                             cudaStream_t st);
+
+cudaError_t launch_read_frags(const FrameParams& P, const Item* items, int n_items, int cam, int rank,
+                              const float4* frag_rgba, const int* frag_key, float4* out_rgba, int* out_key,
+                              cudaStream_t st);
+
+}  // namespace dpv

@@ -1,0 +1,69 @@
+"""Seeded scenes used by the parity tests: the same inputs go to the CUDA
+path (through the C ABI) and to the FP64 oracle."""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List
+
+import numpy as np
+import torch
+
+from paper_2407_00179_b300 import inputs
+
+FLAG = {"hit": 1, "exit": 2, "owner": 4, "ert": 8}
+
+
+@dataclass
+class Scene:
+    field: np.ndarray            # (nz, ny, nx) float32
+    part: inputs.Partition
+    tf: np.ndarray               # (n, 4) float32
+    cams: List[inputs.Camera]
+    width: int
+    height: int
+    step: float = 0.5
+    sigma_max: float = 8.0
+    ert: float = 0.0
+    storage: str = "f32"
+    tile: tuple = (0, 0)
+
+    @property
+    def dims(self):
+        return (self.field.shape[2], self.field.shape[1], self.field.shape[0])
+
+
+def small(seed=0, width=256, height=256, storage="f32", ert=0.0, tile=(0, 0)) -> Scene:
+    """64^3 sum of 8 blobs, 2x1x1 bricks, one camera from (1, 0.7, 0.5)."""
+    dims = (64, 64, 64)
+    f = inputs.field_small(seed, dims).numpy()
+    return Scene(f, inputs.regular_partition(dims, (2, 1, 1)), inputs.make_tf(1234),
+                 [inputs.camera_from_direction(dims, (1.0, 0.7, 0.5))], width, height, storage=storage, ert=ert,
+                 tile=tile)
+
+
+def make(dims, splits=None, kd=None, nblobs=8, seed=0, cams=None, width=64, height=48, **kw) -> Scene:
+    f = inputs.blob_field(dims, inputs.blob_params(nblobs, dims, seed)).numpy()
+    part = inputs.kd_partition(dims, kd, seed=seed) if kd else inputs.regular_partition(dims, splits or (1, 1, 1))
+    cams = cams if cams is not None else [inputs.camera_from_direction(dims, (1.0, 0.7, 0.5))]
+    return Scene(f, part, inputs.make_tf(1234), cams, width, height, **kw)
+
+
+def gpu_device(sc: Scene, order=True):
+    from paper_2407_00179_b300 import dpv
+    dev = dpv.Device(sc.part.num_ranks)
+    dev.set_geometry(sc.dims)
+    fld = torch.from_numpy(sc.field).cuda()
+    dev.commit_partition(fld, sc.part, sc.storage)
+    dev.set_tf(torch.from_numpy(sc.tf).cuda())
+    dev.set_cameras(sc.cams)
+    dev.set_frame(sc.width, sc.height, step_voxels=sc.step, sigma_max=sc.sigma_max, ert=sc.ert, tile=sc.tile,
+                  order=order)
+    return dev
+
+
+def oracle_bricks(orc, sc: Scene):
+    return orc.make_bricks(sc.field, sc.part, orc.DTYPE_NAMES[sc.storage])
+
+
+def oracle_frame(orc, sc: Scene):
+    return orc.Frame(sc.width, sc.height, step_voxels=sc.step, sigma_max=sc.sigma_max, ert=sc.ert)

@@ -1,0 +1,259 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (R10):
+  * FP32 storage: 1e-5 max abs per RGBA channel against the oracle on the
+    same stored values;
+  * reduced precision: 1e-5 against the oracle on the same (dequantised)
+    stored values; the error against the original float32 field is reported;
+  * keys, orders, stored bytes: bit-exact;
+  * K = 1 composite == fragment: bit-exact.
+Pixels where FP32 may legitimately take a different discrete decision than
+FP64 are excluded and counted: a sample within 1e-2 samples of the volume's
+exit (sample count), of a brick face (ownership; only for per-brick
+quantities), or an early-termination opacity within 1e-4 of the threshold.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2407_00179_b300 import build, dpv, inputs
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    dpv.load()
+
+
+def _render(sc, order=True):
+    dev = scenes.gpu_device(sc, order=order)
+    dev.render()
+    dev.ready(True)
+    return dev
+
+
+def _gpu_image(dev, cam=0):
+    rgba, depth = dev.map_frame(cam)
+    return rgba.double().cpu().numpy().reshape(-1, 4), depth.double().cpu().numpy().reshape(-1)
+
+
+def _excluded(flags, which):
+    m = np.zeros(flags.shape, bool)
+    for w in which:
+        m |= (flags & scenes.FLAG[w]) != 0
+    return m
+
+
+def test_small_config_matches_oracle(orc):
+    sc = scenes.small()
+    dev = _render(sc)
+    img, depth = _gpu_image(dev)
+    ref = orc.render_bricks(sc.dims, scenes.oracle_bricks(orc, sc), sc.tf, sc.cams[0], scenes.oracle_frame(orc, sc))
+    full = orc.render_full(sc.field, sc.tf, sc.cams[0], scenes.oracle_frame(orc, sc))
+    ex = _excluded(ref["flags"], ["exit"])
+    assert ex.mean() < 0.01
+    err = np.abs(img - ref["rgba"])[~ex]
+    assert err.max() <= TOL, err.max()
+    assert np.abs(img - full["rgba"])[~ex].max() <= TOL
+    assert ref["rgba"][:, 3].max() > 0.3                      # a non-trivial image
+    # sample count: every non-excluded pixel evaluates exactly its samples
+    st = dev.stats()
+    assert st["error_flags"] == 0
+    n_ref = int(ref["nsamples"].sum())
+    assert abs(st["samples_forward"] - n_ref) <= int(ex.sum())
+    # depth: t of the first sample of the first non-transparent fragment
+    fin = np.isfinite(ref["depth"]) & ~ex
+    np.testing.assert_array_equal(np.isfinite(depth[~ex]), np.isfinite(ref["depth"][~ex]))
+    assert np.abs(depth[fin] - ref["depth"][fin]).max() <= 1e-5 * np.abs(ref["depth"][fin]).max()
+    dev.release()
+
+
+def test_fragments_keys_and_order_bitexact(orc):
+    sc = scenes.small(seed=3)
+    dev = _render(sc)
+    ref = orc.render_bricks(sc.dims, scenes.oracle_bricks(orc, sc), sc.tf, sc.cams[0], scenes.oracle_frame(orc, sc))
+    ex = _excluded(ref["flags"], ["exit", "owner"])
+    assert ex.mean() < 0.1
+    for k in range(sc.part.num_ranks):
+        rgba, key = dev.read_fragments(0, k)
+        key = key.cpu().numpy().reshape(-1)
+        rgba = rgba.double().cpu().numpy().reshape(-1, 4)
+        np.testing.assert_array_equal(key[~ex], ref["frag_key"][~ex, k])
+        ne = (key != dpv.KEY_EMPTY) & ~ex
+        assert np.abs(rgba[ne] - ref["frag_rgba"][ne, k]).max() <= TOL
+    order = dev.order(0).cpu().numpy().reshape(-1, sc.part.num_ranks)
+    np.testing.assert_array_equal(order[~ex], ref["order"][~ex])
+    dev.release()
+
+
+def test_single_rank_composite_is_identity():
+    sc = scenes.make((40, 33, 27), splits=(1, 1, 1), width=61, height=47)
+    dev = _render(sc)
+    rgba, key = dev.read_fragments(0, 0)
+    img, _ = dev.map_frame(0)
+    ne = key != dpv.KEY_EMPTY
+    assert bool(ne.any())
+    assert torch.equal(img[ne], rgba[ne])                          # bit-exact
+    assert torch.equal(img[~ne], torch.zeros_like(img[~ne]))
+    dev.release()
+
+
+CASES = [
+    dict(dims=(48, 40, 44), splits=(2, 2, 2)),
+    dict(dims=(48, 40, 44), splits=(3, 2, 4)),
+    dict(dims=(50, 42, 36), kd=7),
+    dict(dims=(50, 42, 36), kd=13),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("inside", [False, True])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 4), (32, 8)])
+def test_partitions_ragged(orc, case, inside, tile):
+    c = CASES[case]
+    cams = inputs.random_cameras(c["dims"], 2, seed=case, inside=inside)
+    sc = scenes.make(c["dims"], splits=c.get("splits"), kd=c.get("kd"), cams=cams, width=67, height=45, tile=tile)
+    dev = _render(sc)
+    fr = scenes.oracle_frame(orc, sc)
+    bricks = scenes.oracle_bricks(orc, sc)
+    for ci, cam in enumerate(sc.cams):
+        img, _ = _gpu_image(dev, ci)
+        ref = orc.render_bricks(sc.dims, bricks, sc.tf, cam, fr)
+        ex = _excluded(ref["flags"], ["exit"])
+        assert ex.mean() < 0.02
+        assert np.abs(img - ref["rgba"])[~ex].max() <= TOL
+        exo = _excluded(ref["flags"], ["exit", "owner"])
+        order = dev.order(ci).cpu().numpy().reshape(-1, sc.part.num_ranks)
+        np.testing.assert_array_equal(order[~exo], ref["order"][~exo])
+    assert dev.stats()["error_flags"] == 0
+    dev.release()
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16", "fp8"])
+def test_reduced_precision_storage(orc, storage):
+    sc = scenes.make((48, 40, 44), splits=(2, 2, 2), width=96, height=80, storage=storage)
+    dev = _render(sc)
+    bricks = scenes.oracle_bricks(orc, sc)
+    # brick commit: stored values and scale bit-exact
+    for k, b in enumerate(bricks):
+        stored, lo, scale = dev.read_brick(k)
+        got = stored.view(torch.uint8 if storage == "fp8" else torch.int16).cpu().numpy()
+        np.testing.assert_array_equal(got.view(b.data.dtype), b.data)
+        assert np.float32(scale) == np.float32(b.scale)
+    img, _ = _gpu_image(dev)
+    fr = scenes.oracle_frame(orc, sc)
+    ref = orc.render_bricks(sc.dims, bricks, sc.tf, sc.cams[0], fr)
+    ex = _excluded(ref["flags"], ["exit"] + (["owner"] if storage == "fp8" else []))
+    err_arith = np.abs(img - ref["rgba"])[~ex]
+    assert err_arith.max() <= TOL, err_arith.max()
+    # storage error against the original float32 field (reported)
+    f32 = orc.render_full(sc.field, sc.tf, sc.cams[0], fr)
+    err_store = np.abs(img - f32["rgba"])[~ex]
+    print("%s: arithmetic max %.2e; storage max %.2e mean %.2e" % (storage, err_arith.max(), err_store.max(),
+                                                                    err_store.mean()))
+    bound = {"f16": 2e-3, "bf16": 2e-2, "fp8": 1e-1}[storage]
+    assert err_store.max() < bound
+    dev.release()
+
+
+def test_early_termination_per_fragment(orc):
+    tf = inputs.make_tf(1234)
+    tf[:, 3] = np.maximum(tf[:, 3], 0.3)
+    sc = scenes.make((48, 40, 44), splits=(2, 2, 2), width=80, height=64, ert=0.99, sigma_max=40.0)
+    sc.tf = tf
+    dev = _render(sc)
+    img, _ = _gpu_image(dev)
+    ref = orc.render_bricks(sc.dims, scenes.oracle_bricks(orc, sc), sc.tf, sc.cams[0], scenes.oracle_frame(orc, sc))
+    ex = _excluded(ref["flags"], ["exit", "ert", "owner"])
+    assert ex.mean() < 0.2
+    assert np.abs(img - ref["rgba"])[~ex].max() <= TOL
+    # the fragments did terminate early
+    sc0 = scenes.make((48, 40, 44), splits=(2, 2, 2), width=80, height=64, sigma_max=40.0)
+    sc0.tf = tf
+    dev0 = _render(sc0)
+    assert dev.stats()["samples_forward"] < 0.9 * dev0.stats()["samples_forward"]
+    dev.release()
+    dev0.release()
+
+
+def test_forward_is_deterministic():
+    sc = scenes.make((48, 40, 44), kd=7, width=90, height=70)
+    dev = _render(sc)
+    a = dev.map_frame(0)[0].clone()
+    dev.render()
+    b = dev.map_frame(0)[0].clone()
+    assert torch.equal(a, b)
+    dev.release()
+
+
+def test_multi_camera_batch_equals_single(orc):
+    dims = (48, 40, 44)
+    cams = inputs.orbit_cameras(dims, 5, seed=2)
+    sc = scenes.make(dims, kd=9, cams=cams, width=64, height=48)
+    dev = _render(sc)
+    for ci, cam in enumerate(cams):
+        one = scenes.make(dims, kd=9, cams=[cam], width=64, height=48)
+        d1 = _render(one)
+        assert torch.equal(dev.map_frame(ci)[0], d1.map_frame(0)[0])
+        d1.release()
+    dev.release()
+
+
+def test_state_and_argument_errors():
+    sc = scenes.make((20, 18, 16), splits=(2, 1, 1), width=16, height=16)
+    dev = dpv.Device(2)
+    dev.set_geometry(sc.dims)
+    fld = torch.from_numpy(sc.field).cuda()
+    dev.set_tf(torch.from_numpy(sc.tf).cuda())
+    dev.set_cameras(sc.cams)
+    dev.set_frame(16, 16)
+    with pytest.raises(dpv.DPVError) as e:
+        dev.render()
+    assert e.value.status == 2                                       # rank 0 missing
+    dev.commit_brick(0, sc.part.lo[0], sc.part.hi[0], fld)
+    with pytest.raises(dpv.DPVError) as e:
+        dev.render()
+    assert e.value.status == 2 and "rank 1" in str(e.value)
+    dev.commit_brick(1, sc.part.lo[0], sc.part.hi[0], fld)           # overlaps rank 0
+    with pytest.raises(dpv.DPVError) as e:
+        dev.render()
+    assert e.value.status == 1
+    dev.commit_brick(1, sc.part.lo[1], sc.part.hi[1], fld)
+    dev.render()
+    with pytest.raises(dpv.DPVError) as e:
+        dev.map_frame(3)
+    assert e.value.status == 1
+    with pytest.raises(dpv.DPVError) as e:
+        dev.set_frame(10, 10, tile=(12, 4))
+    assert e.value.status == 1
+    with pytest.raises(dpv.DPVError) as e:
+        dev.commit_brick(0, (0, 0, 0), (30, 18, 16), fld)           # outside the volume
+    assert e.value.status == 1
+    dev.release()
+
+
+def test_host_data_commit_equals_device_commit():
+    sc = scenes.make((36, 30, 28), splits=(2, 1, 2), width=40, height=32)
+    d1 = _render(sc)
+    d2 = dpv.Device(sc.part.num_ranks)
+    d2.set_geometry(sc.dims)
+    for k in range(sc.part.num_ranks):
+        # each rank hands over only a box around its own nodes, from host memory
+        lo = np.maximum(sc.part.lo[k] - 2, 0)
+        hi = np.minimum(sc.part.hi[k] + 2, sc.dims)
+        box = sc.field[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+        d2.commit_brick(k, sc.part.lo[k], sc.part.hi[k], np.ascontiguousarray(box), data_lo=lo)
+    d2.set_tf(sc.tf)
+    d2.set_cameras(sc.cams)
+    d2.set_frame(40, 32)
+    d2.render()
+    assert torch.equal(d1.map_frame(0)[0], d2.map_frame(0)[0])
+    d1.release()
+    d2.release()
