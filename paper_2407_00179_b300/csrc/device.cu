@@ -71,7 +71,10 @@ struct dpv_device_t {
     std::vector<CamIn> cams;
     CamIn* d_cam_in = nullptr;
     CamBasis* d_cams = nullptr;
+    CamBasisD* d_camd = nullptr;
     int cam_cap = 0;
+    float4* d_rays = nullptr;           // per camera and pixel ray directions
+    size_t rays_cap = 0;
 
     bool has_frame = false;
     dpv_frame_desc frame{};
@@ -305,17 +308,33 @@ dpv_status prepare(dpv_device dev) {
     if ((int)dev->cams.size() > dev->cam_cap) {
         dev_free(dev->d_cam_in);
         dev_free(dev->d_cams);
+        dev_free(dev->d_camd);
         dev->d_cam_in = nullptr;
         dev->d_cams = nullptr;
+        dev->d_camd = nullptr;
         dev->cam_cap = 0;
         dpv_status s = dev_alloc(dev, (void**)&dev->d_cam_in, sizeof(CamIn) * dev->cams.size(), "cameras");
         if (s) return s;
         s = dev_alloc(dev, (void**)&dev->d_cams, sizeof(CamBasis) * dev->cams.size(), "cameras");
         if (s) return s;
+        s = dev_alloc(dev, (void**)&dev->d_camd, sizeof(CamBasisD) * dev->cams.size(), "cameras");
+        if (s) return s;
         dev->cam_cap = (int)dev->cams.size();
     }
     CK(cudaMemcpyAsync(dev->d_cam_in, dev->cams.data(), sizeof(CamIn) * dev->cams.size(), cudaMemcpyHostToDevice,
                        dev->stream), "upload cameras");
+
+    // per-pixel ray directions
+    size_t nrays = (size_t)P.ncam * P.W * P.H;
+    if (nrays > dev->rays_cap) {
+        dev_free(dev->d_rays);
+        dev->d_rays = nullptr;
+        dev->rays_cap = 0;
+        dpv_status s2 = dev_alloc(dev, (void**)&dev->d_rays, 2 * sizeof(float4) * nrays, "rays");
+        if (s2) return s2;
+        dev->rays_cap = nrays;
+    }
+    P.rays = dev->d_rays;
 
     // schedule: count pass
     free_schedule(dev);
@@ -329,7 +348,7 @@ dpv_status prepare(dpv_device dev) {
     }
     CK(cudaMemsetAsync(dev->d_counters, 0, sizeof(Counters), dev->stream), "reset counters");
     float3 og = make_float3(dev->origin[0], dev->origin[1], dev->origin[2]);
-    CK(launch_cull(P, dev->d_cam_in, og, 1.0f / dev->spacing, dev->d_cams, dev->d_bricks, dev->d_rects,
+    CK(launch_cull(P, dev->d_cam_in, og, dev->spacing, dev->d_cams, dev->d_camd, dev->d_rays, dev->d_bricks, dev->d_rects,
                    dev->d_tile_count, dev->d_tile_first, nullptr, 0, dev->d_counters, false, dev->stream),
        "cull (sizing)");
     dev->launches += 4;
@@ -602,7 +621,7 @@ dpv_status dpvRenderFrame(dpv_device dev) {
     float3 og = make_float3(dev->origin[0], dev->origin[1], dev->origin[2]);
     CK(cudaMemsetAsync(dev->d_counters, 0, sizeof(Counters), dev->stream), "reset counters");
     cudaEvent_t t0 = stage_start(dev);
-    CK(launch_cull(P, dev->d_cam_in, og, inv_sp, dev->d_cams, dev->d_bricks, dev->d_rects, dev->d_tile_count,
+    CK(launch_cull(P, dev->d_cam_in, og, dev->spacing, dev->d_cams, dev->d_camd, dev->d_rays, dev->d_bricks, dev->d_rects, dev->d_tile_count,
                    dev->d_tile_first, dev->d_items, dev->items_cap, dev->d_counters, true, dev->stream),
        "cull");
     stage_stop(dev, DPV_STAGE_CULL, t0);
@@ -617,7 +636,7 @@ dpv_status dpvRenderFrame(dpv_device dev) {
                             P.order_stride ? dev->d_order : nullptr, dev->stream),
        "composite");
     stage_stop(dev, DPV_STAGE_COMPOSITE, t0);
-    dev->launches += 5 + (dev->n_items > 0 ? 1 : 0) + 1;
+    dev->launches += 6 + (dev->n_items > 0 ? 1 : 0) + 1;
     CK(cudaEventRecord(dev->ev_done, dev->stream), "record");
     dev->rendered = true;
     return DPV_OK;
@@ -817,6 +836,8 @@ dpv_status dpvRelease(dpv_device dev) {
         dev_free(dev->d_tf);
         dev_free(dev->d_cam_in);
         dev_free(dev->d_cams);
+        dev_free(dev->d_camd);
+        dev_free(dev->d_rays);
         dev_free(dev->d_out_rgba);
         dev_free(dev->d_out_depth);
         dev_free(dev->d_order);

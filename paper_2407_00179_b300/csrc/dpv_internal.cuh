@@ -31,6 +31,12 @@ struct CamBasis {
     float pad;
 };
 
+// The same camera basis in FP64, for the per-pixel ray setup.
+struct CamBasisD {
+    double f[3], r[3], u[3];
+    double th;
+};
+
 // One rank's brick as the kernels see it.
 struct BrickDev {
     const void* data;  // stored nodes, x fastest
@@ -77,6 +83,7 @@ struct FrameParams {
     int nbricks;
     int order_stride;  // bytes per pixel of the order image (0 = off)
     int items_cap;     // work items the list and fragment pool hold
+    const float4* rays;// per camera and pixel: (d, t_enter), (1/d, t_exit); see k_rays
 };
 
 // A work item read back from the list is used only if it names a valid
@@ -100,38 +107,29 @@ __device__ __forceinline__ void tile_pixel(int t, int tw, int& lx, int& ly) {
 }
 
 // ---------------------------------------------------------------------------
-// rays: pinhole camera, pixel centres, row 0 at the bottom.  Ray origin and
-// direction are returned in node coordinates, with t in world units.
+// rays: pinhole camera, pixel centres, row 0 at the bottom.  The ray setup
+// pass (k_rays) computes every pixel's direction once per frame in FP64 and
+// stores it rounded to FP32, together with its FP32 reciprocal and the ray's
+// interval in the volume.  A ray is the camera's eye in node coordinates
+// plus that direction (node units per world unit of t).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pixel_ray(const CamBasis& c, const FrameParams& P, float inv_spacing, int px,
-                                          int py, float o[3], float d[3]) {
-    float nx = (((px + 0.5f) / P.W) * 2.0f - 1.0f) * ((float)P.W / (float)P.H);
-    float ny = ((py + 0.5f) / P.H) * 2.0f - 1.0f;
-    float a = nx * c.th, b = ny * c.th;
-    float dx = c.f[0] + a * c.r[0] + b * c.u[0];
-    float dy = c.f[1] + a * c.r[1] + b * c.u[1];
-    float dz = c.f[2] + a * c.r[2] + b * c.u[2];
-    float n = inv_spacing / sqrtf(dx * dx + dy * dy + dz * dz);
-    d[0] = dx * n;
-    d[1] = dy * n;
-    d[2] = dz * n;
-    o[0] = c.o[0];
-    o[1] = c.o[1];
-    o[2] = c.o[2];
-}
+struct Ray {
+    float o[3], d[3], inv[3];
+    float te, tx;      // interval in the volume box, clipped to t >= 0
+};
 
 // Parametric interval of a ray in the node-space box [lo, hi] per axis.  An
 // axis the ray is parallel to constrains nothing if the origin lies in
 // [lo, hi) (or [lo, hi] where `closed`), else empties the interval.  Every
-// face plane's t is (plane - o) / d computed one way, so boxes that share a
-// plane get bit-identical boundaries and their sample ranges tile the ray.
-__device__ __forceinline__ void ray_box(const float o[3], const float d[3], const float lo[3], const float hi[3],
-                                        const int closed[3], float& t0, float& t1) {
+// face plane's t is (plane - o) * inv computed one way, so boxes that share
+// a plane get bit-identical boundaries and their sample ranges tile the ray.
+__device__ __forceinline__ void ray_box(const float o[3], const float d[3], const float inv[3], const float lo[3],
+                                        const float hi[3], const int closed[3], float& t0, float& t1) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (d[a] != 0.0f) {
-            float ta = (lo[a] - o[a]) / d[a];
-            float tb = (hi[a] - o[a]) / d[a];
+            float ta = (lo[a] - o[a]) * inv[a];
+            float tb = (hi[a] - o[a]) * inv[a];
             t0 = fmaxf(t0, fminf(ta, tb));
             t1 = fminf(t1, fmaxf(ta, tb));
         } else {
@@ -141,16 +139,32 @@ __device__ __forceinline__ void ray_box(const float o[3], const float d[3], cons
     }
 }
 
-// Interval of the ray in the whole volume, clipped to t >= 0.
-__device__ __forceinline__ bool volume_interval(const FrameParams& P, const float o[3], const float d[3], float& te,
-                                                float& tx) {
+// Interval of the ray in the whole volume [0, dims - 1], clipped to t >= 0.
+__device__ __forceinline__ bool volume_interval(const int dims[3], const float o[3], const float d[3],
+                                                const float inv[3], float& te, float& tx) {
     const float lo[3] = {0.0f, 0.0f, 0.0f};
-    const float hi[3] = {(float)(P.dims[0] - 1), (float)(P.dims[1] - 1), (float)(P.dims[2] - 1)};
+    const float hi[3] = {(float)(dims[0] - 1), (float)(dims[1] - 1), (float)(dims[2] - 1)};
     const int closed[3] = {1, 1, 1};
     te = 0.0f;
     tx = __int_as_float(0x7f800000);
-    ray_box(o, d, lo, hi, closed, te, tx);
+    ray_box(o, d, inv, lo, hi, closed, te, tx);
     return te < tx;
+}
+
+__device__ __forceinline__ void load_ray(const CamBasis& cam, const FrameParams& P, int c, int px, int py, Ray& r) {
+    long long i = ((long long)c * P.H + py) * P.W + px;
+    float4 a = __ldg(P.rays + 2 * i), b = __ldg(P.rays + 2 * i + 1);
+    r.d[0] = a.x;
+    r.d[1] = a.y;
+    r.d[2] = a.z;
+    r.te = a.w;
+    r.inv[0] = b.x;
+    r.inv[1] = b.y;
+    r.inv[2] = b.z;
+    r.tx = b.w;
+    r.o[0] = cam.o[0];
+    r.o[1] = cam.o[1];
+    r.o[2] = cam.o[2];
 }
 
 // Sample index of the first sample at or after t: samples sit at

@@ -117,28 +117,77 @@ cudaError_t launch_commit(const CommitArgs& a, int storage, int src_is_f32, floa
 // cameras and culling (work list)
 // ===========================================================================
 
-__global__ void k_cam_setup(const CamIn* cams, int n, float3 origin, float inv_spacing, CamBasis* out) {
+__global__ void k_cam_setup(const CamIn* cams, int n, float3 origin, float spacing, CamBasis* out,
+                            CamBasisD* outd) {
+    // once per camera, so computed in FP64 and rounded once to FP32
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     CamIn c = cams[i];
-    float f[3] = {c.center[0] - c.eye[0], c.center[1] - c.eye[1], c.center[2] - c.eye[2]};
-    float fn = 1.0f / sqrtf(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    double f[3] = {(double)c.center[0] - c.eye[0], (double)c.center[1] - c.eye[1], (double)c.center[2] - c.eye[2]};
+    double fn = 1.0 / sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
     for (int a = 0; a < 3; ++a) f[a] *= fn;
-    float r[3] = {f[1] * c.up[2] - f[2] * c.up[1], f[2] * c.up[0] - f[0] * c.up[2], f[0] * c.up[1] - f[1] * c.up[0]};
-    float rn = 1.0f / sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    double up[3] = {c.up[0], c.up[1], c.up[2]};
+    double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+    double rn = 1.0 / sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
     for (int a = 0; a < 3; ++a) r[a] *= rn;
-    float u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+    double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
     CamBasis b;
-    const float og[3] = {origin.x, origin.y, origin.z};
+    const double og[3] = {origin.x, origin.y, origin.z};
     for (int a = 0; a < 3; ++a) {
-        b.o[a] = (c.eye[a] - og[a]) * inv_spacing;
-        b.f[a] = f[a];
-        b.r[a] = r[a];
-        b.u[a] = u[a];
+        b.o[a] = (float)(((double)c.eye[a] - og[a]) / (double)spacing);
+        b.f[a] = (float)f[a];
+        b.r[a] = (float)r[a];
+        b.u[a] = (float)u[a];
     }
-    b.th = tanf(c.fovy_deg * 0.008726646259971648f);   // pi / 360
+    double th = tan((double)c.fovy_deg * 0.00872664625997164788);   // pi / 360
+    b.th = (float)th;
     b.pad = 0.0f;
     out[i] = b;
+    CamBasisD bd;
+    for (int a = 0; a < 3; ++a) {
+        bd.f[a] = f[a];
+        bd.r[a] = r[a];
+        bd.u[a] = u[a];
+    }
+    bd.th = th;
+    outd[i] = bd;
+}
+
+// Ray setup: direction of every pixel's ray, normalize(f + x th r + y th u)
+// with x = ((px + 1/2) / W * 2 - 1) * W / H and y = (py + 1/2) / H * 2 - 1,
+// computed in FP64 (the norm by an FP32 reciprocal square root refined with
+// one Newton step in FP64), scaled to node units per world t and rounded
+// once to FP32.  The FP32 reciprocal and the FP32 volume interval follow
+// from the rounded direction, so every kernel sees identical planes.
+__global__ void k_rays(FrameParams P, const CamBasis* cams, const CamBasisD* camd, double inv_spacing, double sx,
+                       double sy, double aspect, float4* rays) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long npix = (long long)P.W * P.H;
+    if (i >= npix * P.ncam) return;
+    int c = (int)(i / npix);
+    int p = (int)(i - c * npix);
+    int px = p % P.W, py = p / P.W;
+    const CamBasisD& b = camd[c];
+    double x = ((px + 0.5) * sx - 1.0) * aspect * b.th;
+    double y = ((py + 0.5) * sy - 1.0) * b.th;
+    double d0 = b.f[0] + x * b.r[0] + y * b.u[0];
+    double d1 = b.f[1] + x * b.r[1] + y * b.u[1];
+    double d2 = b.f[2] + x * b.r[2] + y * b.u[2];
+    double n2 = d0 * d0 + d1 * d1 + d2 * d2;
+    double yr = (double)rsqrtf((float)n2);
+    yr = yr * (1.5 - 0.5 * n2 * yr * yr);
+    double n = yr * inv_spacing;
+    Ray r;
+    r.d[0] = (float)(d0 * n);
+    r.d[1] = (float)(d1 * n);
+    r.d[2] = (float)(d2 * n);
+    for (int a = 0; a < 3; ++a) {
+        r.o[a] = cams[c].o[a];
+        r.inv[a] = 1.0f / r.d[a];
+    }
+    if (!volume_interval(P.dims, r.o, r.d, r.inv, r.te, r.tx)) r.te = r.tx = 0.0f;
+    rays[2 * i] = make_float4(r.d[0], r.d[1], r.d[2], r.te);
+    rays[2 * i + 1] = make_float4(r.inv[0], r.inv[1], r.inv[2], r.tx);
 }
 
 // Screen tile rectangle [x0, x1] x [y0, y1] (inclusive) that may see brick b
@@ -274,11 +323,16 @@ __global__ void k_cull_fill(FrameParams P, const int4* rects, const int* tile_fi
         }
 }
 
-cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 origin, float inv_spacing,
-                        CamBasis* d_cams, const BrickDev* d_bricks, int4* d_rects, int* d_tile_count,
-                        int* d_tile_first, Item* d_items, int cap, Counters* d_counters, bool fill,
-                        cudaStream_t st) {
-    k_cam_setup<<<(P.ncam + 63) / 64, 64, 0, st>>>(d_cam_in, P.ncam, origin, inv_spacing, d_cams);
+cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 origin, float spacing,
+                        CamBasis* d_cams, CamBasisD* d_camd, float4* d_rays, const BrickDev* d_bricks,
+                        int4* d_rects, int* d_tile_count, int* d_tile_first, Item* d_items, int cap,
+                        Counters* d_counters, bool fill, cudaStream_t st) {
+    k_cam_setup<<<(P.ncam + 63) / 64, 64, 0, st>>>(d_cam_in, P.ncam, origin, spacing, d_cams, d_camd);
+    if (fill) {
+        long long n = (long long)P.ncam * P.W * P.H;
+        k_rays<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, d_cams, d_camd, 1.0 / (double)spacing, 2.0 / P.W,
+                                                            2.0 / P.H, (double)P.W / (double)P.H, d_rays);
+    }
     int ncb = P.ncam * P.nbricks;
     k_cull_rects<<<(ncb + 127) / 128, 128, 0, st>>>(P, d_cams, d_bricks, d_rects);
     int nct = P.ncam * P.ntx * P.nty;
@@ -309,25 +363,24 @@ struct MarchState {
 
 // Ray of pixel (px, py) against brick b: its sample range and the local
 // frame.  Returns false when the brick holds no sample of the ray.
-__device__ __forceinline__ bool brick_samples(const FrameParams& P, const CamBasis& cam, const BrickDev& b,
-                                              float inv_spacing, int px, int py, MarchState& m) {
-    float o[3], d[3];
-    pixel_ray(cam, P, inv_spacing, px, py, o, d);
-    float te, tx;
-    if (!volume_interval(P, o, d, te, tx)) return false;
-    float t0 = te, t1 = tx;
-    ray_box(o, d, b.r0, b.r1, b.closed, t0, t1);
+__device__ __forceinline__ bool brick_samples(const FrameParams& P, const CamBasis& cam, int c, const BrickDev& b,
+                                              int px, int py, MarchState& m) {
+    Ray r;
+    load_ray(cam, P, c, px, py, r);
+    if (!(r.te < r.tx)) return false;
+    float t0 = r.te, t1 = r.tx;
+    ray_box(r.o, r.d, r.inv, b.r0, b.r1, b.closed, t0, t1);
     if (!(t0 < t1)) return false;
-    m.j0 = first_sample_at(t0, te, P);
-    m.j1 = first_sample_at(t1, te, P);
+    m.j0 = first_sample_at(t0, r.te, P);
+    m.j1 = first_sample_at(t1, r.te, P);
     if (m.j0 >= m.j1) return false;
-    m.te = te;
-    float tj = te + ((float)m.j0 + 0.5f) * P.dt;
+    m.te = r.te;
+    float tj = r.te + ((float)m.j0 + 0.5f) * P.dt;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        float ol = o[a] - (float)b.s_lo[a];
-        m.q0[a] = fmaf(tj, d[a], ol);
-        m.st[a] = P.dt * d[a];
+        float ol = r.o[a] - (float)b.s_lo[a];
+        m.q0[a] = fmaf(tj, r.d[a], ol);
+        m.st[a] = P.dt * r.d[a];
     }
     return true;
 }
@@ -354,7 +407,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, float inv_spac
     unsigned long long nsamp = 0;
     if (px < P.W && py < P.H) {
         MarchState m;
-        if (brick_samples(P, cam, b, inv_spacing, px, py, m)) {
+        if (brick_samples(P, cam, it.cam, b, px, py, m)) {
             float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.0f;
             int n = m.j1 - m.j0;
             int k = 0;
@@ -460,12 +513,10 @@ __device__ __forceinline__ int next_slot(const int* frag_key, long long first, i
     return bs;
 }
 
-__device__ __forceinline__ float pixel_t_enter(const FrameParams& P, const CamBasis& cam, float inv_spacing, int px,
-                                               int py) {
-    float o[3], d[3], te, tx;
-    pixel_ray(cam, P, inv_spacing, px, py, o, d);
-    volume_interval(P, o, d, te, tx);
-    return te;
+__device__ __forceinline__ float pixel_t_enter(const FrameParams& P, const CamBasis& cam, int c, int px, int py) {
+    Ray r;
+    load_ray(cam, P, c, px, py, r);
+    return r.te;
 }
 
 __global__ void __launch_bounds__(256) k_composite_fwd(FrameParams P, float inv_spacing, const CamBasis* cams,
@@ -525,7 +576,7 @@ __global__ void __launch_bounds__(256) k_composite_fwd(FrameParams P, float inv_
     out_rgba[pix] = make_float4(C0, C1, C2, A);
     float depth = __int_as_float(0x7f800000);
     if (depth_key != KEY_EMPTY) {
-        float te = pixel_t_enter(P, cams[c], inv_spacing, px, py);
+        float te = pixel_t_enter(P, cams[c], c, px, py);
         depth = te + ((float)depth_key + 0.5f) * P.dt;
     }
     out_depth[pix] = depth;
@@ -651,8 +702,44 @@ cudaError_t launch_composite_bwd(const FrameParams& P, const int* tile_first, co
 //   da_i/dsig = dt (1 - a_i),  sigma = sigma_max * alpha_TF
 // then the TF lerp (weights 1-w, w on entries i0, i0+1), ds from the lerp
 // slope, and the eight trilinear weights scatter into the global field.
-// TF gradients go to a shared-memory table per CTA (FP32), flushed to the
-// global FP64 table with one atomic per touched entry.
+//
+// Accumulation: consecutive samples of a ray usually fall in the same TF
+// segment and the same cell, so each thread sums its gradient in registers
+// while the segment (cell) stays the same and flushes on change.  TF
+// flushes go to an FP64 table in shared memory (the entries are sums of
+// many terms of both signs), which is added to the global FP64 table once
+// per CTA; voxel flushes are eight FP32 atomics into the global field.
+
+struct TFRun {
+    int i0 = -1;
+    float a[8];        // entry i0 (rgba), entry i0+1 (rgba)
+};
+
+__device__ __forceinline__ void tf_flush(TFRun& r, double* s_g) {
+    if (r.i0 < 0) return;
+    double* e = s_g + 4 * r.i0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (r.a[c] != 0.0f) atomicAdd(e + c, (double)r.a[c]);
+}
+
+struct CellRun {
+    long long base = -1;   // global index of the cell's (0,0,0) node
+    float a[8];
+};
+
+__device__ __forceinline__ void cell_flush(CellRun& r, float* dvol, long long sy, long long sz) {
+    if (r.base < 0) return;
+    float* v = dvol + r.base;
+    atomicAdd(v, r.a[0]);
+    atomicAdd(v + 1, r.a[1]);
+    atomicAdd(v + sy, r.a[2]);
+    atomicAdd(v + sy + 1, r.a[3]);
+    atomicAdd(v + sz, r.a[4]);
+    atomicAdd(v + sz + 1, r.a[5]);
+    atomicAdd(v + sz + sy, r.a[6]);
+    atomicAdd(v + sz + sy + 1, r.a[7]);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spacing, const CamBasis* cams,
@@ -662,14 +749,9 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spac
                                                    Counters* counters) {
     extern __shared__ float4 s_mem[];
     float4* s_tf = s_mem;
-    float* s_g = (float*)(s_mem + P.ntf);
-    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) {
-        s_tf[i] = tf[i];
-        s_g[4 * i + 0] = 0.f;
-        s_g[4 * i + 1] = 0.f;
-        s_g[4 * i + 2] = 0.f;
-        s_g[4 * i + 3] = 0.f;
-    }
+    double* s_g = (double*)(s_mem + P.ntf);
+    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
+    for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) s_g[i] = 0.0;
     __syncthreads();
 
     Item it = items[blockIdx.x];
@@ -685,14 +767,18 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spac
     long long slot = (long long)blockIdx.x * P.tp + threadIdx.x;
     unsigned long long nsamp = 0;
     const float gscale = Storage<T>::unit_scale ? 1.0f : scale;
+    const long long sy = P.dims[0], sz = (long long)P.dims[0] * P.dims[1];
     if (valid && px < P.W && py < P.H && frag_key[slot] != KEY_EMPTY) {
         MarchState m;
         float4 F = frag_rgba[slot];
         float4 G = frag_grad[slot];
-        if (brick_samples(P, cam, b, inv_spacing, px, py, m) && (G.x != 0.f || G.y != 0.f || G.z != 0.f || G.w != 0.f)) {
+        if (brick_samples(P, cam, it.cam, b, px, py, m) && (G.x != 0.f || G.y != 0.f || G.z != 0.f || G.w != 0.f)) {
             float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.0f;
             float Tend = 1.0f - F.w;
             int n = m.j1 - m.j0;
+            TFRun tr;
+            CellRun cr;
+            const long long gofs = (long long)b.s_lo[2] * sz + (long long)b.s_lo[1] * sy + b.s_lo[0];
             for (int k = 0; k < n; ++k) {
                 float fk = (float)k;
                 int base;
@@ -709,36 +795,46 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spac
                 float gal = G.x * (Tr * c.v.x - S0 * inv1ma) + G.y * (Tr * c.v.y - S1 * inv1ma) +
                             G.z * (Tr * c.v.z - S2 * inv1ma) + G.w * Tend * inv1ma;
                 float g_r = G.x * ta, g_g = G.y * ta, g_b = G.z * ta;
-                float g_a = gal * P.sigma_max * P.dt * (1.0f - al);
+                float g_a = gal * P.sigma_max * P.dt * om;
+                if (c.i0 != tr.i0) {
+                    tf_flush(tr, s_g);
+                    tr.i0 = c.i0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) tr.a[q] = 0.0f;
+                }
                 float w1 = c.w, w0 = 1.0f - c.w;
-                float* e0 = s_g + 4 * c.i0;
-                atomicAdd(e0 + 0, w0 * g_r);
-                atomicAdd(e0 + 1, w0 * g_g);
-                atomicAdd(e0 + 2, w0 * g_b);
-                atomicAdd(e0 + 3, w0 * g_a);
-                atomicAdd(e0 + 4, w1 * g_r);
-                atomicAdd(e0 + 5, w1 * g_g);
-                atomicAdd(e0 + 6, w1 * g_b);
-                atomicAdd(e0 + 7, w1 * g_a);
+                tr.a[0] = fmaf(w0, g_r, tr.a[0]);
+                tr.a[1] = fmaf(w0, g_g, tr.a[1]);
+                tr.a[2] = fmaf(w0, g_b, tr.a[2]);
+                tr.a[3] = fmaf(w0, g_a, tr.a[3]);
+                tr.a[4] = fmaf(w1, g_r, tr.a[4]);
+                tr.a[5] = fmaf(w1, g_g, tr.a[5]);
+                tr.a[6] = fmaf(w1, g_b, tr.a[6]);
+                tr.a[7] = fmaf(w1, g_a, tr.a[7]);
                 if (dvol && c.duds != 0.0f) {
                     float4 ta0 = s_tf[c.i0], ta1 = s_tf[c.i0 + 1];
                     float gs = (g_r * (ta1.x - ta0.x) + g_g * (ta1.y - ta0.y) + g_b * (ta1.z - ta0.z) +
                                 g_a * (ta1.w - ta0.w)) * c.duds * gscale;
                     if (gs != 0.0f) {
-                        // brick-local cell -> global node index
-                        int ix = base % b.sx, iz = base / b.sxy, iy = (base - iz * b.sxy) / b.sx;
-                        long long gx = ix + b.s_lo[0], gy = iy + b.s_lo[1], gz = iz + b.s_lo[2];
-                        long long sy = P.dims[0], sz = (long long)P.dims[0] * P.dims[1];
-                        float* v = dvol + gz * sz + gy * sy + gx;
+                        // brick-local cell -> global node index of its (0,0,0) corner
+                        int iz = base / b.sxy, rem = base - iz * b.sxy, iy = rem / b.sx, ix = rem - iy * b.sx;
+                        long long gb = gofs + (long long)iz * sz + (long long)iy * sy + ix;
+                        if (gb != cr.base) {
+                            cell_flush(cr, dvol, sy, sz);
+                            cr.base = gb;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) cr.a[q] = 0.0f;
+                        }
                         float ax = 1.0f - fx, ay = 1.0f - fy, az = 1.0f - fz;
-                        atomicAdd(v, gs * ax * ay * az);
-                        atomicAdd(v + 1, gs * fx * ay * az);
-                        atomicAdd(v + sy, gs * ax * fy * az);
-                        atomicAdd(v + sy + 1, gs * fx * fy * az);
-                        atomicAdd(v + sz, gs * ax * ay * fz);
-                        atomicAdd(v + sz + 1, gs * fx * ay * fz);
-                        atomicAdd(v + sz + sy, gs * ax * fy * fz);
-                        atomicAdd(v + sz + sy + 1, gs * fx * fy * fz);
+                        float gyz0 = gs * ay * az, gyz1 = gs * fy * az, gyz2 = gs * ay * fz, gyz3 = gs * fy * fz;
+                        cr.a[0] = fmaf(gyz0, ax, cr.a[0]);
+                        cr.a[1] = fmaf(gyz0, fx, cr.a[1]);
+                        cr.a[2] = fmaf(gyz1, ax, cr.a[2]);
+                        cr.a[3] = fmaf(gyz1, fx, cr.a[3]);
+                        cr.a[4] = fmaf(gyz2, ax, cr.a[4]);
+                        cr.a[5] = fmaf(gyz2, fx, cr.a[5]);
+                        cr.a[6] = fmaf(gyz3, ax, cr.a[6]);
+                        cr.a[7] = fmaf(gyz3, fx, cr.a[7]);
                     }
                 }
                 C0 = n0;
@@ -748,14 +844,16 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spac
                 ++nsamp;
                 if (P.ert_on && 1.0f - Tr > P.ert) break;
             }
+            tf_flush(tr, s_g);
+            if (dvol) cell_flush(cr, dvol, sy, sz);
         }
     }
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) {
-        float v = s_g[i];
-        if (v != 0.0f) atomicAdd(dtf + i, (double)v);
+        double v = s_g[i];
+        if (v != 0.0) atomicAdd(dtf + i, v);
     }
 }
 
@@ -765,7 +863,7 @@ cudaError_t launch_march_bwd(int dtype, const FrameParams& P, float inv_spacing,
                              const float4* frag_grad, double* dtf, float* dvol, Counters* counters,
                              cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-    size_t smem = sizeof(float4) * P.ntf * 2;
+    size_t smem = sizeof(float4) * P.ntf + sizeof(double) * 4 * P.ntf;
     if (smem > 48 * 1024) {
         cudaFuncSetAttribute(k_march_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_march_bwd<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

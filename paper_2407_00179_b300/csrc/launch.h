@@ -25,10 +25,10 @@ struct CommitArgs {
 cudaError_t launch_commit(const CommitArgs& a, int storage, int src_is_f32, float given_scale, unsigned int* d_tmp,
                           float* d_scale, void* dst, cudaStream_t st);
 
-cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 origin, float inv_spacing,
-                        CamBasis* d_cams, const BrickDev* d_bricks, int4* d_rects, int* d_tile_count,
-                        int* d_tile_first, Item* d_items, int cap, Counters* d_counters, bool fill,
-                        cudaStream_t st);
+cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 origin, float spacing,
+                        CamBasis* d_cams, CamBasisD* d_camd, float4* d_rays, const BrickDev* d_bricks,
+                        int4* d_rects, int* d_tile_count, int* d_tile_first, Item* d_items, int cap,
+                        Counters* d_counters, bool fill, cudaStream_t st);
 
 cudaError_t launch_march_fwd(int dtype, const FrameParams& P, float inv_spacing, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,

@@ -118,7 +118,7 @@ class _CudaArray:
     """Minimal __cuda_array_interface__ holder for a device pointer."""
 
     def __init__(self, ptr: int, shape, typestr: str):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 3, "strides": None, "stream": None}
 
 

@@ -31,13 +31,26 @@ class Scene:
     def dims(self):
         return (self.field.shape[2], self.field.shape[1], self.field.shape[0])
 
+    @property
+    def spacing(self):
+        """Node spacing exactly as the C ABI receives it (float32)."""
+        return float(np.float32(1.0 / (max(self.dims) - 1)))
+
+
+def f32_camera(c: inputs.Camera) -> inputs.Camera:
+    """The camera exactly as the C ABI receives it (float32 fields), so the
+    oracle and the GPU see the same rays."""
+    r = lambda v: tuple(float(x) for x in np.asarray(v, np.float32))
+    return inputs.Camera(r(c.eye), r(c.center), r(c.up), float(np.float32(c.fovy_deg)))
+
 
 def small(seed=0, width=256, height=256, storage="f32", ert=0.0, tile=(0, 0)) -> Scene:
     """64^3 sum of 8 blobs, 2x1x1 bricks, one camera from (1, 0.7, 0.5)."""
     dims = (64, 64, 64)
     f = inputs.field_small(seed, dims).numpy()
     return Scene(f, inputs.regular_partition(dims, (2, 1, 1)), inputs.make_tf(1234),
-                 [inputs.camera_from_direction(dims, (1.0, 0.7, 0.5))], width, height, storage=storage, ert=ert,
+                 [f32_camera(inputs.camera_from_direction(dims, (1.0, 0.7, 0.5)))], width, height, storage=storage,
+                 ert=ert,
                  tile=tile)
 
 
@@ -45,7 +58,7 @@ def make(dims, splits=None, kd=None, nblobs=8, seed=0, cams=None, width=64, heig
     f = inputs.blob_field(dims, inputs.blob_params(nblobs, dims, seed)).numpy()
     part = inputs.kd_partition(dims, kd, seed=seed) if kd else inputs.regular_partition(dims, splits or (1, 1, 1))
     cams = cams if cams is not None else [inputs.camera_from_direction(dims, (1.0, 0.7, 0.5))]
-    return Scene(f, part, inputs.make_tf(1234), cams, width, height, **kw)
+    return Scene(f, part, inputs.make_tf(1234), [f32_camera(c) for c in cams], width, height, **kw)
 
 
 def gpu_device(sc: Scene, order=True):
@@ -67,3 +80,14 @@ def oracle_bricks(orc, sc: Scene):
 
 def oracle_frame(orc, sc: Scene):
     return orc.Frame(sc.width, sc.height, step_voxels=sc.step, sigma_max=sc.sigma_max, ert=sc.ert)
+
+
+def o_bricks(orc, sc: Scene, cam, **kw):
+    """Oracle partitioned render of camera `cam` with the scene's inputs."""
+    return orc.render_bricks(sc.dims, oracle_bricks(orc, sc), sc.tf, cam, oracle_frame(orc, sc), spacing=sc.spacing,
+                             **kw)
+
+
+def o_full(orc, sc: Scene, cam, field=None, **kw):
+    f = sc.field if field is None else field
+    return orc.render_full(f, sc.tf, cam, oracle_frame(orc, sc), spacing=sc.spacing, **kw)
