@@ -237,6 +237,53 @@ dpv_status dpvResetStats(dpv_device dev);
 /* Turn per-stage CUDA-event timing on (1) or off (0). */
 dpv_status dpvSetProfiling(dpv_device dev, int enable);
 
+/* One rank's brick for dpvRenderNoAlloc: a device pointer to the nodes the
+ * rank stores (its owned range plus one ghost node per side, clipped to the
+ * volume; x fastest) in the scene's storage format, decoded as
+ * scale * stored (scale <= 0 means 1).  Caller-owned. */
+typedef struct {
+    int owned_lo[3], owned_hi[3];
+    const void* data;
+    float scale;
+} dpv_noalloc_brick;
+
+/* Everything dpvRenderNoAlloc reads: the grid, the ranks' bricks (host
+ * array of num_ranks entries, all in `storage`), and the transfer function
+ * (device pointer, tf_n RGBA floats). */
+typedef struct {
+    int dims[3];
+    float origin[3];
+    float spacing;
+    int num_ranks;
+    const dpv_noalloc_brick* bricks;
+    dpv_dtype storage;
+    const float* tf_rgba;
+    int tf_n;
+    float vmin, vmax;
+} dpv_noalloc_scene;
+
+/* Allocation-free render (the paper has no counterpart: this entry point is
+ * for callers that cannot allocate device memory -- applications whose
+ * device memory belongs to their own pool or a framework's caching
+ * allocator, and render loops that cannot afford the device-wide
+ * synchronisation of cudaMalloc and cudaFree).
+ * Renders one camera exactly as dpvRenderFrame does (cull, brick ray-march,
+ * sort-last composite) into the caller's device buffers rgba (height x width
+ * x 4 floats, 16-byte aligned) and depth (height x width floats), on
+ * `cuda_stream`, on the current CUDA device.  It calls no cudaMalloc or
+ * cudaFree: its intermediate buffers live in one fixed 64 MiB device array
+ * that the library holds on every GPU it is loaded on until the process
+ * exits.  A frame needs about width x height x (32 + 20 x num_ranks) bytes
+ * of it (e.g. 512 x 512 with 8 ranks); larger requests fail with
+ * DPV_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address, so that first call should come before any stream capture
+ * on that device.  Every call reuses the
+ * same array, so calls that overlap on the GPU -- on different streams or
+ * from different host threads -- race and must be serialised by the caller.
+ * Asynchronous: returns once the work is queued. */
+dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* scene, const dpv_camera* camera, const dpv_frame_desc* frame,
+                            float* rgba, float* depth, void* cuda_stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* dpvGetLastError(void);
 

@@ -48,6 +48,8 @@ const int kElemSize[4] = {4, 2, 2, 1};
 
 }  // namespace
 
+void dpv::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct dpv_device_t {
     int nranks = 0;
     int cuda_device = 0;

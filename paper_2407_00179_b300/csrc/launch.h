@@ -22,6 +22,9 @@ struct CommitArgs {
     int s_lo[3], s_n[3];
 };
 
+// Message returned by dpvGetLastError() on this host thread.
+void set_last_error(const char* msg);
+
 cudaError_t launch_commit(const CommitArgs& a, int storage, int src_is_f32, float given_scale, unsigned int* d_tmp,
                           float* d_scale, void* dst, cudaStream_t st);
 

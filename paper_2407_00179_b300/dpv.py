@@ -27,7 +27,7 @@ STATUS = {0: "DPV_OK", 1: "DPV_ERR_INVALID_ARG", 2: "DPV_ERR_STATE", 3: "DPV_ERR
 EXPORTS = ["dpvCreateDevice", "dpvSetVolumeGeometry", "dpvCommitBrick", "dpvSetTransferFunction", "dpvSetCameras",
            "dpvSetFrame", "dpvRenderFrame", "dpvFrameReady", "dpvMapFrame", "dpvUnmapFrame", "dpvCopyFrame",
            "dpvReadFragments", "dpvReadBrick", "dpvMapOrder", "dpvBackward", "dpvGetStats", "dpvResetStats", "dpvSetProfiling", "dpvGetLastError",
-           "dpvRelease"]
+           "dpvRelease", "dpvRenderNoAlloc"]
 
 
 class DPVError(RuntimeError):
@@ -49,6 +49,16 @@ class CameraDesc(C.Structure):
 class FrameDesc(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("step_voxels", C.c_float), ("sigma_max", C.c_float),
                 ("ert_threshold", C.c_float), ("tile_w", C.c_int), ("tile_h", C.c_int), ("flags", C.c_int)]
+
+
+class NoAllocBrick(C.Structure):
+    _fields_ = [("owned_lo", C.c_int * 3), ("owned_hi", C.c_int * 3), ("data", C.c_void_p), ("scale", C.c_float)]
+
+
+class NoAllocScene(C.Structure):
+    _fields_ = [("dims", C.c_int * 3), ("origin", C.c_float * 3), ("spacing", C.c_float), ("num_ranks", C.c_int),
+                ("bricks", C.POINTER(NoAllocBrick)), ("storage", C.c_int), ("tf_rgba", C.c_void_p), ("tf_n", C.c_int),
+                ("vmin", C.c_float), ("vmax", C.c_float)]
 
 
 STAGES = ["cull", "march", "composite", "composite_bwd", "march_bwd"]
@@ -97,6 +107,7 @@ def load(path: Optional[str] = None):
         "dpvGetStats": [V, C.POINTER(Stats)],
         "dpvResetStats": [V],
         "dpvSetProfiling": [V, I],
+        "dpvRenderNoAlloc": [C.POINTER(NoAllocScene), C.POINTER(CameraDesc), C.POINTER(FrameDesc), V, V, V],
         "dpvRelease": [V],
     }
     for name, args in sig.items():
@@ -314,6 +325,33 @@ class Device:
 
     def set_profiling(self, on: bool = True):
         _check(load().dpvSetProfiling(self._h, 1 if on else 0))
+
+
+def render_noalloc(dims: Sequence[int], bricks, storage: str, tf: torch.Tensor, camera, width: int, height: int,
+                   rgba: torch.Tensor, depth: torch.Tensor, step_voxels: float = 0.5, sigma_max: float = 8.0,
+                   ert: float = 0.0, tile=(0, 0), vmin: float = 0.0, vmax: float = 1.0, origin=(0.0, 0.0, 0.0),
+                   spacing: Optional[float] = None, stream: Optional[torch.cuda.Stream] = None):
+    """Allocation-free render of one camera (dpvRenderNoAlloc) into caller
+    tensors rgba (H, W, 4) and depth (H, W) on the current CUDA device.
+    bricks: per rank (owned_lo, owned_hi, stored nodes as a device tensor in
+    the storage dtype, scale).  Nothing is allocated on the device; see
+    include/dpv.h for the size limit and the rule that calls must not overlap
+    on the GPU."""
+    sp = 1.0 / (max(dims) - 1) if spacing is None else spacing
+    arr = (NoAllocBrick * len(bricks))()
+    for i, (lo, hi, data, scale) in enumerate(bricks):
+        arr[i] = NoAllocBrick((C.c_int * 3)(*[int(x) for x in lo]), (C.c_int * 3)(*[int(x) for x in hi]),
+                              data.data_ptr(), float(scale))
+    t = tf.detach().to(torch.float32).contiguous()
+    sc = NoAllocScene((C.c_int * 3)(*[int(x) for x in dims]), (C.c_float * 3)(*[float(x) for x in origin]), float(sp),
+                      len(bricks), arr, DTYPES[storage], t.data_ptr(), t.shape[0], float(vmin), float(vmax))
+    cam = CameraDesc((C.c_float * 3)(*camera.eye), (C.c_float * 3)(*camera.center), (C.c_float * 3)(*camera.up),
+                     float(camera.fovy_deg))
+    fr = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
+                   int(tile[1]), 0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(load().dpvRenderNoAlloc(C.byref(sc), C.byref(cam), C.byref(fr), _ptr(rgba), _ptr(depth),
+                                   C.c_void_p(st.cuda_stream)))
 
 
 class RenderFunction(torch.autograd.Function):
