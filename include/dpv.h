@@ -107,6 +107,15 @@ typedef struct {
 } dpv_camera;
 
 #define DPV_FRAME_ORDER 1          /* also produce the per-pixel order (debug) */
+#define DPV_FRAME_STAGED 2         /* stage brick slabs in shared memory instead of
+                                      gathering through L1 (same results for float32
+                                      bricks; a tuning variant) */
+#define DPV_FRAME_LINEAR 4         /* gather the 8 corners from the stored nodes instead
+                                      of the "quad" gather layout (per cell face the 2x2
+                                      corners in one vector, 2 loads per sample) that the
+                                      device builds from each committed brick at the next
+                                      render and keeps (4x the brick's device memory);
+                                      identical results */
 
 /* Frame parameters, identical on all ranks (§3.1.1).  Every camera renders
  * a width x height image.  tile_w/tile_h: pixels per work item (multiples

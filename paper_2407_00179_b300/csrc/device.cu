@@ -9,6 +9,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -42,6 +43,9 @@ struct HostBrick {
     int dtype = 0;
     void* data = nullptr;       // device storage
     size_t bytes = 0;
+    void* quad = nullptr;       // gather layout built from `data` (see Quad)
+    size_t quad_bytes = 0;
+    bool quad_valid = false;
 };
 
 const int kElemSize[4] = {4, 2, 2, 1};
@@ -102,6 +106,7 @@ struct dpv_device_t {
     Counters* d_counters = nullptr;
     cudaEvent_t ev_done = nullptr;
     bool rendered = false;
+    bool use_quad = false;
 
     // profiling: event pairs around stages, resolved by dpvGetStats
     struct Timer {
@@ -277,6 +282,13 @@ dpv_status prepare(dpv_device dev) {
     P.nbricks = dev->nranks;
     P.order_stride = (F.flags & DPV_FRAME_ORDER) ? dev->nranks : 0;
     P.items_cap = 0;
+    // floats of shared memory per staged slab box; DPV_BOX_CAP overrides it
+    // (tuning, and tests that force the unstaged fallback of large slabs)
+    P.box_cap = 6144;
+    if (const char* env = getenv("DPV_BOX_CAP")) {
+        int v = atoi(env);
+        if (v >= 8 && v <= 40000) P.box_cap = v;
+    }
 
     // brick table
     std::vector<BrickDev> table(dev->nranks);
@@ -298,7 +310,34 @@ dpv_status prepare(dpv_device dev) {
         b.sxy = h.s_n[0] * h.s_n[1];
         b.scale_idx = k;
         b.pad = 0;
+        b.quad = nullptr;
+        b.qx = h.s_n[0] - 1;
+        b.qxy = (h.s_n[0] - 1) * (h.s_n[1] - 1);
     }
+    // gather layout (default): built once per committed brick
+    if (!(F.flags & DPV_FRAME_LINEAR)) {
+        for (int k = 0; k < dev->nranks; ++k) {
+            HostBrick& h = dev->bricks[k];
+            size_t qb = quad_bytes(h.dtype, h.s_n);
+            if (h.quad && h.quad_bytes != qb) {
+                dev_free(h.quad);
+                h.quad = nullptr;
+                h.quad_valid = false;
+            }
+            if (!h.quad) {
+                dpv_status s2 = dev_alloc(dev, &h.quad, qb, "gather layout");
+                if (s2) return s2;
+                h.quad_bytes = qb;
+                h.quad_valid = false;
+            }
+            if (!h.quad_valid) {
+                CK(launch_build_quad(h.dtype, h.data, h.s_n, h.quad, dev->stream), "build gather layout");
+                h.quad_valid = true;
+            }
+            table[k].quad = h.quad;
+        }
+    }
+    dev->use_quad = !(F.flags & DPV_FRAME_LINEAR);
     if (!dev->d_bricks) {
         dpv_status s = dev_alloc(dev, (void**)&dev->d_bricks, sizeof(BrickDev) * MAX_RANKS, "brick table");
         if (s) return s;
@@ -447,6 +486,7 @@ dpv_status dpvSetVolumeGeometry(dpv_device dev, const int dims[3], const float o
     DeviceGuard g(dev->cuda_device);
     for (auto& b : dev->bricks) {
         dev_free(b.data);
+        dev_free(b.quad);
         b = HostBrick();
     }
     for (int a = 0; a < 3; ++a) {
@@ -542,6 +582,9 @@ dpv_status dpvCommitBrick(dpv_device dev, int rank, const dpv_brick_desc* d) {
     }
     if (e != cudaSuccess) return cuda_fail(dev, e, "brick commit");
     nb.committed = true;
+    nb.quad = hb.quad;                  // the gather layout is rebuilt at the next render
+    nb.quad_bytes = hb.quad_bytes;
+    nb.quad_valid = false;
     hb = nb;
     dev->dirty = true;
     return DPV_OK;
@@ -628,9 +671,16 @@ dpv_status dpvRenderFrame(dpv_device dev) {
        "cull");
     stage_stop(dev, DPV_STAGE_CULL, t0);
     t0 = stage_start(dev);
-    CK(launch_march_fwd(dev->bricks[0].dtype, P, inv_sp, dev->d_cams, dev->d_bricks, dev->d_scales, dev->d_items,
-                        dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters, dev->stream),
-       "march");
+    if (!(dev->frame.flags & DPV_FRAME_STAGED))
+        CK(launch_march_fwd(dev->bricks[0].dtype, dev->use_quad, P, dev->d_cams, dev->d_bricks, dev->d_scales,
+                            dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters,
+                            dev->stream),
+           "march");
+    else
+        CK(launch_march_fwd_staged(dev->bricks[0].dtype, P, dev->d_cams, dev->d_bricks, dev->d_scales, dev->d_items,
+                                   dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters,
+                                   dev->stream),
+           "march");
     stage_stop(dev, DPV_STAGE_MARCH, t0);
     t0 = stage_start(dev);
     CK(launch_composite_fwd(P, inv_sp, dev->d_cams, dev->d_tile_first, dev->d_tile_count, dev->d_items,
@@ -769,10 +819,16 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
        "composite backward");
     stage_stop(dev, DPV_STAGE_COMPOSITE_BWD, t0);
     t0 = stage_start(dev);
-    CK(launch_march_bwd(dev->bricks[0].dtype, P, 1.0f / dev->spacing, dev->d_cams, dev->d_bricks, dev->d_scales,
-                        dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_frag_grad,
-                        dL_dtf, dL_dvol, dev->d_counters, dev->stream),
-       "march backward");
+    if (!(dev->frame.flags & DPV_FRAME_STAGED))
+        CK(launch_march_bwd(dev->bricks[0].dtype, dev->use_quad, P, dev->d_cams, dev->d_bricks, dev->d_scales,
+                            dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key,
+                            dev->d_frag_grad, dL_dtf, dL_dvol, dev->d_counters, dev->stream),
+           "march backward");
+    else
+        CK(launch_march_bwd_staged(dev->bricks[0].dtype, P, dev->d_cams, dev->d_bricks, dev->d_scales, dev->d_items,
+                                   dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_frag_grad,
+                                   dL_dtf, dL_dvol, dev->d_counters, dev->stream),
+           "march backward");
     stage_stop(dev, DPV_STAGE_MARCH_BWD, t0);
     dev->launches += 1 + (dev->n_items > 0 ? 1 : 0);
     return DPV_OK;
@@ -829,7 +885,10 @@ dpv_status dpvRelease(dpv_device dev) {
     {
         DeviceGuard g(dev->cuda_device);
         if (!dev->poisoned && dev->stream) cudaStreamSynchronize(dev->stream);
-        for (auto& b : dev->bricks) dev_free(b.data);
+        for (auto& b : dev->bricks) {
+            dev_free(b.data);
+            dev_free(b.quad);
+        }
         free_schedule(dev);
         free_frags(dev);
         dev_free(dev->d_scales);

@@ -19,7 +19,9 @@ constexpr int MAX_TF = 4096;
 constexpr int KR = 16;                   // fragments a pixel sorts in registers
 
 // device error bits (Counters::err)
-constexpr unsigned ERR_ITEM_OVERFLOW = 1u;   // culling listed more items than sized for
+constexpr unsigned ERR_ITEM_OVERFLOW = 1u;     // culling listed more items than sized for
+constexpr unsigned ERR_STAGE_OUTSIDE = 2u;     // a staged sample fell outside its slab box (clamped)
+constexpr unsigned ERR_STAGE_INCOMPLETE = 4u;  // a staged ray ended with unmarched samples
 
 // One camera, prepared on the device: eye in node coordinates and the
 // orthonormal look-at basis (world directions are node directions up to the
@@ -47,6 +49,10 @@ struct BrickDev {
     int sx, sxy;       // strides of y and z in nodes
     int scale_idx;     // index into the device scale array
     int pad;
+    const void* quad;  // gather layout (see Quad) or null: per cell (x, y) of
+                       // every z layer, the 2x2 corners v(x,y) v(x+1,y)
+                       // v(x,y+1) v(x+1,y+1) packed in one vector
+    int qx, qxy;       // strides of the gather layout: s_n[0]-1, (s_n[0]-1)(s_n[1]-1)
 };
 
 // A work item: one brick seen through one screen tile of one camera.
@@ -83,6 +89,7 @@ struct FrameParams {
     int nbricks;
     int order_stride;  // bytes per pixel of the order image (0 = off)
     int items_cap;     // work items the list and fragment pool hold
+    int box_cap;       // floats of shared memory per slab box (staged march)
     const float4* rays;// per camera and pixel: (d, t_enter), (1/d, t_exit); see k_rays
 };
 
@@ -207,30 +214,85 @@ struct Storage<__nv_fp8_e4m3> {
     static constexpr bool unit_scale = false;
 };
 
+// Four corners of one (x, y) cell face packed in the gather layout.
+template <typename T>
+struct Quad;
+template <>
+struct Quad<float> {
+    using W = float4;
+    static __device__ __forceinline__ void unpack(W w, float& a, float& b, float& c, float& d) {
+        a = w.x;
+        b = w.y;
+        c = w.z;
+        d = w.w;
+    }
+};
+template <>
+struct Quad<__half> {
+    using W = uint2;
+    static __device__ __forceinline__ void unpack(W w, float& a, float& b, float& c, float& d) {
+        a = __half2float(__ushort_as_half((unsigned short)(w.x & 0xffffu)));
+        b = __half2float(__ushort_as_half((unsigned short)(w.x >> 16)));
+        c = __half2float(__ushort_as_half((unsigned short)(w.y & 0xffffu)));
+        d = __half2float(__ushort_as_half((unsigned short)(w.y >> 16)));
+    }
+};
+template <>
+struct Quad<__nv_bfloat16> {
+    using W = uint2;
+    static __device__ __forceinline__ void unpack(W w, float& a, float& b, float& c, float& d) {
+        a = __uint_as_float(w.x << 16);
+        b = __uint_as_float(w.x & 0xffff0000u);
+        c = __uint_as_float(w.y << 16);
+        d = __uint_as_float(w.y & 0xffff0000u);
+    }
+};
+template <>
+struct Quad<__nv_fp8_e4m3> {
+    using W = unsigned int;
+    static __device__ __forceinline__ float dec(unsigned int byte) {
+        return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)byte, __NV_E4M3)));
+    }
+    static __device__ __forceinline__ void unpack(W w, float& a, float& b, float& c, float& d) {
+        a = dec(w & 0xffu);
+        b = dec((w >> 8) & 0xffu);
+        c = dec((w >> 16) & 0xffu);
+        d = dec(w >> 24);
+    }
+};
+
 // Trilinear value at brick-local node coordinates q (x fastest): cell
 // i = clamp(floor(q), 0, n - 2), weights q - i, lerp in x, then y, then z.
-// The per-brick scale multiplies the interpolated value (equal to scaling
-// each corner, up to rounding).  Returns the cell base index and weights for
-// the adjoint.
-template <typename T>
+// The eight corners come either from the stored nodes (eight loads) or from
+// the gather layout (two vector loads, identical values).  The per-brick
+// scale multiplies the interpolated value (equal to scaling each corner, up
+// to rounding).  Returns the cell and weights for the adjoint.
+template <typename T, bool QUAD>
 __device__ __forceinline__ float trilinear(const BrickDev& b, const T* data, float scale, float qx, float qy,
-                                           float qz, int& base, float& fx, float& fy, float& fz) {
-    int ix = min(max(__float2int_rd(qx), 0), b.s_n[0] - 2);
-    int iy = min(max(__float2int_rd(qy), 0), b.s_n[1] - 2);
-    int iz = min(max(__float2int_rd(qz), 0), b.s_n[2] - 2);
+                                           float qz, int& ix, int& iy, int& iz, float& fx, float& fy, float& fz) {
+    ix = min(max(__float2int_rd(qx), 0), b.s_n[0] - 2);
+    iy = min(max(__float2int_rd(qy), 0), b.s_n[1] - 2);
+    iz = min(max(__float2int_rd(qz), 0), b.s_n[2] - 2);
     fx = qx - (float)ix;
     fy = qy - (float)iy;
     fz = qz - (float)iz;
-    base = ix + iy * b.sx + iz * b.sxy;
-    const T* p = data + base;
-    float v000 = Storage<T>::load(p, 0);
-    float v100 = Storage<T>::load(p, 1);
-    float v010 = Storage<T>::load(p, b.sx);
-    float v110 = Storage<T>::load(p, b.sx + 1);
-    float v001 = Storage<T>::load(p, b.sxy);
-    float v101 = Storage<T>::load(p, b.sxy + 1);
-    float v011 = Storage<T>::load(p, b.sxy + b.sx);
-    float v111 = Storage<T>::load(p, b.sxy + b.sx + 1);
+    float v000, v100, v010, v110, v001, v101, v011, v111;
+    if (QUAD) {
+        using W = typename Quad<T>::W;
+        const W* q = reinterpret_cast<const W*>(b.quad) + (ix + iy * b.qx + iz * b.qxy);
+        Quad<T>::unpack(__ldg(q), v000, v100, v010, v110);
+        Quad<T>::unpack(__ldg(q + b.qxy), v001, v101, v011, v111);
+    } else {
+        const T* p = data + (ix + iy * b.sx + iz * b.sxy);
+        v000 = Storage<T>::load(p, 0);
+        v100 = Storage<T>::load(p, 1);
+        v010 = Storage<T>::load(p, b.sx);
+        v110 = Storage<T>::load(p, b.sx + 1);
+        v001 = Storage<T>::load(p, b.sxy);
+        v101 = Storage<T>::load(p, b.sxy + 1);
+        v011 = Storage<T>::load(p, b.sxy + b.sx);
+        v111 = Storage<T>::load(p, b.sxy + b.sx + 1);
+    }
     float x00 = fmaf(fx, v100 - v000, v000);
     float x10 = fmaf(fx, v110 - v010, v010);
     float x01 = fmaf(fx, v101 - v001, v001);
@@ -270,6 +332,74 @@ __device__ __forceinline__ TFSample tf_lookup(const float4* tab, const FramePara
 // Opacity of one sample: 1 - exp(-sigma_max * a * dt).
 __device__ __forceinline__ float sample_alpha(const FrameParams& P, float a) {
     return -expm1f(-P.sigma_max * a * P.dt);
+}
+
+// ---------------------------------------------------------------------------
+// one ray through one brick
+// ---------------------------------------------------------------------------
+struct MarchState {
+    int j0, j1;        // sample range [j0, j1)
+    float te;          // t_enter of the ray in the volume
+    float q0[3];       // brick-local node position of sample j0
+    float st[3];       // brick-local step per sample
+};
+
+// Ray of pixel (px, py) against brick b: its sample range and the local
+// frame.  Returns false when the brick holds no sample of the ray.
+__device__ __forceinline__ bool brick_samples(const FrameParams& P, const CamBasis& cam, int c, const BrickDev& b,
+                                              int px, int py, MarchState& m) {
+    Ray r;
+    load_ray(cam, P, c, px, py, r);
+    if (!(r.te < r.tx)) return false;
+    float t0 = r.te, t1 = r.tx;
+    ray_box(r.o, r.d, r.inv, b.r0, b.r1, b.closed, t0, t1);
+    if (!(t0 < t1)) return false;
+    m.j0 = first_sample_at(t0, r.te, P);
+    m.j1 = first_sample_at(t1, r.te, P);
+    if (m.j0 >= m.j1) return false;
+    m.te = r.te;
+    float tj = r.te + ((float)m.j0 + 0.5f) * P.dt;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float ol = r.o[a] - (float)b.s_lo[a];
+        m.q0[a] = fmaf(tj, r.d[a], ol);
+        m.st[a] = P.dt * r.d[a];
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// gradient accumulation runs (adjoint march)
+// ---------------------------------------------------------------------------
+struct TFRun {
+    int i0 = -1;
+    float a[8];        // entry i0 (rgba), entry i0+1 (rgba)
+};
+
+__device__ __forceinline__ void tf_flush(TFRun& r, double* s_g) {
+    if (r.i0 < 0) return;
+    double* e = s_g + 4 * r.i0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (r.a[c] != 0.0f) atomicAdd(e + c, (double)r.a[c]);
+}
+
+struct CellRun {
+    long long base = -1;   // global index of the cell's (0,0,0) node
+    float a[8];
+};
+
+__device__ __forceinline__ void cell_flush(CellRun& r, float* dvol, long long sy, long long sz) {
+    if (r.base < 0) return;
+    float* v = dvol + r.base;
+    atomicAdd(v, r.a[0]);
+    atomicAdd(v + 1, r.a[1]);
+    atomicAdd(v + sy, r.a[2]);
+    atomicAdd(v + sy + 1, r.a[3]);
+    atomicAdd(v + sz, r.a[4]);
+    atomicAdd(v + sz + 1, r.a[5]);
+    atomicAdd(v + sz + sy, r.a[6]);
+    atomicAdd(v + sz + sy + 1, r.a[7]);
 }
 
 // ---------------------------------------------------------------------------

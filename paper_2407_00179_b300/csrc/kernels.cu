@@ -8,6 +8,8 @@
 // front to back in one kernel (§5.1.1, "Compositing").  The paper's parallel
 // direct send is replaced by the compositor reading every logical rank's
 // fragments straight from HBM.
+#include <stdlib.h>
+
 #include "dpv_internal.cuh"
 #include "launch.h"
 
@@ -354,42 +356,10 @@ cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 orig
 // RGBA, key = first sample index, or key = EMPTY).  The TF table is staged
 // in shared memory.
 
-struct MarchState {
-    int j0, j1;        // sample range [j0, j1)
-    float te;          // t_enter of the ray in the volume
-    float q0[3];       // brick-local node position of sample j0
-    float st[3];       // brick-local step per sample
-};
-
-// Ray of pixel (px, py) against brick b: its sample range and the local
-// frame.  Returns false when the brick holds no sample of the ray.
-__device__ __forceinline__ bool brick_samples(const FrameParams& P, const CamBasis& cam, int c, const BrickDev& b,
-                                              int px, int py, MarchState& m) {
-    Ray r;
-    load_ray(cam, P, c, px, py, r);
-    if (!(r.te < r.tx)) return false;
-    float t0 = r.te, t1 = r.tx;
-    ray_box(r.o, r.d, r.inv, b.r0, b.r1, b.closed, t0, t1);
-    if (!(t0 < t1)) return false;
-    m.j0 = first_sample_at(t0, r.te, P);
-    m.j1 = first_sample_at(t1, r.te, P);
-    if (m.j0 >= m.j1) return false;
-    m.te = r.te;
-    float tj = r.te + ((float)m.j0 + 0.5f) * P.dt;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float ol = r.o[a] - (float)b.s_lo[a];
-        m.q0[a] = fmaf(tj, r.d[a], ol);
-        m.st[a] = P.dt * r.d[a];
-    }
-    return true;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, float inv_spacing, const CamBasis* cams,
-                                                   const BrickDev* bricks, const float* scales, const Item* items,
-                                                   const float4* tf, float4* frag_rgba, int* frag_key,
-                                                   Counters* counters) {
+template <typename T, bool QUAD>
+__global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
+                                                   const float* scales, const Item* items, const float4* tf,
+                                                   float4* frag_rgba, int* frag_key, Counters* counters) {
     extern __shared__ float4 s_tf[];
     for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
     __syncthreads();
@@ -413,10 +383,10 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, float inv_spac
             int k = 0;
             for (; k < n; ++k) {
                 float fk = (float)k;
-                int base;
+                int ix, iy, iz;
                 float fx, fy, fz;
-                float s = trilinear<T>(b, data, scale, fmaf(fk, m.st[0], m.q0[0]), fmaf(fk, m.st[1], m.q0[1]),
-                                       fmaf(fk, m.st[2], m.q0[2]), base, fx, fy, fz);
+                float s = trilinear<T, QUAD>(b, data, scale, fmaf(fk, m.st[0], m.q0[0]), fmaf(fk, m.st[1], m.q0[1]),
+                                             fmaf(fk, m.st[2], m.q0[2]), ix, iy, iz, fx, fy, fz);
                 TFSample c = tf_lookup(s_tf, P, s);
                 float al = sample_alpha(P, c.v.w);
                 float ta = Tr * al;
@@ -440,24 +410,32 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, float inv_spac
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
 
-cudaError_t launch_march_fwd(int dtype, const FrameParams& P, float inv_spacing, const CamBasis* cams,
+template <typename T, bool QUAD>
+static void fwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
+                       const Item* items, int n_items, const float4* tf, float4* frag_rgba, int* frag_key,
+                       Counters* counters, cudaStream_t st) {
+    size_t smem = sizeof(float4) * P.ntf;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_march_fwd<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_march_fwd<T, QUAD><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
+                                                      counters);
+}
+
+cudaError_t launch_march_fwd(int dtype, bool quad, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
                              cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-    size_t smem = sizeof(float4) * P.ntf;
-    if (smem > 48 * 1024) {
-        cudaFuncSetAttribute(k_march_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_march_fwd<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_march_fwd<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_march_fwd<__nv_fp8_e4m3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
+#define FWD(T)                                                                                               \
+    (quad ? fwd_launch<T, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, st) \
+          : fwd_launch<T, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, st))
     switch (dtype) {
-        case 0: k_march_fwd<float><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, counters); break;
-        case 1: k_march_fwd<__half><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, counters); break;
-        case 2: k_march_fwd<__nv_bfloat16><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, counters); break;
-        default: k_march_fwd<__nv_fp8_e4m3><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, counters); break;
+        case 0: FWD(float); break;
+        case 1: FWD(__half); break;
+        case 2: FWD(__nv_bfloat16); break;
+        default: FWD(__nv_fp8_e4m3); break;
     }
+#undef FWD
     return cudaGetLastError();
 }
 
@@ -705,53 +683,45 @@ cudaError_t launch_composite_bwd(const FrameParams& P, const int* tile_first, co
 //
 // Accumulation: consecutive samples of a ray usually fall in the same TF
 // segment and the same cell, so each thread sums its gradient in registers
-// while the segment (cell) stays the same and flushes on change.  TF
-// flushes go to an FP64 table in shared memory (the entries are sums of
-// many terms of both signs), which is added to the global FP64 table once
-// per CTA; voxel flushes are eight FP32 atomics into the global field.
+// while the segment (cell) stays the same and flushes on change.  Nearby
+// rays share TF segments, so a single shared table would serialise the
+// flushes of a warp on the same addresses; the CTA keeps `ncopy` FP32 copies
+// of the TF gradient table, lane l writing copy l % ncopy (copies offset by
+// one float so equal entries of different copies sit in different banks).
+// At the end the copies are summed and added to the global FP64 table once
+// per touched entry.  Voxel flushes are eight FP32 atomics into the global
+// field.
 
-struct TFRun {
+struct TFRunF {
     int i0 = -1;
     float a[8];        // entry i0 (rgba), entry i0+1 (rgba)
 };
 
-__device__ __forceinline__ void tf_flush(TFRun& r, double* s_g) {
+__device__ __forceinline__ void tf_flush_f(TFRunF& r, float* tab) {
     if (r.i0 < 0) return;
-    double* e = s_g + 4 * r.i0;
+    float* e = tab + 4 * r.i0;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
-        if (r.a[c] != 0.0f) atomicAdd(e + c, (double)r.a[c]);
+        if (r.a[c] != 0.0f) atomicAdd(e + c, r.a[c]);
 }
 
-struct CellRun {
-    long long base = -1;   // global index of the cell's (0,0,0) node
-    float a[8];
-};
-
-__device__ __forceinline__ void cell_flush(CellRun& r, float* dvol, long long sy, long long sz) {
-    if (r.base < 0) return;
-    float* v = dvol + r.base;
-    atomicAdd(v, r.a[0]);
-    atomicAdd(v + 1, r.a[1]);
-    atomicAdd(v + sy, r.a[2]);
-    atomicAdd(v + sy + 1, r.a[3]);
-    atomicAdd(v + sz, r.a[4]);
-    atomicAdd(v + sz + 1, r.a[5]);
-    atomicAdd(v + sz + sy, r.a[6]);
-    atomicAdd(v + sz + sy + 1, r.a[7]);
+int bwd_tf_copies(int ntf) {
+    int c = 8192 / ntf;
+    return c < 1 ? 1 : (c > 8 ? 8 : c);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spacing, const CamBasis* cams,
-                                                   const BrickDev* bricks, const float* scales, const Item* items,
-                                                   const float4* tf, const float4* frag_rgba, const int* frag_key,
-                                                   const float4* frag_grad, double* dtf, float* dvol,
+template <typename T, bool QUAD>
+__global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
+                                                   const float* scales, const Item* items, const float4* tf,
+                                                   const float4* frag_rgba, const int* frag_key,
+                                                   const float4* frag_grad, int ncopy, double* dtf, float* dvol,
                                                    Counters* counters) {
     extern __shared__ float4 s_mem[];
     float4* s_tf = s_mem;
-    double* s_g = (double*)(s_mem + P.ntf);
+    float* s_g = (float*)(s_mem + P.ntf);
+    const int stride = 4 * P.ntf + 1;
     for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
-    for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) s_g[i] = 0.0;
+    for (int i = threadIdx.x; i < ncopy * stride; i += blockDim.x) s_g[i] = 0.0f;
     __syncthreads();
 
     Item it = items[blockIdx.x];
@@ -768,6 +738,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spac
     unsigned long long nsamp = 0;
     const float gscale = Storage<T>::unit_scale ? 1.0f : scale;
     const long long sy = P.dims[0], sz = (long long)P.dims[0] * P.dims[1];
+    float* my_tab = s_g + (threadIdx.x % ncopy) * stride;
     if (valid && px < P.W && py < P.H && frag_key[slot] != KEY_EMPTY) {
         MarchState m;
         float4 F = frag_rgba[slot];
@@ -776,15 +747,15 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spac
             float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.0f;
             float Tend = 1.0f - F.w;
             int n = m.j1 - m.j0;
-            TFRun tr;
+            TFRunF tr;
             CellRun cr;
             const long long gofs = (long long)b.s_lo[2] * sz + (long long)b.s_lo[1] * sy + b.s_lo[0];
             for (int k = 0; k < n; ++k) {
                 float fk = (float)k;
-                int base;
+                int ix, iy, iz;
                 float fx, fy, fz;
-                float s = trilinear<T>(b, data, scale, fmaf(fk, m.st[0], m.q0[0]), fmaf(fk, m.st[1], m.q0[1]),
-                                       fmaf(fk, m.st[2], m.q0[2]), base, fx, fy, fz);
+                float s = trilinear<T, QUAD>(b, data, scale, fmaf(fk, m.st[0], m.q0[0]), fmaf(fk, m.st[1], m.q0[1]),
+                                             fmaf(fk, m.st[2], m.q0[2]), ix, iy, iz, fx, fy, fz);
                 TFSample c = tf_lookup(s_tf, P, s);
                 float al = sample_alpha(P, c.v.w);
                 float ta = Tr * al;
@@ -797,7 +768,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spac
                 float g_r = G.x * ta, g_g = G.y * ta, g_b = G.z * ta;
                 float g_a = gal * P.sigma_max * P.dt * om;
                 if (c.i0 != tr.i0) {
-                    tf_flush(tr, s_g);
+                    tf_flush_f(tr, my_tab);
                     tr.i0 = c.i0;
 #pragma unroll
                     for (int q = 0; q < 8; ++q) tr.a[q] = 0.0f;
@@ -816,8 +787,6 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spac
                     float gs = (g_r * (ta1.x - ta0.x) + g_g * (ta1.y - ta0.y) + g_b * (ta1.z - ta0.z) +
                                 g_a * (ta1.w - ta0.w)) * c.duds * gscale;
                     if (gs != 0.0f) {
-                        // brick-local cell -> global node index of its (0,0,0) corner
-                        int iz = base / b.sxy, rem = base - iz * b.sxy, iy = rem / b.sx, ix = rem - iy * b.sx;
                         long long gb = gofs + (long long)iz * sz + (long long)iy * sy + ix;
                         if (gb != cr.base) {
                             cell_flush(cr, dvol, sy, sz);
@@ -844,7 +813,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spac
                 ++nsamp;
                 if (P.ert_on && 1.0f - Tr > P.ert) break;
             }
-            tf_flush(tr, s_g);
+            tf_flush_f(tr, my_tab);
             if (dvol) cell_flush(cr, dvol, sy, sz);
         }
     }
@@ -852,29 +821,87 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, float inv_spac
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) {
-        double v = s_g[i];
-        if (v != 0.0) atomicAdd(dtf + i, v);
+        float v = 0.0f;
+        for (int c = 0; c < ncopy; ++c) v += s_g[c * stride + i];
+        if (v != 0.0f) atomicAdd(dtf + i, (double)v);
     }
 }
 
-cudaError_t launch_march_bwd(int dtype, const FrameParams& P, float inv_spacing, const CamBasis* cams,
+template <typename T, bool QUAD>
+static void bwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
+                       const Item* items, int n_items, const float4* tf, const float4* frag_rgba, const int* frag_key,
+                       const float4* frag_grad, double* dtf, float* dvol, Counters* counters, cudaStream_t st) {
+    int ncopy = bwd_tf_copies(P.ntf);
+    size_t smem = sizeof(float4) * P.ntf + sizeof(float) * (size_t)ncopy * (4 * P.ntf + 1);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_march_bwd<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_march_bwd<T, QUAD><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
+                                                      frag_grad, ncopy, dtf, dvol, counters);
+}
+
+cudaError_t launch_march_bwd(int dtype, bool quad, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, const float4* frag_rgba, const int* frag_key,
                              const float4* frag_grad, double* dtf, float* dvol, Counters* counters,
                              cudaStream_t st) {
     if (n_items == 0) return cudaSuccess;
-    size_t smem = sizeof(float4) * P.ntf + sizeof(double) * 4 * P.ntf;
-    if (smem > 48 * 1024) {
-        cudaFuncSetAttribute(k_march_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_march_bwd<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_march_bwd<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_march_bwd<__nv_fp8_e4m3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
+#define BWD(T)                                                                                                 \
+    (quad ? bwd_launch<T, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, \
+                                dvol, counters, st)                                                             \
+          : bwd_launch<T, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, \
+                                 dvol, counters, st))
     switch (dtype) {
-        case 0: k_march_bwd<float><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol, counters); break;
-        case 1: k_march_bwd<__half><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol, counters); break;
-        case 2: k_march_bwd<__nv_bfloat16><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol, counters); break;
-        default: k_march_bwd<__nv_fp8_e4m3><<<n_items, P.tp, smem, st>>>(P, inv_spacing, cams, bricks, scales, items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol, counters); break;
+        case 0: BWD(float); break;
+        case 1: BWD(__half); break;
+        case 2: BWD(__nv_bfloat16); break;
+        default: BWD(__nv_fp8_e4m3); break;
+    }
+#undef BWD
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// gather layout (quad): per cell face the 2 x 2 corners in one vector
+// ===========================================================================
+
+template <typename T>
+__global__ void k_build_quad(const T* src, int sx, int sy, int sz, typename Quad<T>::W* dst) {
+    using W = typename Quad<T>::W;
+    long long qx = sx - 1, qxy = (long long)(sx - 1) * (sy - 1);
+    long long n = qxy * sz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        long long z = i / qxy, r = i - z * qxy, y = r / qx, x = r - y * qx;
+        long long o = (z * sy + y) * sx + x;
+        W w;
+        if constexpr (sizeof(T) == 4) {
+            const float* f = (const float*)src;
+            w = make_float4(f[o], f[o + 1], f[o + sx], f[o + sx + 1]);
+        } else if constexpr (sizeof(T) == 2) {
+            const unsigned short* h = (const unsigned short*)src;
+            w = make_uint2((unsigned)h[o] | ((unsigned)h[o + 1] << 16), (unsigned)h[o + sx] | ((unsigned)h[o + sx + 1] << 16));
+        } else {
+            const unsigned char* c = (const unsigned char*)src;
+            w = (unsigned)c[o] | ((unsigned)c[o + 1] << 8) | ((unsigned)c[o + sx] << 16) | ((unsigned)c[o + sx + 1] << 24);
+        }
+        dst[i] = w;
+    }
+}
+
+size_t quad_bytes(int dtype, const int s_n[3]) {
+    size_t cells = (size_t)(s_n[0] - 1) * (s_n[1] - 1) * s_n[2];
+    static const size_t w[4] = {16, 8, 8, 4};
+    return cells * w[dtype];
+}
+
+cudaError_t launch_build_quad(int dtype, const void* src, const int s_n[3], void* dst, cudaStream_t st) {
+    long long n = (long long)(s_n[0] - 1) * (s_n[1] - 1) * s_n[2];
+    long long nb = (n + 255) / 256;
+    int blocks = (int)(nb < 148LL * 32 ? nb : 148LL * 32);
+    switch (dtype) {
+        case 0: k_build_quad<float><<<blocks, 256, 0, st>>>((const float*)src, s_n[0], s_n[1], s_n[2], (float4*)dst); break;
+        case 1: k_build_quad<__half><<<blocks, 256, 0, st>>>((const __half*)src, s_n[0], s_n[1], s_n[2], (uint2*)dst); break;
+        case 2: k_build_quad<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)src, s_n[0], s_n[1], s_n[2], (uint2*)dst); break;
+        default: k_build_quad<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>((const __nv_fp8_e4m3*)src, s_n[0], s_n[1], s_n[2], (unsigned*)dst); break;
     }
     return cudaGetLastError();
 }

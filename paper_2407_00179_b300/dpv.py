@@ -21,6 +21,8 @@ DTYPES = {"f32": 0, "f16": 1, "bf16": 2, "fp8": 3}
 TORCH_STORAGE = {0: torch.float32, 1: torch.float16, 2: torch.bfloat16, 3: torch.float8_e4m3fn}
 KEY_EMPTY = 2 ** 31 - 1
 FRAME_ORDER = 1
+FRAME_STAGED = 2
+FRAME_LINEAR = 4
 STATUS = {0: "DPV_OK", 1: "DPV_ERR_INVALID_ARG", 2: "DPV_ERR_STATE", 3: "DPV_ERR_OUT_OF_MEMORY",
           4: "DPV_ERR_CUDA", 5: "DPV_ERR_TIMEOUT", 6: "DPV_ERR_UNSUPPORTED"}
 
@@ -244,9 +246,11 @@ class Device:
         self.ncam = len(cams)
 
     def set_frame(self, width: int, height: int, step_voxels: float = 0.5, sigma_max: float = 8.0, ert: float = 0.0,
-                  tile=(0, 0), order: bool = False):
+                  tile=(0, 0), order: bool = False, staged: bool = False, gather: str = "quad"):
+        flags = (FRAME_ORDER if order else 0) | (FRAME_STAGED if staged else 0) | (
+            FRAME_LINEAR if gather == "linear" else 0)
         f = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
-                      int(tile[1]), FRAME_ORDER if order else 0)
+                      int(tile[1]), flags)
         _check(load().dpvSetFrame(self._h, C.byref(f)))
         self.width, self.height = int(width), int(height)
 

@@ -26,6 +26,7 @@ class Scene:
     ert: float = 0.0
     storage: str = "f32"
     tile: tuple = (0, 0)
+    staged: bool = False
 
     @property
     def dims(self):
@@ -70,7 +71,7 @@ def gpu_device(sc: Scene, order=True):
     dev.set_tf(torch.from_numpy(sc.tf).cuda())
     dev.set_cameras(sc.cams)
     dev.set_frame(sc.width, sc.height, step_voxels=sc.step, sigma_max=sc.sigma_max, ert=sc.ert, tile=sc.tile,
-                  order=order)
+                  order=order, staged=sc.staged)
     return dev
 
 
