@@ -116,6 +116,12 @@ typedef struct {
                                       device builds from each committed brick at the next
                                       render and keeps (4x the brick's device memory);
                                       identical results */
+#define DPV_FRAME_PERSISTENT 8     /* persistent ray-march: a grid sized to the GPU pulls
+                                      work items from a counter in brick-major order (all
+                                      cameras' tiles of one brick together) */
+#define DPV_FRAME_GRAPH 16         /* replay the frame's launches from a CUDA graph
+                                      captured at the first render after a change (not
+                                      while profiling is on) */
 
 /* Frame parameters, identical on all ranks (§3.1.1).  Every camera renders
  * a width x height image.  tile_w/tile_h: pixels per work item (multiples
@@ -155,6 +161,7 @@ typedef struct {
     double stage_ms[DPV_NUM_STAGES];
     uint32_t stage_calls[DPV_NUM_STAGES];
     uint64_t kernel_launches;
+    uint64_t graph_launches;      /* frames replayed from a CUDA graph since the reset */
 } dpv_stats;
 
 /* Create a device for `num_ranks` logical ranks (1..255) on CUDA device
@@ -239,6 +246,23 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
 
 /* Counters (synchronises the device stream). */
 dpv_status dpvGetStats(dpv_device dev, dpv_stats* out);
+
+/* Result of dpvAutotune. */
+typedef struct {
+    int tile_w, tile_h;   /* chosen tile */
+    int flags;            /* chosen DPV_FRAME_LINEAR / DPV_FRAME_PERSISTENT bits */
+    float ms;             /* mean device time of one frame with the choice */
+    int candidates;       /* configurations timed */
+} dpv_tune_result;
+
+/* Autotuner: time candidate launch configurations of the current scene --
+ * tile shape (16x16, 32x8, 8x32, 64x4) x gather layout (quad, linear) x
+ * schedule (one CTA per work item, persistent brick-major) -- rendering
+ * `frames` frames each after one warm-up frame, and keep the fastest in the
+ * device's frame parameters (other flags are kept).  Needs a renderable
+ * device; blocks the host until done; the last rendered frame is the best
+ * candidate's. */
+dpv_status dpvAutotune(dpv_device dev, int frames, dpv_tune_result* out);
 
 /* Clear the accumulated stage times and the launch count. */
 dpv_status dpvResetStats(dpv_device dev);

@@ -108,6 +108,20 @@ struct dpv_device_t {
     bool rendered = false;
     bool use_quad = false;
 
+    // persistent schedule (DPV_FRAME_PERSISTENT)
+    int* d_sched = nullptr;
+    int* d_hist = nullptr;              // nranks + 1 each
+    int* d_offsets = nullptr;
+    int* d_cursor = nullptr;
+    unsigned long long* d_tmp64 = nullptr;
+    unsigned int* d_work = nullptr;
+    size_t sched_cap = 0;
+
+    // CUDA graph of the per-frame launches (DPV_FRAME_GRAPH)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_failed = false;
+
     // profiling: event pairs around stages, resolved by dpvGetStats
     struct Timer {
         int stage;
@@ -119,6 +133,7 @@ struct dpv_device_t {
     double stage_ms[DPV_NUM_STAGES] = {0};
     uint32_t stage_calls[DPV_NUM_STAGES] = {0};
     uint64_t launches = 0;
+    uint64_t graph_launches = 0;
 };
 
 namespace {
@@ -223,6 +238,12 @@ void free_schedule(dpv_device dev) {
     dev->d_tile_count = dev->d_tile_first = nullptr;
     dev->d_items = nullptr;
     dev->items_cap = 0;
+}
+
+void free_graph(dpv_device dev) {
+    if (dev->graph) cudaGraphExecDestroy(dev->graph);
+    dev->graph = nullptr;
+    dev->graph_failed = false;
 }
 
 void free_frags(dpv_device dev) {
@@ -403,6 +424,22 @@ dpv_status prepare(dpv_device dev) {
     P.items_cap = dev->items_cap;
     if ((s = dev_alloc(dev, (void**)&dev->d_items, sizeof(Item) * (size_t)std::max(1, dev->items_cap), "work list")))
         return s;
+    // pull-order buffers of the persistent launches
+    if ((size_t)std::max(1, dev->items_cap) > dev->sched_cap) {
+        dev_free(dev->d_sched);
+        dev->d_sched = nullptr;
+        dev->sched_cap = 0;
+        if ((s = dev_alloc(dev, (void**)&dev->d_sched, sizeof(int) * (size_t)std::max(1, dev->items_cap), "schedule")))
+            return s;
+        dev->sched_cap = (size_t)std::max(1, dev->items_cap);
+    }
+    if (!dev->d_hist) {
+        if ((s = dev_alloc(dev, (void**)&dev->d_hist, sizeof(int) * (MAX_RANKS + 1) * 3 + 64, "schedule"))) return s;
+        dev->d_offsets = dev->d_hist + (MAX_RANKS + 1);
+        dev->d_cursor = dev->d_hist + 2 * (MAX_RANKS + 1);
+        if ((s = dev_alloc(dev, (void**)&dev->d_tmp64, 64, "schedule"))) return s;
+        dev->d_work = (unsigned int*)(dev->d_tmp64 + 1);
+    }
     // an invalid item (all bits set) until the first fill writes the list
     CK(cudaMemsetAsync(dev->d_items, 0xFF, sizeof(Item) * (size_t)std::max(1, dev->items_cap), dev->stream),
        "clear work list");
@@ -435,8 +472,84 @@ dpv_status prepare(dpv_device dev) {
         if ((s = dev_alloc(dev, (void**)&dev->d_order, nord, "order image"))) return s;
         dev->order_cap = nord;
     }
+    free_graph(dev);
     dev->dirty = false;
     return DPV_OK;
+}
+
+// Issue one frame's launches on stream `st`: ray setup and culling, the
+// brick ray-march, the sort-last composite.  Stage timers are recorded only
+// when `timed` (not while capturing a graph).
+dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
+    const FrameParams& P = dev->P;
+    float3 og = make_float3(dev->origin[0], dev->origin[1], dev->origin[2]);
+    const bool persistent = (dev->frame.flags & DPV_FRAME_PERSISTENT) && !(dev->frame.flags & DPV_FRAME_STAGED);
+    CK(cudaMemsetAsync(dev->d_counters, 0, sizeof(Counters), st), "reset counters");
+    cudaEvent_t t0 = timed ? stage_start(dev) : nullptr;
+    CK(launch_cull(P, dev->d_cam_in, og, dev->spacing, dev->d_cams, dev->d_camd, dev->d_rays, dev->d_bricks,
+                   dev->d_rects, dev->d_tile_count, dev->d_tile_first, dev->d_items, dev->items_cap, dev->d_counters,
+                   true, st),
+       "cull");
+    Schedule sch{dev->d_sched, dev->d_work, 0};
+    if (persistent)
+        CK(launch_schedule(P, dev->d_items, dev->n_items, 1, dev->d_hist, dev->d_offsets, dev->d_cursor,
+                           dev->d_tmp64, dev->d_sched, st),
+           "schedule");
+    if (timed) stage_stop(dev, DPV_STAGE_CULL, t0);
+    t0 = timed ? stage_start(dev) : nullptr;
+    if (!(dev->frame.flags & DPV_FRAME_STAGED))
+        CK(launch_march_fwd(dev->bricks[0].dtype, dev->use_quad, P, dev->d_cams, dev->d_bricks, dev->d_scales,
+                            dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters,
+                            st, persistent ? &sch : nullptr),
+           "march");
+    else
+        CK(launch_march_fwd_staged(dev->bricks[0].dtype, P, dev->d_cams, dev->d_bricks, dev->d_scales, dev->d_items,
+                                   dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters, st),
+           "march");
+    if (timed) stage_stop(dev, DPV_STAGE_MARCH, t0);
+    t0 = timed ? stage_start(dev) : nullptr;
+    CK(launch_composite_fwd(P, 1.0f / dev->spacing, dev->d_cams, dev->d_tile_first, dev->d_tile_count, dev->d_items,
+                            dev->d_frag_rgba, dev->d_frag_key, dev->d_out_rgba, dev->d_out_depth,
+                            P.order_stride ? dev->d_order : nullptr, st),
+       "composite");
+    if (timed) stage_stop(dev, DPV_STAGE_COMPOSITE, t0);
+    dev->launches += 6 + (persistent ? 3 : 0) + (dev->n_items > 0 ? 1 : 0) + 1;
+    return DPV_OK;
+}
+
+// Capture the per-frame launches into a graph (once per prepared frame).
+// On a capture failure the device falls back to direct launches.
+void ensure_graph(dpv_device dev) {
+    if (dev->graph || dev->graph_failed) return;
+    if (!dev->cap_stream && cudaStreamCreateWithFlags(&dev->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        dev->graph_failed = true;
+        return;
+    }
+    cudaGraph_t g = nullptr;
+    uint64_t launches = dev->launches;
+    if (cudaStreamBeginCapture(dev->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        dev->graph_failed = true;
+        return;
+    }
+    dpv_status s = enqueue_render(dev, dev->cap_stream, false);
+    cudaError_t e = cudaStreamEndCapture(dev->cap_stream, &g);
+    dev->launches = launches;
+    if (s != DPV_OK || e != cudaSuccess || !g) {
+        cudaGetLastError();
+        dev->poisoned = false;                // a failed capture issued no work
+        if (g) cudaGraphDestroy(g);
+        dev->graph_failed = true;
+        return;
+    }
+    e = cudaGraphInstantiate(&dev->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        dev->graph = nullptr;
+        dev->graph_failed = true;
+    }
 }
 
 }  // namespace
@@ -661,34 +774,18 @@ dpv_status dpvRenderFrame(dpv_device dev) {
         if ((s = check_partition(dev))) return s;
         if ((s = prepare(dev))) return s;
     }
-    const FrameParams& P = dev->P;
-    float inv_sp = 1.0f / dev->spacing;
-    float3 og = make_float3(dev->origin[0], dev->origin[1], dev->origin[2]);
-    CK(cudaMemsetAsync(dev->d_counters, 0, sizeof(Counters), dev->stream), "reset counters");
-    cudaEvent_t t0 = stage_start(dev);
-    CK(launch_cull(P, dev->d_cam_in, og, dev->spacing, dev->d_cams, dev->d_camd, dev->d_rays, dev->d_bricks, dev->d_rects, dev->d_tile_count,
-                   dev->d_tile_first, dev->d_items, dev->items_cap, dev->d_counters, true, dev->stream),
-       "cull");
-    stage_stop(dev, DPV_STAGE_CULL, t0);
-    t0 = stage_start(dev);
-    if (!(dev->frame.flags & DPV_FRAME_STAGED))
-        CK(launch_march_fwd(dev->bricks[0].dtype, dev->use_quad, P, dev->d_cams, dev->d_bricks, dev->d_scales,
-                            dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters,
-                            dev->stream),
-           "march");
-    else
-        CK(launch_march_fwd_staged(dev->bricks[0].dtype, P, dev->d_cams, dev->d_bricks, dev->d_scales, dev->d_items,
-                                   dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters,
-                                   dev->stream),
-           "march");
-    stage_stop(dev, DPV_STAGE_MARCH, t0);
-    t0 = stage_start(dev);
-    CK(launch_composite_fwd(P, inv_sp, dev->d_cams, dev->d_tile_first, dev->d_tile_count, dev->d_items,
-                            dev->d_frag_rgba, dev->d_frag_key, dev->d_out_rgba, dev->d_out_depth,
-                            P.order_stride ? dev->d_order : nullptr, dev->stream),
-       "composite");
-    stage_stop(dev, DPV_STAGE_COMPOSITE, t0);
-    dev->launches += 6 + (dev->n_items > 0 ? 1 : 0) + 1;
+    if ((dev->frame.flags & DPV_FRAME_GRAPH) && !dev->profiling) {
+        ensure_graph(dev);
+        if (dev->graph) {
+            CK(cudaGraphLaunch(dev->graph, dev->stream), "graph launch");
+            ++dev->graph_launches;
+            dev->launches += 6 + ((dev->frame.flags & DPV_FRAME_PERSISTENT) ? 3 : 0) + (dev->n_items > 0 ? 1 : 0) + 1;
+        } else if ((s = enqueue_render(dev, dev->stream, true))) {
+            return s;
+        }
+    } else if ((s = enqueue_render(dev, dev->stream, true))) {
+        return s;
+    }
     CK(cudaEventRecord(dev->ev_done, dev->stream), "record");
     dev->rendered = true;
     return DPV_OK;
@@ -819,10 +916,13 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
        "composite backward");
     stage_stop(dev, DPV_STAGE_COMPOSITE_BWD, t0);
     t0 = stage_start(dev);
+    const bool persistent = (dev->frame.flags & DPV_FRAME_PERSISTENT) != 0;
+    Schedule sch{dev->d_sched, dev->d_work, 0};   // the pull order built by the render
     if (!(dev->frame.flags & DPV_FRAME_STAGED))
         CK(launch_march_bwd(dev->bricks[0].dtype, dev->use_quad, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                             dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key,
-                            dev->d_frag_grad, dL_dtf, dL_dvol, dev->d_counters, dev->stream),
+                            dev->d_frag_grad, dL_dtf, dL_dvol, dev->d_counters, dev->stream,
+                            persistent ? &sch : nullptr),
            "march backward");
     else
         CK(launch_march_bwd_staged(dev->bricks[0].dtype, P, dev->d_cams, dev->d_bricks, dev->d_scales, dev->d_items,
@@ -857,6 +957,71 @@ dpv_status dpvGetStats(dpv_device dev, dpv_stats* out) {
         out->stage_calls[i] = dev->stage_calls[i];
     }
     out->kernel_launches = dev->launches;
+    out->graph_launches = dev->graph_launches;
+    return DPV_OK;
+}
+
+dpv_status dpvAutotune(dpv_device dev, int frames, dpv_tune_result* out) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (frames < 1) return fail(DPV_ERR_INVALID_ARG, "frames must be >= 1");
+    if (!dev->has_frame) return fail(DPV_ERR_STATE, "no frame parameters");
+    DeviceGuard g(dev->cuda_device);
+    const dpv_frame_desc keep = dev->frame;
+    const int tune_bits = DPV_FRAME_LINEAR | DPV_FRAME_PERSISTENT | DPV_FRAME_STAGED;
+    const int tiles[4][2] = {{16, 16}, {32, 8}, {8, 32}, {64, 4}};
+    const int sched_bits[4] = {0, DPV_FRAME_LINEAR, DPV_FRAME_PERSISTENT, DPV_FRAME_PERSISTENT | DPV_FRAME_LINEAR};
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a), "tune event");
+    CK(cudaEventCreate(&b), "tune event");
+    const bool prof = dev->profiling;
+    dev->profiling = false;
+    float best = 1e30f;
+    dpv_frame_desc best_f = keep;
+    int tried = 0;
+    for (auto& t : tiles) {
+        for (int sb : sched_bits) {
+            dpv_frame_desc f = keep;
+            f.tile_w = t[0];
+            f.tile_h = t[1];
+            f.flags = (keep.flags & ~(tune_bits | DPV_FRAME_GRAPH)) | sb;
+            dev->frame = f;
+            dev->dirty = true;
+            if ((s = dpvRenderFrame(dev)) != DPV_OK) break;
+            CK(cudaEventRecord(a, dev->stream), "tune record");
+            for (int i = 0; i < frames && s == DPV_OK; ++i) s = dpvRenderFrame(dev);
+            if (s != DPV_OK) break;
+            CK(cudaEventRecord(b, dev->stream), "tune record");
+            CK(cudaEventSynchronize(b), "tune sync");
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, a, b), "tune time");
+            ms /= frames;
+            ++tried;
+            if (ms < best) {
+                best = ms;
+                best_f = f;
+            }
+        }
+        if (s != DPV_OK) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    dev->profiling = prof;
+    best_f.flags |= keep.flags & DPV_FRAME_GRAPH;
+    dev->frame = best_f;
+    dev->dirty = true;
+    if (s != DPV_OK) {
+        dev->frame = keep;
+        return s;
+    }
+    if ((s = dpvRenderFrame(dev)) != DPV_OK) return s;
+    if (out) {
+        out->tile_w = best_f.tile_w;
+        out->tile_h = best_f.tile_h;
+        out->flags = best_f.flags & tune_bits;
+        out->ms = best;
+        out->candidates = tried;
+    }
     return DPV_OK;
 }
 
@@ -870,6 +1035,7 @@ dpv_status dpvResetStats(dpv_device dev) {
         dev->stage_calls[i] = 0;
     }
     dev->launches = 0;
+    dev->graph_launches = 0;
     return DPV_OK;
 }
 
@@ -903,6 +1069,11 @@ dpv_status dpvRelease(dpv_device dev) {
         dev_free(dev->d_out_depth);
         dev_free(dev->d_order);
         dev_free(dev->d_counters);
+        dev_free(dev->d_sched);
+        dev_free(dev->d_hist);
+        dev_free(dev->d_tmp64);
+        free_graph(dev);
+        if (dev->cap_stream) cudaStreamDestroy(dev->cap_stream);
         if (dev->ev_done) cudaEventDestroy(dev->ev_done);
         for (auto& t : dev->pending) {
             cudaEventDestroy(t.a);

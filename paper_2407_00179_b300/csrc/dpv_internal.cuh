@@ -261,46 +261,89 @@ struct Quad<__nv_fp8_e4m3> {
     }
 };
 
+// The eight corners of the last cell a ray sampled, kept in registers:
+// consecutive samples (step < 1 voxel) mostly stay in the same cell, and a
+// step to the next cell in z shares a face; only what changed is loaded.
+// Used by the eight-load (linear) gather; the quad gather loads its two
+// faces every sample, which measures faster than the divergent reuse tests.
+template <typename T, bool QUAD>
+struct CornerCache {
+    int ix = -1, iy = -1, iz = -1;
+    float v[8];
+
+    __device__ __forceinline__ void face(const BrickDev& b, const T* data, int x, int y, int z, float& a, float& c,
+                                         float& d, float& e) const {
+        if (QUAD) {
+            using W = typename Quad<T>::W;
+            const W* q = reinterpret_cast<const W*>(b.quad) + (x + y * b.qx + z * b.qxy);
+            Quad<T>::unpack(__ldg(q), a, c, d, e);
+        } else {
+            const T* p = data + (x + y * b.sx + z * b.sxy);
+            a = Storage<T>::load(p, 0);
+            c = Storage<T>::load(p, 1);
+            d = Storage<T>::load(p, b.sx);
+            e = Storage<T>::load(p, b.sx + 1);
+        }
+    }
+
+    __device__ __forceinline__ void fetch(const BrickDev& b, const T* data, int x, int y, int z) {
+        if (x == ix && y == iy && z == iz) return;
+        if (x == ix && y == iy && z == iz + 1) {
+            v[0] = v[4];
+            v[1] = v[5];
+            v[2] = v[6];
+            v[3] = v[7];
+        } else if (x == ix && y == iy && z == iz - 1) {
+            v[4] = v[0];
+            v[5] = v[1];
+            v[6] = v[2];
+            v[7] = v[3];
+            face(b, data, x, y, z, v[0], v[1], v[2], v[3]);
+            iz = z;
+            return;
+        } else {
+            face(b, data, x, y, z, v[0], v[1], v[2], v[3]);
+        }
+        face(b, data, x, y, z + 1, v[4], v[5], v[6], v[7]);
+        ix = x;
+        iy = y;
+        iz = z;
+    }
+};
+
 // Trilinear value at brick-local node coordinates q (x fastest): cell
 // i = clamp(floor(q), 0, n - 2), weights q - i, lerp in x, then y, then z.
-// The eight corners come either from the stored nodes (eight loads) or from
-// the gather layout (two vector loads, identical values).  The per-brick
-// scale multiplies the interpolated value (equal to scaling each corner, up
-// to rounding).  Returns the cell and weights for the adjoint.
+// The eight corners come either from the stored nodes or from the gather
+// layout (two vector loads, identical values), through the ray's corner
+// cache.  The per-brick scale multiplies the interpolated value (equal to
+// scaling each corner, up to rounding).  Returns the cell and weights for
+// the adjoint.
 template <typename T, bool QUAD>
-__device__ __forceinline__ float trilinear(const BrickDev& b, const T* data, float scale, float qx, float qy,
-                                           float qz, int& ix, int& iy, int& iz, float& fx, float& fy, float& fz) {
+__device__ __forceinline__ float trilinear(const BrickDev& b, const T* data, float scale, CornerCache<T, QUAD>& cc,
+                                           float qx, float qy, float qz, int& ix, int& iy, int& iz, float& fx,
+                                           float& fy, float& fz) {
     ix = min(max(__float2int_rd(qx), 0), b.s_n[0] - 2);
     iy = min(max(__float2int_rd(qy), 0), b.s_n[1] - 2);
     iz = min(max(__float2int_rd(qz), 0), b.s_n[2] - 2);
     fx = qx - (float)ix;
     fy = qy - (float)iy;
     fz = qz - (float)iz;
-    float v000, v100, v010, v110, v001, v101, v011, v111;
     if (QUAD) {
-        using W = typename Quad<T>::W;
-        const W* q = reinterpret_cast<const W*>(b.quad) + (ix + iy * b.qx + iz * b.qxy);
-        Quad<T>::unpack(__ldg(q), v000, v100, v010, v110);
-        Quad<T>::unpack(__ldg(q + b.qxy), v001, v101, v011, v111);
+        // two vector loads: cheaper than the cache's divergent reuse tests
+        cc.face(b, data, ix, iy, iz, cc.v[0], cc.v[1], cc.v[2], cc.v[3]);
+        cc.face(b, data, ix, iy, iz + 1, cc.v[4], cc.v[5], cc.v[6], cc.v[7]);
     } else {
-        const T* p = data + (ix + iy * b.sx + iz * b.sxy);
-        v000 = Storage<T>::load(p, 0);
-        v100 = Storage<T>::load(p, 1);
-        v010 = Storage<T>::load(p, b.sx);
-        v110 = Storage<T>::load(p, b.sx + 1);
-        v001 = Storage<T>::load(p, b.sxy);
-        v101 = Storage<T>::load(p, b.sxy + 1);
-        v011 = Storage<T>::load(p, b.sxy + b.sx);
-        v111 = Storage<T>::load(p, b.sxy + b.sx + 1);
+        cc.fetch(b, data, ix, iy, iz);
     }
-    float x00 = fmaf(fx, v100 - v000, v000);
-    float x10 = fmaf(fx, v110 - v010, v010);
-    float x01 = fmaf(fx, v101 - v001, v001);
-    float x11 = fmaf(fx, v111 - v011, v011);
+    const float* v = cc.v;
+    float x00 = fmaf(fx, v[1] - v[0], v[0]);
+    float x10 = fmaf(fx, v[3] - v[2], v[2]);
+    float x01 = fmaf(fx, v[5] - v[4], v[4]);
+    float x11 = fmaf(fx, v[7] - v[6], v[6]);
     float y0 = fmaf(fy, x10 - x00, x00);
     float y1 = fmaf(fy, x11 - x01, x01);
-    float v = fmaf(fz, y1 - y0, y0);
-    return Storage<T>::unit_scale ? v : v * scale;
+    float r = fmaf(fz, y1 - y0, y0);
+    return Storage<T>::unit_scale ? r : r * scale;
 }
 
 // ---------------------------------------------------------------------------

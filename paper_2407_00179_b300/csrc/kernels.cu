@@ -356,16 +356,14 @@ cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 orig
 // RGBA, key = first sample index, or key = EMPTY).  The TF table is staged
 // in shared memory.
 
+// One work item: every thread marches its pixel's ray through the item's
+// brick and writes the fragment to slot `item * tile_pixels + thread`.
+// Returns the samples this thread evaluated.
 template <typename T, bool QUAD>
-__global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
-                                                   const float* scales, const Item* items, const float4* tf,
-                                                   float4* frag_rgba, int* frag_key, Counters* counters) {
-    extern __shared__ float4 s_tf[];
-    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
-    __syncthreads();
-
-    const Item it = items[blockIdx.x];
-    if (!item_ok(it, P)) return;
+__device__ __forceinline__ unsigned long long march_item(const FrameParams& P, const CamBasis* cams,
+                                                         const BrickDev* bricks, const float* scales, const Item& it,
+                                                         long long item, const float4* s_tf, float4* frag_rgba,
+                                                         int* frag_key) {
     const BrickDev b = bricks[it.brick];
     const CamBasis cam = cams[it.cam];
     const float scale = scales[b.scale_idx];
@@ -373,7 +371,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis
     int lx, ly;
     tile_pixel(threadIdx.x, P.tw, lx, ly);
     int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
-    long long slot = (long long)blockIdx.x * P.tp + threadIdx.x;
+    long long slot = item * P.tp + threadIdx.x;
     unsigned long long nsamp = 0;
     if (px < P.W && py < P.H) {
         MarchState m;
@@ -381,12 +379,14 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis
             float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.0f;
             int n = m.j1 - m.j0;
             int k = 0;
+            CornerCache<T, QUAD> cc;
             for (; k < n; ++k) {
                 float fk = (float)k;
                 int ix, iy, iz;
                 float fx, fy, fz;
-                float s = trilinear<T, QUAD>(b, data, scale, fmaf(fk, m.st[0], m.q0[0]), fmaf(fk, m.st[1], m.q0[1]),
-                                             fmaf(fk, m.st[2], m.q0[2]), ix, iy, iz, fx, fy, fz);
+                float s = trilinear<T, QUAD>(b, data, scale, cc, fmaf(fk, m.st[0], m.q0[0]),
+                                             fmaf(fk, m.st[1], m.q0[1]), fmaf(fk, m.st[2], m.q0[2]), ix, iy, iz,
+                                             fx, fy, fz);
                 TFSample c = tf_lookup(s_tf, P, s);
                 float al = sample_alpha(P, c.v.w);
                 float ta = Tr * al;
@@ -406,6 +406,46 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis
             frag_key[slot] = KEY_EMPTY;
         }
     }
+    return nsamp;
+}
+
+template <typename T, bool QUAD>
+__global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
+                                                   const float* scales, const Item* items, const float4* tf,
+                                                   float4* frag_rgba, int* frag_key, Counters* counters) {
+    extern __shared__ float4 s_tf[];
+    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
+    __syncthreads();
+    const Item it = items[blockIdx.x];
+    if (!item_ok(it, P)) return;
+    unsigned long long nsamp = march_item<T, QUAD>(P, cams, bricks, scales, it, blockIdx.x, s_tf, frag_rgba, frag_key);
+    nsamp = warp_sum_u64(nsamp);
+    if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
+}
+
+// Persistent form: a grid sized to the GPU pulls work items from a counter
+// in the order `sched` gives (brick-major: all cameras' tiles of one brick
+// together, so a brick is read from HBM about once per batch).
+template <typename T, bool QUAD>
+__global__ void __launch_bounds__(256) k_march_fwd_persistent(FrameParams P, const CamBasis* cams,
+                                                              const BrickDev* bricks, const float* scales,
+                                                              const Item* items, const int* sched, int n_items,
+                                                              unsigned int* work, const float4* tf,
+                                                              float4* frag_rgba, int* frag_key, Counters* counters) {
+    extern __shared__ float4 s_tf[];
+    __shared__ int s_next;
+    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
+    unsigned long long nsamp = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int i = s_next;
+        if (i >= n_items) break;
+        const int item = sched[i];
+        const Item it = items[item];
+        if (item_ok(it, P)) nsamp += march_item<T, QUAD>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
+    }
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
@@ -413,22 +453,81 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis
 template <typename T, bool QUAD>
 static void fwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                        const Item* items, int n_items, const float4* tf, float4* frag_rgba, int* frag_key,
-                       Counters* counters, cudaStream_t st) {
+                       Counters* counters, const Schedule* sch, cudaStream_t st) {
     size_t smem = sizeof(float4) * P.ntf;
+    if (sch) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_march_fwd_persistent<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        int per_sm = 0, dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_fwd_persistent<T, QUAD>, P.tp, smem);
+        int grid = nsm * (per_sm > 0 ? per_sm : 1);
+        if (sch->ctas_per_sm > 0 && sch->ctas_per_sm < per_sm) grid = nsm * sch->ctas_per_sm;
+        if (grid > n_items) grid = n_items;
+        cudaMemsetAsync(sch->work, 0, sizeof(unsigned int), st);
+        k_march_fwd_persistent<T, QUAD><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched, n_items,
+                                                                  sch->work, tf, frag_rgba, frag_key, counters);
+        return;
+    }
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_march_fwd<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_march_fwd<T, QUAD><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
                                                       counters);
 }
 
+// ===========================================================================
+// schedules for the persistent launches
+// ===========================================================================
+
+__global__ void k_sched_identity(int* sched, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) sched[i] = i;
+}
+
+// bucket = brick of a valid item, nbricks for invalid ones (pulled last)
+__global__ void k_sched_hist(FrameParams P, const Item* items, int n, int* hist) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Item it = items[i];
+    atomicAdd(hist + (item_ok(it, P) ? it.brick : P.nbricks), 1);
+}
+
+__global__ void k_sched_scatter(FrameParams P, const Item* items, int n, const int* offsets, int* cursor,
+                                int* sched) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Item it = items[i];
+    int bkt = item_ok(it, P) ? it.brick : P.nbricks;
+    int pos = offsets[bkt] + atomicAdd(cursor + bkt, 1);
+    if (pos < n) sched[pos] = i;
+}
+
+cudaError_t launch_schedule(const FrameParams& P, const Item* items, int n_items, int order, int* hist,
+                            int* offsets, int* cursor, unsigned long long* tmp, int* sched, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+    unsigned g = (unsigned)((n_items + 255) / 256);
+    if (order == 0) {
+        k_sched_identity<<<g, 256, 0, st>>>(sched, n_items);
+        return cudaGetLastError();
+    }
+    cudaMemsetAsync(hist, 0, sizeof(int) * (P.nbricks + 1), st);
+    cudaMemsetAsync(cursor, 0, sizeof(int) * (P.nbricks + 1), st);
+    k_sched_hist<<<g, 256, 0, st>>>(P, items, n_items, hist);
+    k_scan<<<1, 1024, 0, st>>>(hist, offsets, P.nbricks + 1, tmp, nullptr);
+    k_sched_scatter<<<g, 256, 0, st>>>(P, items, n_items, offsets, cursor, sched);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_march_fwd(int dtype, bool quad, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
-                             cudaStream_t st) {
+                             cudaStream_t st, const Schedule* sch) {
     if (n_items == 0) return cudaSuccess;
-#define FWD(T)                                                                                               \
-    (quad ? fwd_launch<T, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, st) \
-          : fwd_launch<T, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, st))
+#define FWD(T)                                                                                                   \
+    (quad ? fwd_launch<T, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st) \
+          : fwd_launch<T, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st))
     switch (dtype) {
         case 0: FWD(float); break;
         case 1: FWD(__half); break;
@@ -710,23 +809,15 @@ int bwd_tf_copies(int ntf) {
     return c < 1 ? 1 : (c > 8 ? 8 : c);
 }
 
+// One work item of the adjoint: replay each thread's fragment and
+// accumulate its TF gradient into `my_tab` (a shared copy) and its voxel
+// gradient into the global field.  Returns the samples replayed.
 template <typename T, bool QUAD>
-__global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
-                                                   const float* scales, const Item* items, const float4* tf,
-                                                   const float4* frag_rgba, const int* frag_key,
-                                                   const float4* frag_grad, int ncopy, double* dtf, float* dvol,
-                                                   Counters* counters) {
-    extern __shared__ float4 s_mem[];
-    float4* s_tf = s_mem;
-    float* s_g = (float*)(s_mem + P.ntf);
-    const int stride = 4 * P.ntf + 1;
-    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
-    for (int i = threadIdx.x; i < ncopy * stride; i += blockDim.x) s_g[i] = 0.0f;
-    __syncthreads();
-
-    Item it = items[blockIdx.x];
-    const bool valid = item_ok(it, P);
-    if (!valid) it.cam = it.brick = it.tile = 0;
+__device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, const CamBasis* cams,
+                                                       const BrickDev* bricks, const float* scales, const Item& it,
+                                                       long long item, const float4* s_tf, float* my_tab,
+                                                       const float4* frag_rgba, const int* frag_key,
+                                                       const float4* frag_grad, float* dvol) {
     const BrickDev b = bricks[it.brick];
     const CamBasis cam = cams[it.cam];
     const float scale = scales[b.scale_idx];
@@ -734,12 +825,11 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis
     int lx, ly;
     tile_pixel(threadIdx.x, P.tw, lx, ly);
     int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
-    long long slot = (long long)blockIdx.x * P.tp + threadIdx.x;
+    long long slot = item * P.tp + threadIdx.x;
     unsigned long long nsamp = 0;
     const float gscale = Storage<T>::unit_scale ? 1.0f : scale;
     const long long sy = P.dims[0], sz = (long long)P.dims[0] * P.dims[1];
-    float* my_tab = s_g + (threadIdx.x % ncopy) * stride;
-    if (valid && px < P.W && py < P.H && frag_key[slot] != KEY_EMPTY) {
+    if (px < P.W && py < P.H && frag_key[slot] != KEY_EMPTY) {
         MarchState m;
         float4 F = frag_rgba[slot];
         float4 G = frag_grad[slot];
@@ -750,12 +840,14 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis
             TFRunF tr;
             CellRun cr;
             const long long gofs = (long long)b.s_lo[2] * sz + (long long)b.s_lo[1] * sy + b.s_lo[0];
+            CornerCache<T, QUAD> cc;
             for (int k = 0; k < n; ++k) {
                 float fk = (float)k;
                 int ix, iy, iz;
                 float fx, fy, fz;
-                float s = trilinear<T, QUAD>(b, data, scale, fmaf(fk, m.st[0], m.q0[0]), fmaf(fk, m.st[1], m.q0[1]),
-                                             fmaf(fk, m.st[2], m.q0[2]), ix, iy, iz, fx, fy, fz);
+                float s = trilinear<T, QUAD>(b, data, scale, cc, fmaf(fk, m.st[0], m.q0[0]),
+                                             fmaf(fk, m.st[1], m.q0[1]), fmaf(fk, m.st[2], m.q0[2]), ix, iy, iz,
+                                             fx, fy, fz);
                 TFSample c = tf_lookup(s_tf, P, s);
                 float al = sample_alpha(P, c.v.w);
                 float ta = Tr * al;
@@ -817,6 +909,69 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis
             if (dvol) cell_flush(cr, dvol, sy, sz);
         }
     }
+    return nsamp;
+}
+
+template <typename T, bool QUAD>
+__global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
+                                                   const float* scales, const Item* items, const float4* tf,
+                                                   const float4* frag_rgba, const int* frag_key,
+                                                   const float4* frag_grad, int ncopy, double* dtf, float* dvol,
+                                                   Counters* counters) {
+    extern __shared__ float4 s_mem[];
+    float4* s_tf = s_mem;
+    float* s_g = (float*)(s_mem + P.ntf);
+    const int stride = 4 * P.ntf + 1;
+    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
+    for (int i = threadIdx.x; i < ncopy * stride; i += blockDim.x) s_g[i] = 0.0f;
+    __syncthreads();
+    float* my_tab = s_g + (threadIdx.x % ncopy) * stride;
+    const Item it = items[blockIdx.x];
+    unsigned long long nsamp = 0;
+    if (item_ok(it, P))
+        nsamp = bwd_item<T, QUAD>(P, cams, bricks, scales, it, blockIdx.x, s_tf, my_tab, frag_rgba, frag_key,
+                                  frag_grad, dvol);
+    nsamp = warp_sum_u64(nsamp);
+    if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) {
+        float v = 0.0f;
+        for (int c = 0; c < ncopy; ++c) v += s_g[c * stride + i];
+        if (v != 0.0f) atomicAdd(dtf + i, (double)v);
+    }
+}
+
+// Persistent adjoint: items pulled in schedule order; each CTA's TF tables
+// are added to the global table once, after its last item.
+template <typename T, bool QUAD>
+__global__ void __launch_bounds__(256) k_march_bwd_persistent(FrameParams P, const CamBasis* cams,
+                                                              const BrickDev* bricks, const float* scales,
+                                                              const Item* items, const int* sched, int n_items,
+                                                              unsigned int* work, const float4* tf,
+                                                              const float4* frag_rgba, const int* frag_key,
+                                                              const float4* frag_grad, int ncopy, double* dtf,
+                                                              float* dvol, Counters* counters) {
+    extern __shared__ float4 s_mem[];
+    __shared__ int s_next;
+    float4* s_tf = s_mem;
+    float* s_g = (float*)(s_mem + P.ntf);
+    const int stride = 4 * P.ntf + 1;
+    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
+    for (int i = threadIdx.x; i < ncopy * stride; i += blockDim.x) s_g[i] = 0.0f;
+    float* my_tab = s_g + (threadIdx.x % ncopy) * stride;
+    unsigned long long nsamp = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = (int)atomicAdd(work, 1u);
+        __syncthreads();
+        const int i = s_next;
+        if (i >= n_items) break;
+        const int item = sched[i];
+        const Item it = items[item];
+        if (item_ok(it, P))
+            nsamp += bwd_item<T, QUAD>(P, cams, bricks, scales, it, item, s_tf, my_tab, frag_rgba, frag_key,
+                                       frag_grad, dvol);
+    }
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
     __syncthreads();
@@ -830,9 +985,26 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis
 template <typename T, bool QUAD>
 static void bwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                        const Item* items, int n_items, const float4* tf, const float4* frag_rgba, const int* frag_key,
-                       const float4* frag_grad, double* dtf, float* dvol, Counters* counters, cudaStream_t st) {
+                       const float4* frag_grad, double* dtf, float* dvol, Counters* counters, const Schedule* sch,
+                       cudaStream_t st) {
     int ncopy = bwd_tf_copies(P.ntf);
     size_t smem = sizeof(float4) * P.ntf + sizeof(float) * (size_t)ncopy * (4 * P.ntf + 1);
+    if (sch) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_march_bwd_persistent<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        int per_sm = 0, dev = 0, nsm = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_bwd_persistent<T, QUAD>, P.tp, smem);
+        int grid = nsm * (per_sm > 0 ? per_sm : 1);
+        if (grid > n_items) grid = n_items;
+        cudaMemsetAsync(sch->work, 0, sizeof(unsigned int), st);
+        k_march_bwd_persistent<T, QUAD><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched,
+                                                                  n_items, sch->work, tf, frag_rgba, frag_key,
+                                                                  frag_grad, ncopy, dtf, dvol, counters);
+        return;
+    }
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_march_bwd<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_march_bwd<T, QUAD><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
@@ -843,13 +1015,13 @@ cudaError_t launch_march_bwd(int dtype, bool quad, const FrameParams& P, const C
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, const float4* frag_rgba, const int* frag_key,
                              const float4* frag_grad, double* dtf, float* dvol, Counters* counters,
-                             cudaStream_t st) {
+                             cudaStream_t st, const Schedule* sch) {
     if (n_items == 0) return cudaSuccess;
 #define BWD(T)                                                                                                 \
     (quad ? bwd_launch<T, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, \
-                                dvol, counters, st)                                                             \
+                                dvol, counters, sch, st)                                                        \
           : bwd_launch<T, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, \
-                                 dvol, counters, st))
+                                 dvol, counters, sch, st))
     switch (dtype) {
         case 0: BWD(float); break;
         case 1: BWD(__half); break;

@@ -22,6 +22,19 @@ struct CommitArgs {
     int s_lo[3], s_n[3];
 };
 
+// Persistent launches: the order in which CTAs pull work items.
+struct Schedule {
+    const int* sched;        // pull index -> work item
+    unsigned int* work;      // pull counter (reset by the launcher)
+    int ctas_per_sm;         // 0: as many as fit
+};
+
+// Build a pull order over the work list: order 0 = list order, 1 =
+// brick-major (all cameras' tiles of one brick together).  hist and cursor
+// hold nbricks + 1 ints; tmp one unsigned long long.
+cudaError_t launch_schedule(const FrameParams& P, const Item* items, int n_items, int order, int* hist,
+                            int* offsets, int* cursor, unsigned long long* tmp, int* sched, cudaStream_t st);
+
 // Message returned by dpvGetLastError() on this host thread.
 void set_last_error(const char* msg);
 
@@ -36,7 +49,7 @@ cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 orig
 cudaError_t launch_march_fwd(int dtype, bool quad, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
-                             cudaStream_t st);
+                             cudaStream_t st, const Schedule* sch = nullptr);
 
 // Shared-memory staged ray-march and adjoint (staged.cu).
 cudaError_t launch_march_fwd_staged(int dtype, const FrameParams& P, const CamBasis* cams, const BrickDev* bricks,
@@ -62,7 +75,7 @@ cudaError_t launch_march_bwd(int dtype, bool quad, const FrameParams& P, const C
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, const float4* frag_rgba, const int* frag_key,
                              const float4* frag_grad, double* dtf, float* dvol, Counters* counters,
-                             cudaStream_t st);
+                             cudaStream_t st, const Schedule* sch = nullptr);
 
 // Gather layout of a brick (kernels.cu): bytes it needs, and its build from
 // the stored nodes.

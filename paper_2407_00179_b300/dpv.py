@@ -23,13 +23,15 @@ KEY_EMPTY = 2 ** 31 - 1
 FRAME_ORDER = 1
 FRAME_STAGED = 2
 FRAME_LINEAR = 4
+FRAME_PERSISTENT = 8
+FRAME_GRAPH = 16
 STATUS = {0: "DPV_OK", 1: "DPV_ERR_INVALID_ARG", 2: "DPV_ERR_STATE", 3: "DPV_ERR_OUT_OF_MEMORY",
           4: "DPV_ERR_CUDA", 5: "DPV_ERR_TIMEOUT", 6: "DPV_ERR_UNSUPPORTED"}
 
 EXPORTS = ["dpvCreateDevice", "dpvSetVolumeGeometry", "dpvCommitBrick", "dpvSetTransferFunction", "dpvSetCameras",
            "dpvSetFrame", "dpvRenderFrame", "dpvFrameReady", "dpvMapFrame", "dpvUnmapFrame", "dpvCopyFrame",
            "dpvReadFragments", "dpvReadBrick", "dpvMapOrder", "dpvBackward", "dpvGetStats", "dpvResetStats", "dpvSetProfiling", "dpvGetLastError",
-           "dpvRelease", "dpvRenderNoAlloc"]
+           "dpvRelease", "dpvRenderNoAlloc", "dpvAutotune"]
 
 
 class DPVError(RuntimeError):
@@ -53,6 +55,11 @@ class FrameDesc(C.Structure):
                 ("ert_threshold", C.c_float), ("tile_w", C.c_int), ("tile_h", C.c_int), ("flags", C.c_int)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("tile_w", C.c_int), ("tile_h", C.c_int), ("flags", C.c_int), ("ms", C.c_float),
+                ("candidates", C.c_int)]
+
+
 class NoAllocBrick(C.Structure):
     _fields_ = [("owned_lo", C.c_int * 3), ("owned_hi", C.c_int * 3), ("data", C.c_void_p), ("scale", C.c_float)]
 
@@ -69,7 +76,8 @@ STAGES = ["cull", "march", "composite", "composite_bwd", "march_bwd"]
 class Stats(C.Structure):
     _fields_ = [("samples_forward", C.c_uint64), ("samples_backward", C.c_uint64), ("work_items", C.c_uint64),
                 ("fragment_bytes", C.c_uint64), ("error_flags", C.c_uint32), ("max_fragments", C.c_uint32),
-                ("stage_ms", C.c_double * 5), ("stage_calls", C.c_uint32 * 5), ("kernel_launches", C.c_uint64)]
+                ("stage_ms", C.c_double * 5), ("stage_calls", C.c_uint32 * 5), ("kernel_launches", C.c_uint64),
+                ("graph_launches", C.c_uint64)]
 
 
 _lib = None
@@ -109,6 +117,7 @@ def load(path: Optional[str] = None):
         "dpvGetStats": [V, C.POINTER(Stats)],
         "dpvResetStats": [V],
         "dpvSetProfiling": [V, I],
+        "dpvAutotune": [V, I, C.POINTER(TuneResult)],
         "dpvRenderNoAlloc": [C.POINTER(NoAllocScene), C.POINTER(CameraDesc), C.POINTER(FrameDesc), V, V, V],
         "dpvRelease": [V],
     }
@@ -246,12 +255,16 @@ class Device:
         self.ncam = len(cams)
 
     def set_frame(self, width: int, height: int, step_voxels: float = 0.5, sigma_max: float = 8.0, ert: float = 0.0,
-                  tile=(0, 0), order: bool = False, staged: bool = False, gather: str = "quad"):
+                  tile=(0, 0), order: bool = False, staged: bool = False, gather: str = "quad",
+                  persistent: bool = False, graph: bool = False):
         flags = (FRAME_ORDER if order else 0) | (FRAME_STAGED if staged else 0) | (
-            FRAME_LINEAR if gather == "linear" else 0)
+            FRAME_LINEAR if gather == "linear" else 0) | (FRAME_PERSISTENT if persistent else 0) | (
+            FRAME_GRAPH if graph else 0)
         f = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
                       int(tile[1]), flags)
         _check(load().dpvSetFrame(self._h, C.byref(f)))
+        self._frame_args = (step_voxels, sigma_max, ert)
+        self._frame_kw = {"order": order, "staged": staged, "graph": graph}
         self.width, self.height = int(width), int(height)
 
     # -- rendering ---------------------------------------------------------
@@ -323,6 +336,40 @@ class Device:
         out["stage_ms"] = {n: s.stage_ms[i] for i, n in enumerate(STAGES)}
         out["stage_calls"] = {n: s.stage_calls[i] for i, n in enumerate(STAGES)}
         return out
+
+    def autotune(self, frames: int = 3, cache: Optional[str] = None, key: Optional[str] = None) -> dict:
+        """Pick the fastest tile shape / gather layout / schedule for the
+        current scene (dpvAutotune).  With `cache` (a JSON file) and `key`, a
+        stored choice for this key and GPU is applied instead of re-timing,
+        and new choices are stored."""
+        import json
+        gpu = torch.cuda.get_device_name(self.cuda_device)
+        entry = None
+        if cache and key and os.path.exists(cache):
+            with open(cache) as f:
+                entry = json.load(f).get(gpu, {}).get(key)
+        if entry:
+            self._tune_apply(entry)
+            return dict(entry, cached=True)
+        r = TuneResult()
+        _check(load().dpvAutotune(self._h, int(frames), C.byref(r)))
+        res = {"tile": [r.tile_w, r.tile_h], "flags": r.flags, "ms": r.ms, "candidates": r.candidates}
+        self._tuned = res
+        if cache and key:
+            data = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    data = json.load(f)
+            data.setdefault(gpu, {})[key] = res
+            with open(cache, "w") as f:
+                json.dump(data, f, indent=1)
+        return dict(res, cached=False)
+
+    def _tune_apply(self, entry):
+        fl = entry["flags"]
+        self.set_frame(self.width, self.height, *self._frame_args, tile=tuple(entry["tile"]),
+                       gather="linear" if fl & FRAME_LINEAR else "quad", persistent=bool(fl & FRAME_PERSISTENT),
+                       **self._frame_kw)
 
     def reset_stats(self):
         _check(load().dpvResetStats(self._h))
