@@ -162,11 +162,12 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
         out = oracle.render_bricks(cfg["dims"], bricks, tf, cam, fr, pix=pix)
         return time.perf_counter() - t, int(out["nsamples"].sum()), len(pix)
 
-    # calibrate on the middle rows, then size the sample for the budget
-    dt, ns, npx = run([H // 2])
-    rate = max(ns, 1) / max(dt, 1e-6)
-    per_row = max(ns, 1)
-    nrows = int(min(H, max(1, budget_s * rate / per_row)))
+    # calibrate on 8 rows spread over the image, then size the sample so the
+    # oracle works about budget_s seconds
+    cal = np.linspace(0, H - 1, 8).astype(int)
+    dt, ns, npx = run(cal)
+    per_row_s = max(dt, 1e-6) / len(cal)
+    nrows = int(min(H, max(8, budget_s / per_row_s)))
     rows = np.linspace(0, H - 1, nrows).astype(int)
     dt, ns, npx = run(rows)
     return {"value": ns / dt / 1e9, "unit": "Gsamples/s", "cores": ncores, "kind": "oracle",
@@ -233,6 +234,12 @@ def run_ours(args, cfg_name, cfg):
     dev.set_tf(tf)
     dev.set_cameras(cams)
     dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=(args.tile_w, args.tile_h))
+    tune = None
+    if not args.no_autotune:
+        tune = dev.autotune(frames=3)
+        fl = tune["flags"]
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=tuple(tune["tile"]),
+                      gather="linear" if fl & dpv.FRAME_LINEAR else "quad", persistent=bool(fl & dpv.FRAME_PERSISTENT))
     # fixed upstream gradient: d/dI of mean (I - I*)^2 with I* from a perturbed TF
     dev.set_tf(torch.from_numpy(inputs.perturb_tf(tf_np, 0)).to(device))
     dev.render()
@@ -296,6 +303,50 @@ def run_ours(args, cfg_name, cfg):
     achieved = bytes_per_launch / (march_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
 
+    # many cameras: the same forward replayed from a CUDA graph, and the
+    # cameras rendered as separate float32 per-camera frames for comparison
+    batch = None
+    if ncam > 1:
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=tuple(tune["tile"]) if tune else
+                      (args.tile_w, args.tile_h), gather="linear" if tune and tune["flags"] & dpv.FRAME_LINEAR else
+                      "quad", persistent=bool(tune and tune["flags"] & dpv.FRAME_PERSISTENT), graph=True)
+        for _ in range(2):
+            dev.render()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            dev.render()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = g0.elapsed_time(g1) / args.steps
+        batched_img = dev.frames()[0].clone()
+        graph_used = dev.stats()["graph_launches"]
+        sep_ms = 0.0
+        err = 0.0
+        sep = dpv.Device(part.num_ranks, local)
+        sep.set_geometry(cfg["dims"])
+        sep.commit_partition(field, part, "f32")
+        sep.set_tf(tf)
+        for c, cam in enumerate(cams):
+            sep.set_cameras([cam])
+            sep.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"])
+            sep.render()
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for _ in range(2):
+                sep.render()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            sep_ms += s0.elapsed_time(s1) / 2
+            err = max(err, float((sep.map_frame(0)[0] - batched_img[c]).abs().max()))
+        sep.release()
+        batch = {"graph_fwd_ms_per_step": graph_ms, "graph_launches": int(graph_used),
+                 "separate_f32_ms": sep_ms, "separate_f32_gsamples_per_s": st["samples_forward"] / (sep_ms * 1e-3) / 1e9,
+                 "speedup_vs_separate_f32": sep_ms / graph_ms,
+                 "max_abs_diff_vs_separate_f32": err}
+
     # end to end through the public API: TF from pinned host memory in, the
     # composited frames to pinned host memory out, every step
     tf_host = torch.from_numpy(tf_np).pin_memory()
@@ -334,8 +385,8 @@ def run_ours(args, cfg_name, cfg):
         "data": "synthetic (seeded field, TF, cameras; no paper dataset)",
         "config": {"workload": cfg_name, "dims": list(cfg["dims"]), "bricks": part.num_ranks,
                    "cameras_per_gpu": ncam, "image": [W, H], "storage": cfg["storage"], "ert": cfg["ert"],
-                   "step_voxels": 0.5, "sigma_max": 8.0, "tile": [dev.width and args.tile_w or 16,
-                                                                 args.tile_h or 16],
+                   "step_voxels": 0.5, "sigma_max": 8.0,
+                   "tile": list(tune["tile"]) if tune else [args.tile_w or 16, args.tile_h or 16],
                    "l2": "inputs larger than L2 (%d MiB volume), no flush" % (
                        np.prod(cfg["dims"]) * bpv // 2 ** 20),
                    "parallelism": "weak: each GPU renders its own cameras over its own copy of the bricks"},
@@ -356,7 +407,10 @@ def run_ours(args, cfg_name, cfg):
         "gpu_launches": int(launches),
         "clocks": clk,
         "error_flags": st["error_flags"],
+        "autotune": tune,
     }
+    if batch:
+        line["batched"] = batch
     if rank == 0 and not args.no_cpu_baseline:
         try:
             cb = cpu_baseline(cfg_name, cfg, field.cpu().numpy(), part, tf_np, cams, budget_s=args.ref_budget)
@@ -382,6 +436,7 @@ def main():
     ap.add_argument("--tile-h", type=int, default=0)
     ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     if args.impl == "reference":

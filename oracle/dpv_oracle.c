@@ -186,6 +186,7 @@ float orc_brick_scale(const float* v, int64_t n, int dtype) {
 /* Quantise float32 values to a storage format: stored = round(v / scale),
  * the division in float32, rounding to nearest even (fp8 saturates). */
 void orc_quantize(const float* v, int64_t n, int dtype, float scale, void* out) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         float q = v[i] / scale;
         switch (dtype) {
