@@ -53,12 +53,17 @@ CONFIGS = {
     # 256^3 f32, 16 blobs, 2x2x2, 32 sphere cameras at 512^2
     "diff": dict(dims=(256, 256, 256), field="diff", splits=(2, 2, 2), ncam=32, width=512, height=512, ert=0.0,
                  storage="f32", cams="sphere"),
+    # 2048^3, 4-octave noise + 256 blobs, 4x4x4 bricks, 8 orbit cameras at 3840x2160, bf16 / fp8 storage
+    "large_bf16": dict(dims=(2048, 2048, 2048), field="large", splits=(4, 4, 4), ncam=8, width=3840, height=2160,
+                       ert=0.0, storage="bf16", cams="orbit", compare_f32=False),
+    "large_fp8": dict(dims=(2048, 2048, 2048), field="large", splits=(4, 4, 4), ncam=8, width=3840, height=2160,
+                      ert=0.0, storage="fp8", cams="orbit", compare_f32=False),
 }
 
 
 def _field(cfg, device):
     fn = {"mid": inputs.field_mid, "small": inputs.field_small, "turbulent": inputs.field_turbulent,
-          "diff": inputs.field_diff}[cfg["field"]]
+          "diff": inputs.field_diff, "large": inputs.field_large}[cfg["field"]]
     return fn(0, cfg["dims"], device=device)
 
 
@@ -230,6 +235,12 @@ def run_ours(args, cfg_name, cfg):
     dev = dpv.Device(part.num_ranks, local)
     dev.set_geometry(cfg["dims"])
     dev.commit_partition(field, part, cfg["storage"])
+    compare_f32 = cfg.get("compare_f32", True)
+    # keep a host copy for the CPU baseline and free the device field
+    field_host = field.cpu().numpy() if (rank == 0 and not args.no_cpu_baseline) else None
+    field_dev = field if (compare_f32 and ncam > 1) else None
+    del field
+    torch.cuda.empty_cache()
     tf = torch.from_numpy(tf_np).to(device)
     dev.set_tf(tf)
     dev.set_cameras(cams)
@@ -306,7 +317,7 @@ def run_ours(args, cfg_name, cfg):
     # many cameras: the same forward replayed from a CUDA graph, and the
     # cameras rendered as separate float32 per-camera frames for comparison
     batch = None
-    if ncam > 1:
+    if ncam > 1 and compare_f32:
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=tuple(tune["tile"]) if tune else
                       (args.tile_w, args.tile_h), gather="linear" if tune and tune["flags"] & dpv.FRAME_LINEAR else
                       "quad", persistent=bool(tune and tune["flags"] & dpv.FRAME_PERSISTENT), graph=True)
@@ -326,7 +337,7 @@ def run_ours(args, cfg_name, cfg):
         err = 0.0
         sep = dpv.Device(part.num_ranks, local)
         sep.set_geometry(cfg["dims"])
-        sep.commit_partition(field, part, "f32")
+        sep.commit_partition(field_dev, part, "f32")
         sep.set_tf(tf)
         for c, cam in enumerate(cams):
             sep.set_cameras([cam])
@@ -413,7 +424,7 @@ def run_ours(args, cfg_name, cfg):
         line["batched"] = batch
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            cb = cpu_baseline(cfg_name, cfg, field.cpu().numpy(), part, tf_np, cams, budget_s=args.ref_budget)
+            cb = cpu_baseline(cfg_name, cfg, field_host, part, tf_np, cams, budget_s=args.ref_budget)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         except Exception as e:  # the oracle is a reported baseline, never the product
             line["cpu_baseline"] = {"value": None, "unit": "Gsamples/s", "cores": None, "kind": "oracle",

@@ -88,9 +88,10 @@ def _axis_coords(n: int, sp: float, device) -> torch.Tensor:
     return torch.arange(n, device=device, dtype=torch.float64).to(torch.float32) * sp
 
 
-def blob_field(dims: Sequence[int], blobs: Blobs, device="cpu", clamp=True) -> torch.Tensor:
+def blob_field(dims: Sequence[int], blobs: Blobs, device="cpu", clamp=True, trunc: float = 6.0) -> torch.Tensor:
     """Sum of isotropic Gaussians, evaluated in float32, optionally clamped to
-    [0, 1].  Blobs are truncated at 6 sigma (below 2e-8 of their amplitude)."""
+    [0, 1].  Blobs are truncated at `trunc` sigma (6: below 2e-8 of their
+    amplitude)."""
     nx, ny, nz = dims
     sp = default_spacing(dims)
     out = torch.zeros((nz, ny, nx), dtype=torch.float32, device=device)
@@ -98,7 +99,7 @@ def blob_field(dims: Sequence[int], blobs: Blobs, device="cpu", clamp=True) -> t
     ys = _axis_coords(ny, sp, device)
     zs = _axis_coords(nz, sp, device)
     for c, s, a in zip(blobs.centers, blobs.sigmas, blobs.amps):
-        r = 6.0 * s
+        r = trunc * s
         lo = [max(0, int(math.floor((c[k] - r) / sp))) for k in range(3)]
         hi = [min(d, int(math.ceil((c[k] + r) / sp)) + 1) for k, d in enumerate(dims)]
         if any(h <= l for l, h in zip(lo, hi)):
@@ -142,7 +143,8 @@ def value_noise(dims: Sequence[int], octaves: int, seed: int = 0, f0: float = 4.
                 device="cpu", normalize=True) -> torch.Tensor:
     """Multi-octave value noise: octave o has f0 * 2**o lattice cells per world
     unit and amplitude 0.5**o; lattice values come from a seeded PCG hash and
-    are blended with a quintic smoothstep.  Normalised to [0, 1] by min/max."""
+    are blended with a quintic smoothstep, separably (x, then y, then z).
+    Normalised to [0, 1] by min/max."""
     nx, ny, nz = dims
     sp = default_spacing(dims)
     out = torch.zeros((nz, ny, nx), dtype=torch.float32, device=device)
@@ -151,29 +153,24 @@ def value_noise(dims: Sequence[int], octaves: int, seed: int = 0, f0: float = 4.
     for o in range(octaves):
         freq = f0 * (2 ** o)
         amp = 0.5 ** o
-        axes = []
+        idx, wts = [], []
         for c in coords:
             u = c * freq
             i = torch.floor(u)
-            axes.append((i.to(torch.int64), _smooth5(u - i)))
-        (ix, fx), (iy, fy), (iz, fz) = axes
-        # process z-slabs to bound temporary memory
-        slab = max(1, (1 << 24) // (nx * ny))
+            idx.append(i.to(torch.int64))
+            wts.append(_smooth5(u - i))
+        (ix, iy, iz), (wx, wy, wz) = idx, wts
+        lat = [torch.arange(int(i.min()), int(i.max()) + 2, device=device, dtype=torch.int64) for i in idx]
+        L = _lattice_value(lat[0][None, None, :], lat[1][None, :, None], lat[2][:, None, None], o, nseed)
+        rx, ry, rz = ix - lat[0][0], iy - lat[1][0], iz - lat[2][0]
+        T1 = L[:, :, rx] * (1.0 - wx) + L[:, :, rx + 1] * wx                      # (Lz, Ly, nx)
+        T2 = T1[:, ry, :] * (1.0 - wy)[None, :, None] + T1[:, ry + 1, :] * wy[None, :, None]   # (Lz, ny, nx)
+        del T1
+        slab = max(1, (1 << 26) // (nx * ny))
         for z0 in range(0, nz, slab):
             z1 = min(nz, z0 + slab)
-            izs, fzs = iz[z0:z1], fz[z0:z1]
-            acc = None
-            for dz in (0, 1):
-                wz = fzs if dz else 1.0 - fzs
-                for dy in (0, 1):
-                    wy = fy if dy else 1.0 - fy
-                    for dx in (0, 1):
-                        wx = fx if dx else 1.0 - fx
-                        val = _lattice_value((ix + dx)[None, None, :], (iy + dy)[None, :, None],
-                                             (izs + dz)[:, None, None], o, nseed)
-                        term = val * (wz[:, None, None] * wy[None, :, None] * wx[None, None, :])
-                        acc = term if acc is None else acc + term
-            out[z0:z1] += amp * acc
+            out[z0:z1].add_(torch.lerp(T2[rz[z0:z1]], T2[rz[z0:z1] + 1], wz[z0:z1, None, None]), alpha=amp)
+        del T2
     if normalize:
         out = _normalize01(out)
     return out
@@ -217,12 +214,21 @@ def field_diff(seed: int = 0, dims=(256, 256, 256), device="cpu") -> torch.Tenso
 
 
 def field_large(seed: int = 0, dims=(2048, 2048, 2048), device="cpu") -> torch.Tensor:
-    """4-octave value noise plus 256 blobs, min/max normalised."""
-    b = blob_field(dims, blob_params(256, dims, seed), device=device, clamp=False)
+    """4-octave value noise plus 256 small blobs (sigma U[0.01, 0.03],
+    truncated at 5 sigma), min/max normalised."""
+    b = blob_field(dims, blob_params(256, dims, seed, sigma_range=(0.01, 0.03)), device=device, clamp=False,
+                   trunc=5.0)
     n = value_noise(dims, 4, seed, device=device)
     b.add_(n, alpha=0.5)
     del n
-    return _normalize01(b)
+    return _normalize01_(b)
+
+
+def _normalize01_(f: torch.Tensor) -> torch.Tensor:
+    """In-place min/max normalisation (for fields too large to copy)."""
+    lo = f.min()
+    hi = f.max()
+    return f.sub_(lo).div_(hi - lo)
 
 
 # --------------------------------------------------------------------------
