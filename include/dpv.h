@@ -306,7 +306,7 @@ typedef struct {
  * `cuda_stream`, on the current CUDA device.  It calls no cudaMalloc or
  * cudaFree: its intermediate buffers live in one fixed 64 MiB device array
  * that the library holds on every GPU it is loaded on until the process
- * exits.  A frame needs about width x height x (32 + 20 x num_ranks) bytes
+ * exits.  A frame needs about width x height x (80 + 20 x num_ranks) bytes
  * of it (e.g. 512 x 512 with 8 ranks); larger requests fail with
  * DPV_ERR_INVALID_ARG.  The first call on a device looks up the array's
  * device address, so that first call should come before any stream capture

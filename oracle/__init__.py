@@ -103,7 +103,7 @@ def max_threads() -> int:
 
 @dataclass
 class Frame:
-    """Frame parameters (R2, R4, R6): image size, step in voxels, sigma_max,
+    """Frame parameters: image size, step in voxels, sigma_max,
     per-fragment early-termination threshold (0 = off) and the ambiguity
     bands used for flags."""
     width: int
@@ -142,7 +142,7 @@ def _pix(pix, frame: Frame):
 
 
 # ---------------------------------------------------------------------------
-# number formats and bricks (R1, a0)
+# number formats and bricks (brick commit)
 # ---------------------------------------------------------------------------
 
 def brick_scale(values: np.ndarray, dtype: int) -> np.float32:
@@ -222,7 +222,7 @@ def _bricks_c(bricks: List[Brick]):
 # ---------------------------------------------------------------------------
 
 def camera_ray(cam, width: int, height: int, px: int, py: int):
-    """Eye and unit direction of the ray through pixel (px, py) (R5)."""
+    """Eye and unit direction of the ray through pixel (px, py)."""
     o = np.zeros(3)
     d = np.zeros(3)
     c = _camera(cam)
@@ -304,7 +304,7 @@ def composite(frag_rgba: np.ndarray, frag_key: np.ndarray):
 
 def kd_order(partition, eye_node) -> np.ndarray:
     """Front-to-back leaf order of the partition's k-d tree from a point given
-    in node coordinates (R7)."""
+    in node coordinates."""
     K = partition.num_ranks
     out = np.zeros(K, np.uint8)
     ax = np.ascontiguousarray(partition.axis, np.int32)

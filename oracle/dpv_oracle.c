@@ -17,15 +17,15 @@
  *     front to back (§5.1.1, "Compositing");
  *   - the final frame exists on rank 0 (§3.1.3).
  * The paper gives no rendering equations.  The emission-absorption model,
- * the sampling rule and everything numeric are the readings listed in the
- * design notes (R1..R12), restated here where they are used.
+ * the sampling rule and everything numeric are readings of that text,
+ * each stated where it is used.
  *
  * Everything is FP64.  Stored brick values (f32, f16, bf16, fp8 e4m3) are
  * decoded per access and never copied into an FP64 array.
  *
  * Parity status: every function below is pinned by a CPU test against a
  * closed form, an invariant, a library routine or brute force, except the
- * camera convention (R5) which is pinned only by geometric properties.
+ * camera convention, which is pinned only by geometric properties.
  */
 #include <math.h>
 #include <stdint.h>
@@ -203,7 +203,7 @@ void orc_dequantize(const void* data, int64_t n, int dtype, double scale, double
 }
 
 /* ------------------------------------------------------------------------ */
-/* bricks (R1)                                                               */
+/* bricks                                                                    */
 /* ------------------------------------------------------------------------ */
 
 /* Nodes a rank stores: its owned nodes [lo, hi) plus one ghost node on each
@@ -253,7 +253,7 @@ static int owns(const orc_grid* g, const orc_brick* b, const double q[3]) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* trilinear interpolation (R1)                                              */
+/* trilinear interpolation                                                   */
 /* ------------------------------------------------------------------------ */
 
 /* Trilinear value at node-space point q from a box of nodes [b_lo, b_lo+b_n)
@@ -290,7 +290,7 @@ static double trilinear(const void* data, int dtype, double scale, const int b_l
 }
 
 /* ------------------------------------------------------------------------ */
-/* transfer function (R3)                                                    */
+/* transfer function                                                         */
 /* ------------------------------------------------------------------------ */
 
 /* Piecewise-linear RGBA lookup: u = clamp((s - vmin) / (vmax - vmin), 0, 1) *
@@ -313,7 +313,7 @@ static void tf_lookup(const orc_tf* tf, double s, double out[4], int* i0_out, do
 }
 
 /* ------------------------------------------------------------------------ */
-/* camera (R5)                                                               */
+/* camera                                                                    */
 /* ------------------------------------------------------------------------ */
 
 static void normalize3(double v[3]) {
@@ -370,7 +370,7 @@ static int ray_box(const double o[3], const double d[3], const double lo[3], con
 }
 
 /* ------------------------------------------------------------------------ */
-/* samples along a ray (R2)                                                  */
+/* samples along a ray                                                       */
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
@@ -416,7 +416,7 @@ static void sample_point(const orc_grid* g, const orc_rayinfo* ri, int64_t j, do
 }
 
 /* ------------------------------------------------------------------------ */
-/* emission-absorption (R4)                                                  */
+/* emission-absorption                                                       */
 /* ------------------------------------------------------------------------ */
 
 /* Classify one sample: TF colour c and opacity alpha = 1 - exp(-sigma dt)
@@ -658,7 +658,7 @@ void orc_composite(int npix, int K, const double* frag_rgba, const int32_t* frag
 }
 
 /* ------------------------------------------------------------------------ */
-/* k-d visibility order (R7)                                                 */
+/* k-d visibility order                                                      */
 /* ------------------------------------------------------------------------ */
 
 /* Front-to-back order of the leaves of a k-d tree seen from a point: at each

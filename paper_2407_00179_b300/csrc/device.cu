@@ -392,7 +392,7 @@ dpv_status prepare(dpv_device dev) {
         dev_free(dev->d_rays);
         dev->d_rays = nullptr;
         dev->rays_cap = 0;
-        dpv_status s2 = dev_alloc(dev, (void**)&dev->d_rays, 2 * sizeof(float4) * nrays, "rays");
+        dpv_status s2 = dev_alloc(dev, (void**)&dev->d_rays, RAY_VECS * sizeof(float4) * nrays, "rays");
         if (s2) return s2;
         dev->rays_cap = nrays;
     }

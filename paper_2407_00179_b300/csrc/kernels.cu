@@ -147,6 +147,7 @@ __global__ void k_cam_setup(const CamIn* cams, int n, float3 origin, float spaci
     out[i] = b;
     CamBasisD bd;
     for (int a = 0; a < 3; ++a) {
+        bd.o[a] = ((double)c.eye[a] - og[a]) / (double)spacing;
         bd.f[a] = f[a];
         bd.r[a] = r[a];
         bd.u[a] = u[a];
@@ -158,9 +159,15 @@ __global__ void k_cam_setup(const CamIn* cams, int n, float3 origin, float spaci
 // Ray setup: direction of every pixel's ray, normalize(f + x th r + y th u)
 // with x = ((px + 1/2) / W * 2 - 1) * W / H and y = (py + 1/2) / H * 2 - 1,
 // computed in FP64 (the norm by an FP32 reciprocal square root refined with
-// one Newton step in FP64), scaled to node units per world t and rounded
-// once to FP32.  The FP32 reciprocal and the FP32 volume interval follow
-// from the rounded direction, so every kernel sees identical planes.
+// one Newton step in FP64) and scaled to node units per world t.  Stored per
+// ray (RAY_VECS float4):
+//   0: direction rounded to FP32, t_enter      (FP32, from the FP32 slab)
+//   1: FP32 reciprocal direction, t_exit
+//   2: entry point eye + t_enter d, high FP32 part (FP64 slab and product)
+//   3: entry point, low part (FP64 value minus the high part)
+//   4: direction, low part
+// The FP32 parts fix the sample ranges (identical planes in every kernel);
+// the pairs place each brick's first sample accurately.
 __global__ void k_rays(FrameParams P, const CamBasis* cams, const CamBasisD* camd, double inv_spacing, double sx,
                        double sy, double aspect, float4* rays) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -179,17 +186,40 @@ __global__ void k_rays(FrameParams P, const CamBasis* cams, const CamBasisD* cam
     double yr = (double)rsqrtf((float)n2);
     yr = yr * (1.5 - 0.5 * n2 * yr * yr);
     double n = yr * inv_spacing;
+    const double dd[3] = {d0 * n, d1 * n, d2 * n};
     Ray r;
-    r.d[0] = (float)(d0 * n);
-    r.d[1] = (float)(d1 * n);
-    r.d[2] = (float)(d2 * n);
     for (int a = 0; a < 3; ++a) {
+        r.d[a] = (float)dd[a];
         r.o[a] = cams[c].o[a];
         r.inv[a] = 1.0f / r.d[a];
     }
     if (!volume_interval(P.dims, r.o, r.d, r.inv, r.te, r.tx)) r.te = r.tx = 0.0f;
-    rays[2 * i] = make_float4(r.d[0], r.d[1], r.d[2], r.te);
-    rays[2 * i + 1] = make_float4(r.inv[0], r.inv[1], r.inv[2], r.tx);
+    // FP64 entry point: slab against [0, dims - 1] with the FP64 ray
+    const double eo[3] = {b.o[0], b.o[1], b.o[2]};
+    double te = 0.0, tx = 1e300;
+    for (int a = 0; a < 3; ++a) {
+        if (dd[a] != 0.0) {
+            double inv = (double)(1.0f / (float)dd[a]);
+            inv = inv * (2.0 - dd[a] * inv);
+            inv = inv * (2.0 - dd[a] * inv);
+            double ta = (0.0 - eo[a]) * inv, tb = ((double)(P.dims[a] - 1) - eo[a]) * inv;
+            te = fmax(te, fmin(ta, tb));
+            tx = fmin(tx, fmax(ta, tb));
+        }
+    }
+    float ph[3], pl[3], dl[3];
+    for (int a = 0; a < 3; ++a) {
+        double pe = eo[a] + te * dd[a];
+        ph[a] = (float)pe;
+        pl[a] = (float)(pe - (double)ph[a]);
+        dl[a] = (float)(dd[a] - (double)r.d[a]);
+    }
+    float4* o = rays + RAY_VECS * i;
+    o[0] = make_float4(r.d[0], r.d[1], r.d[2], r.te);
+    o[1] = make_float4(r.inv[0], r.inv[1], r.inv[2], r.tx);
+    o[2] = make_float4(ph[0], ph[1], ph[2], 0.0f);
+    o[3] = make_float4(pl[0], pl[1], pl[2], 0.0f);
+    o[4] = make_float4(dl[0], dl[1], dl[2], 0.0f);
 }
 
 // Screen tile rectangle [x0, x1] x [y0, y1] (inclusive) that may see brick b
@@ -380,13 +410,13 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
             int n = m.j1 - m.j0;
             int k = 0;
             CornerCache<T, QUAD> cc;
+            SampleWalker wk;
+            wk.init(b);
             for (; k < n; ++k) {
-                float fk = (float)k;
                 int ix, iy, iz;
                 float fx, fy, fz;
-                float s = trilinear<T, QUAD>(b, data, scale, cc, fmaf(fk, m.st[0], m.q0[0]),
-                                             fmaf(fk, m.st[1], m.q0[1]), fmaf(fk, m.st[2], m.q0[2]), ix, iy, iz,
-                                             fx, fy, fz);
+                wk.at(m, k, ix, iy, iz, fx, fy, fz);
+                float s = trilinear<T, QUAD>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
                 TFSample c = tf_lookup(s_tf, P, s);
                 float al = sample_alpha(P, c.v.w);
                 float ta = Tr * al;
@@ -841,13 +871,13 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
             CellRun cr;
             const long long gofs = (long long)b.s_lo[2] * sz + (long long)b.s_lo[1] * sy + b.s_lo[0];
             CornerCache<T, QUAD> cc;
+            SampleWalker wk;
+            wk.init(b);
             for (int k = 0; k < n; ++k) {
-                float fk = (float)k;
                 int ix, iy, iz;
                 float fx, fy, fz;
-                float s = trilinear<T, QUAD>(b, data, scale, cc, fmaf(fk, m.st[0], m.q0[0]),
-                                             fmaf(fk, m.st[1], m.q0[1]), fmaf(fk, m.st[2], m.q0[2]), ix, iy, iz,
-                                             fx, fy, fz);
+                wk.at(m, k, ix, iy, iz, fx, fy, fz);
+                float s = trilinear<T, QUAD>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
                 TFSample c = tf_lookup(s_tf, P, s);
                 float al = sample_alpha(P, c.v.w);
                 float ta = Tr * al;

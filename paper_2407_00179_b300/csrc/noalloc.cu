@@ -164,7 +164,7 @@ extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_ca
     size_t o_cam = take(sizeof(CamBasis));
     size_t o_camd = take(sizeof(CamBasisD));
     size_t o_counters = take(sizeof(Counters));
-    size_t o_rays = take(2 * sizeof(float4) * npix);
+    size_t o_rays = take(RAY_VECS * sizeof(float4) * npix);
     size_t o_rects = take(sizeof(int4) * K);
     size_t o_count = take(sizeof(int) * ntiles);
     size_t o_first = take(sizeof(int) * ntiles);

@@ -38,10 +38,14 @@ constexpr int SLAB_CELLS = 8;     // cells per slab along D (halved when the box
 __device__ __forceinline__ float sel3(const float v[3], int a) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
 __device__ __forceinline__ int sel3(const int v[3], int a) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
 
-// clamped cell index of sample k on axis a
+// clamped cell index of sample k on axis a (the sample walker's position)
 __device__ __forceinline__ int cell_at(const MarchState& m, const BrickDev& b, int a, int k) {
-    float q = fmaf((float)k, sel3(m.st, a), sel3(m.q0, a));
-    return min(max(__float2int_rd(q), 0), sel3(b.s_n, a) - 2);
+    SampleWalker w;
+    w.init(b);
+    int c[3];
+    float f[3];
+    w.at(m, k, c[0], c[1], c[2], f[0], f[1], f[2]);
+    return sel3(c, a);
 }
 
 // First sample index e >= k whose cell on D lies beyond the slab [slo, shi]
@@ -106,16 +110,9 @@ struct SamplePos {
     float fx, fy, fz;
 };
 
-__device__ __forceinline__ SamplePos sample_pos(const MarchState& m, const BrickDev& b, int k) {
-    float fk = (float)k;
-    float qx = fmaf(fk, m.st[0], m.q0[0]), qy = fmaf(fk, m.st[1], m.q0[1]), qz = fmaf(fk, m.st[2], m.q0[2]);
+__device__ __forceinline__ SamplePos sample_pos(const MarchState& m, const BrickDev& b, SampleWalker& w, int k) {
     SamplePos s;
-    s.ix = min(max(__float2int_rd(qx), 0), b.s_n[0] - 2);
-    s.iy = min(max(__float2int_rd(qy), 0), b.s_n[1] - 2);
-    s.iz = min(max(__float2int_rd(qz), 0), b.s_n[2] - 2);
-    s.fx = qx - (float)s.ix;
-    s.fy = qy - (float)s.iy;
-    s.fz = qz - (float)s.iz;
+    w.at(m, k, s.ix, s.iy, s.iz, s.fx, s.fy, s.fz);
     return s;
 }
 
@@ -287,6 +284,8 @@ __global__ void __launch_bounds__(256) k_march_fwd_staged(FrameParams P, const C
     MarchState m;
     int n = 0;
     if (inimg && brick_samples(P, cam, it.cam, b, px, py, m)) n = m.j1 - m.j0;
+    SampleWalker wk;
+    wk.init(b);
     int D, A1, A2;
     bool up;
     tile_axis(P, cam, it, D, up);
@@ -316,7 +315,7 @@ __global__ void __launch_bounds__(256) k_march_fwd_staged(FrameParams P, const C
     // rays travelling against the tile's direction: straight from global memory
     if (n > 0 && !staged) {
         for (; k < n; ++k) {
-            SamplePos p = sample_pos(m, b, k);
+            SamplePos p = sample_pos(m, b, wk, k);
             float v[8];
             corners_global<T>(b, data, scale, p.ix + p.iy * b.sx + p.iz * b.sxy, v);
             if (step(v, p)) break;
@@ -347,7 +346,7 @@ __global__ void __launch_bounds__(256) k_march_fwd_staged(FrameParams P, const C
                 load_box<T>(b, data, scale, bx, s_box, nullptr);
                 __syncthreads();
                 for (; active && k < e; ++k) {
-                    SamplePos p = sample_pos(m, b, k);
+                    SamplePos p = sample_pos(m, b, wk, k);
                     float v[8];
                     corners_box(s_box, bx, p, v, &counters->err);
                     if (step(v, p)) {
@@ -358,7 +357,7 @@ __global__ void __launch_bounds__(256) k_march_fwd_staged(FrameParams P, const C
                 }
             } else {
                 for (; active && k < e; ++k) {
-                    SamplePos p = sample_pos(m, b, k);
+                    SamplePos p = sample_pos(m, b, wk, k);
                     float v[8];
                     corners_global<T>(b, data, scale, p.ix + p.iy * b.sx + p.iz * b.sxy, v);
                     if (step(v, p)) {
@@ -423,6 +422,8 @@ __global__ void __launch_bounds__(256) k_march_bwd_staged(FrameParams P, const C
     MarchState m;
     int n = 0;
     float4 F = make_float4(0.f, 0.f, 0.f, 0.f), G = F;
+    SampleWalker wk;
+    wk.init(b);
     if (px < P.W && py < P.H && frag_key[slot] != KEY_EMPTY) {
         G = frag_grad[slot];
         if ((G.x != 0.f || G.y != 0.f || G.z != 0.f || G.w != 0.f) && brick_samples(P, cam, it.cam, b, px, py, m)) {
@@ -527,7 +528,7 @@ __global__ void __launch_bounds__(256) k_march_bwd_staged(FrameParams P, const C
 
     if (n > 0 && !staged) {
         for (; k < n; ++k) {
-            SamplePos p = sample_pos(m, b, k);
+            SamplePos p = sample_pos(m, b, wk, k);
             float v[8];
             corners_global<T>(b, data, scale, p.ix + p.iy * b.sx + p.iz * b.sxy, v);
             if (step(v, p, nullptr)) break;
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(256) k_march_bwd_staged(FrameParams P, const C
                 load_box<T>(b, data, scale, bx, s_box, dvol ? s_gbox : nullptr);
                 __syncthreads();
                 for (; active && k < e; ++k) {
-                    SamplePos p = sample_pos(m, b, k);
+                    SamplePos p = sample_pos(m, b, wk, k);
                     float v[8];
                     corners_box(s_box, bx, p, v, &counters->err);
                     if (step(v, p, &bx)) {
@@ -584,7 +585,7 @@ __global__ void __launch_bounds__(256) k_march_bwd_staged(FrameParams P, const C
                 }
             } else {
                 for (; active && k < e; ++k) {
-                    SamplePos p = sample_pos(m, b, k);
+                    SamplePos p = sample_pos(m, b, wk, k);
                     float v[8];
                     corners_global<T>(b, data, scale, p.ix + p.iy * b.sx + p.iz * b.sxy, v);
                     if (step(v, p, nullptr)) {

@@ -1,7 +1,7 @@
 """GPU adjoint parity (compositor + ray-march replay) against the FP64 oracle
 gradient and against FP64 central finite differences of the oracle forward.
 
-Tolerances (R10): GPU vs FP64 gradient, max relative error 1e-3 on entries
+Tolerances: GPU vs FP64 gradient, max relative error 1e-3 on entries
 above 1e-3 of the largest, relative L2 1e-4; GPU vs central differences with
 eps = 1e-3 on 64 seeded TF entries, relative 1e-2 with an absolute floor of
 1e-3 of the largest gradient."""
@@ -30,7 +30,7 @@ def _scene(ert=0.0, storage="f32"):
 
 
 def _rel_checks(gpu, ref, what, kappa=None):
-    """R10 gradient bar: relative L2 <= 1e-4, and on entries above 1e-3 of
+    """Gradient bar: relative L2 <= 1e-4, and on entries above 1e-3 of
     the largest, |gpu - ref| <= 1e-3 |ref| + 3 kappa, where kappa is how much
     the FP64 oracle's own answer moves when the eye is perturbed by 1e-7
     relative (about one FP32 rounding of the ray geometry).  Entries that are

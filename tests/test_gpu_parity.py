@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
 the same seeded inputs.
 
-Tolerances (R10):
+Tolerances:
   * FP32 storage: 1e-5 max abs per RGBA channel against the oracle on the
     same stored values;
   * reduced precision: 1e-5 against the oracle on the same (dequantised)

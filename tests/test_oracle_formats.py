@@ -1,4 +1,4 @@
-"""Oracle pins: storage formats and brick extraction (brick commit, R1).
+"""Oracle pins: storage formats and brick extraction (brick commit).
 
 The oracle's own float16 / bfloat16 / fp8-e4m3 encoders and decoders are
 checked against library conversions (numpy float16, torch bfloat16 and

@@ -1,6 +1,6 @@
 """Oracle pins for the forward render.
 
-* camera convention (R5): geometric properties of the rays;
+* camera convention: geometric properties of the rays;
 * closed form 1 (constant slab): A = 1 - exp(-sigma d), C = c A;
 * closed form 2 (linear extinction): the midpoint samples integrate a linear
   sigma exactly, on axis-aligned and oblique rays;
