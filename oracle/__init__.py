@@ -73,7 +73,7 @@ def lib():
         P = C.c_void_p
         _lib.orc_render_full.argtypes = [P, P, P, P, P, C.c_int, P, P, P, P]
         _lib.orc_render_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P, P, P, P, P]
-        _lib.orc_grad_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P]
+        _lib.orc_grad_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, C.c_double]
         _lib.orc_composite.argtypes = [C.c_int, C.c_int, P, P, P, P]
         _lib.orc_kd_order.argtypes = [C.c_int, P, P, P, P, P, P]
         _lib.orc_kd_order.restype = C.c_int
@@ -272,10 +272,20 @@ def render_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, 
     return res
 
 
+KNOT_EPS = 4e-3   # knot ambiguity band, in TF entries (u units)
+
+
 def grad_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, grad_rgba: np.ndarray, pix=None,
-                vmin=0.0, vmax=1.0, want_volume=True, origin=(0.0, 0.0, 0.0), spacing=None):
+                vmin=0.0, vmax=1.0, want_volume=True, origin=(0.0, 0.0, 0.0), spacing=None, knot_eps=None):
     """FP64 reverse-mode gradient of sum(grad_rgba * image) with respect to the
-    TF table (n x 4) and the global field (nz, ny, nx)."""
+    TF table (n x 4) and the global field (nz, ny, nx).
+
+    With knot_eps (in TF entries, e.g. KNOT_EPS) also returns the knot
+    ambiguity of the field gradient (nz, ny, nx): per voxel, how far a
+    correct gradient may lie from the returned one because samples within
+    knot_eps of a TF knot may take either one-sided slope there.  The lerp's
+    derivative jumps at such knots, so an s rounded to the other side of one
+    gives the other, equally correct, derivative."""
     g = _grid(dims, origin, spacing)
     t, tab = _tf(tf, vmin, vmax)
     cam_c = _camera(cam)
@@ -286,8 +296,12 @@ def grad_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, gr
     gr = np.ascontiguousarray(grad_rgba, dtype=np.float64).reshape(n, 4)
     dtf = np.zeros((tab.shape[0], 4))
     dvol = np.zeros((dims[2], dims[1], dims[0])) if want_volume else None
+    damb = np.zeros((dims[2], dims[1], dims[0])) if knot_eps is not None else None
     lib().orc_grad_bricks(C.byref(g), K, barr, C.byref(t), C.byref(cam_c), C.byref(fr), n, pp, _p(gr), _p(dtf),
-                          _p(dvol) if dvol is not None else None)
+                          _p(dvol) if dvol is not None else None, _p(damb) if damb is not None else None,
+                          float(knot_eps or 0.0))
+    if knot_eps is not None:
+        return dtf, dvol, damb
     return dtf, dvol
 
 

@@ -695,10 +695,19 @@ typedef struct {
     int brick;
     double s, alpha, c[3];
     int i0;
-    double w, duds;
+    double w, duds, u;   /* u: (s - vmin) / (vmax - vmin) (N - 1), not clamped */
+    int flat;            /* all 8 corner values equal: s is exact in any arithmetic */
+    double vlo, vhi;     /* smallest and largest corner value */
     int64_t idx[8];
     double wt[8];
 } tape_entry;
+
+/* Slope d(Tab[k+1][c] - Tab[k][c]) du/ds of channel c on TF segment k, with
+ * the segments outside [0, N - 2] standing for the clamped ends (slope 0). */
+static double seg_slope(const orc_tf* tf, int k, int c) {
+    if (k < 0 || k > tf->n - 2) return 0.0;
+    return (tf->rgba[4 * (k + 1) + c] - tf->rgba[4 * k + c]) * (double)(tf->n - 1) / (tf->vmax - tf->vmin);
+}
 
 /* Reverse-mode gradient of sum_k <g_k, I_k> over listed pixels, where I_k is
  * the partitioned render (fragments + composite, ERT as in the forward).
@@ -709,10 +718,28 @@ typedef struct {
  * closed-form adjoint:
  *   over:  C' = C + (1 - A) C_k,  A' = A + (1 - A) A_k
  *   EA:    C' = C + T alpha c,    T' = T (1 - alpha),  A_k = 1 - T_end
- *   alpha = 1 - exp(-sigma_max a dt);  TF lerp;  trilinear. */
+ *   alpha = 1 - exp(-sigma_max a dt);  TF lerp;  trilinear.
+ *
+ * Knot ambiguity (optional damb, global nodes, accumulated): the lerp is not
+ * differentiable in s at a knot where the slope changes; there the gradient
+ * takes the segment to the right (the left one at u = N - 1).  A sample
+ * whose u = (s - vmin) / (vmax - vmin) (N - 1) lies within knot_eps of a
+ * knot m is one a rounded s may place on either side of m, and either
+ * one-sided derivative is then a correct answer.  A sample whose eight
+ * corner values are equal is the exception: any interpolation by convex
+ * combinations returns that value exactly, so it cannot change sides.  At
+ * the two end knots the other side is the clamp (slope 0), which a sample
+ * reaches only if s can leave [vmin, vmax]; interpolation by convex
+ * combinations keeps s within its corners' range, so only samples with a
+ * corner outside [vmin, vmax] count there.  For the other samples near a
+ * knot damb
+ * collects, per voxel, |ds-adjoint with the other segment - with the chosen
+ * one| times the trilinear weight: how far a correct gradient may lie from
+ * dvol.  Both sides of m use the same value adjoints, since the TF value is
+ * continuous there. */
 void orc_grad_bricks(const orc_grid* g, int K, const orc_brick* bricks, const orc_tf* tf, const orc_camera* cam,
                      const orc_frame* fr, int npix, const int32_t* pix, const double* grad_rgba, double* dtf,
-                     double* dvol) {
+                     double* dvol, double* damb, double knot_eps) {
     int nthreads = 1;
 #ifdef _OPENMP
     nthreads = omp_get_max_threads();
@@ -764,6 +791,14 @@ void orc_grad_bricks(const orc_grid* g, int K, const orc_brick* bricks, const or
                                  bn + 3 * owner, q, e->idx, e->wt);
                 double v[4];
                 tf_lookup(tf, e->s, v, &e->i0, &e->w, &e->duds);
+                e->u = (e->s - tf->vmin) / (tf->vmax - tf->vmin) * (double)(tf->n - 1);
+                e->vlo = e->vhi = bricks[owner].scale * decode(bricks[owner].data, bricks[owner].dtype, e->idx[0]);
+                for (int c = 1; c < 8; ++c) {
+                    double vc = bricks[owner].scale * decode(bricks[owner].data, bricks[owner].dtype, e->idx[c]);
+                    if (vc < e->vlo) e->vlo = vc;
+                    if (vc > e->vhi) e->vhi = vc;
+                }
+                e->flat = e->vlo == e->vhi;
                 e->c[0] = v[0]; e->c[1] = v[1]; e->c[2] = v[2];
                 e->alpha = 1.0 - exp(-fr->sigma_max * v[3] * ri.dt);
                 count[owner]++;
@@ -821,6 +856,35 @@ void orc_grad_bricks(const orc_grid* g, int K, const orc_brick* bricks, const or
                         gw += gv[c] * (tf->rgba[4 * (e->i0 + 1) + c] - tf->rgba[4 * e->i0 + c]);
                     }
                     double gs = gw * e->duds;
+                    double gs_amb = 0.0;
+                    if (damb) {
+                        double m = floor(e->u + 0.5);
+                        if (!e->flat && fabs(e->u - m) < knot_eps) {
+                            /* segment the gradient took, and the other one at knot m */
+                            int chosen = e->duds == 0.0 ? (e->u < 0.0 ? -1 : tf->n - 1) : e->i0;
+                            int other = chosen == (int)m ? (int)m - 1 : (int)m;
+                            /* the clamped side of an end knot is out of reach
+                             * while every corner lies inside [vmin, vmax] */
+                            int reach = 1;
+                            if (other < 0 && e->vlo >= tf->vmin) reach = 0;
+                            if (other > tf->n - 2 && e->vhi <= tf->vmax) reach = 0;
+                            double galt = 0.0;
+                            for (int c = 0; c < 4; ++c) galt += gv[c] * seg_slope(tf, other, c);
+                            if (reach) gs_amb = fabs(galt - gs);
+                        }
+                    }
+                    if (damb && gs_amb != 0.0) {
+                        const int* lo = bl + 3 * e->brick;
+                        const int* nn = bn + 3 * e->brick;
+                        for (int c = 0; c < 8; ++c) {
+                            int64_t li = e->idx[c];
+                            int x = (int)(li % nn[0]), y = (int)((li / nn[0]) % nn[1]), z = (int)(li / ((int64_t)nn[0] * nn[1]));
+                            int64_t gi = ((int64_t)(z + lo[2]) * g->dims[1] + (y + lo[1])) * g->dims[0] + (x + lo[0]);
+                            double contrib = gs_amb * e->wt[c] * fabs((double)bricks[e->brick].scale);
+#pragma omp atomic
+                            damb[gi] += contrib;
+                        }
+                    }
                     if (dvol && gs != 0.0) {
                         const int* lo = bl + 3 * e->brick;
                         const int* nn = bn + 3 * e->brick;

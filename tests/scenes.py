@@ -92,3 +92,45 @@ def o_bricks(orc, sc: Scene, cam, **kw):
 def o_full(orc, sc: Scene, cam, field=None, **kw):
     f = sc.field if field is None else field
     return orc.render_full(f, sc.tf, cam, oracle_frame(orc, sc), spacing=sc.spacing, **kw)
+
+
+def grad_checks(gpu, ref, what, kappa=None, amb=None):
+    """Gradient bar: relative L2 <= 1e-4, and on entries above 1e-3 of
+    the largest, |gpu - ref| <= 1e-3 |ref| + 3 kappa + amb.
+
+    kappa is how much the FP64 oracle's own answer moves when the eye is
+    perturbed by 1e-7 relative (about one FP32 rounding of the ray
+    geometry).  Entries that are sums of large cancelling terms are only
+    determined to that level once the geometry is rounded to FP32, whatever
+    the arithmetic after it; the FP32 path rounds the geometry in three
+    independent places (eye in node coordinates, ray direction, per-brick
+    sample anchor), hence 3 kappa.
+
+    amb is the oracle's knot ambiguity of a field gradient: where a sample
+    lies within rounding of a TF knot whose slope changes, either one-sided
+    derivative is correct, and amb is how far that can move the entry.  The
+    relative L2 is taken over what is left of each entry's error after amb."""
+    m = np.abs(ref).max()
+    assert m > 0
+    big = np.abs(ref) > 1e-3 * m
+    err = np.abs(gpu - ref)
+    rel = err[big] / np.abs(ref[big])
+    a = np.zeros_like(ref) if amb is None else amb
+    l2 = np.linalg.norm(np.maximum(err - a, 0.0)) / np.linalg.norm(ref)
+    k = np.zeros_like(ref) if kappa is None else kappa
+    bound = 1e-3 * np.abs(ref) + 3.0 * k + a
+    viol = big & (err > bound)
+    w = np.argsort(rel)[-3:]
+    print("%s: max rel %.2e (over %d entries), rel L2 %.2e (raw %.2e), %d beyond 1e-3|ref| + 3 kappa + amb "
+          "(%d entries with amb > 0); worst: %s" % (
+              what, rel.max(), big.sum(), l2, np.linalg.norm(gpu - ref) / np.linalg.norm(ref), viol.sum(),
+              int((a > 0).sum()),
+              ", ".join("gpu %.6e ref %.6e kappa %.1e amb %.1e (|ref|/max %.1e)" % (
+                  gpu[big][i], ref[big][i], k[big][i], a[big][i], abs(ref[big][i]) / m) for i in w)))
+    return l2, int(viol.sum())
+
+
+def perturbed_eye(cam, eps):
+    """The camera with its eye scaled by (1 + eps): about one FP32 rounding
+    of the ray geometry for eps = 1e-7."""
+    return inputs.Camera(tuple(float(x) * (1.0 + eps) for x in cam.eye), cam.center, cam.up, cam.fovy_deg)

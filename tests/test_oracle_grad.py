@@ -100,3 +100,53 @@ def test_planted_sign_error_fails_fd(orc):
         np.float64(t1[i, 3]) - np.float64(t0[i, 3]))
     assert abs(fd - dtf[i, 3]) < 1e-4 * abs(fd)
     assert abs(fd - (-dtf[i, 3])) > 0.5 * abs(fd)
+
+
+def _knot_problem(orc, value, tab, toward=None):
+    """Field of `value` and its float32 neighbour toward `toward` in a
+    checkerboard (constant if toward is None)."""
+    dims = (6, 5, 4)
+    f = np.full((dims[2], dims[1], dims[0]), value, np.float32)
+    if toward is not None:
+        z, y, x = np.indices(f.shape)
+        f[(x + y + z) % 2 == 1] = np.nextafter(np.float32(value), np.float32(toward))
+    part = inputs.regular_partition(dims, (2, 1, 1))
+    cam = inputs.camera_from_direction(dims, (1, 0.6, 0.45))
+    W, H = 9, 7
+    g = np.random.default_rng(5).normal(size=(W * H, 4))
+    fr = orc.Frame(W, H, sigma_max=20.0)
+    return orc.grad_bricks(dims, orc.make_bricks(f, part, orc.F32), tab, cam, fr, g, knot_eps=orc.KNOT_EPS)
+
+
+def test_knot_ambiguity_covers_the_one_sided_jump(orc):
+    """At a TF knot where the slope changes, the field gradient jumps between
+    the two one-sided derivatives.  A constant field one float32 step above
+    and one below the knot (checkerboards of two neighbouring float32
+    values) gives the two sides; their difference must be covered by the
+    reported knot ambiguity (triangle inequality over the samples), which is
+    exactly zero for a field away from every knot, for a TF whose slope does
+    not change at the knot, and for samples whose corners are all equal.
+    Tables are dyadic, so equal slopes are equal in floating point."""
+    n = 257
+    u = np.arange(n) / 256.0
+    kinked = np.stack([u, np.full(n, 0.3), 1.0 - u, 0.25 + 0.5 * np.abs(u - 0.5)], 1).astype(np.float32)
+    linear = np.stack([u, np.full(n, 0.3), 1.0 - u, 0.25 + 0.5 * u], 1).astype(np.float32)
+    half = np.float32(0.5)                    # knot 128
+    above, below = np.nextafter(half, np.float32(1)), np.nextafter(half, np.float32(0))
+    _, dv_hi, amb_hi = _knot_problem(orc, above, kinked, toward=1.0)
+    _, dv_lo, amb_lo = _knot_problem(orc, below, kinked, toward=0.0)
+    m = np.abs(dv_hi).max()
+    jump = np.abs(dv_hi - dv_lo)
+    assert jump.max() > 1e-2 * m                      # the kink is real
+    assert np.all(jump <= amb_hi * (1 + 1e-6) + 1e-9 * m)
+    assert np.all(jump <= amb_lo * (1 + 1e-6) + 1e-9 * m)
+    assert amb_hi.max() <= 4 * jump.max()             # and not a blanket bound
+    # away from every knot: mid-segment value
+    _, _, amb_mid = _knot_problem(orc, np.float32(0.5 + 0.5 / 256), kinked, toward=1.0)
+    assert amb_mid.max() == 0.0
+    # no slope change at the knot: nothing is ambiguous
+    _, dv_lin, amb_lin = _knot_problem(orc, above, linear, toward=1.0)
+    assert np.abs(dv_lin).max() > 0 and amb_lin.max() == 0.0
+    # equal corners: s is exact, so it stays on its side of the knot
+    _, dv_flat, amb_flat = _knot_problem(orc, above, kinked)
+    assert np.abs(dv_flat).max() > 0 and amb_flat.max() == 0.0
