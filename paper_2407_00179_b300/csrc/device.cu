@@ -108,6 +108,15 @@ struct dpv_device_t {
     bool rendered = false;
     bool use_quad = false;
 
+    // face adjoint buffer of the backward (float4 per cell face of every
+    // brick) and each owner's neighbour list for the gather that follows
+    float4* d_gface = nullptr;
+    size_t gface_cap = 0;               // slots allocated
+    size_t gface_slots = 0;             // slots the current bricks need
+    int* d_nb_first = nullptr;          // nranks + 1
+    int* d_nb = nullptr;                // nranks * nranks
+    long long max_owned = 0;            // largest owned node count
+
     // persistent schedule (DPV_FRAME_PERSISTENT)
     int* d_sched = nullptr;
     int* d_hist = nullptr;              // nranks + 1 each
@@ -297,6 +306,7 @@ dpv_status prepare(dpv_device dev) {
     P.ert = F.ert_threshold;
     P.ert_on = (F.ert_threshold > 0.0f && F.ert_threshold < 1.0f) ? 1 : 0;
     P.vmin = dev->vmin;
+    P.vmax = dev->vmax;
     P.tf_scale = (float)(dev->ntf - 1) / (dev->vmax - dev->vmin);
     P.ntf = dev->ntf;
     for (int a = 0; a < 3; ++a) P.dims[a] = dev->dims[a];
@@ -334,6 +344,47 @@ dpv_status prepare(dpv_device dev) {
         b.quad = nullptr;
         b.qx = h.s_n[0] - 1;
         b.qxy = (h.s_n[0] - 1) * (h.s_n[1] - 1);
+        for (int a = 0; a < 3; ++a) {
+            b.o_lo[a] = h.lo[a];
+            b.o_hi[a] = h.hi[a];
+        }
+    }
+    // face adjoint buffer offsets, and per owner the bricks whose stored box
+    // meets its owned box (itself first): the copies the gather sums
+    {
+        size_t off = 0;
+        long long mo = 0;
+        std::vector<int> first(dev->nranks + 1, 0), nb;
+        for (int k = 0; k < dev->nranks; ++k) {
+            const HostBrick& h = dev->bricks[k];
+            table[k].gface_off = (long long)off;
+            off += face_slots(h.s_n);
+            mo = std::max(mo, (long long)(h.hi[0] - h.lo[0]) * (h.hi[1] - h.lo[1]) * (h.hi[2] - h.lo[2]));
+            first[k] = (int)nb.size();
+            nb.push_back(k);
+            for (int m = 0; m < dev->nranks; ++m) {
+                if (m == k) continue;
+                const HostBrick& c = dev->bricks[m];
+                bool meet = true;
+                for (int a = 0; a < 3; ++a) meet = meet && c.s_lo[a] < h.hi[a] && h.lo[a] < c.s_lo[a] + c.s_n[a];
+                if (meet) nb.push_back(m);
+            }
+        }
+        first[dev->nranks] = (int)nb.size();
+        dev->gface_slots = off;
+        dev->max_owned = mo;
+        if (!dev->d_nb_first) {
+            dpv_status s2 = dev_alloc(dev, (void**)&dev->d_nb_first, sizeof(int) * (MAX_RANKS + 1), "neighbour lists");
+            if (s2) return s2;
+            s2 = dev_alloc(dev, (void**)&dev->d_nb, sizeof(int) * MAX_RANKS * MAX_RANKS, "neighbour lists");
+            if (s2) return s2;
+        }
+        CK(cudaMemcpyAsync(dev->d_nb_first, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice,
+                           dev->stream), "upload neighbour lists");
+        CK(cudaMemcpyAsync(dev->d_nb, nb.data(), sizeof(int) * nb.size(), cudaMemcpyHostToDevice, dev->stream),
+           "upload neighbour lists");
+        // the uploads read host vectors that end with this scope
+        CK(cudaStreamSynchronize(dev->stream), "upload neighbour lists");
     }
     // gather layout (default): built once per committed brick
     if (!(F.flags & DPV_FRAME_LINEAR)) {
@@ -906,7 +957,31 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
             return s;
     }
     CK(cudaMemsetAsync(dL_dtf, 0, sizeof(double) * 4 * dev->ntf, dev->stream), "zero dtf");
-    if (dL_dvol)
+    // field gradient: through the face adjoint buffer (two vector atomics per
+    // cell flush, then one gather that writes every node) where it fits in
+    // half of the free device memory; DPV_FACE_GRAD=0 selects the scalar
+    // atomics into the field instead
+    const bool staged = (dev->frame.flags & DPV_FRAME_STAGED) != 0;
+    bool faces = dL_dvol && !staged && dev->gface_slots > 0;
+    if (faces) {
+        if (const char* env = getenv("DPV_FACE_GRAD")) faces = atoi(env) != 0;
+    }
+    if (faces && dev->gface_cap < dev->gface_slots) {
+        dev_free(dev->d_gface);
+        dev->d_gface = nullptr;
+        dev->gface_cap = 0;
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        if (dev->gface_slots * sizeof(float4) <= free_b / 2 &&
+            cudaMalloc((void**)&dev->d_gface, dev->gface_slots * sizeof(float4)) == cudaSuccess)
+            dev->gface_cap = dev->gface_slots;
+        else
+            cudaGetLastError();
+    }
+    faces = faces && dev->d_gface && dev->gface_cap >= dev->gface_slots;
+    if (faces)
+        CK(cudaMemsetAsync(dev->d_gface, 0, dev->gface_slots * sizeof(float4), dev->stream), "zero face buffer");
+    else if (dL_dvol)
         CK(cudaMemsetAsync(dL_dvol, 0, sizeof(float) * (size_t)dev->dims[0] * dev->dims[1] * dev->dims[2], dev->stream),
            "zero dvol");
     CK(cudaMemsetAsync(&dev->d_counters->samples_bwd, 0, sizeof(unsigned long long), dev->stream), "reset counter");
@@ -918,13 +993,19 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
     t0 = stage_start(dev);
     const bool persistent = (dev->frame.flags & DPV_FRAME_PERSISTENT) != 0;
     Schedule sch{dev->d_sched, dev->d_work, 0};   // the pull order built by the render
-    if (!(dev->frame.flags & DPV_FRAME_STAGED))
+    if (!staged) {
         CK(launch_march_bwd(dev->bricks[0].dtype, dev->use_quad, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                             dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key,
-                            dev->d_frag_grad, dL_dtf, dL_dvol, dev->d_counters, dev->stream,
-                            persistent ? &sch : nullptr),
+                            dev->d_frag_grad, dL_dtf, faces ? nullptr : dL_dvol, faces ? dev->d_gface : nullptr,
+                            dev->d_counters, dev->stream, persistent ? &sch : nullptr),
            "march backward");
-    else
+        if (faces) {
+            CK(launch_face_gather(dev->d_bricks, dev->nranks, dev->d_nb_first, dev->d_nb, dev->max_owned,
+                                  dev->d_gface, dev->dims, dL_dvol, dev->stream),
+               "face gather");
+            dev->launches += 1;
+        }
+    } else
         CK(launch_march_bwd_staged(dev->bricks[0].dtype, P, dev->d_cams, dev->d_bricks, dev->d_scales, dev->d_items,
                                    dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_frag_grad,
                                    dL_dtf, dL_dvol, dev->d_counters, dev->stream),
@@ -1057,6 +1138,9 @@ dpv_status dpvRelease(dpv_device dev) {
         }
         free_schedule(dev);
         free_frags(dev);
+        dev_free(dev->d_gface);
+        dev_free(dev->d_nb_first);
+        dev_free(dev->d_nb);
         dev_free(dev->d_scales);
         dev_free(dev->d_tmp);
         dev_free(dev->d_bricks);

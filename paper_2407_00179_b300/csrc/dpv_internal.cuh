@@ -55,6 +55,8 @@ struct BrickDev {
                        // every z layer, the 2x2 corners v(x,y) v(x+1,y)
                        // v(x,y+1) v(x+1,y+1) packed in one vector
     int qx, qxy;       // strides of the gather layout: s_n[0]-1, (s_n[0]-1)(s_n[1]-1)
+    int o_lo[3], o_hi[3];  // owned global nodes [o_lo, o_hi)
+    long long gface_off;   // first face of this brick in the face adjoint buffer
 };
 
 // A work item: one brick seen through one screen tile of one camera.
@@ -84,7 +86,8 @@ struct FrameParams {
     float sigma_max;
     float ert;         // local opacity threshold
     int ert_on;
-    float vmin;        // TF domain start
+    float vmin;        // TF domain [vmin, vmax]
+    float vmax;
     float tf_scale;    // (n - 1) / (vmax - vmin)
     int ntf;           // TF entries
     int dims[3];       // global nodes per axis
@@ -367,14 +370,16 @@ struct TFSample {
     float4 v;          // interpolated RGBA
     int i0;            // left entry
     float w;           // weight of the right entry
-    float duds;        // du/ds (0 where clamped)
+    float duds;        // du/ds (0 where s lies outside [vmin, vmax])
 };
 
 __device__ __forceinline__ TFSample tf_lookup(const float4* tab, const FrameParams& P, float s) {
     TFSample r;
     float u = (s - P.vmin) * P.tf_scale;
     float hi = (float)(P.ntf - 1);
-    r.duds = (u >= 0.0f && u <= hi) ? P.tf_scale : 0.0f;
+    // the clamp is decided on s itself, so a rounded u never moves a sample
+    // inside the domain onto the clamped side
+    r.duds = (s >= P.vmin && s <= P.vmax) ? P.tf_scale : 0.0f;
     u = fminf(fmaxf(u, 0.0f), hi);
     r.i0 = min(__float2int_rd(u), P.ntf - 2);
     r.w = u - (float)r.i0;
@@ -485,11 +490,16 @@ __device__ __forceinline__ void tf_flush(TFRun& r, double* s_g) {
         if (r.a[c] != 0.0f) atomicAdd(e + c, (double)r.a[c]);
 }
 
+// Adjoint of one cell's eight corners, summed in registers while a ray stays
+// in the cell.  a[0..3] are the corners of the cell's lower z face in the
+// order (x,y) (x+1,y) (x,y+1) (x+1,y+1); a[4..7] those of its upper face.
 struct CellRun {
-    long long base = -1;   // global index of the cell's (0,0,0) node
+    long long base = -1;   // the cell: its lower face's index in the face
+                           // buffer, or its (0,0,0) node in the global field
     float a[8];
 };
 
+// Scalar form: eight FP32 atomics into the global field (base = node index).
 __device__ __forceinline__ void cell_flush(CellRun& r, float* dvol, long long sy, long long sz) {
     if (r.base < 0) return;
     float* v = dvol + r.base;
@@ -501,6 +511,16 @@ __device__ __forceinline__ void cell_flush(CellRun& r, float* dvol, long long sy
     atomicAdd(v + sz + 1, r.a[5]);
     atomicAdd(v + sz + sy, r.a[6]);
     atomicAdd(v + sz + sy + 1, r.a[7]);
+}
+
+// Face form: two 16-byte vector atomics into the face adjoint buffer (laid
+// out like the gather layout: one float4 per cell face, base = the lower
+// face, base + qxy the upper one); k_face_gather later sums each node's four
+// face slots of every brick that stores it.
+__device__ __forceinline__ void cell_flush_faces(CellRun& r, float4* gface, long long qxy) {
+    if (r.base < 0) return;
+    atomicAdd(gface + r.base, make_float4(r.a[0], r.a[1], r.a[2], r.a[3]));
+    atomicAdd(gface + r.base + qxy, make_float4(r.a[4], r.a[5], r.a[6], r.a[7]));
 }
 
 // ---------------------------------------------------------------------------

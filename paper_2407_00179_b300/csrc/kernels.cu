@@ -815,11 +815,13 @@ cudaError_t launch_composite_bwd(const FrameParams& P, const int* tile_first, co
 // while the segment (cell) stays the same and flushes on change.  Nearby
 // rays share TF segments, so a single shared table would serialise the
 // flushes of a warp on the same addresses; the CTA keeps `ncopy` FP32 copies
-// of the TF gradient table, lane l writing copy l % ncopy (copies offset by
-// one float so equal entries of different copies sit in different banks).
+// of the TF gradient table (bwd_tf_copies), lane l writing copy l % ncopy
+// (copies offset by one float so equal entries of different copies sit in
+// different banks).
 // At the end the copies are summed and added to the global FP64 table once
-// per touched entry.  Voxel flushes are eight FP32 atomics into the global
-// field.
+// per touched entry.  Voxel flushes are two float4 atomics into the face
+// adjoint buffer (gather layout; k_face_gather then writes the field), or,
+// without that buffer, eight FP32 atomics into the global field.
 
 struct TFRunF {
     int i0 = -1;
@@ -834,9 +836,12 @@ __device__ __forceinline__ void tf_flush_f(TFRunF& r, float* tab) {
         if (r.a[c] != 0.0f) atomicAdd(e + c, r.a[c]);
 }
 
+// Copies of the FP32 TF gradient table per CTA: as many as fit in 64 KB of
+// shared memory, at most 16 (lanes l and l + 16 of a warp, two pixel rows
+// apart, share one), so that three CTAs still fit on an SM.
 int bwd_tf_copies(int ntf) {
-    int c = 8192 / ntf;
-    return c < 1 ? 1 : (c > 8 ? 8 : c);
+    int c = 65536 / (16 * ntf);
+    return c < 1 ? 1 : (c > 16 ? 16 : c);
 }
 
 // One work item of the adjoint: replay each thread's fragment and
@@ -847,7 +852,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                                                        const BrickDev* bricks, const float* scales, const Item& it,
                                                        long long item, const float4* s_tf, float* my_tab,
                                                        const float4* frag_rgba, const int* frag_key,
-                                                       const float4* frag_grad, float* dvol) {
+                                                       const float4* frag_grad, float* dvol, float4* gface) {
     const BrickDev b = bricks[it.brick];
     const CamBasis cam = cams[it.cam];
     const float scale = scales[b.scale_idx];
@@ -904,14 +909,18 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 tr.a[5] = fmaf(w1, g_g, tr.a[5]);
                 tr.a[6] = fmaf(w1, g_b, tr.a[6]);
                 tr.a[7] = fmaf(w1, g_a, tr.a[7]);
-                if (dvol && c.duds != 0.0f) {
+                if ((dvol || gface) && c.duds != 0.0f) {
                     float4 ta0 = s_tf[c.i0], ta1 = s_tf[c.i0 + 1];
                     float gs = (g_r * (ta1.x - ta0.x) + g_g * (ta1.y - ta0.y) + g_b * (ta1.z - ta0.z) +
                                 g_a * (ta1.w - ta0.w)) * c.duds * gscale;
                     if (gs != 0.0f) {
-                        long long gb = gofs + (long long)iz * sz + (long long)iy * sy + ix;
+                        long long gb = gface ? b.gface_off + (long long)iz * b.qxy + (long long)iy * b.qx + ix
+                                             : gofs + (long long)iz * sz + (long long)iy * sy + ix;
                         if (gb != cr.base) {
-                            cell_flush(cr, dvol, sy, sz);
+                            if (gface)
+                                cell_flush_faces(cr, gface, b.qxy);
+                            else
+                                cell_flush(cr, dvol, sy, sz);
                             cr.base = gb;
 #pragma unroll
                             for (int q = 0; q < 8; ++q) cr.a[q] = 0.0f;
@@ -936,7 +945,10 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 if (P.ert_on && 1.0f - Tr > P.ert) break;
             }
             tf_flush_f(tr, my_tab);
-            if (dvol) cell_flush(cr, dvol, sy, sz);
+            if (gface)
+                cell_flush_faces(cr, gface, b.qxy);
+            else if (dvol)
+                cell_flush(cr, dvol, sy, sz);
         }
     }
     return nsamp;
@@ -947,7 +959,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis
                                                    const float* scales, const Item* items, const float4* tf,
                                                    const float4* frag_rgba, const int* frag_key,
                                                    const float4* frag_grad, int ncopy, double* dtf, float* dvol,
-                                                   Counters* counters) {
+                                                   float4* gface, Counters* counters) {
     extern __shared__ float4 s_mem[];
     float4* s_tf = s_mem;
     float* s_g = (float*)(s_mem + P.ntf);
@@ -960,7 +972,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis
     unsigned long long nsamp = 0;
     if (item_ok(it, P))
         nsamp = bwd_item<T, QUAD>(P, cams, bricks, scales, it, blockIdx.x, s_tf, my_tab, frag_rgba, frag_key,
-                                  frag_grad, dvol);
+                                  frag_grad, dvol, gface);
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
     __syncthreads();
@@ -980,7 +992,7 @@ __global__ void __launch_bounds__(256) k_march_bwd_persistent(FrameParams P, con
                                                               unsigned int* work, const float4* tf,
                                                               const float4* frag_rgba, const int* frag_key,
                                                               const float4* frag_grad, int ncopy, double* dtf,
-                                                              float* dvol, Counters* counters) {
+                                                              float* dvol, float4* gface, Counters* counters) {
     extern __shared__ float4 s_mem[];
     __shared__ int s_next;
     float4* s_tf = s_mem;
@@ -1000,7 +1012,7 @@ __global__ void __launch_bounds__(256) k_march_bwd_persistent(FrameParams P, con
         const Item it = items[item];
         if (item_ok(it, P))
             nsamp += bwd_item<T, QUAD>(P, cams, bricks, scales, it, item, s_tf, my_tab, frag_rgba, frag_key,
-                                       frag_grad, dvol);
+                                       frag_grad, dvol, gface);
     }
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
@@ -1015,8 +1027,8 @@ __global__ void __launch_bounds__(256) k_march_bwd_persistent(FrameParams P, con
 template <typename T, bool QUAD>
 static void bwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                        const Item* items, int n_items, const float4* tf, const float4* frag_rgba, const int* frag_key,
-                       const float4* frag_grad, double* dtf, float* dvol, Counters* counters, const Schedule* sch,
-                       cudaStream_t st) {
+                       const float4* frag_grad, double* dtf, float* dvol, float4* gface, Counters* counters,
+                       const Schedule* sch, cudaStream_t st) {
     int ncopy = bwd_tf_copies(P.ntf);
     size_t smem = sizeof(float4) * P.ntf + sizeof(float) * (size_t)ncopy * (4 * P.ntf + 1);
     if (sch) {
@@ -1032,26 +1044,26 @@ static void bwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDe
         cudaMemsetAsync(sch->work, 0, sizeof(unsigned int), st);
         k_march_bwd_persistent<T, QUAD><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched,
                                                                   n_items, sch->work, tf, frag_rgba, frag_key,
-                                                                  frag_grad, ncopy, dtf, dvol, counters);
+                                                                  frag_grad, ncopy, dtf, dvol, gface, counters);
         return;
     }
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_march_bwd<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_march_bwd<T, QUAD><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
-                                                      frag_grad, ncopy, dtf, dvol, counters);
+                                                      frag_grad, ncopy, dtf, dvol, gface, counters);
 }
 
 cudaError_t launch_march_bwd(int dtype, bool quad, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, const float4* frag_rgba, const int* frag_key,
-                             const float4* frag_grad, double* dtf, float* dvol, Counters* counters,
-                             cudaStream_t st, const Schedule* sch) {
+                             const float4* frag_grad, double* dtf, float* dvol, float4* gface,
+                             Counters* counters, cudaStream_t st, const Schedule* sch) {
     if (n_items == 0) return cudaSuccess;
 #define BWD(T)                                                                                                 \
     (quad ? bwd_launch<T, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, \
-                                dvol, counters, sch, st)                                                        \
+                                dvol, gface, counters, sch, st)                                                 \
           : bwd_launch<T, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, \
-                                 dvol, counters, sch, st))
+                                 dvol, gface, counters, sch, st))
     switch (dtype) {
         case 0: BWD(float); break;
         case 1: BWD(__half); break;
@@ -1105,6 +1117,57 @@ cudaError_t launch_build_quad(int dtype, const void* src, const int s_n[3], void
         case 2: k_build_quad<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)src, s_n[0], s_n[1], s_n[2], (uint2*)dst); break;
         default: k_build_quad<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>((const __nv_fp8_e4m3*)src, s_n[0], s_n[1], s_n[2], (unsigned*)dst); break;
     }
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// face adjoint buffer -> global field gradient
+// ===========================================================================
+//
+// Node (x, y, z) of a brick is corner (0,0) of face (x, y), corner (1,0) of
+// face (x-1, y), corner (0,1) of face (x, y-1) and corner (1,1) of face
+// (x-1, y-1) in layer z, where those faces exist.  A global node's gradient
+// is the sum of those slots over every brick storing a copy of it (its owner
+// and the bricks whose ghost layer holds it), added in neighbour-list order.
+
+size_t face_slots(const int s_n[3]) { return (size_t)(s_n[0] - 1) * (s_n[1] - 1) * s_n[2]; }
+
+__global__ void k_face_gather(const BrickDev* bricks, const int* nb_first, const int* nb, const float4* gface,
+                              int dims0, int dims1, float* dvol) {
+    const int o = blockIdx.y;
+    const BrickDev bo = bricks[o];
+    const int nx = bo.o_hi[0] - bo.o_lo[0], ny = bo.o_hi[1] - bo.o_lo[1], nz = bo.o_hi[2] - bo.o_lo[2];
+    const long long nxy = (long long)nx * ny, n = nxy * nz;
+    const int j0 = nb_first[o], j1 = nb_first[o + 1];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long zz = i / nxy, r = i - zz * nxy, yy = r / nx;
+        const int gx = bo.o_lo[0] + (int)(r - yy * nx), gy = bo.o_lo[1] + (int)yy, gz = bo.o_lo[2] + (int)zz;
+        float v = 0.0f;
+        for (int j = j0; j < j1; ++j) {
+            const BrickDev& b = bricks[nb[j]];
+            const int lx = gx - b.s_lo[0], ly = gy - b.s_lo[1], lz = gz - b.s_lo[2];
+            if (lx < 0 || ly < 0 || lz < 0 || lx >= b.s_n[0] || ly >= b.s_n[1] || lz >= b.s_n[2]) continue;
+            const float4* F = gface + b.gface_off + (long long)lz * b.qxy;
+            const bool xl = lx >= 1, xr = lx <= b.s_n[0] - 2, yl = ly >= 1, yr = ly <= b.s_n[1] - 2;
+            const long long r0 = (long long)ly * b.qx, r1 = r0 - b.qx;
+            if (xr && yr) v += F[r0 + lx].x;
+            if (xl && yr) v += F[r0 + lx - 1].y;
+            if (xr && yl) v += F[r1 + lx].z;
+            if (xl && yl) v += F[r1 + lx - 1].w;
+        }
+        dvol[((long long)gz * dims1 + gy) * dims0 + gx] = v;
+    }
+}
+
+cudaError_t launch_face_gather(const BrickDev* bricks, int nbricks, const int* nb_first, const int* nb,
+                               long long max_owned, const float4* gface, const int dims[3], float* dvol,
+                               cudaStream_t st) {
+    if (nbricks <= 0 || max_owned <= 0) return cudaSuccess;
+    long long bx = (max_owned + 255) / 256;
+    if (bx > 2048) bx = 2048;
+    dim3 grid((unsigned)bx, (unsigned)nbricks);
+    k_face_gather<<<grid, 256, 0, st>>>(bricks, nb_first, nb, gface, dims[0], dims[1], dvol);
     return cudaGetLastError();
 }
 

@@ -74,8 +74,18 @@ cudaError_t launch_composite_bwd(const FrameParams& P, const int* tile_first, co
 cudaError_t launch_march_bwd(int dtype, bool quad, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, const float4* frag_rgba, const int* frag_key,
-                             const float4* frag_grad, double* dtf, float* dvol, Counters* counters,
-                             cudaStream_t st, const Schedule* sch = nullptr);
+                             const float4* frag_grad, double* dtf, float* dvol, float4* gface,
+                             Counters* counters, cudaStream_t st, const Schedule* sch = nullptr);
+
+// Face adjoint buffer (kernels.cu): float4 slots it needs for a brick (one
+// per cell face, as the gather layout), and the pass that turns the buffer
+// into the global field gradient: every owned node of every brick is
+// written once (no zeroing needed) with the sum of its face slots over the
+// bricks in its owner's neighbour list nb[nb_first[o] .. nb_first[o+1]).
+size_t face_slots(const int s_n[3]);
+cudaError_t launch_face_gather(const BrickDev* bricks, int nbricks, const int* nb_first, const int* nb,
+                               long long max_owned, const float4* gface, const int dims[3], float* dvol,
+                               cudaStream_t st);
 
 // Gather layout of a brick (kernels.cu): bytes it needs, and its build from
 // the stored nodes.

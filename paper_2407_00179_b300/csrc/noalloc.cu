@@ -106,7 +106,10 @@ extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_ca
             b.r0[a] = lo < 0.0f ? 0.0f : lo;
             b.r1[a] = hi > (float)(sc->dims[a] - 1) ? (float)(sc->dims[a] - 1) : hi;
             b.closed[a] = h.owned_hi[a] >= sc->dims[a] ? 1 : 0;
+            b.o_lo[a] = h.owned_lo[a];
+            b.o_hi[a] = h.owned_hi[a];
         }
+        b.gface_off = 0;   // no backward here
         if (nodes > 0x7fffffffLL) return na_fail(DPV_ERR_UNSUPPORTED, "brick too large");
         total += v;
         for (int m = 0; m < k; ++m) {
@@ -141,6 +144,7 @@ extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_ca
     P.ert = fr->ert_threshold;
     P.ert_on = (fr->ert_threshold > 0.0f && fr->ert_threshold < 1.0f) ? 1 : 0;
     P.vmin = sc->vmin;
+    P.vmax = sc->vmax;
     P.tf_scale = (float)(sc->tf_n - 1) / (sc->vmax - sc->vmin);
     P.ntf = sc->tf_n;
     for (int a = 0; a < 3; ++a) P.dims[a] = sc->dims[a];
