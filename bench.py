@@ -37,6 +37,10 @@ from paper_2407_00179_b300 import inputs  # noqa: E402
 
 METRIC = "Gsamples/s and composited frames/s at 1 B300 (% HBM roofline); backward Gsamples/s"
 BYTES_PER_VOXEL = {"f32": 4, "f16": 2, "bf16": 2, "fp8": 1}
+# DRAM bytes (read + write) per launch of the timed kernels, from one ncu
+# capture of this workload (profiles/ holds the summary and the command);
+# absent where no capture of the current kernel exists
+TRAFFIC = {}
 
 CONFIGS = {
     # 512^3 f32, 64 blobs + 3-octave noise, 2x2x2 bricks, 1920x1080, ERT 0.99
@@ -256,7 +260,7 @@ def run_ours(args, cfg_name, cfg):
     dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=(args.tile_w, args.tile_h))
     tune = None
     if not args.no_autotune:
-        tune = dev.autotune(frames=3)
+        tune = dev.autotune(frames=3, cache=args.autotune_cache, key=cfg_name)
         fl = tune["flags"]
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=tuple(tune["tile"]),
                       gather="linear" if fl & dpv.FRAME_LINEAR else "quad", persistent=bool(fl & dpv.FRAME_PERSISTENT))
@@ -321,6 +325,7 @@ def run_ours(args, cfg_name, cfg):
     march_bwd_ms = st["stage_ms"]["march_bwd"] / max(1, st["stage_calls"]["march_bwd"])
     bytes_per_launch = st["samples_forward"] * 8 * bpv
     achieved = bytes_per_launch / (march_ms * 1e-3) / 1e9
+    bwd_achieved = st["samples_backward"] * (8 * bpv + 8 * 4) / (march_bwd_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
 
     # many cameras: the same forward replayed from a CUDA graph, and the
@@ -416,11 +421,18 @@ def run_ours(args, cfg_name, cfg):
                      "ms_per_step": bwd_ms / args.steps},
         "samples_per_step": {"forward": st["samples_forward"], "backward": st["samples_backward"]},
         "stage_ms_per_step": {k: v / max(1, args.steps) for k, v in st["stage_ms"].items()},
+        "value_basis": "forward samples evaluated / forward time (cull + march + composite) of the timed steps; "
+                       "each step also runs the backward, reported under 'backward' and in ms_per_step",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_march_fwd<%s>" % cfg["storage"],
+                     "traffic": TRAFFIC.get((cfg_name, "march")), "kernel": "k_march_fwd<%s>" % cfg["storage"],
                      "model": "stencil bytes: 8 corners x %d B per evaluated sample" % bpv,
-                     "peak_kind": peak_kind,
-                     "backward_frac": st["samples_backward"] * 8 * bpv / (march_bwd_ms * 1e-3) / 1e9 / peak},
+                     "peak_kind": peak_kind},
+        "roofline_backward": {"bound": "hbm", "achieved": bwd_achieved, "peak": peak, "unit": "GB/s",
+                              "frac": bwd_achieved / peak, "traffic": TRAFFIC.get((cfg_name, "march_bwd")),
+                              "kernel": "k_march_bwd<%s> (+ k_face_gather)" % cfg["storage"],
+                              "model": "stencil bytes: 8 corners x %d B read + 8 x 4 B field-gradient adds per "
+                                       "replayed sample" % bpv,
+                              "peak_kind": peak_kind},
         "e2e": {"value": e2e_val * ws_factor, "unit": "Gsamples/s", "h2d_bytes_per_step": int(tf_np.nbytes),
                 "d2h_bytes_per_step": int(ncam * H * W * 16), "what": "set TF from pinned host, render, copy frames"
                 " to pinned host, per step (forward)"},
@@ -457,6 +469,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune-cache", default=None,
+                    help="JSON file: reuse the stored launch choice for this workload and GPU, else tune and store it")
     args = ap.parse_args()
     cfg = CONFIGS[args.config]
     if args.impl == "reference":

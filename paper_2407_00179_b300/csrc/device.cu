@@ -77,7 +77,7 @@ struct dpv_device_t {
     std::vector<CamIn> cams;
     CamIn* d_cam_in = nullptr;
     CamBasis* d_cams = nullptr;
-    CamBasisD* d_camd = nullptr;
+    CamBasisDF* d_camd = nullptr;
     int cam_cap = 0;
     float4* d_rays = nullptr;           // per camera and pixel ray directions
     size_t rays_cap = 0;
@@ -115,7 +115,7 @@ struct dpv_device_t {
     size_t gface_slots = 0;             // slots the current bricks need
     int* d_nb_first = nullptr;          // nranks + 1
     int* d_nb = nullptr;                // nranks * nranks
-    long long max_owned = 0;            // largest owned node count
+    long long max_rows = 0;             // most owned (y, z) node rows of a brick
 
     // persistent schedule (DPV_FRAME_PERSISTENT)
     int* d_sched = nullptr;
@@ -359,7 +359,7 @@ dpv_status prepare(dpv_device dev) {
             const HostBrick& h = dev->bricks[k];
             table[k].gface_off = (long long)off;
             off += face_slots(h.s_n);
-            mo = std::max(mo, (long long)(h.hi[0] - h.lo[0]) * (h.hi[1] - h.lo[1]) * (h.hi[2] - h.lo[2]));
+            mo = std::max(mo, (long long)(h.hi[1] - h.lo[1]) * (h.hi[2] - h.lo[2]));
             first[k] = (int)nb.size();
             nb.push_back(k);
             for (int m = 0; m < dev->nranks; ++m) {
@@ -372,7 +372,7 @@ dpv_status prepare(dpv_device dev) {
         }
         first[dev->nranks] = (int)nb.size();
         dev->gface_slots = off;
-        dev->max_owned = mo;
+        dev->max_rows = mo;
         if (!dev->d_nb_first) {
             dpv_status s2 = dev_alloc(dev, (void**)&dev->d_nb_first, sizeof(int) * (MAX_RANKS + 1), "neighbour lists");
             if (s2) return s2;
@@ -430,7 +430,7 @@ dpv_status prepare(dpv_device dev) {
         if (s) return s;
         s = dev_alloc(dev, (void**)&dev->d_cams, sizeof(CamBasis) * dev->cams.size(), "cameras");
         if (s) return s;
-        s = dev_alloc(dev, (void**)&dev->d_camd, sizeof(CamBasisD) * dev->cams.size(), "cameras");
+        s = dev_alloc(dev, (void**)&dev->d_camd, sizeof(CamBasisDF) * dev->cams.size(), "cameras");
         if (s) return s;
         dev->cam_cap = (int)dev->cams.size();
     }
@@ -1000,7 +1000,7 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
                             dev->d_counters, dev->stream, persistent ? &sch : nullptr),
            "march backward");
         if (faces) {
-            CK(launch_face_gather(dev->d_bricks, dev->nranks, dev->d_nb_first, dev->d_nb, dev->max_owned,
+            CK(launch_face_gather(dev->d_bricks, dev->nranks, dev->d_nb_first, dev->d_nb, dev->max_rows,
                                   dev->d_gface, dev->dims, dL_dvol, dev->stream),
                "face gather");
             dev->launches += 1;

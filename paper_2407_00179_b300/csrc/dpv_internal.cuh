@@ -35,11 +35,71 @@ struct CamBasis {
 };
 
 // The same camera basis in FP64, for the per-pixel ray setup.
-struct CamBasisD {
-    double o[3];       // eye in node coordinates
-    double f[3], r[3], u[3];
-    double th;
+// A value held as the unevaluated sum hi + lo of two floats, |lo| <= ulp(hi)/2:
+// about 48 significant bits at FP32 speed (FP64 runs at a small fraction of
+// the FP32 rate on this GPU).
+struct DF {
+    float hi, lo;
 };
+
+// Per camera in double-float, rounded once from FP64: eye in node
+// coordinates, basis, the pixel scale k = tan(fovy / 2) / H (screen
+// x = (2 px + 1 - W) k, y = (2 py + 1 - H) k) and 1 / spacing.
+struct CamBasisDF {
+    DF o[3];
+    DF f[3], r[3], u[3];
+    DF k;
+    DF inv_spacing;
+};
+
+// Double-float arithmetic from the error-free transformations: Knuth's
+// TwoSum, Dekker's Fast2Sum (|a| >= |b|), and the product error by FMA.
+__device__ __forceinline__ DF df_fast2sum(float a, float b) {
+    float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_2sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    return DF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF df_2prod(float a, float b) {
+    float p = a * b;
+    return DF{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+    DF s = df_2sum(x.hi, y.hi), t = df_2sum(x.lo, y.lo);
+    s = df_fast2sum(s.hi, s.lo + t.hi);
+    return df_fast2sum(s.hi, s.lo + t.lo);
+}
+__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.hi, -x.lo}; }
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+    DF p = df_2prod(x.hi, y.hi);
+    return df_fast2sum(p.hi, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
+}
+__device__ __forceinline__ DF df_mulf(DF x, float b) {
+    DF p = df_2prod(x.hi, b);
+    return df_fast2sum(p.hi, fmaf(x.lo, b, p.lo));
+}
+// 1 / y: the FP32 quotient and one Newton step in double-float
+__device__ __forceinline__ DF df_rcp(DF y) {
+    float r0 = 1.0f / y.hi;
+    DF p = df_mulf(y, r0);                 // y r0 = 1 - e
+    float e = (1.0f - p.hi) - p.lo;
+    return df_fast2sum(r0, r0 * e);
+}
+// 1 / sqrt(y), y > 0: the FP32 estimate and one Newton step in double-float
+__device__ __forceinline__ DF df_rsqrt(DF y) {
+    float r0 = rsqrtf(y.hi);
+    DF q = df_mulf(df_mulf(y, r0), r0);    // y r0^2 = 1 - e
+    float e = (1.0f - q.hi) - q.lo;
+    return df_fast2sum(r0, 0.5f * r0 * e);
+}
+__device__ __forceinline__ bool df_lt(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ DF df_of(double v) {
+    float hi = (float)v;
+    return DF{hi, (float)(v - (double)hi)};
+}
 
 // One rank's brick as the kernels see it.
 struct BrickDev {

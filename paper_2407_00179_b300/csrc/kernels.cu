@@ -119,9 +119,10 @@ cudaError_t launch_commit(const CommitArgs& a, int storage, int src_is_f32, floa
 // cameras and culling (work list)
 // ===========================================================================
 
-__global__ void k_cam_setup(const CamIn* cams, int n, float3 origin, float spacing, CamBasis* out,
-                            CamBasisD* outd) {
-    // once per camera, so computed in FP64 and rounded once to FP32
+__global__ void k_cam_setup(const CamIn* cams, int n, float3 origin, float spacing, int H, CamBasis* out,
+                            CamBasisDF* outd) {
+    // once per camera, so computed in FP64 and rounded once to FP32 (and to
+    // double-float for the ray setup)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     CamIn c = cams[i];
@@ -135,8 +136,10 @@ __global__ void k_cam_setup(const CamIn* cams, int n, float3 origin, float spaci
     double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
     CamBasis b;
     const double og[3] = {origin.x, origin.y, origin.z};
+    double o[3];
     for (int a = 0; a < 3; ++a) {
-        b.o[a] = (float)(((double)c.eye[a] - og[a]) / (double)spacing);
+        o[a] = ((double)c.eye[a] - og[a]) / (double)spacing;
+        b.o[a] = (float)o[a];
         b.f[a] = (float)f[a];
         b.r[a] = (float)r[a];
         b.u[a] = (float)u[a];
@@ -145,74 +148,76 @@ __global__ void k_cam_setup(const CamIn* cams, int n, float3 origin, float spaci
     b.th = (float)th;
     b.pad = 0.0f;
     out[i] = b;
-    CamBasisD bd;
+    CamBasisDF bd;
     for (int a = 0; a < 3; ++a) {
-        bd.o[a] = ((double)c.eye[a] - og[a]) / (double)spacing;
-        bd.f[a] = f[a];
-        bd.r[a] = r[a];
-        bd.u[a] = u[a];
+        bd.o[a] = df_of(o[a]);
+        bd.f[a] = df_of(f[a]);
+        bd.r[a] = df_of(r[a]);
+        bd.u[a] = df_of(u[a]);
     }
-    bd.th = th;
+    bd.k = df_of(th / (double)H);
+    bd.inv_spacing = df_of(1.0 / (double)spacing);
     outd[i] = bd;
 }
 
 // Ray setup: direction of every pixel's ray, normalize(f + x th r + y th u)
-// with x = ((px + 1/2) / W * 2 - 1) * W / H and y = (py + 1/2) / H * 2 - 1,
-// computed in FP64 (the norm by an FP32 reciprocal square root refined with
-// one Newton step in FP64) and scaled to node units per world t.  Stored per
-// ray (RAY_VECS float4):
+// with x = ((px + 1/2) / W * 2 - 1) * W / H and y = (py + 1/2) / H * 2 - 1
+// (that is x th = (2 px + 1 - W) th / H, y th = (2 py + 1 - H) th / H),
+// scaled to node units per world t, in double-float arithmetic (the norm by
+// an FP32 reciprocal square root and one Newton step).  Stored per ray
+// (RAY_VECS float4):
 //   0: direction rounded to FP32, t_enter      (FP32, from the FP32 slab)
 //   1: FP32 reciprocal direction, t_exit
-//   2: entry point eye + t_enter d, high FP32 part (FP64 slab and product)
-//   3: entry point, low part (FP64 value minus the high part)
+//   2: entry point eye + t_enter d, high FP32 part (double-float slab and
+//      product)
+//   3: entry point, low part
 //   4: direction, low part
 // The FP32 parts fix the sample ranges (identical planes in every kernel);
 // the pairs place each brick's first sample accurately.
-__global__ void k_rays(FrameParams P, const CamBasis* cams, const CamBasisD* camd, double inv_spacing, double sx,
-                       double sy, double aspect, float4* rays) {
+__global__ void k_rays(FrameParams P, const CamBasis* cams, const CamBasisDF* camd, float4* rays) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long npix = (long long)P.W * P.H;
     if (i >= npix * P.ncam) return;
     int c = (int)(i / npix);
     int p = (int)(i - c * npix);
     int px = p % P.W, py = p / P.W;
-    const CamBasisD& b = camd[c];
-    double x = ((px + 0.5) * sx - 1.0) * aspect * b.th;
-    double y = ((py + 0.5) * sy - 1.0) * b.th;
-    double d0 = b.f[0] + x * b.r[0] + y * b.u[0];
-    double d1 = b.f[1] + x * b.r[1] + y * b.u[1];
-    double d2 = b.f[2] + x * b.r[2] + y * b.u[2];
-    double n2 = d0 * d0 + d1 * d1 + d2 * d2;
-    double yr = (double)rsqrtf((float)n2);
-    yr = yr * (1.5 - 0.5 * n2 * yr * yr);
-    double n = yr * inv_spacing;
-    const double dd[3] = {d0 * n, d1 * n, d2 * n};
+    const CamBasisDF& b = camd[c];
+    const DF x = df_mulf(b.k, (float)(2 * px + 1 - P.W));
+    const DF y = df_mulf(b.k, (float)(2 * py + 1 - P.H));
+    DF d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = df_add(b.f[a], df_add(df_mul(x, b.r[a]), df_mul(y, b.u[a])));
+    const DF n2 = df_add(df_add(df_mul(d[0], d[0]), df_mul(d[1], d[1])), df_mul(d[2], d[2]));
+    const DF n = df_mul(df_rsqrt(n2), b.inv_spacing);
+    DF dd[3];
     Ray r;
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        r.d[a] = (float)dd[a];
+        dd[a] = df_mul(d[a], n);
+        r.d[a] = dd[a].hi;                 // the FP32 rounding of the direction
         r.o[a] = cams[c].o[a];
         r.inv[a] = 1.0f / r.d[a];
     }
     if (!volume_interval(P.dims, r.o, r.d, r.inv, r.te, r.tx)) r.te = r.tx = 0.0f;
-    // FP64 entry point: slab against [0, dims - 1] with the FP64 ray
-    const double eo[3] = {b.o[0], b.o[1], b.o[2]};
-    double te = 0.0, tx = 1e300;
+    // accurate entry point: slab against [0, dims - 1] with the double-float ray
+    DF te = DF{0.0f, 0.0f};
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (dd[a] != 0.0) {
-            double inv = (double)(1.0f / (float)dd[a]);
-            inv = inv * (2.0 - dd[a] * inv);
-            inv = inv * (2.0 - dd[a] * inv);
-            double ta = (0.0 - eo[a]) * inv, tb = ((double)(P.dims[a] - 1) - eo[a]) * inv;
-            te = fmax(te, fmin(ta, tb));
-            tx = fmin(tx, fmax(ta, tb));
+        if (dd[a].hi != 0.0f) {
+            const DF inv = df_rcp(dd[a]);
+            const DF ta = df_mul(df_neg(b.o[a]), inv);
+            const DF tb = df_mul(df_add(DF{(float)(P.dims[a] - 1), 0.0f}, df_neg(b.o[a])), inv);
+            const DF near = df_lt(ta, tb) ? ta : tb;
+            if (df_lt(te, near)) te = near;
         }
     }
     float ph[3], pl[3], dl[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double pe = eo[a] + te * dd[a];
-        ph[a] = (float)pe;
-        pl[a] = (float)(pe - (double)ph[a]);
-        dl[a] = (float)(dd[a] - (double)r.d[a]);
+        const DF pe = df_add(b.o[a], df_mul(te, dd[a]));
+        ph[a] = pe.hi;
+        pl[a] = pe.lo;
+        dl[a] = dd[a].lo;
     }
     float4* o = rays + RAY_VECS * i;
     o[0] = make_float4(r.d[0], r.d[1], r.d[2], r.te);
@@ -356,14 +361,13 @@ __global__ void k_cull_fill(FrameParams P, const int4* rects, const int* tile_fi
 }
 
 cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 origin, float spacing,
-                        CamBasis* d_cams, CamBasisD* d_camd, float4* d_rays, const BrickDev* d_bricks,
+                        CamBasis* d_cams, CamBasisDF* d_camd, float4* d_rays, const BrickDev* d_bricks,
                         int4* d_rects, int* d_tile_count, int* d_tile_first, Item* d_items, int cap,
                         Counters* d_counters, bool fill, cudaStream_t st) {
-    k_cam_setup<<<(P.ncam + 63) / 64, 64, 0, st>>>(d_cam_in, P.ncam, origin, spacing, d_cams, d_camd);
+    k_cam_setup<<<(P.ncam + 63) / 64, 64, 0, st>>>(d_cam_in, P.ncam, origin, spacing, P.H, d_cams, d_camd);
     if (fill) {
         long long n = (long long)P.ncam * P.W * P.H;
-        k_rays<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, d_cams, d_camd, 1.0 / (double)spacing, 2.0 / P.W,
-                                                            2.0 / P.H, (double)P.W / (double)P.H, d_rays);
+        k_rays<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, d_cams, d_camd, d_rays);
     }
     int ncb = P.ncam * P.nbricks;
     k_cull_rects<<<(ncb + 127) / 128, 128, 0, st>>>(P, d_cams, d_bricks, d_rects);
@@ -1132,42 +1136,93 @@ cudaError_t launch_build_quad(int dtype, const void* src, const int s_n[3], void
 
 size_t face_slots(const int s_n[3]) { return (size_t)(s_n[0] - 1) * (s_n[1] - 1) * s_n[2]; }
 
-__global__ void k_face_gather(const BrickDev* bricks, const int* nb_first, const int* nb, const float4* gface,
-                              int dims0, int dims1, float* dvol) {
+// Rows of nodes a thread gathers at once (face rows ly - 1 .. ly + GR - 1
+// are loaded together, each once, so their latencies overlap).
+constexpr int GR = 4;
+
+__global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, const int* nb_first, const int* nb,
+                                                     const float4* gface, int dims0, int dims1, float* dvol) {
     const int o = blockIdx.y;
     const BrickDev bo = bricks[o];
     const int nx = bo.o_hi[0] - bo.o_lo[0], ny = bo.o_hi[1] - bo.o_lo[1], nz = bo.o_hi[2] - bo.o_lo[2];
-    const long long nxy = (long long)nx * ny, n = nxy * nz;
+    const int ngy = (ny + GR - 1) / GR;
+    const int ngroups = ngy * nz;
     const int j0 = nb_first[o], j1 = nb_first[o + 1];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long zz = i / nxy, r = i - zz * nxy, yy = r / nx;
-        const int gx = bo.o_lo[0] + (int)(r - yy * nx), gy = bo.o_lo[1] + (int)yy, gz = bo.o_lo[2] + (int)zz;
-        float v = 0.0f;
-        for (int j = j0; j < j1; ++j) {
-            const BrickDev& b = bricks[nb[j]];
-            const int lx = gx - b.s_lo[0], ly = gy - b.s_lo[1], lz = gz - b.s_lo[2];
-            if (lx < 0 || ly < 0 || lz < 0 || lx >= b.s_n[0] || ly >= b.s_n[1] || lz >= b.s_n[2]) continue;
-            const float4* F = gface + b.gface_off + (long long)lz * b.qxy;
-            const bool xl = lx >= 1, xr = lx <= b.s_n[0] - 2, yl = ly >= 1, yr = ly <= b.s_n[1] - 2;
-            const long long r0 = (long long)ly * b.qx, r1 = r0 - b.qx;
-            if (xr && yr) v += F[r0 + lx].x;
-            if (xl && yr) v += F[r0 + lx - 1].y;
-            if (xr && yl) v += F[r1 + lx].z;
-            if (xl && yl) v += F[r1 + lx - 1].w;
+    const int lane = threadIdx.x & 31;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int yy0 = (grp % ngy) * GR, zz = grp / ngy;
+        const int gy0 = bo.o_lo[1] + yy0, gz = bo.o_lo[2] + zz;
+        const int ly0 = gy0 - bo.s_lo[1], lz = gz - bo.s_lo[2];
+        const float4* F = gface + bo.gface_off + (long long)lz * bo.qxy;
+        // block-uniform trip count: the shuffles below need every lane
+        for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
+            const int xo = x0 + threadIdx.x;
+            const bool act = xo < nx;
+            const int gx = bo.o_lo[0] + xo, lx = gx - bo.s_lo[0];
+            const bool xl = lx >= 1, xr = lx <= bo.s_n[0] - 2;
+            // face rows ly0 - 1 + k, k = 0 .. GR: this node's face and, from
+            // lane - 1 (the node at x - 1), the face to its left
+            float4 A[GR + 1];
+            float Ly[GR + 1], Lw[GR + 1];
+#pragma unroll
+            for (int k = 0; k <= GR; ++k) {
+                const int fy = ly0 - 1 + k;
+                const bool ok = act && xr && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
+                A[k] = ok ? F[(long long)fy * bo.qx + lx] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k <= GR; ++k) {
+                Ly[k] = __shfl_up_sync(0xffffffffu, A[k].y, 1);
+                Lw[k] = __shfl_up_sync(0xffffffffu, A[k].w, 1);
+            }
+            if (lane == 0 || xo == 0) {
+#pragma unroll
+                for (int k = 0; k <= GR; ++k) {
+                    const int fy = ly0 - 1 + k;
+                    const bool ok = act && xl && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
+                    const float4 q = ok ? F[(long long)fy * bo.qx + lx - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    Ly[k] = q.y;
+                    Lw[k] = q.w;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < GR; ++k) {
+                const int yy = yy0 + k;
+                if (!act || yy >= ny) continue;
+                const int gy = gy0 + k;
+                // node row ly0 + k: corner (0,0) of face row k+1, (1,0) of its
+                // left face, (0,1) of face row k, (1,1) of its left face
+                float v = A[k + 1].x + Ly[k + 1] + A[k].z + Lw[k];
+                // ghost copies in other bricks exist only for nodes on the
+                // owned box's surface
+                if (yy == 0 || yy == ny - 1 || zz == 0 || zz == nz - 1 || xo == 0 || xo == nx - 1) {
+                    for (int j = j0 + 1; j < j1; ++j) {
+                        const BrickDev& b = bricks[nb[j]];
+                        const int mx = gx - b.s_lo[0], my = gy - b.s_lo[1], mz = gz - b.s_lo[2];
+                        if (mx < 0 || my < 0 || mz < 0 || mx >= b.s_n[0] || my >= b.s_n[1] || mz >= b.s_n[2]) continue;
+                        const float4* G = gface + b.gface_off + (long long)mz * b.qxy;
+                        const bool bxl = mx >= 1, bxr = mx <= b.s_n[0] - 2, byl = my >= 1, byr = my <= b.s_n[1] - 2;
+                        const long long q0 = (long long)my * b.qx, q1 = q0 - b.qx;
+                        if (bxr && byr) v += G[q0 + mx].x;
+                        if (bxl && byr) v += G[q0 + mx - 1].y;
+                        if (bxr && byl) v += G[q1 + mx].z;
+                        if (bxl && byl) v += G[q1 + mx - 1].w;
+                    }
+                }
+                dvol[((long long)gz * dims1 + gy) * dims0 + gx] = v;
+            }
         }
-        dvol[((long long)gz * dims1 + gy) * dims0 + gx] = v;
     }
 }
 
 cudaError_t launch_face_gather(const BrickDev* bricks, int nbricks, const int* nb_first, const int* nb,
-                               long long max_owned, const float4* gface, const int dims[3], float* dvol,
+                               long long max_rows, const float4* gface, const int dims[3], float* dvol,
                                cudaStream_t st) {
-    if (nbricks <= 0 || max_owned <= 0) return cudaSuccess;
-    long long bx = (max_owned + 255) / 256;
-    if (bx > 2048) bx = 2048;
+    if (nbricks <= 0 || max_rows <= 0) return cudaSuccess;
+    long long groups = (max_rows + GR - 1) / GR;
+    long long bx = groups < 4096 ? groups : 4096;
     dim3 grid((unsigned)bx, (unsigned)nbricks);
-    k_face_gather<<<grid, 256, 0, st>>>(bricks, nb_first, nb, gface, dims[0], dims[1], dvol);
+    k_face_gather<<<grid, 128, 0, st>>>(bricks, nb_first, nb, gface, dims[0], dims[1], dvol);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ cudaError_t launch_commit(const CommitArgs& a, int storage, int src_is_f32, floa
                           float* d_scale, void* dst, cudaStream_t st);
 
 cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 origin, float spacing,
-                        CamBasis* d_cams, CamBasisD* d_camd, float4* d_rays, const BrickDev* d_bricks,
+                        CamBasis* d_cams, CamBasisDF* d_camd, float4* d_rays, const BrickDev* d_bricks,
                         int4* d_rects, int* d_tile_count, int* d_tile_first, Item* d_items, int cap,
                         Counters* d_counters, bool fill, cudaStream_t st);
 
@@ -84,7 +84,7 @@ cudaError_t launch_march_bwd(int dtype, bool quad, const FrameParams& P, const C
 // bricks in its owner's neighbour list nb[nb_first[o] .. nb_first[o+1]).
 size_t face_slots(const int s_n[3]);
 cudaError_t launch_face_gather(const BrickDev* bricks, int nbricks, const int* nb_first, const int* nb,
-                               long long max_owned, const float4* gface, const int dims[3], float* dvol,
+                               long long max_rows, const float4* gface, const int dims[3], float* dvol,
                                cudaStream_t st);
 
 // Gather layout of a brick (kernels.cu): bytes it needs, and its build from

@@ -166,7 +166,7 @@ extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_ca
     size_t o_scales = take(sizeof(float) * K);
     size_t o_camin = take(sizeof(CamIn));
     size_t o_cam = take(sizeof(CamBasis));
-    size_t o_camd = take(sizeof(CamBasisD));
+    size_t o_camd = take(sizeof(CamBasisDF));
     size_t o_counters = take(sizeof(Counters));
     size_t o_rays = take(RAY_VECS * sizeof(float4) * npix);
     size_t o_rects = take(sizeof(int4) * K);
@@ -197,7 +197,7 @@ extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_ca
     float* d_scales = (float*)(base + o_scales);
     CamIn* d_camin = (CamIn*)(base + o_camin);
     CamBasis* d_cam = (CamBasis*)(base + o_cam);
-    CamBasisD* d_camd = (CamBasisD*)(base + o_camd);
+    CamBasisDF* d_camd = (CamBasisDF*)(base + o_camd);
     Counters* d_counters = (Counters*)(base + o_counters);
     float4* d_rays = (float4*)(base + o_rays);
     int4* d_rects = (int4*)(base + o_rects);
