@@ -263,7 +263,7 @@ def run_ours(args, cfg_name, cfg):
         tune = dev.autotune(frames=3, cache=args.autotune_cache, key=cfg_name)
         fl = tune["flags"]
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=tuple(tune["tile"]),
-                      gather="linear" if fl & dpv.FRAME_LINEAR else "quad", persistent=bool(fl & dpv.FRAME_PERSISTENT))
+                      gather=dpv.gather_of(fl), persistent=bool(fl & dpv.FRAME_PERSISTENT))
     # fixed upstream gradient: d/dI of mean (I - I*)^2 with I* from a perturbed TF
     dev.set_tf(torch.from_numpy(inputs.perturb_tf(tf_np, 0)).to(device))
     dev.render()
@@ -333,8 +333,7 @@ def run_ours(args, cfg_name, cfg):
     batch = None
     if ncam > 1 and compare_f32:
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=tuple(tune["tile"]) if tune else
-                      (args.tile_w, args.tile_h), gather="linear" if tune and tune["flags"] & dpv.FRAME_LINEAR else
-                      "quad", persistent=bool(tune and tune["flags"] & dpv.FRAME_PERSISTENT), graph=True)
+                      (args.tile_w, args.tile_h), gather=dpv.gather_of(tune["flags"]) if tune else "auto", persistent=bool(tune and tune["flags"] & dpv.FRAME_PERSISTENT), graph=True)
         for _ in range(2):
             dev.render()
         torch.cuda.synchronize()

@@ -110,18 +110,22 @@ typedef struct {
 #define DPV_FRAME_STAGED 2         /* stage brick slabs in shared memory instead of
                                       gathering through L1 (same results for float32
                                       bricks; a tuning variant) */
-#define DPV_FRAME_LINEAR 4         /* gather the 8 corners from the stored nodes instead
-                                      of the "quad" gather layout (per cell face the 2x2
-                                      corners in one vector, 2 loads per sample) that the
-                                      device builds from each committed brick at the next
-                                      render and keeps (4x the brick's device memory);
-                                      identical results */
+/* Gather layout of the ray-march (identical results in every layout).  By
+ * default the device builds, at the next render, the "cell" layout (per cell
+ * its 8 corners in one vector: one load per sample, 8x the bricks' device
+ * memory) when it fits in half of the free device memory, else the "quad"
+ * layout (per cell face the 2x2 corners in one vector: two loads per sample,
+ * 4x), and keeps it.  The flags below force a layout; LINEAR takes
+ * precedence, then CELL, then QUAD. */
+#define DPV_FRAME_LINEAR 4         /* gather the 8 corners from the stored nodes */
 #define DPV_FRAME_PERSISTENT 8     /* persistent ray-march: a grid sized to the GPU pulls
                                       work items from a counter in brick-major order (all
                                       cameras' tiles of one brick together) */
 #define DPV_FRAME_GRAPH 16         /* replay the frame's launches from a CUDA graph
                                       captured at the first render after a change (not
                                       while profiling is on) */
+#define DPV_FRAME_CELL 32          /* the cell layout, whether or not it fits */
+#define DPV_FRAME_QUAD 64          /* the quad layout */
 
 /* Frame parameters, identical on all ranks (§3.1.1).  Every camera renders
  * a width x height image.  tile_w/tile_h: pixels per work item (multiples
@@ -250,7 +254,8 @@ dpv_status dpvGetStats(dpv_device dev, dpv_stats* out);
 /* Result of dpvAutotune. */
 typedef struct {
     int tile_w, tile_h;   /* chosen tile */
-    int flags;            /* chosen DPV_FRAME_LINEAR / DPV_FRAME_PERSISTENT bits */
+    int flags;            /* chosen layout (DPV_FRAME_CELL / QUAD / LINEAR) and
+                             DPV_FRAME_PERSISTENT bits */
     float ms;             /* mean device time of one frame with the choice */
     int candidates;       /* configurations timed */
 } dpv_tune_result;

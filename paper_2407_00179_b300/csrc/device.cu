@@ -43,9 +43,10 @@ struct HostBrick {
     int dtype = 0;
     void* data = nullptr;       // device storage
     size_t bytes = 0;
-    void* quad = nullptr;       // gather layout built from `data` (see Quad)
-    size_t quad_bytes = 0;
-    bool quad_valid = false;
+    void* gather = nullptr;     // gather layout built from `data` (quad or cell)
+    size_t gather_bytes = 0;
+    int gather_kind = -1;       // GATHER_QUAD or GATHER_CELL
+    bool gather_valid = false;
 };
 
 const int kElemSize[4] = {4, 2, 2, 1};
@@ -106,7 +107,7 @@ struct dpv_device_t {
     Counters* d_counters = nullptr;
     cudaEvent_t ev_done = nullptr;
     bool rendered = false;
-    bool use_quad = false;
+    int gather = GATHER_QUAD;           // layout of the current frame
 
     // face adjoint buffer of the backward (float4 per cell face of every
     // brick) and each owner's neighbour list for the gather that follows
@@ -287,6 +288,22 @@ dpv_status check_partition(dpv_device dev) {
     return DPV_OK;
 }
 
+// Whether the cell gather layout of every brick fits in half of the device
+// memory that is free once the layouts held now are released.
+bool cell_fits(dpv_device dev) {
+    size_t need = 0, held = 0;
+    for (const HostBrick& h : dev->bricks) {
+        need += cell_bytes(h.dtype, h.s_n);
+        if (h.gather) held += h.gather_bytes;
+    }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return need <= (free_b + held) / 2;
+}
+
 // Build FrameParams, upload the brick table, run the cull once to size the
 // work list and fragment pool, and (re)allocate buffers.
 dpv_status prepare(dpv_device dev) {
@@ -341,7 +358,7 @@ dpv_status prepare(dpv_device dev) {
         b.sxy = h.s_n[0] * h.s_n[1];
         b.scale_idx = k;
         b.pad = 0;
-        b.quad = nullptr;
+        b.gather = nullptr;
         b.qx = h.s_n[0] - 1;
         b.qxy = (h.s_n[0] - 1) * (h.s_n[1] - 1);
         for (int a = 0; a < 3; ++a) {
@@ -386,30 +403,40 @@ dpv_status prepare(dpv_device dev) {
         // the uploads read host vectors that end with this scope
         CK(cudaStreamSynchronize(dev->stream), "upload neighbour lists");
     }
-    // gather layout (default): built once per committed brick
-    if (!(F.flags & DPV_FRAME_LINEAR)) {
+    // gather layout (by flag, else cell where it fits, else quad): built
+    // once per committed brick and layout
+    const int kind = (F.flags & DPV_FRAME_LINEAR) ? GATHER_LINEAR
+                     : (F.flags & DPV_FRAME_CELL) ? GATHER_CELL
+                     : (F.flags & DPV_FRAME_QUAD) ? GATHER_QUAD
+                     : cell_fits(dev)             ? GATHER_CELL
+                                                  : GATHER_QUAD;
+    if (kind != GATHER_LINEAR) {
         for (int k = 0; k < dev->nranks; ++k) {
             HostBrick& h = dev->bricks[k];
-            size_t qb = quad_bytes(h.dtype, h.s_n);
-            if (h.quad && h.quad_bytes != qb) {
-                dev_free(h.quad);
-                h.quad = nullptr;
-                h.quad_valid = false;
+            size_t gb = kind == GATHER_CELL ? cell_bytes(h.dtype, h.s_n) : quad_bytes(h.dtype, h.s_n);
+            if (h.gather && (h.gather_bytes != gb || h.gather_kind != kind)) {
+                dev_free(h.gather);
+                h.gather = nullptr;
+                h.gather_valid = false;
             }
-            if (!h.quad) {
-                dpv_status s2 = dev_alloc(dev, &h.quad, qb, "gather layout");
+            if (!h.gather) {
+                dpv_status s2 = dev_alloc(dev, &h.gather, gb, "gather layout");
                 if (s2) return s2;
-                h.quad_bytes = qb;
-                h.quad_valid = false;
+                h.gather_bytes = gb;
+                h.gather_kind = kind;
+                h.gather_valid = false;
             }
-            if (!h.quad_valid) {
-                CK(launch_build_quad(h.dtype, h.data, h.s_n, h.quad, dev->stream), "build gather layout");
-                h.quad_valid = true;
+            if (!h.gather_valid) {
+                if (kind == GATHER_CELL)
+                    CK(launch_build_cell(h.dtype, h.data, h.s_n, h.gather, dev->stream), "build gather layout");
+                else
+                    CK(launch_build_quad(h.dtype, h.data, h.s_n, h.gather, dev->stream), "build gather layout");
+                h.gather_valid = true;
             }
-            table[k].quad = h.quad;
+            table[k].gather = h.gather;
         }
     }
-    dev->use_quad = !(F.flags & DPV_FRAME_LINEAR);
+    dev->gather = kind;
     if (!dev->d_bricks) {
         dpv_status s = dev_alloc(dev, (void**)&dev->d_bricks, sizeof(BrickDev) * MAX_RANKS, "brick table");
         if (s) return s;
@@ -549,7 +576,7 @@ dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
     if (timed) stage_stop(dev, DPV_STAGE_CULL, t0);
     t0 = timed ? stage_start(dev) : nullptr;
     if (!(dev->frame.flags & DPV_FRAME_STAGED))
-        CK(launch_march_fwd(dev->bricks[0].dtype, dev->use_quad, P, dev->d_cams, dev->d_bricks, dev->d_scales,
+        CK(launch_march_fwd(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                             dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters,
                             st, persistent ? &sch : nullptr),
            "march");
@@ -650,7 +677,7 @@ dpv_status dpvSetVolumeGeometry(dpv_device dev, const int dims[3], const float o
     DeviceGuard g(dev->cuda_device);
     for (auto& b : dev->bricks) {
         dev_free(b.data);
-        dev_free(b.quad);
+        dev_free(b.gather);
         b = HostBrick();
     }
     for (int a = 0; a < 3; ++a) {
@@ -746,9 +773,10 @@ dpv_status dpvCommitBrick(dpv_device dev, int rank, const dpv_brick_desc* d) {
     }
     if (e != cudaSuccess) return cuda_fail(dev, e, "brick commit");
     nb.committed = true;
-    nb.quad = hb.quad;                  // the gather layout is rebuilt at the next render
-    nb.quad_bytes = hb.quad_bytes;
-    nb.quad_valid = false;
+    nb.gather = hb.gather;              // the gather layout is rebuilt at the next render
+    nb.gather_bytes = hb.gather_bytes;
+    nb.gather_kind = hb.gather_kind;
+    nb.gather_valid = false;
     hb = nb;
     dev->dirty = true;
     return DPV_OK;
@@ -994,7 +1022,7 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
     const bool persistent = (dev->frame.flags & DPV_FRAME_PERSISTENT) != 0;
     Schedule sch{dev->d_sched, dev->d_work, 0};   // the pull order built by the render
     if (!staged) {
-        CK(launch_march_bwd(dev->bricks[0].dtype, dev->use_quad, P, dev->d_cams, dev->d_bricks, dev->d_scales,
+        CK(launch_march_bwd(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                             dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key,
                             dev->d_frag_grad, dL_dtf, faces ? nullptr : dL_dvol, faces ? dev->d_gface : nullptr,
                             dev->d_counters, dev->stream, persistent ? &sch : nullptr),
@@ -1049,9 +1077,18 @@ dpv_status dpvAutotune(dpv_device dev, int frames, dpv_tune_result* out) {
     if (!dev->has_frame) return fail(DPV_ERR_STATE, "no frame parameters");
     DeviceGuard g(dev->cuda_device);
     const dpv_frame_desc keep = dev->frame;
-    const int tune_bits = DPV_FRAME_LINEAR | DPV_FRAME_PERSISTENT | DPV_FRAME_STAGED;
+    const int tune_bits =
+        DPV_FRAME_LINEAR | DPV_FRAME_CELL | DPV_FRAME_QUAD | DPV_FRAME_PERSISTENT | DPV_FRAME_STAGED;
     const int tiles[4][2] = {{16, 16}, {32, 8}, {8, 32}, {64, 4}};
-    const int sched_bits[4] = {0, DPV_FRAME_LINEAR, DPV_FRAME_PERSISTENT, DPV_FRAME_PERSISTENT | DPV_FRAME_LINEAR};
+    // layouts: cell (where it fits), quad, linear; each per-item and persistent
+    std::vector<int> sched_bits;
+    const int layouts[3] = {DPV_FRAME_CELL, DPV_FRAME_QUAD, DPV_FRAME_LINEAR};
+    const bool cell_ok = cell_fits(dev);
+    for (int l : layouts) {
+        if (l == DPV_FRAME_CELL && !cell_ok) continue;
+        sched_bits.push_back(l);
+        sched_bits.push_back(l | DPV_FRAME_PERSISTENT);
+    }
     cudaEvent_t a = nullptr, b = nullptr;
     CK(cudaEventCreate(&a), "tune event");
     CK(cudaEventCreate(&b), "tune event");
@@ -1060,8 +1097,9 @@ dpv_status dpvAutotune(dpv_device dev, int frames, dpv_tune_result* out) {
     float best = 1e30f;
     dpv_frame_desc best_f = keep;
     int tried = 0;
-    for (auto& t : tiles) {
-        for (int sb : sched_bits) {
+    // layout outermost: each layout is built once
+    for (int sb : sched_bits) {
+        for (auto& t : tiles) {
             dpv_frame_desc f = keep;
             f.tile_w = t[0];
             f.tile_h = t[1];
@@ -1134,7 +1172,7 @@ dpv_status dpvRelease(dpv_device dev) {
         if (!dev->poisoned && dev->stream) cudaStreamSynchronize(dev->stream);
         for (auto& b : dev->bricks) {
             dev_free(b.data);
-            dev_free(b.quad);
+            dev_free(b.gather);
         }
         free_schedule(dev);
         free_frags(dev);

@@ -35,6 +35,11 @@ struct CamBasis {
 };
 
 // The same camera basis in FP64, for the per-pixel ray setup.
+// Gather layouts of the brick ray-march (template parameter G).
+constexpr int GATHER_LINEAR = 0;   // the stored nodes, eight scalar loads
+constexpr int GATHER_QUAD = 1;     // two face vectors per sample
+constexpr int GATHER_CELL = 2;     // one cell vector per sample
+
 // A value held as the unevaluated sum hi + lo of two floats, |lo| <= ulp(hi)/2:
 // about 48 significant bits at FP32 speed (FP64 runs at a small fraction of
 // the FP32 rate on this GPU).
@@ -111,10 +116,12 @@ struct BrickDev {
     int sx, sxy;       // strides of y and z in nodes
     int scale_idx;     // index into the device scale array
     int pad;
-    const void* quad;  // gather layout (see Quad) or null: per cell (x, y) of
-                       // every z layer, the 2x2 corners v(x,y) v(x+1,y)
-                       // v(x,y+1) v(x+1,y+1) packed in one vector
-    int qx, qxy;       // strides of the gather layout: s_n[0]-1, (s_n[0]-1)(s_n[1]-1)
+    const void* gather;// gather layout or null (GATHER_LINEAR): GATHER_QUAD,
+                       // per cell face (x, y) of every z layer the 2x2
+                       // corners v(x,y) v(x+1,y) v(x,y+1) v(x+1,y+1) in one
+                       // vector (see Quad); GATHER_CELL, per cell its eight
+                       // corners in one vector (see Cell)
+    int qx, qxy;       // strides of both layouts: s_n[0]-1, (s_n[0]-1)(s_n[1]-1)
     int o_lo[3], o_hi[3];  // owned global nodes [o_lo, o_hi)
     long long gface_off;   // first face of this brick in the face adjoint buffer
 };
@@ -347,21 +354,71 @@ struct Quad<__nv_fp8_e4m3> {
     }
 };
 
+// Eight corners of one cell, corner c = dx + 2 dy + 4 dz, in one aligned
+// vector of the cell gather layout: a single load per sample (256-bit for
+// float32).
+template <typename T>
+struct Cell;
+template <>
+struct Cell<float> {
+    static __device__ __forceinline__ void load(const void* base, long long cell, float v[8]) {
+        const float* p = reinterpret_cast<const float*>(base) + 8 * cell;
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+            : "l"(p));
+    }
+};
+template <>
+struct Cell<__half> {
+    static __device__ __forceinline__ void load(const void* base, long long cell, float v[8]) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(base) + cell);
+        const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = __half2float(__ushort_as_half((unsigned short)(u[k] & 0xffffu)));
+            v[2 * k + 1] = __half2float(__ushort_as_half((unsigned short)(u[k] >> 16)));
+        }
+    }
+};
+template <>
+struct Cell<__nv_bfloat16> {
+    static __device__ __forceinline__ void load(const void* base, long long cell, float v[8]) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(base) + cell);
+        const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = __uint_as_float(u[k] << 16);
+            v[2 * k + 1] = __uint_as_float(u[k] & 0xffff0000u);
+        }
+    }
+};
+template <>
+struct Cell<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ void load(const void* base, long long cell, float v[8]) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(base) + cell);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = Quad<__nv_fp8_e4m3>::dec((w.x >> (8 * k)) & 0xffu);
+            v[4 + k] = Quad<__nv_fp8_e4m3>::dec((w.y >> (8 * k)) & 0xffu);
+        }
+    }
+};
+
 // The eight corners of the last cell a ray sampled, kept in registers:
 // consecutive samples (step < 1 voxel) mostly stay in the same cell, and a
 // step to the next cell in z shares a face; only what changed is loaded.
 // Used by the eight-load (linear) gather; the quad gather loads its two
 // faces every sample, which measures faster than the divergent reuse tests.
-template <typename T, bool QUAD>
+template <typename T, int G>
 struct CornerCache {
     int ix = -1, iy = -1, iz = -1;
     float v[8];
 
     __device__ __forceinline__ void face(const BrickDev& b, const T* data, int x, int y, int z, float& a, float& c,
                                          float& d, float& e) const {
-        if (QUAD) {
+        if (G == GATHER_QUAD) {
             using W = typename Quad<T>::W;
-            const W* q = reinterpret_cast<const W*>(b.quad) + (x + y * b.qx + z * b.qxy);
+            const W* q = reinterpret_cast<const W*>(b.gather) + (x + y * b.qx + z * b.qxy);
             Quad<T>::unpack(__ldg(q), a, c, d, e);
         } else {
             const T* p = data + (x + y * b.sx + z * b.sxy);
@@ -398,14 +455,17 @@ struct CornerCache {
 };
 
 // Trilinear value in cell (ix, iy, iz) with weights (fx, fy, fz) (x
-// fastest): lerp in x, then y, then z.  The eight corners come either from
-// the stored nodes or from the gather layout (two vector loads, identical
-// values), through the ray's corner cache.  The per-brick scale multiplies
-// the interpolated value (equal to scaling each corner, up to rounding).
-template <typename T, bool QUAD>
-__device__ __forceinline__ float trilinear(const BrickDev& b, const T* data, float scale, CornerCache<T, QUAD>& cc,
+// fastest): lerp in x, then y, then z.  The eight corners come from the
+// stored nodes through the ray's corner cache (GATHER_LINEAR), from two
+// face vectors (GATHER_QUAD) or from one cell vector (GATHER_CELL): the
+// same values in every case.  The per-brick scale multiplies the
+// interpolated value (equal to scaling each corner, up to rounding).
+template <typename T, int G>
+__device__ __forceinline__ float trilinear(const BrickDev& b, const T* data, float scale, CornerCache<T, G>& cc,
                                            int ix, int iy, int iz, float fx, float fy, float fz) {
-    if (QUAD) {
+    if (G == GATHER_CELL) {
+        Cell<T>::load(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy, cc.v);
+    } else if (G == GATHER_QUAD) {
         // two vector loads: cheaper than the cache's divergent reuse tests
         cc.face(b, data, ix, iy, iz, cc.v[0], cc.v[1], cc.v[2], cc.v[3]);
         cc.face(b, data, ix, iy, iz + 1, cc.v[4], cc.v[5], cc.v[6], cc.v[7]);

@@ -393,7 +393,7 @@ cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 orig
 // One work item: every thread marches its pixel's ray through the item's
 // brick and writes the fragment to slot `item * tile_pixels + thread`.
 // Returns the samples this thread evaluated.
-template <typename T, bool QUAD>
+template <typename T, int GL>
 __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, const CamBasis* cams,
                                                          const BrickDev* bricks, const float* scales, const Item& it,
                                                          long long item, const float4* s_tf, float4* frag_rgba,
@@ -413,14 +413,14 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
             float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.0f;
             int n = m.j1 - m.j0;
             int k = 0;
-            CornerCache<T, QUAD> cc;
+            CornerCache<T, GL> cc;
             SampleWalker wk;
             wk.init(b);
             for (; k < n; ++k) {
                 int ix, iy, iz;
                 float fx, fy, fz;
                 wk.at(m, k, ix, iy, iz, fx, fy, fz);
-                float s = trilinear<T, QUAD>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
+                float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
                 TFSample c = tf_lookup(s_tf, P, s);
                 float al = sample_alpha(P, c.v.w);
                 float ta = Tr * al;
@@ -443,7 +443,7 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
     return nsamp;
 }
 
-template <typename T, bool QUAD>
+template <typename T, int GL>
 __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
                                                    const float* scales, const Item* items, const float4* tf,
                                                    float4* frag_rgba, int* frag_key, Counters* counters) {
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis
     __syncthreads();
     const Item it = items[blockIdx.x];
     if (!item_ok(it, P)) return;
-    unsigned long long nsamp = march_item<T, QUAD>(P, cams, bricks, scales, it, blockIdx.x, s_tf, frag_rgba, frag_key);
+    unsigned long long nsamp = march_item<T, GL>(P, cams, bricks, scales, it, blockIdx.x, s_tf, frag_rgba, frag_key);
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis
 // Persistent form: a grid sized to the GPU pulls work items from a counter
 // in the order `sched` gives (brick-major: all cameras' tiles of one brick
 // together, so a brick is read from HBM about once per batch).
-template <typename T, bool QUAD>
+template <typename T, int GL>
 __global__ void __launch_bounds__(256) k_march_fwd_persistent(FrameParams P, const CamBasis* cams,
                                                               const BrickDev* bricks, const float* scales,
                                                               const Item* items, const int* sched, int n_items,
@@ -478,36 +478,36 @@ __global__ void __launch_bounds__(256) k_march_fwd_persistent(FrameParams P, con
         if (i >= n_items) break;
         const int item = sched[i];
         const Item it = items[item];
-        if (item_ok(it, P)) nsamp += march_item<T, QUAD>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
+        if (item_ok(it, P)) nsamp += march_item<T, GL>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
     }
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
 
-template <typename T, bool QUAD>
+template <typename T, int GL>
 static void fwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                        const Item* items, int n_items, const float4* tf, float4* frag_rgba, int* frag_key,
                        Counters* counters, const Schedule* sch, cudaStream_t st) {
     size_t smem = sizeof(float4) * P.ntf;
     if (sch) {
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_march_fwd_persistent<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_march_fwd_persistent<T, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         int per_sm = 0, dev = 0, nsm = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_fwd_persistent<T, QUAD>, P.tp, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_fwd_persistent<T, GL>, P.tp, smem);
         int grid = nsm * (per_sm > 0 ? per_sm : 1);
         if (sch->ctas_per_sm > 0 && sch->ctas_per_sm < per_sm) grid = nsm * sch->ctas_per_sm;
         if (grid > n_items) grid = n_items;
         cudaMemsetAsync(sch->work, 0, sizeof(unsigned int), st);
-        k_march_fwd_persistent<T, QUAD><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched, n_items,
+        k_march_fwd_persistent<T, GL><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched, n_items,
                                                                   sch->work, tf, frag_rgba, frag_key, counters);
         return;
     }
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_march_fwd<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_march_fwd<T, QUAD><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
+        cudaFuncSetAttribute(k_march_fwd<T, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_march_fwd<T, GL><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
                                                       counters);
 }
 
@@ -554,14 +554,18 @@ cudaError_t launch_schedule(const FrameParams& P, const Item* items, int n_items
     return cudaGetLastError();
 }
 
-cudaError_t launch_march_fwd(int dtype, bool quad, const FrameParams& P, const CamBasis* cams,
+cudaError_t launch_march_fwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
                              cudaStream_t st, const Schedule* sch) {
     if (n_items == 0) return cudaSuccess;
-#define FWD(T)                                                                                                   \
-    (quad ? fwd_launch<T, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st) \
-          : fwd_launch<T, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st))
+#define FWD(T)                                                                                                    \
+    (gather == GATHER_CELL                                                                                            \
+         ? fwd_launch<T, GATHER_CELL>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st) \
+     : gather == GATHER_QUAD                                                                                          \
+         ? fwd_launch<T, GATHER_QUAD>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st) \
+         : fwd_launch<T, GATHER_LINEAR>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, \
+                                        st))
     switch (dtype) {
         case 0: FWD(float); break;
         case 1: FWD(__half); break;
@@ -851,7 +855,7 @@ int bwd_tf_copies(int ntf) {
 // One work item of the adjoint: replay each thread's fragment and
 // accumulate its TF gradient into `my_tab` (a shared copy) and its voxel
 // gradient into the global field.  Returns the samples replayed.
-template <typename T, bool QUAD>
+template <typename T, int GL>
 __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, const CamBasis* cams,
                                                        const BrickDev* bricks, const float* scales, const Item& it,
                                                        long long item, const float4* s_tf, float* my_tab,
@@ -879,14 +883,14 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
             TFRunF tr;
             CellRun cr;
             const long long gofs = (long long)b.s_lo[2] * sz + (long long)b.s_lo[1] * sy + b.s_lo[0];
-            CornerCache<T, QUAD> cc;
+            CornerCache<T, GL> cc;
             SampleWalker wk;
             wk.init(b);
             for (int k = 0; k < n; ++k) {
                 int ix, iy, iz;
                 float fx, fy, fz;
                 wk.at(m, k, ix, iy, iz, fx, fy, fz);
-                float s = trilinear<T, QUAD>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
+                float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
                 TFSample c = tf_lookup(s_tf, P, s);
                 float al = sample_alpha(P, c.v.w);
                 float ta = Tr * al;
@@ -958,8 +962,8 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
     return nsamp;
 }
 
-template <typename T, bool QUAD>
-__global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
+template <typename T, int GL>
+__global__ void __launch_bounds__(256, 3) k_march_bwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
                                                    const float* scales, const Item* items, const float4* tf,
                                                    const float4* frag_rgba, const int* frag_key,
                                                    const float4* frag_grad, int ncopy, double* dtf, float* dvol,
@@ -975,7 +979,7 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis
     const Item it = items[blockIdx.x];
     unsigned long long nsamp = 0;
     if (item_ok(it, P))
-        nsamp = bwd_item<T, QUAD>(P, cams, bricks, scales, it, blockIdx.x, s_tf, my_tab, frag_rgba, frag_key,
+        nsamp = bwd_item<T, GL>(P, cams, bricks, scales, it, blockIdx.x, s_tf, my_tab, frag_rgba, frag_key,
                                   frag_grad, dvol, gface);
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
@@ -989,8 +993,8 @@ __global__ void __launch_bounds__(256) k_march_bwd(FrameParams P, const CamBasis
 
 // Persistent adjoint: items pulled in schedule order; each CTA's TF tables
 // are added to the global table once, after its last item.
-template <typename T, bool QUAD>
-__global__ void __launch_bounds__(256) k_march_bwd_persistent(FrameParams P, const CamBasis* cams,
+template <typename T, int GL>
+__global__ void __launch_bounds__(256, 3) k_march_bwd_persistent(FrameParams P, const CamBasis* cams,
                                                               const BrickDev* bricks, const float* scales,
                                                               const Item* items, const int* sched, int n_items,
                                                               unsigned int* work, const float4* tf,
@@ -1015,7 +1019,7 @@ __global__ void __launch_bounds__(256) k_march_bwd_persistent(FrameParams P, con
         const int item = sched[i];
         const Item it = items[item];
         if (item_ok(it, P))
-            nsamp += bwd_item<T, QUAD>(P, cams, bricks, scales, it, item, s_tf, my_tab, frag_rgba, frag_key,
+            nsamp += bwd_item<T, GL>(P, cams, bricks, scales, it, item, s_tf, my_tab, frag_rgba, frag_key,
                                        frag_grad, dvol, gface);
     }
     nsamp = warp_sum_u64(nsamp);
@@ -1028,7 +1032,7 @@ __global__ void __launch_bounds__(256) k_march_bwd_persistent(FrameParams P, con
     }
 }
 
-template <typename T, bool QUAD>
+template <typename T, int GL>
 static void bwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                        const Item* items, int n_items, const float4* tf, const float4* frag_rgba, const int* frag_key,
                        const float4* frag_grad, double* dtf, float* dvol, float4* gface, Counters* counters,
@@ -1037,37 +1041,41 @@ static void bwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDe
     size_t smem = sizeof(float4) * P.ntf + sizeof(float) * (size_t)ncopy * (4 * P.ntf + 1);
     if (sch) {
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_march_bwd_persistent<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_march_bwd_persistent<T, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         int per_sm = 0, dev = 0, nsm = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_bwd_persistent<T, QUAD>, P.tp, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_bwd_persistent<T, GL>, P.tp, smem);
         int grid = nsm * (per_sm > 0 ? per_sm : 1);
         if (grid > n_items) grid = n_items;
         cudaMemsetAsync(sch->work, 0, sizeof(unsigned int), st);
-        k_march_bwd_persistent<T, QUAD><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched,
+        k_march_bwd_persistent<T, GL><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched,
                                                                   n_items, sch->work, tf, frag_rgba, frag_key,
                                                                   frag_grad, ncopy, dtf, dvol, gface, counters);
         return;
     }
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_march_bwd<T, QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_march_bwd<T, QUAD><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
+        cudaFuncSetAttribute(k_march_bwd<T, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_march_bwd<T, GL><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
                                                       frag_grad, ncopy, dtf, dvol, gface, counters);
 }
 
-cudaError_t launch_march_bwd(int dtype, bool quad, const FrameParams& P, const CamBasis* cams,
+cudaError_t launch_march_bwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, const float4* frag_rgba, const int* frag_key,
                              const float4* frag_grad, double* dtf, float* dvol, float4* gface,
                              Counters* counters, cudaStream_t st, const Schedule* sch) {
     if (n_items == 0) return cudaSuccess;
-#define BWD(T)                                                                                                 \
-    (quad ? bwd_launch<T, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, \
-                                dvol, gface, counters, sch, st)                                                 \
-          : bwd_launch<T, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, \
-                                 dvol, gface, counters, sch, st))
+#define BWD(T)                                                                                                  \
+    (gather == GATHER_CELL                                                                                          \
+         ? bwd_launch<T, GATHER_CELL>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad,   \
+                                      dtf, dvol, gface, counters, sch, st)                                          \
+     : gather == GATHER_QUAD                                                                                        \
+         ? bwd_launch<T, GATHER_QUAD>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad,   \
+                                      dtf, dvol, gface, counters, sch, st)                                          \
+         : bwd_launch<T, GATHER_LINEAR>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, \
+                                        dtf, dvol, gface, counters, sch, st))
     switch (dtype) {
         case 0: BWD(float); break;
         case 1: BWD(__half); break;
@@ -1120,6 +1128,61 @@ cudaError_t launch_build_quad(int dtype, const void* src, const int s_n[3], void
         case 1: k_build_quad<__half><<<blocks, 256, 0, st>>>((const __half*)src, s_n[0], s_n[1], s_n[2], (uint2*)dst); break;
         case 2: k_build_quad<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)src, s_n[0], s_n[1], s_n[2], (uint2*)dst); break;
         default: k_build_quad<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>((const __nv_fp8_e4m3*)src, s_n[0], s_n[1], s_n[2], (unsigned*)dst); break;
+    }
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// gather layout (cell): per cell its eight corners in one vector
+// ===========================================================================
+
+template <typename T>
+__global__ void k_build_cell(const T* src, int sx, int sy, int sz, void* dst) {
+    const long long cx = sx - 1, cxy = (long long)(sx - 1) * (sy - 1);
+    const long long n = cxy * (sz - 1);
+    const long long sxy = (long long)sx * sy;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long z = i / cxy, r = i - z * cxy, y = r / cx, x = r - y * cx;
+        const long long o = (z * sy + y) * sx + x;
+        const long long c[8] = {o, o + 1, o + sx, o + sx + 1, o + sxy, o + sxy + 1, o + sxy + sx, o + sxy + sx + 1};
+        if constexpr (sizeof(T) == 4) {
+            const float* f = (const float*)src;
+            float4* d = (float4*)dst + 2 * i;
+            d[0] = make_float4(f[c[0]], f[c[1]], f[c[2]], f[c[3]]);
+            d[1] = make_float4(f[c[4]], f[c[5]], f[c[6]], f[c[7]]);
+        } else if constexpr (sizeof(T) == 2) {
+            const unsigned short* h = (const unsigned short*)src;
+            unsigned u[4];
+            for (int k = 0; k < 4; ++k) u[k] = (unsigned)h[c[2 * k]] | ((unsigned)h[c[2 * k + 1]] << 16);
+            ((uint4*)dst)[i] = make_uint4(u[0], u[1], u[2], u[3]);
+        } else {
+            const unsigned char* b = (const unsigned char*)src;
+            unsigned lo = 0, hi = 0;
+            for (int k = 0; k < 4; ++k) {
+                lo |= (unsigned)b[c[k]] << (8 * k);
+                hi |= (unsigned)b[c[4 + k]] << (8 * k);
+            }
+            ((uint2*)dst)[i] = make_uint2(lo, hi);
+        }
+    }
+}
+
+size_t cell_bytes(int dtype, const int s_n[3]) {
+    size_t cells = (size_t)(s_n[0] - 1) * (s_n[1] - 1) * (s_n[2] - 1);
+    static const size_t w[4] = {32, 16, 16, 8};
+    return cells * w[dtype];
+}
+
+cudaError_t launch_build_cell(int dtype, const void* src, const int s_n[3], void* dst, cudaStream_t st) {
+    long long n = (long long)(s_n[0] - 1) * (s_n[1] - 1) * (s_n[2] - 1);
+    long long nb = (n + 255) / 256;
+    int blocks = (int)(nb < 65536 ? nb : 65536);
+    if (blocks < 1) return cudaSuccess;
+    switch (dtype) {
+        case 0: k_build_cell<float><<<blocks, 256, 0, st>>>((const float*)src, s_n[0], s_n[1], s_n[2], dst); break;
+        case 1: k_build_cell<__half><<<blocks, 256, 0, st>>>((const __half*)src, s_n[0], s_n[1], s_n[2], dst); break;
+        case 2: k_build_cell<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)src, s_n[0], s_n[1], s_n[2], dst); break;
+        default: k_build_cell<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>((const __nv_fp8_e4m3*)src, s_n[0], s_n[1], s_n[2], dst); break;
     }
     return cudaGetLastError();
 }

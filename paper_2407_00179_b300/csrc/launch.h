@@ -46,7 +46,7 @@ cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 orig
                         int4* d_rects, int* d_tile_count, int* d_tile_first, Item* d_items, int cap,
                         Counters* d_counters, bool fill, cudaStream_t st);
 
-cudaError_t launch_march_fwd(int dtype, bool quad, const FrameParams& P, const CamBasis* cams,
+cudaError_t launch_march_fwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
                              cudaStream_t st, const Schedule* sch = nullptr);
@@ -71,7 +71,7 @@ cudaError_t launch_composite_bwd(const FrameParams& P, const int* tile_first, co
                                  const float4* frag_rgba, const int* frag_key, const float4* grad_img,
                                  float4* frag_grad, cudaStream_t st);
 
-cudaError_t launch_march_bwd(int dtype, bool quad, const FrameParams& P, const CamBasis* cams,
+cudaError_t launch_march_bwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, const float4* frag_rgba, const int* frag_key,
                              const float4* frag_grad, double* dtf, float* dvol, float4* gface,
@@ -91,6 +91,9 @@ cudaError_t launch_face_gather(const BrickDev* bricks, int nbricks, const int* n
 // the stored nodes.
 size_t quad_bytes(int dtype, const int s_n[3]);
 cudaError_t launch_build_quad(int dtype, const void* src, const int s_n[3], void* dst, cudaStream_t st);
+// Cell gather layout: bytes it needs and its build (eight corners per cell).
+size_t cell_bytes(int dtype, const int s_n[3]);
+cudaError_t launch_build_cell(int dtype, const void* src, const int s_n[3], void* dst, cudaStream_t st);
 
 cudaError_t launch_read_frags(const FrameParams& P, const Item* items, int n_items, int cam, int rank,
                               const float4* frag_rgba, const int* frag_key, float4* out_rgba, int* out_key,

@@ -225,7 +225,7 @@ extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_ca
     float3 og = make_float3(sc->origin[0], sc->origin[1], sc->origin[2]);
     NA_CK(launch_cull(P, d_camin, og, sc->spacing, d_cam, d_camd, d_rays, d_table, d_rects, d_count, d_first, d_items,
                       (int)cap, d_counters, true, st));
-    NA_CK(launch_march_fwd((int)sc->storage, false, P, d_cam, d_table, d_scales, d_items, (int)cap,
+    NA_CK(launch_march_fwd((int)sc->storage, GATHER_LINEAR, P, d_cam, d_table, d_scales, d_items, (int)cap,
                            (const float4*)sc->tf_rgba, d_frgba, d_fkey, d_counters, st));
     NA_CK(launch_composite_fwd(P, 1.0f / sc->spacing, d_cam, d_first, d_count, d_items, d_frgba, d_fkey,
                                (float4*)rgba, depth, nullptr, st));

@@ -25,6 +25,20 @@ FRAME_STAGED = 2
 FRAME_LINEAR = 4
 FRAME_PERSISTENT = 8
 FRAME_GRAPH = 16
+FRAME_CELL = 32
+FRAME_QUAD = 64
+GATHER_FLAGS = {"auto": 0, "cell": FRAME_CELL, "quad": FRAME_QUAD, "linear": FRAME_LINEAR}
+
+
+def gather_of(flags: int) -> str:
+    """Gather layout name of frame flags (as dpvAutotune returns them)."""
+    if flags & FRAME_LINEAR:
+        return "linear"
+    if flags & FRAME_CELL:
+        return "cell"
+    if flags & FRAME_QUAD:
+        return "quad"
+    return "auto"
 STATUS = {0: "DPV_OK", 1: "DPV_ERR_INVALID_ARG", 2: "DPV_ERR_STATE", 3: "DPV_ERR_OUT_OF_MEMORY",
           4: "DPV_ERR_CUDA", 5: "DPV_ERR_TIMEOUT", 6: "DPV_ERR_UNSUPPORTED"}
 
@@ -255,11 +269,14 @@ class Device:
         self.ncam = len(cams)
 
     def set_frame(self, width: int, height: int, step_voxels: float = 0.5, sigma_max: float = 8.0, ert: float = 0.0,
-                  tile=(0, 0), order: bool = False, staged: bool = False, gather: str = "quad",
+                  tile=(0, 0), order: bool = False, staged: bool = False, gather: str = "auto",
                   persistent: bool = False, graph: bool = False):
-        flags = (FRAME_ORDER if order else 0) | (FRAME_STAGED if staged else 0) | (
-            FRAME_LINEAR if gather == "linear" else 0) | (FRAME_PERSISTENT if persistent else 0) | (
-            FRAME_GRAPH if graph else 0)
+        """gather: "auto" (cell layout where it fits in half of the free
+        device memory, else quad), "cell", "quad" or "linear"."""
+        if gather not in GATHER_FLAGS:
+            raise ValueError("gather must be one of %s" % sorted(GATHER_FLAGS))
+        flags = (FRAME_ORDER if order else 0) | (FRAME_STAGED if staged else 0) | GATHER_FLAGS[gather] | (
+            FRAME_PERSISTENT if persistent else 0) | (FRAME_GRAPH if graph else 0)
         f = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
                       int(tile[1]), flags)
         _check(load().dpvSetFrame(self._h, C.byref(f)))
@@ -368,8 +385,7 @@ class Device:
     def _tune_apply(self, entry):
         fl = entry["flags"]
         self.set_frame(self.width, self.height, *self._frame_args, tile=tuple(entry["tile"]),
-                       gather="linear" if fl & FRAME_LINEAR else "quad", persistent=bool(fl & FRAME_PERSISTENT),
-                       **self._frame_kw)
+                       gather=gather_of(fl), persistent=bool(fl & FRAME_PERSISTENT), **self._frame_kw)
 
     def reset_stats(self):
         _check(load().dpvResetStats(self._h))

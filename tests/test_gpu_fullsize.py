@@ -49,7 +49,7 @@ def _bench_device(cfg, field, part, cams):
     tune = dev.autotune(frames=1)
     fl = tune["flags"]
     dev.set_frame(cfg["width"], cfg["height"], step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"],
-                  tile=tuple(tune["tile"]), gather="linear" if fl & dpv.FRAME_LINEAR else "quad",
+                  tile=tuple(tune["tile"]), gather=dpv.gather_of(fl),
                   persistent=bool(fl & dpv.FRAME_PERSISTENT), order=True)
     dev.render()
     return dev

@@ -120,15 +120,17 @@ np.savez(sys.argv[1], img=img, tf=tf.cpu().numpy(), vol=vol.cpu().numpy(), err=d
     np.testing.assert_allclose(a["vol"], b["vol"], rtol=1e-4, atol=1e-6 * np.abs(b["vol"]).max())
 
 
+@pytest.mark.parametrize("other", ["linear", "cell"])
 @pytest.mark.parametrize("i", range(len(SCENES)))
-def test_quad_gather_layout_equals_linear(i):
-    """The default gather layout (2x2 corners per vector) reads the same
-    stored values as the eight-load path: identical frames and fragments,
-    and the adjoint differs only in atomic summation order."""
+def test_gather_layouts_agree(i, other):
+    """The default gather layout (2x2 corners per vector), the cell layout
+    (eight corners per vector) and the eight-load path read the same stored
+    values: identical frames and fragments, and the adjoint differs only in
+    atomic summation order."""
     sc = _scene(i)
     sc.staged = False
     devs = []
-    for gather in ("quad", "linear"):
+    for gather in ("quad", other):
         dev = scenes.gpu_device(sc, order=False)
         dev.set_frame(sc.width, sc.height, step_voxels=sc.step, sigma_max=sc.sigma_max, ert=sc.ert, tile=sc.tile,
                       gather=gather)
@@ -148,3 +150,24 @@ def test_quad_gather_layout_equals_linear(i):
     assert torch.allclose(va, vb, rtol=1e-4, atol=1e-6 * float(vb.abs().max()))
     a.release()
     b.release()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "fp8"])
+def test_cell_layout_every_storage(storage):
+    """The cell layout's eight-corner decode for every storage type equals
+    the eight-load path: identical frames on an uneven k-d partition."""
+    dims = (44, 38, 34)
+    cams = inputs.random_cameras(dims, 2, seed=31)
+    sc = scenes.make(dims, kd=6, cams=cams, width=72, height=52, storage=storage, tile=(16, 8))
+    imgs = []
+    for gather in ("cell", "linear"):
+        dev = scenes.gpu_device(sc, order=False)
+        dev.set_frame(sc.width, sc.height, step_voxels=sc.step, sigma_max=sc.sigma_max, ert=sc.ert, tile=sc.tile,
+                      gather=gather)
+        dev.render()
+        assert dev.stats()["error_flags"] == 0
+        imgs.append([dev.map_frame(c)[0].clone() for c in range(len(sc.cams))])
+        dev.release()
+    for a, b in zip(*imgs):
+        assert float(b[..., 3].max()) > 0.1
+        assert torch.equal(a, b)
