@@ -40,7 +40,10 @@ BYTES_PER_VOXEL = {"f32": 4, "f16": 2, "bf16": 2, "fp8": 1}
 # DRAM bytes (read + write) per launch of the timed kernels, from one ncu
 # capture of this workload (profiles/ holds the summary and the command);
 # absent where no capture of the current kernel exists
-TRAFFIC = {}
+TRAFFIC = {
+    ("mid", "march"): 4.708e9,        # k_march_fwd<float, cell>: 4.679 GB read + 28.7 MB written
+    ("mid", "march_bwd"): 12.38e9,    # k_march_bwd<float, cell> 9.61 GB + k_face_gather 2.77 GB
+}
 
 CONFIGS = {
     # 512^3 f32, 64 blobs + 3-octave noise, 2x2x2 bricks, 1920x1080, ERT 0.99
