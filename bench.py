@@ -149,6 +149,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_over_ranks(dist, device, times, counts):
+    """Whole-job figures of a run on several ranks: the max over ranks of each
+    timed interval and the sum over ranks of each work count (ranks render
+    different cameras, so their sample counts differ).  With dist None (one
+    process) the inputs come back unchanged."""
+    if dist is None:
+        return list(times), list(counts)
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(x) for x in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return t.tolist(), c.tolist()
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -318,10 +332,9 @@ def run_ours(args, cfg_name, cfg):
     n_fwd = st["samples_forward"] * args.steps          # per step counts are deterministic
     n_bwd = st["samples_backward"] * args.steps
     launches = st["kernel_launches"]
-    if pg:
-        t = torch.tensor([total_ms, fwd_ms, bwd_ms], dtype=torch.float64, device=device)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms, fwd_ms, bwd_ms = t.tolist()
+    frames = ncam * args.steps
+    (total_ms, fwd_ms, bwd_ms), (n_fwd, n_bwd, frames) = reduce_over_ranks(
+        pg, device, [total_ms, fwd_ms, bwd_ms], [n_fwd, n_bwd, frames])
     # roofline of the dominant kernel (forward ray-march): stencil bytes
     bpv = BYTES_PER_VOXEL[cfg["storage"]]
     march_ms = st["stage_ms"]["march"] / max(1, st["stage_calls"]["march"])
@@ -394,9 +407,9 @@ def run_ours(args, cfg_name, cfg):
             dev.copy_frame(c, frame_host[c])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - w0
-    e2e_val = st["samples_forward"] * e2e_steps / e2e_s / 1e9
-    ws_factor = ws
-    value = n_fwd / (fwd_ms * 1e-3) / 1e9 * ws_factor
+    (e2e_s,), (e2e_n,) = reduce_over_ranks(pg, device, [e2e_s], [st["samples_forward"] * e2e_steps])
+    e2e_val = e2e_n / e2e_s / 1e9
+    value = n_fwd / (fwd_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC,
         "value": value,
@@ -417,11 +430,11 @@ def run_ours(args, cfg_name, cfg):
                    "l2": "inputs larger than L2 (%d MiB volume), no flush" % (
                        np.prod(cfg["dims"]) * bpv // 2 ** 20),
                    "parallelism": "weak: each GPU renders its own cameras over its own copy of the bricks"},
-        "frames_per_s": ncam * args.steps / (fwd_ms * 1e-3) * ws_factor,
+        "frames_per_s": frames / (fwd_ms * 1e-3),
         "forward_ms_per_step": fwd_ms / args.steps,
-        "backward": {"value": n_bwd / (bwd_ms * 1e-3) / 1e9 * ws_factor, "unit": "Gsamples/s",
+        "backward": {"value": n_bwd / (bwd_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
                      "ms_per_step": bwd_ms / args.steps},
-        "samples_per_step": {"forward": st["samples_forward"], "backward": st["samples_backward"]},
+        "samples_per_step": {"forward": n_fwd / args.steps, "backward": n_bwd / args.steps},
         "stage_ms_per_step": {k: v / max(1, args.steps) for k, v in st["stage_ms"].items()},
         "value_basis": "forward samples evaluated / forward time (cull + march + composite) of the timed steps; "
                        "each step also runs the backward, reported under 'backward' and in ms_per_step",
@@ -435,7 +448,7 @@ def run_ours(args, cfg_name, cfg):
                               "model": "stencil bytes: 8 corners x %d B read + 8 x 4 B field-gradient adds per "
                                        "replayed sample" % bpv,
                               "peak_kind": peak_kind},
-        "e2e": {"value": e2e_val * ws_factor, "unit": "Gsamples/s", "h2d_bytes_per_step": int(tf_np.nbytes),
+        "e2e": {"value": e2e_val, "unit": "Gsamples/s", "h2d_bytes_per_step": int(tf_np.nbytes),
                 "d2h_bytes_per_step": int(ncam * H * W * 16), "what": "set TF from pinned host, render, copy frames"
                 " to pinned host, per step (forward)"},
         "gpu_launches": int(launches),
