@@ -48,7 +48,7 @@ TRAFFIC = {
 CONFIGS = {
     # 512^3 f32, 64 blobs + 3-octave noise, 2x2x2 bricks, 1920x1080, ERT 0.99
     "mid": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
-                storage="f32", cams="direction"),
+                storage="f32", cams="direction", compare_storage="f16"),
     "mid_f16": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
                     storage="f16", cams="direction"),
     # 64^3 f32, 8 blobs, 2x1x1 bricks, 256x256, no ERT
@@ -268,7 +268,7 @@ def run_ours(args, cfg_name, cfg):
     compare_f32 = cfg.get("compare_f32", True)
     # keep a host copy for the CPU baseline and free the device field
     field_host = field.cpu().numpy() if (rank == 0 and not args.no_cpu_baseline) else None
-    field_dev = field if (compare_f32 and ncam > 1) else None
+    field_dev = field if ((compare_f32 and ncam > 1) or cfg.get("compare_storage")) else None
     del field
     torch.cuda.empty_cache()
     tf = torch.from_numpy(tf_np).to(device)
@@ -387,6 +387,37 @@ def run_ours(args, cfg_name, cfg):
                  "speedup_vs_separate_f32": sep_ms / graph_ms,
                  "max_abs_diff_vs_separate_f32": err}
 
+    # the same frame from reduced-precision storage at FP32 accumulation:
+    # forward rate and image error against the float32-storage frame
+    storage_cmp = None
+    if cfg.get("compare_storage"):
+        cs = cfg["compare_storage"]
+        ref_img = dev.frames()[0].clone()
+        alt = dpv.Device(part.num_ranks, local)
+        alt.set_geometry(cfg["dims"])
+        alt.commit_partition(field_dev, part, cs)
+        alt.set_tf(tf)
+        alt.set_cameras(cams)
+        fl = tune["flags"] if tune else 0
+        alt.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"],
+                      tile=tuple(tune["tile"]) if tune else (args.tile_w, args.tile_h), gather=dpv.gather_of(fl),
+                      persistent=bool(fl & dpv.FRAME_PERSISTENT))
+        for _ in range(max(3, args.warmup)):
+            alt.render()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            alt.render()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        alt_ms = a0.elapsed_time(a1) / args.steps
+        diff = (alt.frames()[0] - ref_img).abs()
+        storage_cmp = {"storage": cs, "forward_ms_per_step": alt_ms,
+                       "value": alt.stats()["samples_forward"] / (alt_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+                       "image_error_vs_f32_storage": {"max": float(diff.max()), "mean": float(diff.mean())}}
+        alt.release()
+
     # end to end through the public API: TF from pinned host memory in, the
     # composited frames to pinned host memory out, every step
     tf_host = torch.from_numpy(tf_np).pin_memory()
@@ -458,6 +489,8 @@ def run_ours(args, cfg_name, cfg):
     }
     if batch:
         line["batched"] = batch
+    if storage_cmp:
+        line["storage_comparison"] = storage_cmp
     if rank == 0 and not args.no_cpu_baseline:
         try:
             cb = cpu_baseline(cfg_name, cfg, field_host, part, tf_np, cams, budget_s=args.ref_budget)

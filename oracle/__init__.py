@@ -27,6 +27,8 @@ DTYPE_NAMES = {"f32": F32, "f16": F16, "bf16": BF16, "fp8": FP8}
 NP_STORAGE = {F32: np.float32, F16: np.uint16, BF16: np.uint16, FP8: np.uint8}
 KEY_EMPTY = 2 ** 31 - 1
 FLAG_HIT, FLAG_EXIT_AMBIG, FLAG_OWNER_AMBIG, FLAG_ERT_AMBIG = 1, 2, 4, 8
+FLAG_ISO_AMBIG = 16
+ISO_EPS = 5e-5   # iso ambiguity band on s (a rounded sample may cross otherwise)
 
 
 def build(force: bool = False) -> str:
@@ -75,6 +77,8 @@ def lib():
         _lib.orc_render_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P, P, P, P, P]
         _lib.orc_grad_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, C.c_double]
         _lib.orc_composite.argtypes = [C.c_int, C.c_int, P, P, P, P]
+        _lib.orc_render_iso.argtypes = [P, P, C.c_int, P, P, P, P, C.c_double, C.c_double, C.c_int, P, P, P, P, P,
+                                        P, P]
         _lib.orc_kd_order.argtypes = [C.c_int, P, P, P, P, P, P]
         _lib.orc_kd_order.restype = C.c_int
         _lib.orc_camera_ray.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
@@ -269,6 +273,39 @@ def render_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, 
                             _p(res["rgba"]), _p(res["depth"]), _p(res["order"]), _p(res["frag_rgba"]),
                             _p(res["frag_key"]), _p(res["frag_nsamp"]), _p(res["frag_margin"]),
                             _p(res["nsamples"]), _p(res["flags"]))
+    return res
+
+
+def render_iso(dims, tf: np.ndarray, cam, frame: Frame, iso: float, field=None, bricks=None, pix=None, vmin=0.0,
+               vmax=1.0, origin=(0.0, 0.0, 0.0), spacing=None, iso_eps=ISO_EPS):
+    """FP64 iso-surface render: the first sample pair of the ray across
+    which [s >= iso] changes, the surface point interpolated linearly between
+    them, shaded TF rgb(iso) x (0.25 + 0.75 |N.d|/(|N||d|)), opaque.  With
+    `field` (nz, ny, nx float32) the plain definition on the whole field;
+    with `bricks` each brick finds the first hit among the pairs whose later
+    sample it owns, and the depth composite keeps the smallest key.
+    Returns rgba, depth (+inf: no hit), key (-1: no hit), dsdt
+    (|s_h - s_{h-1}|), frag_key (bricks; 2^31 - 1 = none) and flags."""
+    if (field is None) == (bricks is None):
+        raise ValueError("give exactly one of field and bricks")
+    g = _grid(dims, origin, spacing)
+    t, tab = _tf(tf, vmin, vmax)
+    cam_c = _camera(cam)
+    fr = frame.c()
+    n, pp, keep = _pix(pix, frame)
+    K = len(bricks) if bricks is not None else 1
+    res = {"rgba": np.zeros((n, 4)), "depth": np.zeros(n), "key": np.zeros(n, np.int64), "dsdt": np.zeros(n),
+           "frag_key": np.zeros((n, K), np.int32), "flags": np.zeros(n, np.uint8)}
+    if bricks is not None:
+        barr, keep_b = _bricks_c(bricks)
+        f_ptr = None
+    else:
+        f = np.ascontiguousarray(field, dtype=np.float32)
+        assert f.shape == (dims[2], dims[1], dims[0])
+        barr, f_ptr = None, _p(f)
+    lib().orc_render_iso(C.byref(g), f_ptr, K, barr, C.byref(t), C.byref(cam_c), C.byref(fr), float(iso),
+                         float(iso_eps), n, pp, _p(res["rgba"]), _p(res["depth"]), _p(res["key"]), _p(res["dsdt"]),
+                         _p(res["frag_key"]) if bricks is not None else None, _p(res["flags"]))
     return res
 
 

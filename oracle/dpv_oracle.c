@@ -47,6 +47,7 @@
 #define ORC_FLAG_EXIT_AMBIG 2
 #define ORC_FLAG_OWNER_AMBIG 4
 #define ORC_FLAG_ERT_AMBIG 8
+#define ORC_FLAG_ISO_AMBIG 16
 
 typedef struct {
     int dims[3];          /* nodes per axis */
@@ -655,6 +656,199 @@ void orc_composite(int npix, int K, const double* frag_rgba, const int32_t* frag
     }
     free(fs);
     free(ord);
+}
+
+/* ------------------------------------------------------------------------ */
+/* iso-surface fragments (first hit per brick, depth composite)              */
+/* ------------------------------------------------------------------------ */
+
+/* Readings (the paper's z-composited surfaces, its teaser's in-situ
+ * iso-surface and the compositing tests of §7; no equations are given):
+ *   - the samples are the volume-rendering samples of the ray (t_j, s_j);
+ *   - the hit is the first pair (j - 1, j), j >= 1, across which
+ *     [s >= iso] changes; h = j;
+ *   - the surface point lies at t* = t_{h-1} + f dt with
+ *     f = (iso - s_{h-1}) / (s_h - s_{h-1}) (linear between the samples);
+ *   - data-parallel form: the brick owning sample j tests the pair
+ *     (j - 1, j), evaluating s_{j-1} itself (it lies in its ghost layer),
+ *     and keeps its first hit as its fragment; the composite takes the
+ *     fragment with the smallest key (opaque surfaces: nearest first);
+ *   - colour: TF rgb at iso times 0.25 + 0.75 |N.d| / (|N| |d|), N the
+ *     gradient of the trilinear interpolant of the cell holding the surface
+ *     point (in the reporting brick), d the ray direction; factor 1 where
+ *     N = 0; alpha 1.  No hit: (0, 0, 0, 0) and depth +inf.
+ * Flagged ISO_AMBIG (a rounded s or point may decide otherwise): a sample up
+ * to the hit (all samples without a hit) within iso_eps of iso, or the
+ * surface point within 1e-4 of a cell face. */
+
+/* Gradient of the trilinear interpolant at node-space point q in the cell
+ * trilinear() would use (decoded, scaled corners). */
+static void trilinear_grad(const void* data, int dtype, double scale, const int b_lo[3], const int b_n[3],
+                           const double q[3], double g[3], double frac[3]) {
+    int i[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        int c = (int)floor(q[a]);
+        if (c < b_lo[a]) c = b_lo[a];
+        if (c > b_lo[a] + b_n[a] - 2) c = b_lo[a] + b_n[a] - 2;
+        i[a] = c - b_lo[a];
+        f[a] = q[a] - c;
+        if (frac) frac[a] = f[a];
+    }
+    double v[8];
+    for (int c = 0; c < 8; ++c) {
+        int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+        int64_t k = ((int64_t)(i[2] + dz) * b_n[1] + (i[1] + dy)) * b_n[0] + (i[0] + dx);
+        v[c] = scale * decode(data, dtype, k);
+    }
+    double fx = f[0], fy = f[1], fz = f[2];
+    g[0] = (1 - fz) * ((1 - fy) * (v[1] - v[0]) + fy * (v[3] - v[2])) + fz * ((1 - fy) * (v[5] - v[4]) + fy * (v[7] - v[6]));
+    g[1] = (1 - fz) * ((1 - fx) * (v[2] - v[0]) + fx * (v[3] - v[1])) + fz * ((1 - fx) * (v[6] - v[4]) + fx * (v[7] - v[5]));
+    g[2] = (1 - fy) * ((1 - fx) * (v[4] - v[0]) + fx * (v[5] - v[1])) + fy * ((1 - fx) * (v[6] - v[2]) + fx * (v[7] - v[3]));
+}
+
+typedef struct {
+    int64_t key;          /* hit sample index h, or -1 */
+    double f;             /* fraction between samples h - 1 and h */
+    double dsdt;          /* |s_h - s_{h-1}| */
+    double rgba[4];
+} iso_frag;
+
+/* Value source of a brick (or of the whole field: K = 1, the grid box). */
+typedef struct {
+    const void* data;
+    int dtype;
+    double scale;
+    int lo[3], n[3];
+} iso_src;
+
+static double src_value(const iso_src* b, const double q[3]) {
+    return trilinear(b->data, b->dtype, b->scale, b->lo, b->n, q, NULL, NULL);
+}
+
+/* Surface colour and cell-face ambiguity of a hit in source b. */
+static void iso_shade(const orc_grid* g, const orc_rayinfo* ri, const iso_src* b, const orc_tf* tf, double iso,
+                      int64_t h, double f, double rgba[4], int* fl) {
+    double t = ri->t_enter + (h - 0.5 + f) * ri->dt;
+    double q[3];
+    for (int a = 0; a < 3; ++a) {
+        q[a] = (ri->o[a] + t * ri->d[a] - g->origin[a]) / g->spacing;
+        if (q[a] < 0.0) q[a] = 0.0;
+        if (q[a] > g->dims[a] - 1) q[a] = g->dims[a] - 1;
+    }
+    double gr[3], fr3[3];
+    trilinear_grad(b->data, b->dtype, b->scale, b->lo, b->n, q, gr, fr3);
+    for (int a = 0; a < 3; ++a)
+        if (fr3[a] < 1e-4 || fr3[a] > 1.0 - 1e-4) *fl |= ORC_FLAG_ISO_AMBIG;
+    double nn = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+    double dn = sqrt(ri->d[0] * ri->d[0] + ri->d[1] * ri->d[1] + ri->d[2] * ri->d[2]);
+    double k = 1.0;
+    if (nn > 0.0) k = 0.25 + 0.75 * fabs(gr[0] * ri->d[0] + gr[1] * ri->d[1] + gr[2] * ri->d[2]) / (nn * dn);
+    double v[4];
+    tf_lookup(tf, iso, v, NULL, NULL, NULL);
+    for (int c = 0; c < 3; ++c) rgba[c] = v[c] * k;
+    rgba[3] = 1.0;
+}
+
+/* One pixel.  K sources with their owned boxes (bricks), or K = 1 and no
+ * bricks (the whole field, which owns every sample).  Outputs the composited
+ * colour, depth, key, |s_h - s_{h-1}|, per-brick keys and flags. */
+static void iso_pixel(const orc_grid* g, int K, const orc_brick* bricks, const iso_src* src, const orc_tf* tf,
+                      const orc_camera* cam, const orc_frame* fr, double iso, double iso_eps, int px, int py,
+                      double rgba[4], double* depth, int64_t* key, double* dsdt, int32_t* frag_key, int* flags,
+                      iso_frag* fs) {
+    orc_rayinfo ri;
+    ray_samples(g, cam, fr, px, py, &ri);
+    int fl = ri.flags;
+    for (int b = 0; b < K; ++b) fs[b].key = -1;
+    int owner = -1;
+    int64_t first_hit = -1;
+    for (int64_t j = 0; j < ri.n; ++j) {
+        double q[3], qp[3];
+        sample_point(g, &ri, j, q, NULL);
+        owner = bricks ? find_owner(g, K, bricks, q, owner) : 0;
+        if (owner < 0) continue;
+        double s = src_value(&src[owner], q);
+        if (first_hit < 0 && fabs(s - iso) < iso_eps) fl |= ORC_FLAG_ISO_AMBIG;
+        if (j == 0 || fs[owner].key >= 0) continue;
+        sample_point(g, &ri, j - 1, qp, NULL);
+        double sp = src_value(&src[owner], qp);       /* s_{j-1} in this brick */
+        if ((sp >= iso) != (s >= iso)) {
+            iso_frag* fg = &fs[owner];
+            fg->key = j;
+            fg->f = (iso - sp) / (s - sp);
+            fg->dsdt = fabs(s - sp);
+            int dummy = 0;
+            iso_shade(g, &ri, &src[owner], tf, iso, j, fg->f, fg->rgba, first_hit < 0 ? &fl : &dummy);
+            if (first_hit < 0) first_hit = j;
+        }
+    }
+    /* depth composite: the smallest key */
+    int best = -1;
+    for (int b = 0; b < K; ++b) {
+        if (frag_key) frag_key[b] = fs[b].key >= 0 ? (int32_t)fs[b].key : 2147483647;
+        if (fs[b].key >= 0 && (best < 0 || fs[b].key < fs[best].key)) best = b;
+    }
+    if (best >= 0) {
+        for (int c = 0; c < 4; ++c) rgba[c] = fs[best].rgba[c];
+        *depth = ri.t_enter + (fs[best].key - 0.5 + fs[best].f) * ri.dt;
+        *key = fs[best].key;
+        *dsdt = fs[best].dsdt;
+    } else {
+        rgba[0] = rgba[1] = rgba[2] = rgba[3] = 0.0;
+        *depth = INFINITY;
+        *key = -1;
+        *dsdt = 0.0;
+    }
+    *flags = fl;
+}
+
+/* Iso-surface render of the whole float32 field (the plain definition) or of
+ * the bricks (fragments + depth composite).  Per listed pixel k: rgba[4k..],
+ * depth[k], key[k] (-1: no hit), dsdt[k], frag_key[K k + b] (bricks only),
+ * flags[k]. */
+void orc_render_iso(const orc_grid* g, const float* field, int K, const orc_brick* bricks, const orc_tf* tf,
+                    const orc_camera* cam, const orc_frame* fr, double iso, double iso_eps, int npix,
+                    const int32_t* pix, double* rgba, double* depth, int64_t* key, double* dsdt, int32_t* frag_key,
+                    uint8_t* flags) {
+    int nsrc = bricks ? K : 1;
+    iso_src* src = (iso_src*)malloc(sizeof(iso_src) * nsrc);
+    for (int b = 0; b < nsrc; ++b) {
+        if (bricks) {
+            src[b].data = bricks[b].data;
+            src[b].dtype = bricks[b].dtype;
+            src[b].scale = bricks[b].scale;
+            orc_stored_box(g->dims, bricks[b].owned_lo, bricks[b].owned_hi, src[b].lo, src[b].n);
+        } else {
+            src[b].data = field;
+            src[b].dtype = ORC_F32;
+            src[b].scale = 1.0;
+            for (int a = 0; a < 3; ++a) {
+                src[b].lo[a] = 0;
+                src[b].n[a] = g->dims[a];
+            }
+        }
+    }
+#pragma omp parallel
+    {
+        iso_frag* fs = (iso_frag*)malloc(sizeof(iso_frag) * nsrc);
+#pragma omp for schedule(dynamic, 16)
+        for (int k = 0; k < npix; ++k) {
+            int p = pix ? pix[k] : k;
+            int fl = 0;
+            int64_t kk;
+            double ds, dep;
+            iso_pixel(g, nsrc, bricks, src, tf, cam, fr, iso, iso_eps, p % fr->width, p / fr->width,
+                      rgba + 4 * (int64_t)k, &dep, &kk, &ds, frag_key && bricks ? frag_key + (int64_t)K * k : NULL,
+                      &fl, fs);
+            if (depth) depth[k] = dep;
+            if (key) key[k] = kk;
+            if (dsdt) dsdt[k] = ds;
+            if (flags) flags[k] = (uint8_t)fl;
+        }
+        free(fs);
+    }
+    free(src);
 }
 
 /* ------------------------------------------------------------------------ */
