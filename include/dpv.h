@@ -126,11 +126,24 @@ typedef struct {
                                       while profiling is on) */
 #define DPV_FRAME_CELL 32          /* the cell layout, whether or not it fits */
 #define DPV_FRAME_QUAD 64          /* the quad layout */
+#define DPV_FRAME_ISO 128          /* iso-surface fragments instead of volume rendering
+                                      (the paper's z-composited opaque surfaces, §7):
+                                      each brick reports the first sample pair (j-1, j)
+                                      of the ray, j its own, across which [s >= iso_value]
+                                      changes (it evaluates s_{j-1} in its ghost layer);
+                                      the surface point is interpolated linearly between
+                                      the two samples; colour = TF rgb(iso_value) x
+                                      (0.25 + 0.75 |N.d| / (|N||d|)), N the gradient of
+                                      the trilinear interpolant, alpha 1; the composite
+                                      keeps the nearest fragment (smallest key) and its
+                                      interpolated depth.  No hit: (0,0,0,0), depth +inf.
+                                      No backward (DPV_ERR_UNSUPPORTED), not with
+                                      DPV_FRAME_STAGED. */
 
 /* Frame parameters, identical on all ranks (§3.1.1).  Every camera renders
  * a width x height image.  tile_w/tile_h: pixels per work item (multiples
  * of 8 and 4; 0 = autotuned default).  ert_threshold <= 0 or >= 1 disables
- * early termination. */
+ * early termination.  iso_value: the level of DPV_FRAME_ISO. */
 typedef struct {
     int width, height;
     float step_voxels;
@@ -138,6 +151,7 @@ typedef struct {
     float ert_threshold;
     int tile_w, tile_h;
     int flags;
+    float iso_value;
 } dpv_frame_desc;
 
 /* Pipeline stages timed when profiling is on (dpvSetProfiling). */

@@ -679,7 +679,8 @@ void orc_composite(int npix, int K, const double* frag_rgba, const int32_t* frag
  *     N = 0; alpha 1.  No hit: (0, 0, 0, 0) and depth +inf.
  * Flagged ISO_AMBIG (a rounded s or point may decide otherwise): a sample up
  * to the hit (all samples without a hit) within iso_eps of iso, or the
- * surface point within 1e-4 of a cell face. */
+ * surface point within 1e-4 of a cell face; OWNER_AMBIG: a sample up to the
+ * hit near an internal brick face. */
 
 /* Gradient of the trilinear interpolant at node-space point q in the cell
  * trilinear() would use (decoded, scaled corners). */
@@ -764,12 +765,16 @@ static void iso_pixel(const orc_grid* g, int K, const orc_brick* bricks, const i
     int owner = -1;
     int64_t first_hit = -1;
     for (int64_t j = 0; j < ri.n; ++j) {
-        double q[3], qp[3];
-        sample_point(g, &ri, j, q, NULL);
+        double q[3], qp[3], tj;
+        sample_point(g, &ri, j, q, &tj);
         owner = bricks ? find_owner(g, K, bricks, q, owner) : 0;
         if (owner < 0) continue;
         double s = src_value(&src[owner], q);
         if (first_hit < 0 && fabs(s - iso) < iso_eps) fl |= ORC_FLAG_ISO_AMBIG;
+        /* up to the hit, a sample the GPU may give to the neighbour brick
+         * (whose per-brick scale differs under fp8 storage) */
+        if (first_hit < 0 && bricks && near_internal_face(g, &bricks[owner], &ri, tj, fr->amb_samples))
+            fl |= ORC_FLAG_OWNER_AMBIG;
         if (j == 0 || fs[owner].key >= 0) continue;
         sample_point(g, &ri, j - 1, qp, NULL);
         double sp = src_value(&src[owner], qp);       /* s_{j-1} in this brick */

@@ -332,6 +332,8 @@ dpv_status prepare(dpv_device dev) {
     P.items_cap = 0;
     // floats of shared memory per staged slab box; DPV_BOX_CAP overrides it
     // (tuning, and tests that force the unstaged fallback of large slabs)
+    P.iso_on = (F.flags & DPV_FRAME_ISO) ? 1 : 0;
+    P.iso = F.iso_value;
     P.box_cap = 6144;
     if (const char* env = getenv("DPV_BOX_CAP")) {
         int v = atoi(env);
@@ -561,7 +563,9 @@ dpv_status prepare(dpv_device dev) {
 dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
     const FrameParams& P = dev->P;
     float3 og = make_float3(dev->origin[0], dev->origin[1], dev->origin[2]);
-    const bool persistent = (dev->frame.flags & DPV_FRAME_PERSISTENT) && !(dev->frame.flags & DPV_FRAME_STAGED);
+    const bool iso = P.iso_on != 0;
+    const bool persistent = (dev->frame.flags & DPV_FRAME_PERSISTENT) && !(dev->frame.flags & DPV_FRAME_STAGED) &&
+                            !iso;
     CK(cudaMemsetAsync(dev->d_counters, 0, sizeof(Counters), st), "reset counters");
     cudaEvent_t t0 = timed ? stage_start(dev) : nullptr;
     CK(launch_cull(P, dev->d_cam_in, og, dev->spacing, dev->d_cams, dev->d_camd, dev->d_rays, dev->d_bricks,
@@ -575,7 +579,12 @@ dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
            "schedule");
     if (timed) stage_stop(dev, DPV_STAGE_CULL, t0);
     t0 = timed ? stage_start(dev) : nullptr;
-    if (!(dev->frame.flags & DPV_FRAME_STAGED))
+    if (iso)
+        CK(launch_iso_fwd(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
+                          dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters,
+                          st),
+           "iso march");
+    else if (!(dev->frame.flags & DPV_FRAME_STAGED))
         CK(launch_march_fwd(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                             dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters,
                             st, persistent ? &sch : nullptr),
@@ -586,10 +595,16 @@ dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
            "march");
     if (timed) stage_stop(dev, DPV_STAGE_MARCH, t0);
     t0 = timed ? stage_start(dev) : nullptr;
-    CK(launch_composite_fwd(P, 1.0f / dev->spacing, dev->d_cams, dev->d_tile_first, dev->d_tile_count, dev->d_items,
-                            dev->d_frag_rgba, dev->d_frag_key, dev->d_out_rgba, dev->d_out_depth,
-                            P.order_stride ? dev->d_order : nullptr, st),
-       "composite");
+    if (iso)
+        CK(launch_composite_iso(P, dev->d_cams, dev->d_tile_first, dev->d_tile_count, dev->d_items, dev->d_frag_rgba,
+                                dev->d_frag_key, dev->d_out_rgba, dev->d_out_depth,
+                                P.order_stride ? dev->d_order : nullptr, st),
+           "composite");
+    else
+        CK(launch_composite_fwd(P, 1.0f / dev->spacing, dev->d_cams, dev->d_tile_first, dev->d_tile_count,
+                                dev->d_items, dev->d_frag_rgba, dev->d_frag_key, dev->d_out_rgba, dev->d_out_depth,
+                                P.order_stride ? dev->d_order : nullptr, st),
+           "composite");
     if (timed) stage_stop(dev, DPV_STAGE_COMPOSITE, t0);
     dev->launches += 6 + (persistent ? 3 : 0) + (dev->n_items > 0 ? 1 : 0) + 1;
     return DPV_OK;
@@ -833,6 +848,10 @@ dpv_status dpvSetFrame(dpv_device dev, const dpv_frame_desc* f) {
     int tw = f->tile_w > 0 ? f->tile_w : 16, th = f->tile_h > 0 ? f->tile_h : 16;
     if (tw % 8 || th % 4 || tw * th > 256)
         return fail(DPV_ERR_INVALID_ARG, "tile %dx%d: width a multiple of 8, height of 4, at most 256 pixels", tw, th);
+    if ((f->flags & DPV_FRAME_ISO) && (f->flags & DPV_FRAME_STAGED))
+        return fail(DPV_ERR_UNSUPPORTED, "iso-surface frames have no staged form");
+    if ((f->flags & DPV_FRAME_ISO) && !isfinite(f->iso_value))
+        return fail(DPV_ERR_INVALID_ARG, "iso_value must be finite");
     dev->frame = *f;
     dev->has_frame = true;
     dev->dirty = true;
@@ -977,6 +996,7 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
     dpv_status s = check_dev(dev);
     if (s) return s;
     if (!dev->rendered || dev->dirty) return fail(DPV_ERR_STATE, "backward needs the fragments of a render");
+    if (dev->P.iso_on) return fail(DPV_ERR_UNSUPPORTED, "the adjoint is of the volume-rendering mode");
     if (!dL_drgba || !dL_dtf) return fail(DPV_ERR_INVALID_ARG, "gradient pointers NULL");
     DeviceGuard g(dev->cuda_device);
     const FrameParams& P = dev->P;

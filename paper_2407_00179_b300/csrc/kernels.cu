@@ -577,6 +577,141 @@ cudaError_t launch_march_fwd(int dtype, int gather, const FrameParams& P, const 
 }
 
 // ===========================================================================
+// iso-surface fragments (DPV_FRAME_ISO)
+// ===========================================================================
+//
+// Each thread tests the sample pairs (j - 1, j) whose later sample j its
+// brick owns, evaluating s_{j-1} itself (it lies in the ghost layer), and
+// stops at the first pair across which [s >= iso] changes.  The surface
+// point sits at fraction f = (iso - s_{j-1}) / (s_j - s_{j-1}) between the
+// two samples; its shading uses the gradient of the trilinear interpolant of
+// the cell holding it.  Fragment: (shaded rgb, f), key j; the compositor
+// keeps the smallest key.
+
+template <typename T, int GL>
+__device__ __forceinline__ unsigned long long iso_item(const FrameParams& P, const CamBasis* cams,
+                                                       const BrickDev* bricks, const float* scales, const Item& it,
+                                                       long long item, const float4* s_tf, float4* frag_rgba,
+                                                       int* frag_key) {
+    const BrickDev b = bricks[it.brick];
+    const CamBasis cam = cams[it.cam];
+    const float scale = scales[b.scale_idx];
+    const T* data = (const T*)b.data;
+    int lx, ly;
+    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
+    long long slot = item * P.tp + threadIdx.x;
+    unsigned long long nsamp = 0;
+    if (px < P.W && py < P.H) {
+        MarchState m;
+        int key = KEY_EMPTY;
+        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (brick_samples(P, cam, it.cam, b, px, py, m)) {
+            const int n = m.j1 - m.j0;
+            CornerCache<T, GL> cc;
+            SampleWalker wk;
+            wk.init(b);
+            int ix, iy, iz;
+            float fx, fy, fz;
+            // the sample before the brick's first one (none before the ray's first)
+            int k = m.j0 == 0 ? 0 : -1;
+            wk.at(m, k, ix, iy, iz, fx, fy, fz);
+            float sp = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
+            ++nsamp;
+            for (++k; k < n; ++k) {
+                wk.at(m, k, ix, iy, iz, fx, fy, fz);
+                const float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
+                ++nsamp;
+                if ((sp >= P.iso) != (s >= P.iso)) {
+                    const float f = (P.iso - sp) / (s - sp);
+                    // the surface point, at sample index k - 1 + f of the brick
+                    const float fk = (float)(k - 1) + f;
+                    int c[3];
+                    float w[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float q = fmaf(fk, m.st[a], m.q0[a]);
+                        c[a] = min(max(__float2int_rd(q), 0), b.s_n[a] - 2);
+                        w[a] = q - (float)c[a];
+                    }
+                    trilinear<T, GL>(b, data, scale, cc, c[0], c[1], c[2], w[0], w[1], w[2]);
+                    // gradient of the interpolant: each component the
+                    // bilinear lerp of the cell's edge differences along
+                    // that axis; explicit fma / rounded products, so every
+                    // gather layout gives the same bits
+                    const float* v = cc.v;
+                    auto lerp = [](float t, float a, float b2) { return fmaf(t, b2 - a, a); };
+                    const float gx = lerp(w[2], lerp(w[1], v[1] - v[0], v[3] - v[2]), lerp(w[1], v[5] - v[4], v[7] - v[6]));
+                    const float gy = lerp(w[2], lerp(w[0], v[2] - v[0], v[3] - v[1]), lerp(w[0], v[6] - v[4], v[7] - v[5]));
+                    const float gz = lerp(w[1], lerp(w[0], v[4] - v[0], v[5] - v[1]), lerp(w[0], v[6] - v[2], v[7] - v[3]));
+                    const float nn = sqrtf(fmaf(gx, gx, fmaf(gy, gy, __fmul_rn(gz, gz))));
+                    const float dn =
+                        sqrtf(fmaf(m.st[0], m.st[0], fmaf(m.st[1], m.st[1], __fmul_rn(m.st[2], m.st[2]))));
+                    float fac = 1.0f;
+                    if (nn > 0.0f) {
+                        const float dot = fmaf(gx, m.st[0], fmaf(gy, m.st[1], __fmul_rn(gz, m.st[2])));
+                        fac = fmaf(0.75f, __fdiv_rn(fabsf(dot), __fmul_rn(nn, dn)), 0.25f);
+                    }
+                    const TFSample col = tf_lookup(s_tf, P, P.iso);
+                    out = make_float4(__fmul_rn(col.v.x, fac), __fmul_rn(col.v.y, fac), __fmul_rn(col.v.z, fac), f);
+                    key = m.j0 + k;
+                    break;
+                }
+                sp = s;
+            }
+        }
+        frag_rgba[slot] = out;
+        frag_key[slot] = key;
+    }
+    return nsamp;
+}
+
+template <typename T, int GL>
+__global__ void __launch_bounds__(256) k_iso_fwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
+                                                 const float* scales, const Item* items, const float4* tf,
+                                                 float4* frag_rgba, int* frag_key, Counters* counters) {
+    extern __shared__ float4 s_tf[];
+    for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
+    __syncthreads();
+    const Item it = items[blockIdx.x];
+    unsigned long long nsamp = 0;
+    if (item_ok(it, P)) nsamp = iso_item<T, GL>(P, cams, bricks, scales, it, blockIdx.x, s_tf, frag_rgba, frag_key);
+    nsamp = warp_sum_u64(nsamp);
+    if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
+}
+
+template <typename T, int GL>
+static void iso_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
+                       const Item* items, int n_items, const float4* tf, float4* frag_rgba, int* frag_key,
+                       Counters* counters, cudaStream_t st) {
+    size_t smem = sizeof(float4) * P.ntf;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_iso_fwd<T, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_iso_fwd<T, GL><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key, counters);
+}
+
+cudaError_t launch_iso_fwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
+                           const BrickDev* bricks, const float* scales, const Item* items, int n_items,
+                           const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters, cudaStream_t st) {
+    if (n_items == 0) return cudaSuccess;
+#define ISO(T)                                                                                                   \
+    (gather == GATHER_CELL   ? iso_launch<T, GATHER_CELL>(P, cams, bricks, scales, items, n_items, tf, frag_rgba,    \
+                                                          frag_key, counters, st)                                 \
+     : gather == GATHER_QUAD ? iso_launch<T, GATHER_QUAD>(P, cams, bricks, scales, items, n_items, tf, frag_rgba,    \
+                                                          frag_key, counters, st)                                 \
+                             : iso_launch<T, GATHER_LINEAR>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, \
+                                                            frag_key, counters, st))
+    switch (dtype) {
+        case 0: ISO(float); break;
+        case 1: ISO(__half); break;
+        case 2: ISO(__nv_bfloat16); break;
+        default: ISO(__nv_fp8_e4m3); break;
+    }
+#undef ISO
+    return cudaGetLastError();
+}
+
+// ===========================================================================
 // sort-last compositor (forward)
 // ===========================================================================
 
@@ -695,6 +830,76 @@ __global__ void __launch_bounds__(256) k_composite_fwd(FrameParams P, float inv_
         depth = te + ((float)depth_key + 0.5f) * P.dt;
     }
     out_depth[pix] = depth;
+}
+
+// Depth composite of iso-surface fragments: the nearest (smallest key)
+// opaque fragment, its depth t_{key-1} + f dt from the fraction it carries
+// in w.  The order image lists the pixel's fragments front to back.
+__global__ void __launch_bounds__(256) k_composite_iso(FrameParams P, const CamBasis* cams, const int* tile_first,
+                                                       const int* tile_count, const Item* items,
+                                                       const float4* frag_rgba, const int* frag_key,
+                                                       float4* out_rgba, float* out_depth, unsigned char* order) {
+    int ct = blockIdx.x;
+    int ntiles = P.ntx * P.nty;
+    int c = ct / ntiles, tile = ct % ntiles;
+    int lx, ly;
+    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    int px = (tile % P.ntx) * P.tw + lx, py = (tile / P.ntx) * P.th + ly;
+    if (px >= P.W || py >= P.H) return;
+    long long first = tile_first[ct];
+    int cnt = tile_count[ct];
+    if (first < 0 || first + cnt > P.items_cap) cnt = 0;    // list overflowed: error bit already set
+    int t = threadIdx.x;
+    SortedFrags s;
+    collect_sorted(frag_key, first, cnt, P.tp, t, s);
+    long long pix = ((long long)c * P.H + py) * P.W + px;
+    unsigned char* ord = order ? order + pix * P.order_stride : nullptr;
+    int front = -1, front_key = KEY_EMPTY;
+    if (s.n <= KR) {
+        if (s.n > 0) {
+            front = s.slot[0];
+            front_key = s.key[0];
+        }
+        if (ord) {
+#pragma unroll
+            for (int i = 0; i < KR; ++i)
+                if (i < s.n && i < P.order_stride) ord[i] = (unsigned char)items[first + s.slot[i]].brick;
+        }
+    } else {
+        int last = -1;
+        for (int i = 0; i < s.n; ++i) {
+            int q = next_slot(frag_key, first, cnt, P.tp, t, last);
+            int k = frag_key[(first + q) * P.tp + t];
+            last = k;
+            if (i == 0) {
+                front = q;
+                front_key = k;
+            }
+            if (ord && i < P.order_stride) ord[i] = (unsigned char)items[first + q].brick;
+        }
+    }
+    if (ord)
+        for (int i = s.n; i < P.order_stride; ++i) ord[i] = 0xFF;
+    float4 rgba = make_float4(0.f, 0.f, 0.f, 0.f);
+    float depth = __int_as_float(0x7f800000);
+    if (front >= 0) {
+        const float4 f = frag_rgba[(first + front) * P.tp + t];
+        rgba = make_float4(f.x, f.y, f.z, 1.0f);
+        const float te = pixel_t_enter(P, cams[c], c, px, py);
+        depth = te + ((float)front_key - 0.5f + f.w) * P.dt;
+    }
+    out_rgba[pix] = rgba;
+    out_depth[pix] = depth;
+}
+
+cudaError_t launch_composite_iso(const FrameParams& P, const CamBasis* cams, const int* tile_first,
+                                 const int* tile_count, const Item* items, const float4* frag_rgba,
+                                 const int* frag_key, float4* out_rgba, float* out_depth, unsigned char* order,
+                                 cudaStream_t st) {
+    int nct = P.ncam * P.ntx * P.nty;
+    k_composite_iso<<<nct, P.tp, 0, st>>>(P, cams, tile_first, tile_count, items, frag_rgba, frag_key, out_rgba,
+                                          out_depth, order);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_composite_fwd(const FrameParams& P, float inv_spacing, const CamBasis* cams,

@@ -51,6 +51,15 @@ cudaError_t launch_march_fwd(int dtype, int gather, const FrameParams& P, const 
                              const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
                              cudaStream_t st, const Schedule* sch = nullptr);
 
+// Iso-surface fragments (DPV_FRAME_ISO) and their depth composite.
+cudaError_t launch_iso_fwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
+                           const BrickDev* bricks, const float* scales, const Item* items, int n_items,
+                           const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters, cudaStream_t st);
+cudaError_t launch_composite_iso(const FrameParams& P, const CamBasis* cams, const int* tile_first,
+                                 const int* tile_count, const Item* items, const float4* frag_rgba,
+                                 const int* frag_key, float4* out_rgba, float* out_depth, unsigned char* order,
+                                 cudaStream_t st);
+
 // Shared-memory staged ray-march and adjoint (staged.cu).
 cudaError_t launch_march_fwd_staged(int dtype, const FrameParams& P, const CamBasis* cams, const BrickDev* bricks,
                                     const float* scales, const Item* items, int n_items, const float4* tf,

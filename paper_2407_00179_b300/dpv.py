@@ -27,6 +27,7 @@ FRAME_PERSISTENT = 8
 FRAME_GRAPH = 16
 FRAME_CELL = 32
 FRAME_QUAD = 64
+FRAME_ISO = 128
 GATHER_FLAGS = {"auto": 0, "cell": FRAME_CELL, "quad": FRAME_QUAD, "linear": FRAME_LINEAR}
 
 
@@ -66,7 +67,8 @@ class CameraDesc(C.Structure):
 
 class FrameDesc(C.Structure):
     _fields_ = [("width", C.c_int), ("height", C.c_int), ("step_voxels", C.c_float), ("sigma_max", C.c_float),
-                ("ert_threshold", C.c_float), ("tile_w", C.c_int), ("tile_h", C.c_int), ("flags", C.c_int)]
+                ("ert_threshold", C.c_float), ("tile_w", C.c_int), ("tile_h", C.c_int), ("flags", C.c_int),
+                ("iso_value", C.c_float)]
 
 
 class TuneResult(C.Structure):
@@ -270,18 +272,21 @@ class Device:
 
     def set_frame(self, width: int, height: int, step_voxels: float = 0.5, sigma_max: float = 8.0, ert: float = 0.0,
                   tile=(0, 0), order: bool = False, staged: bool = False, gather: str = "auto",
-                  persistent: bool = False, graph: bool = False):
+                  persistent: bool = False, graph: bool = False, iso: Optional[float] = None):
         """gather: "auto" (cell layout where it fits in half of the free
-        device memory, else quad), "cell", "quad" or "linear"."""
+        device memory, else quad), "cell", "quad" or "linear".  iso: render
+        iso-surface fragments at that level instead of volume rendering
+        (DPV_FRAME_ISO)."""
         if gather not in GATHER_FLAGS:
             raise ValueError("gather must be one of %s" % sorted(GATHER_FLAGS))
         flags = (FRAME_ORDER if order else 0) | (FRAME_STAGED if staged else 0) | GATHER_FLAGS[gather] | (
-            FRAME_PERSISTENT if persistent else 0) | (FRAME_GRAPH if graph else 0)
+            FRAME_PERSISTENT if persistent else 0) | (FRAME_GRAPH if graph else 0) | (
+            FRAME_ISO if iso is not None else 0)
         f = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
-                      int(tile[1]), flags)
+                      int(tile[1]), flags, float(iso) if iso is not None else 0.0)
         _check(load().dpvSetFrame(self._h, C.byref(f)))
         self._frame_args = (step_voxels, sigma_max, ert)
-        self._frame_kw = {"order": order, "staged": staged, "graph": graph}
+        self._frame_kw = {"order": order, "staged": staged, "graph": graph, "iso": iso}
         self.width, self.height = int(width), int(height)
 
     # -- rendering ---------------------------------------------------------
@@ -415,7 +420,7 @@ def render_noalloc(dims: Sequence[int], bricks, storage: str, tf: torch.Tensor, 
     cam = CameraDesc((C.c_float * 3)(*camera.eye), (C.c_float * 3)(*camera.center), (C.c_float * 3)(*camera.up),
                      float(camera.fovy_deg))
     fr = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
-                   int(tile[1]), 0)
+                   int(tile[1]), 0, 0.0)
     st = stream if stream is not None else torch.cuda.current_stream()
     _check(load().dpvRenderNoAlloc(C.byref(sc), C.byref(cam), C.byref(fr), _ptr(rgba), _ptr(depth),
                                    C.c_void_p(st.cuda_stream)))

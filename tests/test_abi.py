@@ -46,7 +46,7 @@ def test_struct_layouts_match_header():
     # dpv_brick_desc: 6 ints, dtype, float, dtype, pointer, 6 ints, int
     assert C.sizeof(dpv.BrickDesc) == 4 * 9 + 4 + 8 + 4 * 7 + 4
     assert C.sizeof(dpv.CameraDesc) == 40
-    assert C.sizeof(dpv.FrameDesc) == 32
+    assert C.sizeof(dpv.FrameDesc) == 36
     assert C.sizeof(dpv.Stats) == 40 + 8 * 5 + 4 * 5 + 4 + 8 + 8
 
 
