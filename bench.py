@@ -49,6 +49,9 @@ CONFIGS = {
     # 512^3 f32, 64 blobs + 3-octave noise, 2x2x2 bricks, 1920x1080, ERT 0.99
     "mid": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
                 storage="f32", cams="direction", compare_storage="f16"),
+    # iso-surface fragments of the mid field (forward only: no adjoint)
+    "mid_iso": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.0,
+                    storage="f32", cams="direction", iso=0.5),
     "mid_f16": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
                     storage="f16", cams="direction"),
     # 64^3 f32, 8 blobs, 2x1x1 bricks, 256x256, no ERT
@@ -182,9 +185,14 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
     W, H = cfg["width"], cfg["height"]
     cam = cams[0]
 
+    iso = cfg.get("iso")
+
     def run(rows):
         pix = np.concatenate([np.arange(W, dtype=np.int32) + W * int(r) for r in rows])
         t = time.perf_counter()
+        if iso is not None:
+            oracle.render_iso(cfg["dims"], tf, cam, fr, iso, bricks=bricks, pix=pix)
+            return time.perf_counter() - t, 0, len(pix)
         out = oracle.render_bricks(cfg["dims"], bricks, tf, cam, fr, pix=pix)
         return time.perf_counter() - t, int(out["nsamples"].sum()), len(pix)
 
@@ -202,6 +210,14 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
     rows1 = np.linspace(0, H - 1, n1).astype(int)
     dt1, ns1, npx1 = run(rows1)
     oracle.set_threads(ncores)
+    if iso is not None:
+        # the iso oracle evaluates every sample of the ray: its rate is in pixels
+        return {"value": npx / dt / 1e6, "unit": "Mpixels/s", "cores": ncores, "kind": "oracle",
+                "sample": "%d of %d pixel rows (%d pixels) of camera 0, iso-surface, FP64, %.1f s" % (
+                    len(rows), H, npx, dt),
+                "one_core": {"value": npx1 / dt1 / 1e6, "unit": "Mpixels/s", "cores": 1,
+                             "sample": "%d pixel rows (%d pixels) of camera 0, %.1f s" % (len(rows1), npx1, dt1)},
+                "seconds": dt, "samples": npx, "rows": rows}
     return {"value": ns / dt / 1e9, "unit": "Gsamples/s", "cores": ncores, "kind": "oracle",
             "sample": "%d of %d pixel rows (%d pixels, %d samples) of camera 0, FP64, %.1f s" % (
                 len(rows), H, npx, ns, dt),
@@ -229,17 +245,18 @@ def run_reference(args, cfg_name, cfg):
         base = r
     tot_s = sum(r["seconds"] for r in steps)
     tot_n = sum(r["samples"] for r in steps)
-    val = tot_n / tot_s / 1e9
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gsamples/s", "n_gpus": args.gpus,
+    unit = base["unit"]
+    val = tot_n / tot_s / (1e6 if unit == "Mpixels/s" else 1e9)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_s / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
             "config": {"workload": cfg_name, "dims": list(cfg["dims"]), "bricks": part.num_ranks,
                        "cameras": cfg["ncam"], "image": [cfg["width"], cfg["height"]], "storage": cfg["storage"],
                        "ert": cfg["ert"]},
-            "cpu_baseline": {"value": val, "unit": "Gsamples/s", "cores": base["cores"], "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": unit, "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
-            "e2e": {"value": val, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -274,20 +291,23 @@ def run_ours(args, cfg_name, cfg):
     tf = torch.from_numpy(tf_np).to(device)
     dev.set_tf(tf)
     dev.set_cameras(cams)
-    dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=(args.tile_w, args.tile_h))
+    iso = cfg.get("iso")
+    dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=(args.tile_w, args.tile_h), iso=iso)
     tune = None
     if not args.no_autotune:
         tune = dev.autotune(frames=3, cache=args.autotune_cache, key=cfg_name)
         fl = tune["flags"]
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=tuple(tune["tile"]),
-                      gather=dpv.gather_of(fl), persistent=bool(fl & dpv.FRAME_PERSISTENT))
-    # fixed upstream gradient: d/dI of mean (I - I*)^2 with I* from a perturbed TF
-    dev.set_tf(torch.from_numpy(inputs.perturb_tf(tf_np, 0)).to(device))
-    dev.render()
-    target = dev.frames()[0].clone()
-    dev.set_tf(tf)
-    dev.render()
-    grad = (2.0 / target.numel()) * (dev.frames()[0] - target)
+                      gather=dpv.gather_of(fl), persistent=bool(fl & dpv.FRAME_PERSISTENT), iso=iso)
+    grad = None
+    if iso is None:
+        # fixed upstream gradient: d/dI of mean (I - I*)^2 with I* from a perturbed TF
+        dev.set_tf(torch.from_numpy(inputs.perturb_tf(tf_np, 0)).to(device))
+        dev.render()
+        target = dev.frames()[0].clone()
+        dev.set_tf(tf)
+        dev.render()
+        grad = (2.0 / target.numel()) * (dev.frames()[0] - target)
     torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream(device)
@@ -298,7 +318,8 @@ def run_ours(args, cfg_name, cfg):
         dev.render()
         if ev:
             ev[1].record(stream)
-        dev.backward(grad, volume_grad=True)
+        if grad is not None:          # iso-surface frames have no adjoint
+            dev.backward(grad, volume_grad=True)
         if ev:
             ev[2].record(stream)
 
@@ -341,7 +362,7 @@ def run_ours(args, cfg_name, cfg):
     march_bwd_ms = st["stage_ms"]["march_bwd"] / max(1, st["stage_calls"]["march_bwd"])
     bytes_per_launch = st["samples_forward"] * 8 * bpv
     achieved = bytes_per_launch / (march_ms * 1e-3) / 1e9
-    bwd_achieved = st["samples_backward"] * (8 * bpv + 8 * 4) / (march_bwd_ms * 1e-3) / 1e9
+    bwd_achieved = st["samples_backward"] * (8 * bpv + 8 * 4) / (march_bwd_ms * 1e-3) / 1e9 if grad is not None else 0.0
     peak, peak_kind = _peaks()
 
     # many cameras: the same forward replayed from a CUDA graph, and the
@@ -463,22 +484,27 @@ def run_ours(args, cfg_name, cfg):
                    "parallelism": "weak: each GPU renders its own cameras over its own copy of the bricks"},
         "frames_per_s": frames / (fwd_ms * 1e-3),
         "forward_ms_per_step": fwd_ms / args.steps,
-        "backward": {"value": n_bwd / (bwd_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
-                     "ms_per_step": bwd_ms / args.steps},
+        "backward": ({"value": n_bwd / (bwd_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+                      "ms_per_step": bwd_ms / args.steps} if grad is not None else None),
+        "mpixels_per_s": frames * W * H / (fwd_ms * 1e-3) / 1e6,
         "samples_per_step": {"forward": n_fwd / args.steps, "backward": n_bwd / args.steps},
         "stage_ms_per_step": {k: v / max(1, args.steps) for k, v in st["stage_ms"].items()},
-        "value_basis": "forward samples evaluated / forward time (cull + march + composite) of the timed steps; "
-                       "each step also runs the backward, reported under 'backward' and in ms_per_step",
+        "value_basis": ("forward samples evaluated / forward time (cull + march + composite) of the timed steps; "
+                        "each step also runs the backward, reported under 'backward' and in ms_per_step"
+                        if grad is not None else
+                        "samples evaluated up to each brick's first hit / forward time (cull + iso march + depth "
+                        "composite); iso-surface frames have no adjoint, a step is the forward frame"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": TRAFFIC.get((cfg_name, "march")), "kernel": "k_march_fwd<%s>" % cfg["storage"],
+                     "traffic": TRAFFIC.get((cfg_name, "march")),
+                     "kernel": ("k_iso_fwd<%s>" if iso is not None else "k_march_fwd<%s>") % cfg["storage"],
                      "model": "stencil bytes: 8 corners x %d B per evaluated sample" % bpv,
                      "peak_kind": peak_kind},
-        "roofline_backward": {"bound": "hbm", "achieved": bwd_achieved, "peak": peak, "unit": "GB/s",
-                              "frac": bwd_achieved / peak, "traffic": TRAFFIC.get((cfg_name, "march_bwd")),
-                              "kernel": "k_march_bwd<%s> (+ k_face_gather)" % cfg["storage"],
-                              "model": "stencil bytes: 8 corners x %d B read + 8 x 4 B field-gradient adds per "
-                                       "replayed sample" % bpv,
-                              "peak_kind": peak_kind},
+        "roofline_backward": ({"bound": "hbm", "achieved": bwd_achieved, "peak": peak, "unit": "GB/s",
+                               "frac": bwd_achieved / peak, "traffic": TRAFFIC.get((cfg_name, "march_bwd")),
+                               "kernel": "k_march_bwd<%s> (+ k_face_gather)" % cfg["storage"],
+                               "model": "stencil bytes: 8 corners x %d B read + 8 x 4 B field-gradient adds per "
+                                        "replayed sample" % bpv,
+                               "peak_kind": peak_kind} if grad is not None else None),
         "e2e": {"value": e2e_val, "unit": "Gsamples/s", "h2d_bytes_per_step": int(tf_np.nbytes),
                 "d2h_bytes_per_step": int(ncam * H * W * 16), "what": "set TF from pinned host, render, copy frames"
                 " to pinned host, per step (forward)"},
