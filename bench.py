@@ -49,6 +49,11 @@ CONFIGS = {
     # 512^3 f32, 64 blobs + 3-octave noise, 2x2x2 bricks, 1920x1080, ERT 0.99
     "mid": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
                 storage="f32", cams="direction", compare_storage="f16"),
+    # the mid field made opaque (sigma_max 64, termination at 0.99), marched in
+    # visibility order with global early termination (forward only), beside
+    # the sort-last form with per-fragment termination
+    "mid_ordered": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080,
+                        ert=0.99, sigma_max=64.0, storage="f32", cams="direction", ordered=True),
     # iso-surface fragments of the mid field (forward only: no adjoint)
     "mid_iso": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.0,
                     storage="f32", cams="direction", iso=0.5),
@@ -181,7 +186,7 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
     ncores = len(os.sched_getaffinity(0))
     oracle.set_threads(ncores)
     bricks = oracle.make_bricks(field_np, part, oracle.DTYPE_NAMES[cfg["storage"]])
-    fr = oracle.Frame(cfg["width"], cfg["height"], step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"])
+    fr = oracle.Frame(cfg["width"], cfg["height"], step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"])
     W, H = cfg["width"], cfg["height"]
     cam = cams[0]
 
@@ -193,6 +198,9 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
         if iso is not None:
             oracle.render_iso(cfg["dims"], tf, cam, fr, iso, bricks=bricks, pix=pix)
             return time.perf_counter() - t, 0, len(pix)
+        if cfg.get("ordered"):
+            out = oracle.render_ordered(cfg["dims"], tf, cam, fr, bricks=bricks, pix=pix)
+            return time.perf_counter() - t, int(out["nsamples"].sum()), len(pix)
         out = oracle.render_bricks(cfg["dims"], bricks, tf, cam, fr, pix=pix)
         return time.perf_counter() - t, int(out["nsamples"].sum()), len(pix)
 
@@ -292,15 +300,17 @@ def run_ours(args, cfg_name, cfg):
     dev.set_tf(tf)
     dev.set_cameras(cams)
     iso = cfg.get("iso")
-    dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=(args.tile_w, args.tile_h), iso=iso)
+    ordered = bool(cfg.get("ordered"))
+    dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
+                  tile=(args.tile_w, args.tile_h), iso=iso, ordered=ordered)
     tune = None
     if not args.no_autotune:
         tune = dev.autotune(frames=3, cache=args.autotune_cache, key=cfg_name)
         fl = tune["flags"]
-        dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=tuple(tune["tile"]),
-                      gather=dpv.gather_of(fl), persistent=bool(fl & dpv.FRAME_PERSISTENT), iso=iso)
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"], tile=tuple(tune["tile"]),
+                      gather=dpv.gather_of(fl), persistent=bool(fl & dpv.FRAME_PERSISTENT), iso=iso, ordered=ordered)
     grad = None
-    if iso is None:
+    if iso is None and not ordered:
         # fixed upstream gradient: d/dI of mean (I - I*)^2 with I* from a perturbed TF
         dev.set_tf(torch.from_numpy(inputs.perturb_tf(tf_np, 0)).to(device))
         dev.render()
@@ -318,7 +328,7 @@ def run_ours(args, cfg_name, cfg):
         dev.render()
         if ev:
             ev[1].record(stream)
-        if grad is not None:          # iso-surface frames have no adjoint
+        if grad is not None:          # iso-surface and ordered frames have no adjoint
             dev.backward(grad, volume_grad=True)
         if ev:
             ev[2].record(stream)
@@ -369,7 +379,7 @@ def run_ours(args, cfg_name, cfg):
     # cameras rendered as separate float32 per-camera frames for comparison
     batch = None
     if ncam > 1 and compare_f32:
-        dev.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"], tile=tuple(tune["tile"]) if tune else
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"], tile=tuple(tune["tile"]) if tune else
                       (args.tile_w, args.tile_h), gather=dpv.gather_of(tune["flags"]) if tune else "auto", persistent=bool(tune and tune["flags"] & dpv.FRAME_PERSISTENT), graph=True)
         for _ in range(2):
             dev.render()
@@ -391,7 +401,7 @@ def run_ours(args, cfg_name, cfg):
         sep.set_tf(tf)
         for c, cam in enumerate(cams):
             sep.set_cameras([cam])
-            sep.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"])
+            sep.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"])
             sep.render()
             torch.cuda.synchronize()
             s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -420,7 +430,7 @@ def run_ours(args, cfg_name, cfg):
         alt.set_tf(tf)
         alt.set_cameras(cams)
         fl = tune["flags"] if tune else 0
-        alt.set_frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"],
+        alt.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
                       tile=tuple(tune["tile"]) if tune else (args.tile_w, args.tile_h), gather=dpv.gather_of(fl),
                       persistent=bool(fl & dpv.FRAME_PERSISTENT))
         for _ in range(max(3, args.warmup)):
@@ -438,6 +448,39 @@ def run_ours(args, cfg_name, cfg):
                        "value": alt.stats()["samples_forward"] / (alt_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
                        "image_error_vs_f32_storage": {"max": float(diff.max()), "mean": float(diff.mean())}}
         alt.release()
+
+    # the ordered march beside the sort-last form (per-fragment termination)
+    # of the same frame on the same device: time, samples, image difference
+    order_cmp = None
+    if ordered:
+        ord_img = dev.frames()[0].clone()
+        ord_samples = dev.stats()["samples_forward"]
+        # the sort-last form in its own best launch form
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
+                      tile=(args.tile_w, args.tile_h))
+        sl_tune = None
+        if not args.no_autotune:
+            sl_tune = dev.autotune(frames=3)
+            fl = sl_tune["flags"]
+            dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
+                          tile=tuple(sl_tune["tile"]), gather=dpv.gather_of(fl),
+                          persistent=bool(fl & dpv.FRAME_PERSISTENT))
+        for _ in range(max(3, args.warmup)):
+            dev.render()
+        torch.cuda.synchronize()
+        o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        for _ in range(args.steps):
+            dev.render()
+        o1.record(stream)
+        torch.cuda.synchronize()
+        sl_ms = o0.elapsed_time(o1) / args.steps
+        sl_samples = dev.stats()["samples_forward"]
+        d = (dev.frames()[0] - ord_img).abs()
+        order_cmp = {"sort_last_forward_ms_per_step": sl_ms, "sort_last_samples_per_step": sl_samples,
+                     "sort_last_autotune": sl_tune,
+                     "ordered_samples_per_step": ord_samples, "speedup_vs_sort_last": sl_ms / (fwd_ms / args.steps),
+                     "image_difference_vs_sort_last": {"max": float(d.max()), "mean": float(d.mean())}}
 
     # end to end through the public API: TF from pinned host memory in, the
     # composited frames to pinned host memory out, every step
@@ -477,7 +520,8 @@ def run_ours(args, cfg_name, cfg):
         "data": "synthetic (seeded field, TF, cameras; no paper dataset)",
         "config": {"workload": cfg_name, "dims": list(cfg["dims"]), "bricks": part.num_ranks,
                    "cameras_per_gpu": ncam, "image": [W, H], "storage": cfg["storage"], "ert": cfg["ert"],
-                   "step_voxels": 0.5, "sigma_max": 8.0,
+                   "step_voxels": 0.5, "sigma_max": cfg.get("sigma_max", 8.0), "mode": (
+                       "iso-surface" if iso is not None else "ordered" if ordered else "sort-last"),
                    "tile": list(tune["tile"]) if tune else [args.tile_w or 16, args.tile_h or 16],
                    "l2": "inputs larger than L2 (%d MiB volume), no flush" % (
                        np.prod(cfg["dims"]) * bpv // 2 ** 20),
@@ -493,10 +537,14 @@ def run_ours(args, cfg_name, cfg):
                         "each step also runs the backward, reported under 'backward' and in ms_per_step"
                         if grad is not None else
                         "samples evaluated up to each brick's first hit / forward time (cull + iso march + depth "
-                        "composite); iso-surface frames have no adjoint, a step is the forward frame"),
+                        "composite); iso-surface frames have no adjoint, a step is the forward frame"
+                        if iso is not None else
+                        "samples evaluated up to the global termination / forward time (cull + ordered march); "
+                        "ordered frames have no adjoint, a step is the forward frame"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": TRAFFIC.get((cfg_name, "march")),
-                     "kernel": ("k_iso_fwd<%s>" if iso is not None else "k_march_fwd<%s>") % cfg["storage"],
+                     "kernel": ("k_iso_fwd<%s>" if iso is not None else "k_march_ordered<%s>" if ordered
+                                else "k_march_fwd<%s>") % cfg["storage"],
                      "model": "stencil bytes: 8 corners x %d B per evaluated sample" % bpv,
                      "peak_kind": peak_kind},
         "roofline_backward": ({"bound": "hbm", "achieved": bwd_achieved, "peak": peak, "unit": "GB/s",
@@ -517,6 +565,8 @@ def run_ours(args, cfg_name, cfg):
         line["batched"] = batch
     if storage_cmp:
         line["storage_comparison"] = storage_cmp
+    if order_cmp:
+        line["sort_last_comparison"] = order_cmp
     if rank == 0 and not args.no_cpu_baseline:
         try:
             cb = cpu_baseline(cfg_name, cfg, field_host, part, tf_np, cams, budget_s=args.ref_budget)

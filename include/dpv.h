@@ -126,6 +126,15 @@ typedef struct {
                                       while profiling is on) */
 #define DPV_FRAME_CELL 32          /* the cell layout, whether or not it fits */
 #define DPV_FRAME_QUAD 64          /* the quad layout */
+#define DPV_FRAME_ORDERED 256      /* visibility-ordered march with global early termination:
+                                      each ray marches the bricks it crosses front to back
+                                      (entry sample order), carrying the accumulated colour
+                                      and transmittance from brick to brick, and stops once
+                                      the accumulated opacity passes ert_threshold; bricks
+                                      behind are not marched.  Writes the frame directly (no
+                                      fragments, no sort-last composite).  No backward
+                                      (DPV_ERR_UNSUPPORTED); not with DPV_FRAME_STAGED or
+                                      DPV_FRAME_ISO. */
 #define DPV_FRAME_ISO 128          /* iso-surface fragments instead of volume rendering
                                       (the paper's z-composited opaque surfaces, §7):
                                       each brick reports the first sample pair (j-1, j)

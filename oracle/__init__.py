@@ -77,6 +77,7 @@ def lib():
         _lib.orc_render_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P, P, P, P, P]
         _lib.orc_grad_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, C.c_double]
         _lib.orc_composite.argtypes = [C.c_int, C.c_int, P, P, P, P]
+        _lib.orc_render_ordered.argtypes = [P, P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P]
         _lib.orc_render_iso.argtypes = [P, P, C.c_int, P, P, P, P, C.c_double, C.c_double, C.c_int, P, P, P, P, P,
                                         P, P]
         _lib.orc_kd_order.argtypes = [C.c_int, P, P, P, P, P, P]
@@ -273,6 +274,36 @@ def render_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, 
                             _p(res["rgba"]), _p(res["depth"]), _p(res["order"]), _p(res["frag_rgba"]),
                             _p(res["frag_key"]), _p(res["frag_nsamp"]), _p(res["frag_margin"]),
                             _p(res["nsamples"]), _p(res["flags"]))
+    return res
+
+
+def render_ordered(dims, tf: np.ndarray, cam, frame: Frame, field=None, bricks=None, pix=None, vmin=0.0, vmax=1.0,
+                   origin=(0.0, 0.0, 0.0), spacing=None):
+    """FP64 visibility-ordered march with global early termination
+    (frame.ert on the accumulated opacity; 0 = off): with `field` the
+    unpartitioned plain definition, with `bricks` each sample evaluated by
+    its owning brick, bricks in ray order carrying the transmittance.
+    Returns rgba, depth, depth_alpha (opacity the depth's segment adds),
+    nsamples (evaluated) and flags."""
+    if (field is None) == (bricks is None):
+        raise ValueError("give exactly one of field and bricks")
+    g = _grid(dims, origin, spacing)
+    t, tab = _tf(tf, vmin, vmax)
+    cam_c = _camera(cam)
+    fr = frame.c()
+    n, pp, keep = _pix(pix, frame)
+    res = {"rgba": np.zeros((n, 4)), "depth": np.zeros(n), "depth_alpha": np.zeros(n),
+           "nsamples": np.zeros(n, np.int64), "flags": np.zeros(n, np.uint8)}
+    if bricks is not None:
+        barr, keep_b = _bricks_c(bricks)
+        f_ptr, K = None, len(bricks)
+    else:
+        f = np.ascontiguousarray(field, dtype=np.float32)
+        assert f.shape == (dims[2], dims[1], dims[0])
+        barr, f_ptr, K = None, _p(f), 1
+    lib().orc_render_ordered(C.byref(g), f_ptr, K, barr, C.byref(t), C.byref(cam_c), C.byref(fr), n, pp,
+                             _p(res["rgba"]), _p(res["depth"]), _p(res["depth_alpha"]), _p(res["nsamples"]),
+                             _p(res["flags"]))
     return res
 
 

@@ -659,6 +659,89 @@ void orc_composite(int npix, int K, const double* frag_rgba, const int32_t* frag
 }
 
 /* ------------------------------------------------------------------------ */
+/* visibility-ordered march with global early termination                    */
+/* ------------------------------------------------------------------------ */
+
+/* Reading: the bricks a ray crosses are marched in its front-to-back order,
+ * each starting from the transmittance T the bricks in front left, so that
+ * C += T alpha c, T *= (1 - alpha) runs over the ray's samples as one march;
+ * the march stops after the first sample with 1 - T > ert (global early
+ * termination: a brick behind an opaque front is not marched at all).
+ * Depth: t of the first sample of the first brick whose segment adds
+ * opacity.  With field != NULL the unpartitioned plain definition (the whole
+ * float32 field owns every sample); with bricks the owner of each sample
+ * evaluates it.  Per listed pixel: rgba, depth, the opacity the depth's
+ * segment adds (relative to what reaches it), samples evaluated, flags
+ * (EXIT / OWNER / ERT ambiguity as for the sort-last render, the ERT margin
+ * taken on the global opacity). */
+void orc_render_ordered(const orc_grid* g, const float* field, int K, const orc_brick* bricks, const orc_tf* tf,
+                        const orc_camera* cam, const orc_frame* fr, int npix, const int32_t* pix, double* rgba,
+                        double* depth, double* depth_alpha, int64_t* nsamples, uint8_t* flags) {
+    int all_lo[3] = {0, 0, 0};
+    int ert_on = fr->ert > 0.0 && fr->ert < 1.0;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < npix; ++k) {
+        int p = pix ? pix[k] : k;
+        orc_rayinfo ri;
+        ray_samples(g, cam, fr, p % fr->width, p / fr->width, &ri);
+        int fl = ri.flags;
+        double C[3] = {0, 0, 0}, T = 1.0, dep = INFINITY, dep_a = 0.0;
+        int64_t ns = 0;
+        int owner = -1, seg_owner = -1;
+        double seg_T0 = 1.0;
+        int64_t seg_first = 0;
+        for (int64_t j = 0; j < ri.n; ++j) {
+            double q[3], tj;
+            sample_point(g, &ri, j, q, &tj);
+            double s;
+            if (bricks) {
+                owner = find_owner(g, K, bricks, q, owner);
+                if (owner < 0) continue;
+                if (near_internal_face(g, &bricks[owner], &ri, tj, fr->amb_samples)) fl |= ORC_FLAG_OWNER_AMBIG;
+                int bl[3], bn[3];
+                orc_stored_box(g->dims, bricks[owner].owned_lo, bricks[owner].owned_hi, bl, bn);
+                s = trilinear(bricks[owner].data, bricks[owner].dtype, bricks[owner].scale, bl, bn, q, NULL, NULL);
+            } else {
+                owner = 0;
+                s = trilinear(field, ORC_F32, 1.0, all_lo, g->dims, q, NULL, NULL);
+            }
+            if (owner != seg_owner) {          /* a new brick segment begins */
+                if (seg_owner >= 0 && isinf(dep) && T < seg_T0) {
+                    dep = ri.t_enter + (seg_first + 0.5) * ri.dt;
+                    dep_a = 1.0 - T / seg_T0;
+                }
+                seg_owner = owner;
+                seg_T0 = T;
+                seg_first = j;
+            }
+            double c[3], al;
+            classify(tf, fr, ri.dt, s, c, &al);
+            double A_before = 1.0 - T;
+            for (int a = 0; a < 3; ++a) C[a] += T * al * c[a];
+            T *= 1.0 - al;
+            ++ns;
+            if (ert_on && 1.0 - T > fr->ert) {
+                double m1 = (1.0 - T) - fr->ert, m0 = fr->ert - A_before;
+                if ((m1 < m0 ? m1 : m0) < fr->amb_alpha) fl |= ORC_FLAG_ERT_AMBIG;
+                break;
+            }
+        }
+        if (seg_owner >= 0 && isinf(dep) && T < seg_T0) {
+            dep = ri.t_enter + (seg_first + 0.5) * ri.dt;
+            dep_a = 1.0 - T / seg_T0;
+        }
+        if (depth_alpha) depth_alpha[k] = dep_a;
+        rgba[4 * k + 0] = C[0];
+        rgba[4 * k + 1] = C[1];
+        rgba[4 * k + 2] = C[2];
+        rgba[4 * k + 3] = 1.0 - T;
+        if (depth) depth[k] = dep;
+        if (nsamples) nsamples[k] = ns;
+        if (flags) flags[k] = (uint8_t)fl;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* iso-surface fragments (first hit per brick, depth composite)              */
 /* ------------------------------------------------------------------------ */
 

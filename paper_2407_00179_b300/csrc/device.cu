@@ -333,6 +333,7 @@ dpv_status prepare(dpv_device dev) {
     // floats of shared memory per staged slab box; DPV_BOX_CAP overrides it
     // (tuning, and tests that force the unstaged fallback of large slabs)
     P.iso_on = (F.flags & DPV_FRAME_ISO) ? 1 : 0;
+    P.ordered_on = (F.flags & DPV_FRAME_ORDERED) ? 1 : 0;
     P.iso = F.iso_value;
     P.box_cap = 6144;
     if (const char* env = getenv("DPV_BOX_CAP")) {
@@ -564,8 +565,9 @@ dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
     const FrameParams& P = dev->P;
     float3 og = make_float3(dev->origin[0], dev->origin[1], dev->origin[2]);
     const bool iso = P.iso_on != 0;
+    const bool ordered = P.ordered_on != 0;
     const bool persistent = (dev->frame.flags & DPV_FRAME_PERSISTENT) && !(dev->frame.flags & DPV_FRAME_STAGED) &&
-                            !iso;
+                            !iso && !ordered;
     CK(cudaMemsetAsync(dev->d_counters, 0, sizeof(Counters), st), "reset counters");
     cudaEvent_t t0 = timed ? stage_start(dev) : nullptr;
     CK(launch_cull(P, dev->d_cam_in, og, dev->spacing, dev->d_cams, dev->d_camd, dev->d_rays, dev->d_bricks,
@@ -579,6 +581,16 @@ dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
            "schedule");
     if (timed) stage_stop(dev, DPV_STAGE_CULL, t0);
     t0 = timed ? stage_start(dev) : nullptr;
+    if (ordered) {
+        // march and composite in one launch: the frame is written directly
+        CK(launch_march_ordered(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
+                                dev->d_tile_first, dev->d_tile_count, dev->d_items, dev->d_tf, dev->d_out_rgba,
+                                dev->d_out_depth, P.order_stride ? dev->d_order : nullptr, dev->d_counters, st),
+           "ordered march");
+        if (timed) stage_stop(dev, DPV_STAGE_MARCH, t0);
+        dev->launches += 6 + 1;
+        return DPV_OK;
+    }
     if (iso)
         CK(launch_iso_fwd(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                           dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters,
@@ -850,6 +862,8 @@ dpv_status dpvSetFrame(dpv_device dev, const dpv_frame_desc* f) {
         return fail(DPV_ERR_INVALID_ARG, "tile %dx%d: width a multiple of 8, height of 4, at most 256 pixels", tw, th);
     if ((f->flags & DPV_FRAME_ISO) && (f->flags & DPV_FRAME_STAGED))
         return fail(DPV_ERR_UNSUPPORTED, "iso-surface frames have no staged form");
+    if ((f->flags & DPV_FRAME_ORDERED) && (f->flags & (DPV_FRAME_STAGED | DPV_FRAME_ISO)))
+        return fail(DPV_ERR_UNSUPPORTED, "the ordered march has no staged or iso-surface form");
     if ((f->flags & DPV_FRAME_ISO) && !isfinite(f->iso_value))
         return fail(DPV_ERR_INVALID_ARG, "iso_value must be finite");
     dev->frame = *f;
@@ -997,6 +1011,7 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
     if (s) return s;
     if (!dev->rendered || dev->dirty) return fail(DPV_ERR_STATE, "backward needs the fragments of a render");
     if (dev->P.iso_on) return fail(DPV_ERR_UNSUPPORTED, "the adjoint is of the volume-rendering mode");
+    if (dev->P.ordered_on) return fail(DPV_ERR_UNSUPPORTED, "the adjoint is of the sort-last march");
     if (!dL_drgba || !dL_dtf) return fail(DPV_ERR_INVALID_ARG, "gradient pointers NULL");
     DeviceGuard g(dev->cuda_device);
     const FrameParams& P = dev->P;

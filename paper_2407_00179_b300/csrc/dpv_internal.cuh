@@ -162,6 +162,7 @@ struct FrameParams {
     int order_stride;  // bytes per pixel of the order image (0 = off)
     int items_cap;     // work items the list and fragment pool hold
     int box_cap;       // floats of shared memory per slab box (staged march)
+    int ordered_on;    // visibility-ordered march, global early termination
     int iso_on;        // iso-surface fragments instead of volume rendering
     float iso;         // their level
     const float4* rays;// per camera and pixel RAY_VECS float4; see k_rays

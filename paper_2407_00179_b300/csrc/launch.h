@@ -51,6 +51,13 @@ cudaError_t launch_march_fwd(int dtype, int gather, const FrameParams& P, const 
                              const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
                              cudaStream_t st, const Schedule* sch = nullptr);
 
+// Visibility-ordered march with global early termination (DPV_FRAME_ORDERED):
+// one launch over (camera, tile), writing the frame.
+cudaError_t launch_march_ordered(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
+                                 const BrickDev* bricks, const float* scales, const int* tile_first,
+                                 const int* tile_count, const Item* items, const float4* tf, float4* out_rgba,
+                                 float* out_depth, unsigned char* order, Counters* counters, cudaStream_t st);
+
 // Iso-surface fragments (DPV_FRAME_ISO) and their depth composite.
 cudaError_t launch_iso_fwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                            const BrickDev* bricks, const float* scales, const Item* items, int n_items,

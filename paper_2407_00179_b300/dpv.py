@@ -28,6 +28,7 @@ FRAME_GRAPH = 16
 FRAME_CELL = 32
 FRAME_QUAD = 64
 FRAME_ISO = 128
+FRAME_ORDERED = 256
 GATHER_FLAGS = {"auto": 0, "cell": FRAME_CELL, "quad": FRAME_QUAD, "linear": FRAME_LINEAR}
 
 
@@ -272,21 +273,23 @@ class Device:
 
     def set_frame(self, width: int, height: int, step_voxels: float = 0.5, sigma_max: float = 8.0, ert: float = 0.0,
                   tile=(0, 0), order: bool = False, staged: bool = False, gather: str = "auto",
-                  persistent: bool = False, graph: bool = False, iso: Optional[float] = None):
+                  persistent: bool = False, graph: bool = False, iso: Optional[float] = None,
+                  ordered: bool = False):
         """gather: "auto" (cell layout where it fits in half of the free
         device memory, else quad), "cell", "quad" or "linear".  iso: render
         iso-surface fragments at that level instead of volume rendering
-        (DPV_FRAME_ISO)."""
+        (DPV_FRAME_ISO).  ordered: visibility-ordered march with global early
+        termination (DPV_FRAME_ORDERED)."""
         if gather not in GATHER_FLAGS:
             raise ValueError("gather must be one of %s" % sorted(GATHER_FLAGS))
         flags = (FRAME_ORDER if order else 0) | (FRAME_STAGED if staged else 0) | GATHER_FLAGS[gather] | (
             FRAME_PERSISTENT if persistent else 0) | (FRAME_GRAPH if graph else 0) | (
-            FRAME_ISO if iso is not None else 0)
+            FRAME_ISO if iso is not None else 0) | (FRAME_ORDERED if ordered else 0)
         f = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
                       int(tile[1]), flags, float(iso) if iso is not None else 0.0)
         _check(load().dpvSetFrame(self._h, C.byref(f)))
         self._frame_args = (step_voxels, sigma_max, ert)
-        self._frame_kw = {"order": order, "staged": staged, "graph": graph, "iso": iso}
+        self._frame_kw = {"order": order, "staged": staged, "graph": graph, "iso": iso, "ordered": ordered}
         self.width, self.height = int(width), int(height)
 
     # -- rendering ---------------------------------------------------------
