@@ -57,6 +57,12 @@ CONFIGS = {
     # iso-surface fragments of the mid field (forward only: no adjoint)
     "mid_iso": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.0,
                     storage="f32", cams="direction", iso=0.5),
+    # the mid field under a TF that hides the values below 0.4 (opacity 0),
+    # marched with empty-space skipping (macro-cells of 8^3 cells whose value
+    # range reaches only transparent TF entries are not sampled), beside the
+    # same frame without skipping
+    "mid_ess": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
+                    storage="f32", cams="direction", skip=True, tf_cut=0.4),
     "mid_f16": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
                     storage="f16", cams="direction"),
     # 64^3 f32, 8 blobs, 2x1x1 bricks, 256x256, no ERT
@@ -242,7 +248,7 @@ def run_reference(args, cfg_name, cfg):
     dev = "cpu"
     f = _field(cfg, "cuda" if torch.cuda.is_available() else "cpu").cpu().numpy()
     part = _partition(cfg)
-    tf = inputs.make_tf(1234)
+    tf = inputs.make_tf(1234, transparent_below=cfg.get("tf_cut", 0.0))
     cams = _cameras(cfg)
     steps = []
     base = None
@@ -282,7 +288,7 @@ def run_ours(args, cfg_name, cfg):
     device = torch.device("cuda", local)
     field = _field(cfg, device)
     part = _partition(cfg)
-    tf_np = inputs.make_tf(1234)
+    tf_np = inputs.make_tf(1234, transparent_below=cfg.get("tf_cut", 0.0))
     cams = _cameras(cfg, rank)
     W, H = cfg["width"], cfg["height"]
     ncam = len(cams)
@@ -301,14 +307,16 @@ def run_ours(args, cfg_name, cfg):
     dev.set_cameras(cams)
     iso = cfg.get("iso")
     ordered = bool(cfg.get("ordered"))
+    skip = bool(cfg.get("skip"))
     dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
-                  tile=(args.tile_w, args.tile_h), iso=iso, ordered=ordered)
+                  tile=(args.tile_w, args.tile_h), iso=iso, ordered=ordered, skip=skip)
     tune = None
     if not args.no_autotune:
         tune = dev.autotune(frames=3, cache=args.autotune_cache, key=cfg_name)
         fl = tune["flags"]
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"], tile=tuple(tune["tile"]),
-                      gather=dpv.gather_of(fl), persistent=bool(fl & dpv.FRAME_PERSISTENT), iso=iso, ordered=ordered)
+                      gather=dpv.gather_of(fl), persistent=bool(fl & dpv.FRAME_PERSISTENT), iso=iso, ordered=ordered,
+                      skip=skip)
     grad = None
     if iso is None and not ordered:
         # fixed upstream gradient: d/dI of mean (I - I*)^2 with I* from a perturbed TF
@@ -482,6 +490,37 @@ def run_ours(args, cfg_name, cfg):
                      "ordered_samples_per_step": ord_samples, "speedup_vs_sort_last": sl_ms / (fwd_ms / args.steps),
                      "image_difference_vs_sort_last": {"max": float(d.max()), "mean": float(d.mean())}}
 
+    # empty-space skipping beside the same frame without it, in the same
+    # launch form: time, samples evaluated, and the frames (bit-identical)
+    skip_cmp = None
+    if skip:
+        skip_img = dev.frames()[0].clone()
+        skip_samples = dev.stats()["samples_forward"]
+        fl = tune["flags"] if tune else 0
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
+                      tile=tuple(tune["tile"]) if tune else (args.tile_w, args.tile_h), gather=dpv.gather_of(fl),
+                      persistent=bool(fl & dpv.FRAME_PERSISTENT))
+        for _ in range(max(3, args.warmup)):
+            dev.render()
+        torch.cuda.synchronize()
+        dev.reset_stats()
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(args.steps):
+            dev.render()
+        k1.record(stream)
+        torch.cuda.synchronize()
+        full_ms = k0.elapsed_time(k1) / args.steps
+        full_samples = dev.stats()["samples_forward"]
+        skip_cmp = {"no_skip_forward_ms_per_step": full_ms, "no_skip_samples_per_step": full_samples,
+                    "skip_samples_per_step": skip_samples, "evaluated_fraction": skip_samples / max(1, full_samples),
+                    "speedup_vs_no_skip": full_ms / (fwd_ms / args.steps),
+                    "ray_samples_per_s": full_samples * args.steps / (fwd_ms * 1e-3) / 1e9,
+                    "frames_bit_identical": bool(torch.equal(dev.frames()[0], skip_img))}
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
+                      tile=tuple(tune["tile"]) if tune else (args.tile_w, args.tile_h), gather=dpv.gather_of(fl),
+                      persistent=bool(fl & dpv.FRAME_PERSISTENT), skip=True)
+
     # end to end through the public API: TF from pinned host memory in, the
     # composited frames to pinned host memory out, every step
     tf_host = torch.from_numpy(tf_np).pin_memory()
@@ -521,7 +560,8 @@ def run_ours(args, cfg_name, cfg):
         "config": {"workload": cfg_name, "dims": list(cfg["dims"]), "bricks": part.num_ranks,
                    "cameras_per_gpu": ncam, "image": [W, H], "storage": cfg["storage"], "ert": cfg["ert"],
                    "step_voxels": 0.5, "sigma_max": cfg.get("sigma_max", 8.0), "mode": (
-                       "iso-surface" if iso is not None else "ordered" if ordered else "sort-last"),
+                       "iso-surface" if iso is not None else "ordered" if ordered else "sort-last") + (
+                       ", empty-space skipping" if skip else ""),
                    "tile": list(tune["tile"]) if tune else [args.tile_w or 16, args.tile_h or 16],
                    "l2": "inputs larger than L2 (%d MiB volume), no flush" % (
                        np.prod(cfg["dims"]) * bpv // 2 ** 20),
@@ -567,6 +607,9 @@ def run_ours(args, cfg_name, cfg):
         line["storage_comparison"] = storage_cmp
     if order_cmp:
         line["sort_last_comparison"] = order_cmp
+    if skip_cmp:
+        line["skip_comparison"] = skip_cmp
+        line["config"]["tf_transparent_below"] = cfg["tf_cut"]
     if rank == 0 and not args.no_cpu_baseline:
         try:
             cb = cpu_baseline(cfg_name, cfg, field_host, part, tf_np, cams, budget_s=args.ref_budget)

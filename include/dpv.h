@@ -135,6 +135,14 @@ typedef struct {
                                       fragments, no sort-last composite).  No backward
                                       (DPV_ERR_UNSUPPORTED); not with DPV_FRAME_STAGED or
                                       DPV_FRAME_ISO. */
+#define DPV_FRAME_SKIP 512         /* empty-space skipping in the forward march (sort-last
+                                      or ordered): samples inside a macro-cell (8^3 cells)
+                                      whose value range reaches only TF entries of opacity
+                                      0 are not evaluated (their alpha is exactly 0, so the
+                                      frame is bit-identical); the macro-cell ranges are
+                                      built once per committed brick, their transparency
+                                      per render.  Sample counts then count the evaluated
+                                      samples.  The backward replays every sample. */
 #define DPV_FRAME_ISO 128          /* iso-surface fragments instead of volume rendering
                                       (the paper's z-composited opaque surfaces, §7):
                                       each brick reports the first sample pair (j-1, j)
@@ -341,6 +349,9 @@ typedef struct {
  * on that device.  Every call reuses the
  * same array, so calls that overlap on the GPU -- on different streams or
  * from different host threads -- race and must be serialised by the caller.
+ * It marches the linear gather layout and ignores the layout, staged,
+ * persistent and graph bits of frame->flags; DPV_FRAME_ISO, DPV_FRAME_ORDERED
+ * and DPV_FRAME_SKIP return DPV_ERR_UNSUPPORTED (they need device state).
  * Asynchronous: returns once the work is queued. */
 dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* scene, const dpv_camera* camera, const dpv_frame_desc* frame,
                             float* rgba, float* depth, void* cuda_stream);

@@ -47,6 +47,9 @@ struct HostBrick {
     size_t gather_bytes = 0;
     int gather_kind = -1;       // GATHER_QUAD or GATHER_CELL
     bool gather_valid = false;
+    float2* mm = nullptr;       // macro-cell value ranges (empty-space skipping)
+    size_t mm_cells = 0;
+    bool mm_valid = false;
 };
 
 const int kElemSize[4] = {4, 2, 2, 1};
@@ -114,6 +117,10 @@ struct dpv_device_t {
     float4* d_gface = nullptr;
     size_t gface_cap = 0;               // slots allocated
     size_t gface_slots = 0;             // slots the current bricks need
+    unsigned char* d_empty = nullptr;   // macro-cell transparency of every brick
+    size_t empty_cap = 0;
+    int* d_tfz = nullptr;               // TF opaque-entry prefix counts (MAX_TF)
+    int max_macro = 0;                  // most macro-cells of a brick
     int* d_nb_first = nullptr;          // nranks + 1
     int* d_nb = nullptr;                // nranks * nranks
     long long max_rows = 0;             // most owned (y, z) node rows of a brick
@@ -334,6 +341,7 @@ dpv_status prepare(dpv_device dev) {
     // (tuning, and tests that force the unstaged fallback of large slabs)
     P.iso_on = (F.flags & DPV_FRAME_ISO) ? 1 : 0;
     P.ordered_on = (F.flags & DPV_FRAME_ORDERED) ? 1 : 0;
+    P.skip_on = (F.flags & DPV_FRAME_SKIP) ? 1 : 0;
     P.iso = F.iso_value;
     P.box_cap = 6144;
     if (const char* env = getenv("DPV_BOX_CAP")) {
@@ -440,6 +448,57 @@ dpv_status prepare(dpv_device dev) {
         }
     }
     dev->gather = kind;
+    // empty-space skipping: per-brick macro-cell value ranges (once per
+    // committed brick) and one transparency byte per macro-cell
+    for (int k = 0; k < dev->nranks; ++k) {
+        table[k].mm = nullptr;
+        table[k].empty = nullptr;
+        table[k].mx = table[k].mxy = table[k].mn = 0;
+    }
+    dev->max_macro = 0;
+    if (P.skip_on) {
+        size_t total = 0;
+        for (int k = 0; k < dev->nranks; ++k) total += macro_cells(dev->bricks[k].s_n);
+        if (total > dev->empty_cap) {
+            dev_free(dev->d_empty);
+            dev->d_empty = nullptr;
+            dev->empty_cap = 0;
+            dpv_status s2 = dev_alloc(dev, (void**)&dev->d_empty, total, "macro-cell transparency");
+            if (s2) return s2;
+            dev->empty_cap = total;
+        }
+        if (!dev->d_tfz) {
+            dpv_status s2 = dev_alloc(dev, (void**)&dev->d_tfz, sizeof(int) * MAX_TF, "TF prefix");
+            if (s2) return s2;
+        }
+        size_t off = 0;
+        for (int k = 0; k < dev->nranks; ++k) {
+            HostBrick& h = dev->bricks[k];
+            const size_t mc = macro_cells(h.s_n);
+            if (h.mm && h.mm_cells != mc) {
+                dev_free(h.mm);
+                h.mm = nullptr;
+                h.mm_valid = false;
+            }
+            if (!h.mm) {
+                dpv_status s2 = dev_alloc(dev, (void**)&h.mm, sizeof(float2) * mc, "macro-cell ranges");
+                if (s2) return s2;
+                h.mm_cells = mc;
+                h.mm_valid = false;
+            }
+            if (!h.mm_valid) {
+                CK(launch_build_minmax(h.dtype, h.data, h.s_n, h.mm, dev->stream), "macro-cell ranges");
+                h.mm_valid = true;
+            }
+            table[k].mm = h.mm;
+            table[k].empty = dev->d_empty + off;
+            table[k].mx = ((h.s_n[0] - 2) >> MACRO_SHIFT) + 1;
+            table[k].mxy = table[k].mx * (((h.s_n[1] - 2) >> MACRO_SHIFT) + 1);
+            table[k].mn = (int)mc;
+            dev->max_macro = std::max(dev->max_macro, (int)mc);
+            off += mc;
+        }
+    }
     if (!dev->d_bricks) {
         dpv_status s = dev_alloc(dev, (void**)&dev->d_bricks, sizeof(BrickDev) * MAX_RANKS, "brick table");
         if (s) return s;
@@ -579,6 +638,10 @@ dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
         CK(launch_schedule(P, dev->d_items, dev->n_items, 1, dev->d_hist, dev->d_offsets, dev->d_cursor,
                            dev->d_tmp64, dev->d_sched, st),
            "schedule");
+    if (P.skip_on)
+        CK(launch_classify_empty(dev->bricks[0].dtype, P, dev->d_bricks, dev->nranks, dev->d_scales, dev->max_macro,
+                                 dev->d_tf, dev->d_tfz, st),
+           "macro-cell transparency");
     if (timed) stage_stop(dev, DPV_STAGE_CULL, t0);
     t0 = timed ? stage_start(dev) : nullptr;
     if (ordered) {
@@ -705,6 +768,7 @@ dpv_status dpvSetVolumeGeometry(dpv_device dev, const int dims[3], const float o
     for (auto& b : dev->bricks) {
         dev_free(b.data);
         dev_free(b.gather);
+        dev_free(b.mm);
         b = HostBrick();
     }
     for (int a = 0; a < 3; ++a) {
@@ -804,6 +868,9 @@ dpv_status dpvCommitBrick(dpv_device dev, int rank, const dpv_brick_desc* d) {
     nb.gather_bytes = hb.gather_bytes;
     nb.gather_kind = hb.gather_kind;
     nb.gather_valid = false;
+    nb.mm = hb.mm;                      // value ranges too
+    nb.mm_cells = hb.mm_cells;
+    nb.mm_valid = false;
     hb = nb;
     dev->dirty = true;
     return DPV_OK;
@@ -864,6 +931,8 @@ dpv_status dpvSetFrame(dpv_device dev, const dpv_frame_desc* f) {
         return fail(DPV_ERR_UNSUPPORTED, "iso-surface frames have no staged form");
     if ((f->flags & DPV_FRAME_ORDERED) && (f->flags & (DPV_FRAME_STAGED | DPV_FRAME_ISO)))
         return fail(DPV_ERR_UNSUPPORTED, "the ordered march has no staged or iso-surface form");
+    if ((f->flags & DPV_FRAME_SKIP) && (f->flags & (DPV_FRAME_STAGED | DPV_FRAME_ISO)))
+        return fail(DPV_ERR_UNSUPPORTED, "empty-space skipping has no staged or iso-surface form");
     if ((f->flags & DPV_FRAME_ISO) && !isfinite(f->iso_value))
         return fail(DPV_ERR_INVALID_ARG, "iso_value must be finite");
     dev->frame = *f;
@@ -1208,7 +1277,10 @@ dpv_status dpvRelease(dpv_device dev) {
         for (auto& b : dev->bricks) {
             dev_free(b.data);
             dev_free(b.gather);
+            dev_free(b.mm);
         }
+        dev_free(dev->d_empty);
+        dev_free(dev->d_tfz);
         free_schedule(dev);
         free_frags(dev);
         dev_free(dev->d_gface);

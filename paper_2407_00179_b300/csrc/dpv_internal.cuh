@@ -124,7 +124,15 @@ struct BrickDev {
     int qx, qxy;       // strides of both layouts: s_n[0]-1, (s_n[0]-1)(s_n[1]-1)
     int o_lo[3], o_hi[3];  // owned global nodes [o_lo, o_hi)
     long long gface_off;   // first face of this brick in the face adjoint buffer
+    const float2* mm;      // per macro-cell (MACRO^3 cells) min and max of the
+                           // decoded node values (empty-space skipping)
+    unsigned char* empty;  // per macro-cell: 1 where every sample inside has
+                           // TF opacity exactly 0 (rebuilt per render)
+    int mx, mxy, mn;       // macro-cell strides and count
 };
+
+// Empty-space skipping: macro-cells of 2^MACRO_SHIFT cells per axis.
+constexpr int MACRO_SHIFT = 3;
 
 // A work item: one brick seen through one screen tile of one camera.
 struct Item {
@@ -163,6 +171,7 @@ struct FrameParams {
     int items_cap;     // work items the list and fragment pool hold
     int box_cap;       // floats of shared memory per slab box (staged march)
     int ordered_on;    // visibility-ordered march, global early termination
+    int skip_on;       // empty-space skipping in the forward march
     int iso_on;        // iso-surface fragments instead of volume rendering
     float iso;         // their level
     const float4* rays;// per camera and pixel RAY_VECS float4; see k_rays

@@ -10,6 +10,8 @@
 // fragments straight from HBM.
 #include <stdlib.h>
 
+#include <algorithm>
+
 #include "dpv_internal.cuh"
 #include "launch.h"
 
@@ -393,7 +395,7 @@ cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 orig
 // One work item: every thread marches its pixel's ray through the item's
 // brick and writes the fragment to slot `item * tile_pixels + thread`.
 // Returns the samples this thread evaluated.
-template <typename T, int GL>
+template <typename T, int GL, bool SKIP>
 __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, const CamBasis* cams,
                                                          const BrickDev* bricks, const float* scales, const Item& it,
                                                          long long item, const float4* s_tf, float4* frag_rgba,
@@ -416,10 +418,22 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
             CornerCache<T, GL> cc;
             SampleWalker wk;
             wk.init(b);
+            int mlast = -1;
+            bool mempty = false;
             for (; k < n; ++k) {
                 int ix, iy, iz;
                 float fx, fy, fz;
                 wk.at(m, k, ix, iy, iz, fx, fy, fz);
+                if (SKIP) {
+                    // a transparent macro-cell: opacity 0 leaves C and T exactly as they are
+                    const int mi = (iz >> MACRO_SHIFT) * b.mxy + (iy >> MACRO_SHIFT) * b.mx + (ix >> MACRO_SHIFT);
+                    if (mi != mlast) {
+                        mlast = mi;
+                        mempty = b.empty[mi] != 0;
+                    }
+                    if (mempty) continue;
+                }
+                ++nsamp;
                 float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
                 TFSample c = tf_lookup(s_tf, P, s);
                 float al = sample_alpha(P, c.v.w);
@@ -428,12 +442,8 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                 C1 = fmaf(ta, c.v.y, C1);
                 C2 = fmaf(ta, c.v.z, C2);
                 Tr = Tr * (1.0f - al);
-                if (P.ert_on && 1.0f - Tr > P.ert) {
-                    ++k;
-                    break;
-                }
+                if (P.ert_on && 1.0f - Tr > P.ert) break;
             }
-            nsamp = (unsigned long long)k;
             frag_rgba[slot] = make_float4(C0, C1, C2, 1.0f - Tr);
             frag_key[slot] = m.j0;
         } else {
@@ -443,7 +453,7 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
     return nsamp;
 }
 
-template <typename T, int GL>
+template <typename T, int GL, bool SKIP>
 __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
                                                    const float* scales, const Item* items, const float4* tf,
                                                    float4* frag_rgba, int* frag_key, Counters* counters) {
@@ -452,7 +462,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis
     __syncthreads();
     const Item it = items[blockIdx.x];
     if (!item_ok(it, P)) return;
-    unsigned long long nsamp = march_item<T, GL>(P, cams, bricks, scales, it, blockIdx.x, s_tf, frag_rgba, frag_key);
+    unsigned long long nsamp = march_item<T, GL, SKIP>(P, cams, bricks, scales, it, blockIdx.x, s_tf, frag_rgba, frag_key);
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
@@ -460,7 +470,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis
 // Persistent form: a grid sized to the GPU pulls work items from a counter
 // in the order `sched` gives (brick-major: all cameras' tiles of one brick
 // together, so a brick is read from HBM about once per batch).
-template <typename T, int GL>
+template <typename T, int GL, bool SKIP>
 __global__ void __launch_bounds__(256) k_march_fwd_persistent(FrameParams P, const CamBasis* cams,
                                                               const BrickDev* bricks, const float* scales,
                                                               const Item* items, const int* sched, int n_items,
@@ -478,37 +488,49 @@ __global__ void __launch_bounds__(256) k_march_fwd_persistent(FrameParams P, con
         if (i >= n_items) break;
         const int item = sched[i];
         const Item it = items[item];
-        if (item_ok(it, P)) nsamp += march_item<T, GL>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
+        if (item_ok(it, P)) nsamp += march_item<T, GL, SKIP>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
     }
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
 
-template <typename T, int GL>
-static void fwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
+template <typename T, int GL, bool SKIP>
+static void fwd_launch_s(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                        const Item* items, int n_items, const float4* tf, float4* frag_rgba, int* frag_key,
                        Counters* counters, const Schedule* sch, cudaStream_t st) {
     size_t smem = sizeof(float4) * P.ntf;
     if (sch) {
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_march_fwd_persistent<T, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_march_fwd_persistent<T, GL, SKIP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         int per_sm = 0, dev = 0, nsm = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_fwd_persistent<T, GL>, P.tp, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_fwd_persistent<T, GL, SKIP>, P.tp, smem);
         int grid = nsm * (per_sm > 0 ? per_sm : 1);
         if (sch->ctas_per_sm > 0 && sch->ctas_per_sm < per_sm) grid = nsm * sch->ctas_per_sm;
         if (grid > n_items) grid = n_items;
         cudaMemsetAsync(sch->work, 0, sizeof(unsigned int), st);
-        k_march_fwd_persistent<T, GL><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched, n_items,
+        k_march_fwd_persistent<T, GL, SKIP><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched, n_items,
                                                                   sch->work, tf, frag_rgba, frag_key, counters);
         return;
     }
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_march_fwd<T, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_march_fwd<T, GL><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
-                                                      counters);
+        cudaFuncSetAttribute(k_march_fwd<T, GL, SKIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_march_fwd<T, GL, SKIP><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
+                                                            counters);
+}
+
+// empty-space skipping is a template switch: the march without it carries
+// no macro-cell test
+template <typename T, int GL>
+static void fwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
+                       const Item* items, int n_items, const float4* tf, float4* frag_rgba, int* frag_key,
+                       Counters* counters, const Schedule* sch, cudaStream_t st) {
+    if (P.skip_on)
+        fwd_launch_s<T, GL, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st);
+    else
+        fwd_launch_s<T, GL, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st);
 }
 
 // ===========================================================================
@@ -590,7 +612,7 @@ cudaError_t launch_march_fwd(int dtype, int gather, const FrameParams& P, const 
 
 // The samples of one brick segment, continuing (C, Tr); true once the
 // accumulated opacity passed the early-termination threshold.
-template <typename T, int GL>
+template <typename T, int GL, bool SKIP>
 __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickDev& b, float scale,
                                               const float4* s_tf, const MarchState& m, float& C0, float& C1,
                                               float& C2, float& Tr, unsigned long long& nsamp) {
@@ -599,10 +621,20 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
     CornerCache<T, GL> cc;
     SampleWalker wk;
     wk.init(b);
+    int mlast = -1;
+    bool mempty = false;
     for (int k = 0; k < n; ++k) {
         int ix, iy, iz;
         float fx, fy, fz;
         wk.at(m, k, ix, iy, iz, fx, fy, fz);
+        if (SKIP) {
+            const int mi = (iz >> MACRO_SHIFT) * b.mxy + (iy >> MACRO_SHIFT) * b.mx + (ix >> MACRO_SHIFT);
+            if (mi != mlast) {
+                mlast = mi;
+                mempty = b.empty[mi] != 0;
+            }
+            if (mempty) continue;
+        }
         float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
         TFSample c = tf_lookup(s_tf, P, s);
         float al = sample_alpha(P, c.v.w);
@@ -637,7 +669,7 @@ __device__ __forceinline__ int next_segment(const FrameParams& P, const CamBasis
     return bs;
 }
 
-template <typename T, int GL>
+template <typename T, int GL, bool SKIP>
 __global__ void __launch_bounds__(256, 4) k_march_ordered(FrameParams P, const CamBasis* cams,
                                                           const BrickDev* bricks, const float* scales,
                                                           const int* tile_first, const int* tile_count,
@@ -678,7 +710,7 @@ __global__ void __launch_bounds__(256, 4) k_march_ordered(FrameParams P, const C
             MarchState m;
             if (!brick_samples(P, cam, c, b, px, py, m)) continue;
             const float Tb = Tr;
-            stop = march_segment<T, GL>(P, b, scales[b.scale_idx], s_tf, m, C0, C1, C2, Tr, nsamp);
+            stop = march_segment<T, GL, SKIP>(P, b, scales[b.scale_idx], s_tf, m, C0, C1, C2, Tr, nsamp);
             if (Tr < Tb && depth_key == KEY_EMPTY) depth_key = m.j0;
             if (stop && !ord) break;
         }
@@ -697,17 +729,30 @@ __global__ void __launch_bounds__(256, 4) k_march_ordered(FrameParams P, const C
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
 
+template <typename T, int GL, bool SKIP>
+static void ordered_launch_s(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
+                             const int* tile_first, const int* tile_count, const Item* items, const float4* tf,
+                             float4* out_rgba, float* out_depth, unsigned char* order, Counters* counters,
+                             cudaStream_t st) {
+    size_t smem = sizeof(float4) * P.ntf;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_march_ordered<T, GL, SKIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int nct = P.ncam * P.ntx * P.nty;
+    k_march_ordered<T, GL, SKIP><<<nct, P.tp, smem, st>>>(P, cams, bricks, scales, tile_first, tile_count, items, tf,
+                                                          out_rgba, out_depth, order, counters);
+}
+
 template <typename T, int GL>
 static void ordered_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                            const int* tile_first, const int* tile_count, const Item* items, const float4* tf,
                            float4* out_rgba, float* out_depth, unsigned char* order, Counters* counters,
                            cudaStream_t st) {
-    size_t smem = sizeof(float4) * P.ntf;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_march_ordered<T, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int nct = P.ncam * P.ntx * P.nty;
-    k_march_ordered<T, GL><<<nct, P.tp, smem, st>>>(P, cams, bricks, scales, tile_first, tile_count, items, tf,
-                                                    out_rgba, out_depth, order, counters);
+    if (P.skip_on)
+        ordered_launch_s<T, GL, true>(P, cams, bricks, scales, tile_first, tile_count, items, tf, out_rgba, out_depth,
+                                      order, counters, st);
+    else
+        ordered_launch_s<T, GL, false>(P, cams, bricks, scales, tile_first, tile_count, items, tf, out_rgba,
+                                       out_depth, order, counters, st);
 }
 
 cudaError_t launch_march_ordered(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
@@ -1544,6 +1589,113 @@ cudaError_t launch_build_cell(int dtype, const void* src, const int s_n[3], void
         case 2: k_build_cell<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)src, s_n[0], s_n[1], s_n[2], dst); break;
         default: k_build_cell<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>((const __nv_fp8_e4m3*)src, s_n[0], s_n[1], s_n[2], dst); break;
     }
+    return cudaGetLastError();
+}
+
+// ===========================================================================
+// empty-space skipping: macro-cell value ranges and their transparency
+// ===========================================================================
+//
+// A macro-cell covers 2^MACRO_SHIFT cells per axis of a brick's stored
+// region.  Its range [min, max] of decoded node values bounds every sample
+// inside (the interpolant is a convex combination, and rounding is
+// monotone; so is the product with the brick's scale and the TF coordinate
+// u).  The samples then only read TF entries i0(min) .. i0(max) + 1, and if
+// all of those have opacity 0 each sample's alpha is exactly 0: skipping it
+// leaves the colour and transmittance bit for bit as they are.
+
+size_t macro_cells(const int s_n[3]) {
+    size_t m = 1;
+    for (int a = 0; a < 3; ++a) m *= (size_t)(((s_n[a] - 2) >> MACRO_SHIFT) + 1);
+    return m;
+}
+
+template <typename T>
+__global__ void k_build_minmax(const T* data, int sx, int sy, int sz, int mx, int my, int mz, float2* mm) {
+    const long long n = (long long)mx * my * mz;
+    const long long sxy = (long long)sx * sy;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int z = (int)(i / ((long long)mx * my)), r = (int)(i - (long long)z * mx * my), y = r / mx, x = r - y * mx;
+        const int x0 = x << MACRO_SHIFT, y0 = y << MACRO_SHIFT, z0 = z << MACRO_SHIFT;
+        const int x1 = min(x0 + (1 << MACRO_SHIFT), sx - 1), y1 = min(y0 + (1 << MACRO_SHIFT), sy - 1),
+                  z1 = min(z0 + (1 << MACRO_SHIFT), sz - 1);
+        float lo = __int_as_float(0x7f800000), hi = -lo;
+        for (int zz = z0; zz <= z1; ++zz)
+            for (int yy = y0; yy <= y1; ++yy)
+                for (int xx = x0; xx <= x1; ++xx) {
+                    const float v = Storage<T>::load(data, (int)(zz * sxy + (long long)yy * sx + xx));
+                    lo = fminf(lo, v);
+                    hi = fmaxf(hi, v);
+                }
+        mm[i] = make_float2(lo, hi);
+    }
+}
+
+cudaError_t launch_build_minmax(int dtype, const void* data, const int s_n[3], float2* mm, cudaStream_t st) {
+    const int mx = ((s_n[0] - 2) >> MACRO_SHIFT) + 1, my = ((s_n[1] - 2) >> MACRO_SHIFT) + 1,
+              mz = ((s_n[2] - 2) >> MACRO_SHIFT) + 1;
+    const long long n = (long long)mx * my * mz;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+    switch (dtype) {
+        case 0: k_build_minmax<float><<<blocks, 256, 0, st>>>((const float*)data, s_n[0], s_n[1], s_n[2], mx, my, mz, mm); break;
+        case 1: k_build_minmax<__half><<<blocks, 256, 0, st>>>((const __half*)data, s_n[0], s_n[1], s_n[2], mx, my, mz, mm); break;
+        case 2: k_build_minmax<__nv_bfloat16><<<blocks, 256, 0, st>>>((const __nv_bfloat16*)data, s_n[0], s_n[1], s_n[2], mx, my, mz, mm); break;
+        default: k_build_minmax<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>((const __nv_fp8_e4m3*)data, s_n[0], s_n[1], s_n[2], mx, my, mz, mm); break;
+    }
+    return cudaGetLastError();
+}
+
+// Z[i] = number of TF entries j <= i with non-zero opacity (one block).
+__global__ void k_tf_opaque_prefix(const float4* tf, int n, int* z) {
+    __shared__ int s[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        s[threadIdx.x] = (i < n && tf[i].w != 0.0f) ? 1 : 0;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            const int v = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+            __syncthreads();
+            s[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (i < n) z[i] = carry + s[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += s[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// TF entry i0 of tf_lookup for value s (same FP32 steps).
+__device__ __forceinline__ int tf_entry(const FrameParams& P, float s) {
+    float u = (s - P.vmin) * P.tf_scale;
+    u = fminf(fmaxf(u, 0.0f), (float)(P.ntf - 1));
+    return min(__float2int_rd(u), P.ntf - 2);
+}
+
+__global__ void k_classify_empty(FrameParams P, const BrickDev* bricks, const float* scales, int unit_scale,
+                                 const int* z) {
+    const BrickDev b = bricks[blockIdx.y];
+    const float scale = scales[b.scale_idx];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.mn; i += gridDim.x * blockDim.x) {
+        const float2 r = b.mm[i];
+        // the samples' values lie in [r.x scale, r.y scale], rounded as the
+        // march rounds them (f32 storage is not scaled)
+        const float lo = unit_scale ? r.x : r.x * scale, hi = unit_scale ? r.y : r.y * scale;
+        const int e0 = tf_entry(P, lo), e1 = tf_entry(P, hi) + 1;
+        const int opaque = z[e1] - (e0 > 0 ? z[e0 - 1] : 0);
+        b.empty[i] = opaque == 0 ? 1 : 0;
+    }
+}
+
+cudaError_t launch_classify_empty(int dtype, const FrameParams& P, const BrickDev* bricks, int nbricks,
+                                  const float* scales, int max_macro, const float4* tf, int* z, cudaStream_t st) {
+    if (nbricks <= 0 || max_macro <= 0) return cudaSuccess;
+    k_tf_opaque_prefix<<<1, 1024, 0, st>>>(tf, P.ntf, z);
+    const int bx = std::min((max_macro + 255) / 256, 1024);
+    k_classify_empty<<<dim3(bx, nbricks), 256, 0, st>>>(P, bricks, scales, dtype == 0 ? 1 : 0, z);
     return cudaGetLastError();
 }
 

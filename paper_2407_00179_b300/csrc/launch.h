@@ -58,6 +58,14 @@ cudaError_t launch_march_ordered(int dtype, int gather, const FrameParams& P, co
                                  const int* tile_count, const Item* items, const float4* tf, float4* out_rgba,
                                  float* out_depth, unsigned char* order, Counters* counters, cudaStream_t st);
 
+// Empty-space skipping (DPV_FRAME_SKIP): macro-cells a brick needs, their
+// value ranges (built per committed brick), and the per-render transparency
+// from the TF (z: ntf ints of scratch).
+size_t macro_cells(const int s_n[3]);
+cudaError_t launch_build_minmax(int dtype, const void* data, const int s_n[3], float2* mm, cudaStream_t st);
+cudaError_t launch_classify_empty(int dtype, const FrameParams& P, const BrickDev* bricks, int nbricks,
+                                  const float* scales, int max_macro, const float4* tf, int* z, cudaStream_t st);
+
 // Iso-surface fragments (DPV_FRAME_ISO) and their depth composite.
 cudaError_t launch_iso_fwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                            const BrickDev* bricks, const float* scales, const Item* items, int n_items,

@@ -29,6 +29,7 @@ FRAME_CELL = 32
 FRAME_QUAD = 64
 FRAME_ISO = 128
 FRAME_ORDERED = 256
+FRAME_SKIP = 512
 GATHER_FLAGS = {"auto": 0, "cell": FRAME_CELL, "quad": FRAME_QUAD, "linear": FRAME_LINEAR}
 
 
@@ -274,22 +275,24 @@ class Device:
     def set_frame(self, width: int, height: int, step_voxels: float = 0.5, sigma_max: float = 8.0, ert: float = 0.0,
                   tile=(0, 0), order: bool = False, staged: bool = False, gather: str = "auto",
                   persistent: bool = False, graph: bool = False, iso: Optional[float] = None,
-                  ordered: bool = False):
+                  ordered: bool = False, skip: bool = False):
         """gather: "auto" (cell layout where it fits in half of the free
         device memory, else quad), "cell", "quad" or "linear".  iso: render
         iso-surface fragments at that level instead of volume rendering
         (DPV_FRAME_ISO).  ordered: visibility-ordered march with global early
-        termination (DPV_FRAME_ORDERED)."""
+        termination (DPV_FRAME_ORDERED).  skip: empty-space skipping
+        (DPV_FRAME_SKIP)."""
         if gather not in GATHER_FLAGS:
             raise ValueError("gather must be one of %s" % sorted(GATHER_FLAGS))
         flags = (FRAME_ORDER if order else 0) | (FRAME_STAGED if staged else 0) | GATHER_FLAGS[gather] | (
             FRAME_PERSISTENT if persistent else 0) | (FRAME_GRAPH if graph else 0) | (
-            FRAME_ISO if iso is not None else 0) | (FRAME_ORDERED if ordered else 0)
+            FRAME_ISO if iso is not None else 0) | (FRAME_ORDERED if ordered else 0) | (FRAME_SKIP if skip else 0)
         f = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
                       int(tile[1]), flags, float(iso) if iso is not None else 0.0)
         _check(load().dpvSetFrame(self._h, C.byref(f)))
         self._frame_args = (step_voxels, sigma_max, ert)
-        self._frame_kw = {"order": order, "staged": staged, "graph": graph, "iso": iso, "ordered": ordered}
+        self._frame_kw = {"order": order, "staged": staged, "graph": graph, "iso": iso, "ordered": ordered,
+                          "skip": skip}
         self.width, self.height = int(width), int(height)
 
     # -- rendering ---------------------------------------------------------
@@ -405,13 +408,14 @@ class Device:
 def render_noalloc(dims: Sequence[int], bricks, storage: str, tf: torch.Tensor, camera, width: int, height: int,
                    rgba: torch.Tensor, depth: torch.Tensor, step_voxels: float = 0.5, sigma_max: float = 8.0,
                    ert: float = 0.0, tile=(0, 0), vmin: float = 0.0, vmax: float = 1.0, origin=(0.0, 0.0, 0.0),
-                   spacing: Optional[float] = None, stream: Optional[torch.cuda.Stream] = None):
+                   spacing: Optional[float] = None, stream: Optional[torch.cuda.Stream] = None, flags: int = 0):
     """Allocation-free render of one camera (dpvRenderNoAlloc) into caller
     tensors rgba (H, W, 4) and depth (H, W) on the current CUDA device.
     bricks: per rank (owned_lo, owned_hi, stored nodes as a device tensor in
     the storage dtype, scale).  Nothing is allocated on the device; see
     include/dpv.h for the size limit and the rule that calls must not overlap
-    on the GPU."""
+    on the GPU.  flags: DPV_FRAME_* bits (the iso, ordered and skip bits
+    are refused; the layout bits are ignored)."""
     sp = 1.0 / (max(dims) - 1) if spacing is None else spacing
     arr = (NoAllocBrick * len(bricks))()
     for i, (lo, hi, data, scale) in enumerate(bricks):
@@ -423,7 +427,7 @@ def render_noalloc(dims: Sequence[int], bricks, storage: str, tf: torch.Tensor, 
     cam = CameraDesc((C.c_float * 3)(*camera.eye), (C.c_float * 3)(*camera.center), (C.c_float * 3)(*camera.up),
                      float(camera.fovy_deg))
     fr = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
-                   int(tile[1]), 0, 0.0)
+                   int(tile[1]), int(flags), 0.0)
     st = stream if stream is not None else torch.cuda.current_stream()
     _check(load().dpvRenderNoAlloc(C.byref(sc), C.byref(cam), C.byref(fr), _ptr(rgba), _ptr(depth),
                                    C.c_void_p(st.cuda_stream)))

@@ -235,13 +235,15 @@ def _normalize01_(f: torch.Tensor) -> torch.Tensor:
 # transfer function
 # --------------------------------------------------------------------------
 
-def make_tf(seed: int = 1234, n: int = 256, n_ctrl: int = 8) -> np.ndarray:
+def make_tf(seed: int = 1234, n: int = 256, n_ctrl: int = 8, transparent_below: float = 0.0) -> np.ndarray:
     """Piecewise-linear RGBA table of n entries at s_i = i / (n - 1).
 
     n_ctrl control points: sorted positions in [0, 1] with both endpoints
     pinned, RGB uniform in [0, 1], alpha uniform in [0, 1] times the position
-    (an opacity ramp), linearly resampled to n entries.  Returns (n, 4) f32.
-    """
+    (an opacity ramp), linearly resampled to n entries.  With
+    transparent_below > 0 the entries at s_i <= transparent_below get alpha
+    exactly 0 (a classification that hides the low values).  Returns (n, 4)
+    f32."""
     g = rng(seed, STREAM_TF)
     pos = np.sort(g.uniform(0.0, 1.0, size=n_ctrl - 2))
     pos = np.concatenate([[0.0], pos, [1.0]])
@@ -252,6 +254,8 @@ def make_tf(seed: int = 1234, n: int = 256, n_ctrl: int = 8) -> np.ndarray:
     for ch in range(3):
         tab[:, ch] = np.interp(xs, pos, rgb[:, ch])
     tab[:, 3] = np.interp(xs, pos, a)
+    if transparent_below > 0.0:
+        tab[xs <= transparent_below, 3] = 0.0
     return tab.astype(np.float32)
 
 
