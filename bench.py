@@ -490,16 +490,21 @@ def run_ours(args, cfg_name, cfg):
                      "ordered_samples_per_step": ord_samples, "speedup_vs_sort_last": sl_ms / (fwd_ms / args.steps),
                      "image_difference_vs_sort_last": {"max": float(d.max()), "mean": float(d.mean())}}
 
-    # empty-space skipping beside the same frame without it, in the same
+    # empty-space skipping beside the same frame without it, in its own best
     # launch form: time, samples evaluated, and the frames (bit-identical)
     skip_cmp = None
     if skip:
         skip_img = dev.frames()[0].clone()
         skip_samples = dev.stats()["samples_forward"]
-        fl = tune["flags"] if tune else 0
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
-                      tile=tuple(tune["tile"]) if tune else (args.tile_w, args.tile_h), gather=dpv.gather_of(fl),
-                      persistent=bool(fl & dpv.FRAME_PERSISTENT))
+                      tile=(args.tile_w, args.tile_h))
+        ns_tune = None
+        if not args.no_autotune:
+            ns_tune = dev.autotune(frames=3)
+            nfl = ns_tune["flags"]
+            dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
+                          tile=tuple(ns_tune["tile"]), gather=dpv.gather_of(nfl),
+                          persistent=bool(nfl & dpv.FRAME_PERSISTENT))
         for _ in range(max(3, args.warmup)):
             dev.render()
         torch.cuda.synchronize()
@@ -513,10 +518,12 @@ def run_ours(args, cfg_name, cfg):
         full_ms = k0.elapsed_time(k1) / args.steps
         full_samples = dev.stats()["samples_forward"]
         skip_cmp = {"no_skip_forward_ms_per_step": full_ms, "no_skip_samples_per_step": full_samples,
+                    "no_skip_autotune": ns_tune,
                     "skip_samples_per_step": skip_samples, "evaluated_fraction": skip_samples / max(1, full_samples),
                     "speedup_vs_no_skip": full_ms / (fwd_ms / args.steps),
                     "ray_samples_per_s": full_samples * args.steps / (fwd_ms * 1e-3) / 1e9,
                     "frames_bit_identical": bool(torch.equal(dev.frames()[0], skip_img))}
+        fl = tune["flags"] if tune else 0
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
                       tile=tuple(tune["tile"]) if tune else (args.tile_w, args.tile_h), gather=dpv.gather_of(fl),
                       persistent=bool(fl & dpv.FRAME_PERSISTENT), skip=True)

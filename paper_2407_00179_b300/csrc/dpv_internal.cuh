@@ -34,7 +34,6 @@ struct CamBasis {
     float pad;
 };
 
-// The same camera basis in FP64, for the per-pixel ray setup.
 // Gather layouts of the brick ray-march (template parameter G).
 constexpr int GATHER_LINEAR = 0;   // the stored nodes, eight scalar loads
 constexpr int GATHER_QUAD = 1;     // two face vectors per sample
@@ -605,6 +604,39 @@ struct SampleWalker {
         fz = qz - (float)iz;
     }
 };
+
+// Empty-space skipping: the last sample index (>= k, <= n - 1) whose cell
+// still lies in the macro-cell of cell (ix, iy, iz).  Per axis, the sample
+// position q(k') = q0 + k' st stays at least MACRO_EPS inside the
+// macro-cell's face for every k' <= (face -/+ MACRO_EPS - q0) / st - 1; the
+// margin covers the rounding of the division and of q(k') (both well below
+// 1e-3 node for bricks under 4096 nodes).  Faces at the brick's ends, where
+// the cell index is clamped, are never crossed.
+constexpr float MACRO_EPS = 1.0f / 64.0f;
+
+__device__ __forceinline__ int macro_last(const MarchState& m, const SampleWalker& wk, int k, int n, int ix, int iy,
+                                          int iz) {
+    const int c[3] = {ix >> MACRO_SHIFT, iy >> MACRO_SHIFT, iz >> MACRO_SHIFT};
+    float kmax = (float)(n - 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float s = m.st[a];
+        float face;
+        if (s > 0.0f) {
+            const int u = (c[a] + 1) << MACRO_SHIFT;
+            if (u > wk.lim[a]) continue;
+            face = (float)u - MACRO_EPS;
+        } else if (s < 0.0f) {
+            const int l = c[a] << MACRO_SHIFT;
+            if (l == 0) continue;
+            face = (float)l + MACRO_EPS;
+        } else {
+            continue;
+        }
+        kmax = fminf(kmax, floorf((face - m.q0[a]) / s) - 1.0f);
+    }
+    return max(k, (int)kmax);
+}
 
 // ---------------------------------------------------------------------------
 // gradient accumulation runs (adjoint march)

@@ -431,7 +431,10 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                         mlast = mi;
                         mempty = b.empty[mi] != 0;
                     }
-                    if (mempty) continue;
+                    if (mempty) {
+                        k = macro_last(m, wk, k, n, ix, iy, iz);   // past the samples left inside
+                        continue;
+                    }
                 }
                 ++nsamp;
                 float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
@@ -633,7 +636,10 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
                 mlast = mi;
                 mempty = b.empty[mi] != 0;
             }
-            if (mempty) continue;
+            if (mempty) {
+                k = macro_last(m, wk, k, n, ix, iy, iz);
+                continue;
+            }
         }
         float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
         TFSample c = tf_lookup(s_tf, P, s);

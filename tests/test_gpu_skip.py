@@ -110,6 +110,20 @@ def test_skip_layouts_and_ordered(gather, ordered):
     b.release()
 
 
+def test_skip_axis_aligned_views():
+    """Rays (nearly) parallel to a grid axis: their step along the other
+    axes is tiny, where a jump over a macro-cell relies on its margin."""
+    sc = _scene(0)
+    sc.cams = [scenes.f32_camera(inputs.camera_from_direction(sc.dims, d))
+               for d in ((1.0, 0.0, 0.0), (0.0, -1.0, 0.0), (0.0, 0.0, 1.0), (1.0, 1.0, 0.0))]
+    a = _device(sc, skip=True)
+    b = _device(sc, skip=False)
+    _assert_identical(_everything(a, sc), _everything(b, sc))
+    assert a.stats()["samples_forward"] < b.stats()["samples_forward"]
+    a.release()
+    b.release()
+
+
 def test_skip_matches_fp64_oracle(orc):
     sc = _scene(0)
     dev = _device(sc, skip=True)
