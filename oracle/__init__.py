@@ -28,6 +28,7 @@ NP_STORAGE = {F32: np.float32, F16: np.uint16, BF16: np.uint16, FP8: np.uint8}
 KEY_EMPTY = 2 ** 31 - 1
 FLAG_HIT, FLAG_EXIT_AMBIG, FLAG_OWNER_AMBIG, FLAG_ERT_AMBIG = 1, 2, 4, 8
 FLAG_ISO_AMBIG = 16
+FLAG_MACRO_AMBIG = 32
 ISO_EPS = 5e-5   # iso ambiguity band on s (a rounded sample may cross otherwise)
 
 
@@ -80,6 +81,7 @@ def lib():
         _lib.orc_render_ordered.argtypes = [P, P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P]
         _lib.orc_render_iso.argtypes = [P, P, C.c_int, P, P, P, P, C.c_double, C.c_double, C.c_int, P, P, P, P, P,
                                         P, P]
+        _lib.orc_render_deep.argtypes = [P, C.c_int, P, P, P, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P]
         _lib.orc_kd_order.argtypes = [C.c_int, P, P, P, P, P, P]
         _lib.orc_kd_order.restype = C.c_int
         _lib.orc_camera_ray.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
@@ -274,6 +276,31 @@ def render_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, 
                             _p(res["rgba"]), _p(res["depth"]), _p(res["order"]), _p(res["frag_rgba"]),
                             _p(res["frag_key"]), _p(res["frag_nsamp"]), _p(res["frag_margin"]),
                             _p(res["nsamples"]), _p(res["flags"]))
+    return res
+
+
+def render_deep(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, deep: int = 4, pix=None, vmin=0.0,
+                vmax=1.0, origin=(0.0, 0.0, 0.0), spacing=None):
+    """FP64 deep-fragment render: empty-space skipping over macro-cells of
+    8^3 cells splits each brick's segment into one fragment per run of
+    evaluated samples (at most `deep` per brick; later runs continue the
+    last), every fragment of the pixel sorted by key and blended front to
+    back.  Returns rgba, depth, frag_rgba (n, K, deep, 4), frag_key
+    (n, K, deep; 2^31 - 1 = none), frag_count (n, K), nsamples (evaluated)
+    and flags (FLAG_MACRO_AMBIG among them)."""
+    g = _grid(dims, origin, spacing)
+    t, tab = _tf(tf, vmin, vmax)
+    cam_c = _camera(cam)
+    fr = frame.c()
+    K = len(bricks)
+    barr, keep_b = _bricks_c(bricks)
+    n, pp, keep = _pix(pix, frame)
+    res = {"rgba": np.zeros((n, 4)), "depth": np.zeros(n), "frag_rgba": np.zeros((n, K, deep, 4)),
+           "frag_key": np.zeros((n, K, deep), np.int32), "frag_count": np.zeros((n, K), np.int32),
+           "nsamples": np.zeros(n, np.int64), "flags": np.zeros(n, np.uint8)}
+    lib().orc_render_deep(C.byref(g), K, barr, C.byref(t), C.byref(cam_c), C.byref(fr), int(deep), n, pp,
+                          _p(res["rgba"]), _p(res["depth"]), _p(res["frag_rgba"]), _p(res["frag_key"]),
+                          _p(res["frag_count"]), _p(res["nsamples"]), _p(res["flags"]))
     return res
 
 

@@ -742,6 +742,262 @@ void orc_render_ordered(const orc_grid* g, const float* field, int K, const orc_
 }
 
 /* ------------------------------------------------------------------------ */
+/* deep fragments: empty-space skipping splits a brick's segment             */
+/* ------------------------------------------------------------------------ */
+
+/* Readings (the paper's compositor accepts several fragments per pixel from
+ * one rank, §2.1 and §5.1.1, for parts that are not convex or renderers that
+ * emit several segments; it gives no rule for producing them):
+ *   - a brick's stored box is cut into macro-cells of ORC_MACRO^3 cells,
+ *     macro-cell (mx, my, mz) holding the cells 8 m .. 8 m + 7 per axis (the
+ *     last one per axis may hold fewer); its range is the min and max of the
+ *     stored values (times the brick's scale) of the nodes its cells touch;
+ *   - a macro-cell is transparent when every TF entry a sample inside can
+ *     read has opacity exactly 0.  A sample of value v reads entries i0(v)
+ *     and i0(v) + 1 (the lookup of tf_lookup); the values inside lie in the
+ *     range, so the entries read lie in i0(lo) .. i0(hi) + 1;
+ *   - samples in transparent macro-cells have alpha 0 and are not
+ *     evaluated.  The brick's segment then splits: each maximal run of
+ *     evaluated samples (consecutive in j within the brick) is its own
+ *     fragment, premultiplied RGBA over the run, key = j of the run's first
+ *     sample.  At most `deep` fragments per brick and pixel: a run after the
+ *     last one continues it (compositing it separately would give the same
+ *     colour);
+ *   - per-fragment early termination stays per brick: the march of a brick
+ *     stops after the first sample with 1 - prod(1 - alpha) > ert over all
+ *     of the brick's samples so far;
+ *   - the composite sorts every fragment of the pixel by key (keys are
+ *     distinct) and blends front to back; depth = t of the first sample of
+ *     the first fragment with A > 0.
+ * Flags, besides the sort-last render's: MACRO_AMBIG where the kernel's
+ * FP32 arithmetic could decide a split otherwise -- a sample within
+ * 1e-3 node of a face between macro-cells of different transparency, or a
+ * sample in a macro-cell whose range ends lie within 2e-6 n of a TF entry
+ * boundary (u), where the classification changes if i0 moves by one. */
+
+#define ORC_MACRO 8
+#define ORC_DEEP_MAX 16
+#define ORC_FLAG_MACRO_AMBIG 32
+
+typedef struct {
+    int mn[3];            /* macro-cells per axis */
+    uint8_t* empty;       /* 1: transparent */
+    uint8_t* amb;         /* 1: classification within the rounding band */
+} macro_table;
+
+static double tf_u(const orc_tf* tf, double v) {
+    double x = (v - tf->vmin) / (tf->vmax - tf->vmin);
+    if (x < 0.0) x = 0.0;
+    if (x > 1.0) x = 1.0;
+    return x * (tf->n - 1);
+}
+
+static int tf_i0(const orc_tf* tf, double u) {
+    int i0 = (int)floor(u);
+    if (i0 > tf->n - 2) i0 = tf->n - 2;
+    if (i0 < 0) i0 = 0;
+    return i0;
+}
+
+/* entries e0 .. e1 (clamped to the table) all of opacity exactly 0? */
+static int tf_zero(const orc_tf* tf, int e0, int e1) {
+    if (e0 < 0) e0 = 0;
+    if (e1 > tf->n - 1) e1 = tf->n - 1;
+    for (int e = e0; e <= e1; ++e)
+        if (tf->rgba[4 * e + 3] != 0.0f) return 0;
+    return 1;
+}
+
+static void macro_build(const orc_grid* g, const orc_brick* b, const orc_tf* tf, macro_table* mt) {
+    int bl[3], bn[3];
+    orc_stored_box(g->dims, b->owned_lo, b->owned_hi, bl, bn);
+    for (int a = 0; a < 3; ++a) mt->mn[a] = (bn[a] - 2) / ORC_MACRO + 1;
+    int64_t n = (int64_t)mt->mn[0] * mt->mn[1] * mt->mn[2];
+    mt->empty = (uint8_t*)malloc(n);
+    mt->amb = (uint8_t*)malloc(n);
+    double band = 2e-6 * tf->n;
+    for (int mz = 0; mz < mt->mn[2]; ++mz)
+        for (int my = 0; my < mt->mn[1]; ++my)
+            for (int mx = 0; mx < mt->mn[0]; ++mx) {
+                int m0[3] = {mx * ORC_MACRO, my * ORC_MACRO, mz * ORC_MACRO};
+                double lo = INFINITY, hi = -INFINITY;
+                for (int z = m0[2]; z <= m0[2] + ORC_MACRO && z < bn[2]; ++z)
+                    for (int y = m0[1]; y <= m0[1] + ORC_MACRO && y < bn[1]; ++y)
+                        for (int x = m0[0]; x <= m0[0] + ORC_MACRO && x < bn[0]; ++x) {
+                            double v = b->scale * decode(b->data, b->dtype, ((int64_t)z * bn[1] + y) * bn[0] + x);
+                            if (v < lo) lo = v;
+                            if (v > hi) hi = v;
+                        }
+                double ulo = tf_u(tf, lo), uhi = tf_u(tf, hi);
+                int e0 = tf_i0(tf, ulo), e1 = tf_i0(tf, uhi) + 1;
+                int64_t m = ((int64_t)mz * mt->mn[1] + my) * mt->mn[0] + mx;
+                mt->empty[m] = (uint8_t)tf_zero(tf, e0, e1);
+                /* an end within the band of an entry boundary: widen by one */
+                int w0 = fabs(ulo - nearbyint(ulo)) < band ? e0 - 1 : e0;
+                int w1 = fabs(uhi - nearbyint(uhi)) < band ? e1 + 1 : e1;
+                mt->amb[m] = (uint8_t)(tf_zero(tf, w0, w1) != mt->empty[m]);
+            }
+}
+
+static int64_t macro_index(const macro_table* mt, const int c[3]) {
+    return ((int64_t)(c[2] / ORC_MACRO) * mt->mn[1] + c[1] / ORC_MACRO) * mt->mn[0] + c[0] / ORC_MACRO;
+}
+
+typedef struct {
+    double C[ORC_DEEP_MAX][3], T[ORC_DEEP_MAX];
+    int64_t key[ORC_DEEP_MAX];
+    int nf;               /* fragments started */
+    int in_run;           /* the brick's previous sample was evaluated */
+    double Tb;            /* transmittance over the brick's samples */
+    int done;
+    int32_t nsamp;
+} deep_state;
+
+/* Deep-fragment render (readings above).  Outputs per listed pixel k (any
+ * pointer may be NULL): rgba, depth; frag_rgba[((k K + b) deep + i) 4 ..],
+ * frag_key[(k K + b) deep + i] (2^31 - 1 past the brick's count),
+ * frag_count[k K + b]; nsamples (evaluated); flags. */
+void orc_render_deep(const orc_grid* g, int K, const orc_brick* bricks, const orc_tf* tf, const orc_camera* cam,
+                     const orc_frame* fr, int deep, int npix, const int32_t* pix, double* rgba, double* depth,
+                     double* frag_rgba, int32_t* frag_key, int32_t* frag_count, int64_t* nsamples,
+                     uint8_t* flags) {
+    if (deep < 1) deep = 1;
+    if (deep > ORC_DEEP_MAX) deep = ORC_DEEP_MAX;
+    macro_table* mt = (macro_table*)malloc(sizeof(macro_table) * K);
+    for (int b = 0; b < K; ++b) macro_build(g, &bricks[b], tf, &mt[b]);
+    int ert_on = fr->ert > 0.0 && fr->ert < 1.0;
+#pragma omp parallel
+    {
+        deep_state* ds = (deep_state*)malloc(sizeof(deep_state) * K);
+        int nfr = K * deep;
+        int* ob = (int*)malloc(sizeof(int) * nfr);
+        int* oi = (int*)malloc(sizeof(int) * nfr);
+#pragma omp for schedule(dynamic, 16)
+        for (int k = 0; k < npix; ++k) {
+            int p = pix ? pix[k] : k;
+            orc_rayinfo ri;
+            ray_samples(g, cam, fr, p % fr->width, p / fr->width, &ri);
+            int fl = ri.flags;
+            for (int b = 0; b < K; ++b) {
+                ds[b].nf = 0;
+                ds[b].in_run = 0;
+                ds[b].Tb = 1.0;
+                ds[b].done = 0;
+                ds[b].nsamp = 0;
+            }
+            int owner = -1;
+            for (int64_t j = 0; j < ri.n; ++j) {
+                double q[3], tj;
+                sample_point(g, &ri, j, q, &tj);
+                owner = find_owner(g, K, bricks, q, owner);
+                if (owner < 0) continue;
+                const orc_brick* B = &bricks[owner];
+                deep_state* f = &ds[owner];
+                if (near_internal_face(g, B, &ri, tj, fr->amb_samples)) fl |= ORC_FLAG_OWNER_AMBIG;
+                if (f->done) continue;
+                int bl[3], bn[3], c[3];
+                orc_stored_box(g->dims, B->owned_lo, B->owned_hi, bl, bn);
+                for (int a = 0; a < 3; ++a) {
+                    int ci = (int)floor(q[a]);
+                    if (ci < bl[a]) ci = bl[a];
+                    if (ci > bl[a] + bn[a] - 2) ci = bl[a] + bn[a] - 2;
+                    c[a] = ci - bl[a];
+                }
+                const macro_table* M = &mt[owner];
+                int64_t m = macro_index(M, c);
+                if (M->amb[m]) fl |= ORC_FLAG_MACRO_AMBIG;
+                for (int a = 0; a < 3; ++a) {        /* near a face to a macro-cell of the other kind */
+                    double ql = q[a] - bl[a];
+                    int face = ORC_MACRO * (int)nearbyint(ql / ORC_MACRO);
+                    if (face <= 0 || face > bn[a] - 2 || fabs(ql - face) >= 1e-3) continue;
+                    int c2[3] = {c[0], c[1], c[2]};
+                    c2[a] = c[a] >= face ? face - 1 : face;
+                    if (M->empty[macro_index(M, c2)] != M->empty[m]) fl |= ORC_FLAG_MACRO_AMBIG;
+                }
+                if (M->empty[m]) {
+                    f->in_run = 0;
+                    continue;
+                }
+                if (!f->in_run && f->nf < deep) {     /* a new run: a new fragment */
+                    int i = f->nf++;
+                    f->C[i][0] = f->C[i][1] = f->C[i][2] = 0.0;
+                    f->T[i] = 1.0;
+                    f->key[i] = j;
+                }
+                f->in_run = 1;
+                int i = f->nf - 1;
+                double s = trilinear(B->data, B->dtype, B->scale, bl, bn, q, NULL, NULL);
+                double col[3], al;
+                classify(tf, fr, ri.dt, s, col, &al);
+                double A_before = 1.0 - f->Tb;
+                for (int a = 0; a < 3; ++a) f->C[i][a] += f->T[i] * al * col[a];
+                f->T[i] *= 1.0 - al;
+                f->Tb *= 1.0 - al;
+                f->nsamp++;
+                if (ert_on && 1.0 - f->Tb > fr->ert) {
+                    f->done = 1;
+                    double m1 = (1.0 - f->Tb) - fr->ert, m0 = fr->ert - A_before;
+                    if ((m1 < m0 ? m1 : m0) < fr->amb_alpha) fl |= ORC_FLAG_ERT_AMBIG;
+                }
+            }
+            /* every fragment of the pixel, by ascending key (insertion sort) */
+            int nall = 0;
+            for (int b = 0; b < K; ++b)
+                for (int i = 0; i < ds[b].nf; ++i) {
+                    int at = nall++;
+                    while (at > 0 && ds[ob[at - 1]].key[oi[at - 1]] > ds[b].key[i]) {
+                        ob[at] = ob[at - 1];
+                        oi[at] = oi[at - 1];
+                        --at;
+                    }
+                    ob[at] = b;
+                    oi[at] = i;
+                }
+            double C[3] = {0, 0, 0}, A = 0.0, dep = INFINITY;
+            for (int r = 0; r < nall; ++r) {
+                const deep_state* f = &ds[ob[r]];
+                int i = oi[r];
+                double Ak = 1.0 - f->T[i];
+                for (int a = 0; a < 3; ++a) C[a] += (1.0 - A) * f->C[i][a];
+                A += (1.0 - A) * Ak;
+                if (Ak > 0.0 && isinf(dep)) dep = ri.t_enter + (f->key[i] + 0.5) * ri.dt;
+            }
+            if (rgba) {
+                rgba[4 * k + 0] = C[0];
+                rgba[4 * k + 1] = C[1];
+                rgba[4 * k + 2] = C[2];
+                rgba[4 * k + 3] = A;
+            }
+            if (depth) depth[k] = dep;
+            int64_t ns = 0;
+            for (int b = 0; b < K; ++b) {
+                int64_t o = (int64_t)K * k + b;
+                for (int i = 0; i < deep; ++i) {
+                    int64_t oo = o * deep + i;
+                    int live = i < ds[b].nf;
+                    if (frag_rgba)
+                        for (int a = 0; a < 4; ++a)
+                            frag_rgba[4 * oo + a] = !live ? 0.0 : a < 3 ? ds[b].C[i][a] : 1.0 - ds[b].T[i];
+                    if (frag_key) frag_key[oo] = live ? (int32_t)ds[b].key[i] : ORC_KEY_EMPTY;
+                }
+                if (frag_count) frag_count[o] = ds[b].nf;
+                ns += ds[b].nsamp;
+            }
+            if (nsamples) nsamples[k] = ns;
+            if (flags) flags[k] = (uint8_t)fl;
+        }
+        free(ds);
+        free(ob);
+        free(oi);
+    }
+    for (int b = 0; b < K; ++b) {
+        free(mt[b].empty);
+        free(mt[b].amb);
+    }
+    free(mt);
+}
+
+/* ------------------------------------------------------------------------ */
 /* iso-surface fragments (first hit per brick, depth composite)              */
 /* ------------------------------------------------------------------------ */
 
