@@ -523,7 +523,24 @@ def run_ours(args, cfg_name, cfg):
                     "speedup_vs_no_skip": full_ms / (fwd_ms / args.steps),
                     "ray_samples_per_s": full_samples * args.steps / (fwd_ms * 1e-3) / 1e9,
                     "frames_bit_identical": bool(torch.equal(dev.frames()[0], skip_img))}
+        # deep fragments: the same skipping, each brick's segment split at
+        # its transparent macro-cells into up to DEEP_MAX fragments
         fl = tune["flags"] if tune else 0
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
+                      tile=tuple(tune["tile"]) if tune else (args.tile_w, args.tile_h), gather=dpv.gather_of(fl),
+                      persistent=bool(fl & dpv.FRAME_PERSISTENT), deep=True)
+        for _ in range(max(3, args.warmup)):
+            dev.render()
+        torch.cuda.synchronize()
+        k0.record(stream)
+        for _ in range(args.steps):
+            dev.render()
+        k1.record(stream)
+        torch.cuda.synchronize()
+        d = (dev.frames()[0] - skip_img).abs()
+        skip_cmp["deep_fragments"] = {"forward_ms_per_step": k0.elapsed_time(k1) / args.steps,
+                                      "max_layers_per_brick": dpv.DEEP_MAX,
+                                      "image_difference_vs_skip": {"max": float(d.max()), "mean": float(d.mean())}}
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
                       tile=tuple(tune["tile"]) if tune else (args.tile_w, args.tile_h), gather=dpv.gather_of(fl),
                       persistent=bool(fl & dpv.FRAME_PERSISTENT), skip=True)

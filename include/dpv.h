@@ -143,6 +143,20 @@ typedef struct {
                                       built once per committed brick, their transparency
                                       per render.  Sample counts then count the evaluated
                                       samples.  The backward replays every sample. */
+#define DPV_FRAME_DEEP 1024       /* deep fragments: empty-space skipping (implied) splits
+                                      a brick's ray segment at its transparent macro-cells,
+                                      each run of evaluated samples becoming its own
+                                      fragment (key = the run's first sample index); up to
+                                      DPV_DEEP_MAX per brick and pixel, later runs continue
+                                      the last one.  The compositor sorts the variable
+                                      count per pixel (§2.1, §5.1.1: several fragments per
+                                      pixel from one rank).  Early termination stays on the
+                                      brick's accumulated opacity.  Forward only (the
+                                      adjoint returns DPV_ERR_UNSUPPORTED); not with
+                                      STAGED, ISO or ORDERED.  The order image then has
+                                      num_ranks x DPV_DEEP_MAX entries per pixel, one brick
+                                      id per fragment. */
+#define DPV_DEEP_MAX 4
 #define DPV_FRAME_ISO 128          /* iso-surface fragments instead of volume rendering
                                       (the paper's z-composited opaque surfaces, §7):
                                       each brick reports the first sample pair (j-1, j)
@@ -256,6 +270,12 @@ dpv_status dpvCopyFrame(dpv_device dev, int camera, float* rgba, float* depth);
  * device buffers rgba (height x width x 4, premultiplied) and key (height x
  * width int32; 2^31 - 1 = empty, also for pixels the rank was culled from). */
 dpv_status dpvReadFragments(dpv_device dev, int camera, int rank, float* rgba, int32_t* key);
+
+/* Debug/test: as dpvReadFragments, for fragment layer `layer` of a frame
+ * rendered with DPV_FRAME_DEEP (0 <= layer < DPV_DEEP_MAX; layers past a
+ * pixel's fragment count read as empty).  Without DPV_FRAME_DEEP only layer 0
+ * exists.  DPV_ERR_INVALID_ARG for a layer out of range. */
+dpv_status dpvReadDeepFragments(dpv_device dev, int camera, int rank, int layer, float* rgba, int32_t* key);
 
 /* Debug/test: copy rank `rank`'s stored nodes (owned + ghost box, x
  * fastest, in the storage format) to the caller's device buffer `dst` (NULL

@@ -335,13 +335,14 @@ dpv_status prepare(dpv_device dev) {
     P.ntf = dev->ntf;
     for (int a = 0; a < 3; ++a) P.dims[a] = dev->dims[a];
     P.nbricks = dev->nranks;
-    P.order_stride = (F.flags & DPV_FRAME_ORDER) ? dev->nranks : 0;
+    P.deep = (F.flags & DPV_FRAME_DEEP) ? DEEP_LAYERS : 1;
+    P.order_stride = (F.flags & DPV_FRAME_ORDER) ? dev->nranks * P.deep : 0;
     P.items_cap = 0;
     // floats of shared memory per staged slab box; DPV_BOX_CAP overrides it
     // (tuning, and tests that force the unstaged fallback of large slabs)
     P.iso_on = (F.flags & DPV_FRAME_ISO) ? 1 : 0;
     P.ordered_on = (F.flags & DPV_FRAME_ORDERED) ? 1 : 0;
-    P.skip_on = (F.flags & DPV_FRAME_SKIP) ? 1 : 0;
+    P.skip_on = (F.flags & (DPV_FRAME_SKIP | DPV_FRAME_DEEP)) ? 1 : 0;   // deep fragments skip
     P.iso = F.iso_value;
     P.box_cap = 6144;
     if (const char* env = getenv("DPV_BOX_CAP")) {
@@ -585,12 +586,13 @@ dpv_status prepare(dpv_device dev) {
        "clear work list");
 
     // fragment pool
-    if ((size_t)dev->n_items > dev->frag_cap) {
+    // (P.deep fragment layers per item)
+    if ((size_t)dev->n_items * P.deep > dev->frag_cap) {
         free_frags(dev);
-        size_t slots = (size_t)dev->n_items * P.tp;
+        size_t slots = (size_t)dev->n_items * P.deep * P.tp;
         if ((s = dev_alloc(dev, (void**)&dev->d_frag_rgba, sizeof(float4) * slots, "fragment pool"))) return s;
         if ((s = dev_alloc(dev, (void**)&dev->d_frag_key, sizeof(int) * slots, "fragment pool"))) return s;
-        dev->frag_cap = (size_t)dev->n_items;
+        dev->frag_cap = (size_t)dev->n_items * P.deep;
     }
     // frame buffers
     size_t npix = (size_t)P.ncam * P.W * P.H;
@@ -933,6 +935,8 @@ dpv_status dpvSetFrame(dpv_device dev, const dpv_frame_desc* f) {
         return fail(DPV_ERR_UNSUPPORTED, "the ordered march has no staged or iso-surface form");
     if ((f->flags & DPV_FRAME_SKIP) && (f->flags & (DPV_FRAME_STAGED | DPV_FRAME_ISO)))
         return fail(DPV_ERR_UNSUPPORTED, "empty-space skipping has no staged or iso-surface form");
+    if ((f->flags & DPV_FRAME_DEEP) && (f->flags & (DPV_FRAME_STAGED | DPV_FRAME_ISO | DPV_FRAME_ORDERED)))
+        return fail(DPV_ERR_UNSUPPORTED, "deep fragments have no staged, iso-surface or ordered form");
     if ((f->flags & DPV_FRAME_ISO) && !isfinite(f->iso_value))
         return fail(DPV_ERR_INVALID_ARG, "iso_value must be finite");
     dev->frame = *f;
@@ -1030,18 +1034,24 @@ dpv_status dpvCopyFrame(dpv_device dev, int camera, float* rgba, float* depth) {
     return DPV_OK;
 }
 
-dpv_status dpvReadFragments(dpv_device dev, int camera, int rank, float* rgba, int32_t* key) {
+dpv_status dpvReadDeepFragments(dpv_device dev, int camera, int rank, int layer, float* rgba, int32_t* key) {
     dpv_status s = check_dev(dev);
     if (s) return s;
     if (!dev->rendered) return fail(DPV_ERR_STATE, "no frame rendered yet");
     if (camera < 0 || camera >= dev->P.ncam) return fail(DPV_ERR_INVALID_ARG, "camera %d out of range", camera);
     if (rank < 0 || rank >= dev->nranks) return fail(DPV_ERR_INVALID_ARG, "rank %d out of range", rank);
+    if (layer < 0 || layer >= dev->P.deep)
+        return fail(DPV_ERR_INVALID_ARG, "layer %d out of range (the frame has %d)", layer, dev->P.deep);
     if (!rgba || !key) return fail(DPV_ERR_INVALID_ARG, "output NULL");
     DeviceGuard g(dev->cuda_device);
-    CK(launch_read_frags(dev->P, dev->d_items, dev->n_items, camera, rank, dev->d_frag_rgba, dev->d_frag_key,
+    CK(launch_read_frags(dev->P, dev->d_items, dev->n_items, camera, rank, layer, dev->d_frag_rgba, dev->d_frag_key,
                          (float4*)rgba, key, dev->stream),
        "read fragments");
     return DPV_OK;
+}
+
+dpv_status dpvReadFragments(dpv_device dev, int camera, int rank, float* rgba, int32_t* key) {
+    return dpvReadDeepFragments(dev, camera, rank, 0, rgba, key);
 }
 
 dpv_status dpvReadBrick(dpv_device dev, int rank, void* dst, int stored_lo[3], int stored_dims[3], float* scale) {
@@ -1081,6 +1091,7 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
     if (!dev->rendered || dev->dirty) return fail(DPV_ERR_STATE, "backward needs the fragments of a render");
     if (dev->P.iso_on) return fail(DPV_ERR_UNSUPPORTED, "the adjoint is of the volume-rendering mode");
     if (dev->P.ordered_on) return fail(DPV_ERR_UNSUPPORTED, "the adjoint is of the sort-last march");
+    if (dev->P.deep > 1) return fail(DPV_ERR_UNSUPPORTED, "the adjoint is of one fragment per brick");
     if (!dL_drgba || !dL_dtf) return fail(DPV_ERR_INVALID_ARG, "gradient pointers NULL");
     DeviceGuard g(dev->cuda_device);
     const FrameParams& P = dev->P;

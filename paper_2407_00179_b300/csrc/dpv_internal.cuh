@@ -132,6 +132,8 @@ struct BrickDev {
 
 // Empty-space skipping: macro-cells of 2^MACRO_SHIFT cells per axis.
 constexpr int MACRO_SHIFT = 3;
+// Deep fragments: fragment layers per work item (DPV_DEEP_MAX).
+constexpr int DEEP_LAYERS = 4;
 
 // A work item: one brick seen through one screen tile of one camera.
 struct Item {
@@ -171,6 +173,7 @@ struct FrameParams {
     int box_cap;       // floats of shared memory per slab box (staged march)
     int ordered_on;    // visibility-ordered march, global early termination
     int skip_on;       // empty-space skipping in the forward march
+    int deep;          // fragment layers per work item: 1, or DEEP_LAYERS (deep fragments)
     int iso_on;        // iso-surface fragments instead of volume rendering
     float iso;         // their level
     const float4* rays;// per camera and pixel RAY_VECS float4; see k_rays

@@ -456,7 +456,91 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
     return nsamp;
 }
 
-template <typename T, int GL, bool SKIP>
+// Deep fragments (DPV_FRAME_DEEP): empty-space skipping splits the brick's
+// segment, each run of evaluated samples between transparent macro-cells
+// becoming its own fragment with the run's first sample as key (the general
+// case of several fragments per pixel from one rank, §2.1, §5.1.1).  Layer
+// d of item i is at slot ((i DEEP_LAYERS + d) tp + thread); from the
+// DEEP_LAYERS-th run on, the runs continue the last fragment.  Early
+// termination stays on the brick's transmittance Tb, as in the sort-last
+// march.
+template <typename T, int GL>
+__device__ __forceinline__ unsigned long long march_item_deep(const FrameParams& P, const CamBasis* cams,
+                                                              const BrickDev* bricks, const float* scales,
+                                                              const Item& it, long long item, const float4* s_tf,
+                                                              float4* frag_rgba, int* frag_key) {
+    const BrickDev b = bricks[it.brick];
+    const CamBasis cam = cams[it.cam];
+    const float scale = scales[b.scale_idx];
+    const T* data = (const T*)b.data;
+    int lx, ly;
+    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
+    const long long base = item * DEEP_LAYERS * P.tp + threadIdx.x;     // layer d at base + d tp
+    unsigned long long nsamp = 0;
+    if (px < P.W && py < P.H) {
+        int nf = 0;
+        MarchState m;
+        if (brick_samples(P, cam, it.cam, b, px, py, m)) {
+            float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.0f, Tb = 1.0f;
+            const int n = m.j1 - m.j0;
+            CornerCache<T, GL> cc;
+            SampleWalker wk;
+            wk.init(b);
+            int mlast = -1;
+            bool mempty = false, run = false;
+            for (int k = 0; k < n; ++k) {
+                int ix, iy, iz;
+                float fx, fy, fz;
+                wk.at(m, k, ix, iy, iz, fx, fy, fz);
+                const int mi = (iz >> MACRO_SHIFT) * b.mxy + (iy >> MACRO_SHIFT) * b.mx + (ix >> MACRO_SHIFT);
+                if (mi != mlast) {
+                    mlast = mi;
+                    mempty = b.empty[mi] != 0;
+                }
+                if (mempty) {
+                    run = false;
+                    k = macro_last(m, wk, k, n, ix, iy, iz);
+                    continue;
+                }
+                if (!run && nf < DEEP_LAYERS) {          // a new run: close the last fragment, open one
+                    if (nf > 0) frag_rgba[base + (long long)(nf - 1) * P.tp] = make_float4(C0, C1, C2, 1.0f - Tr);
+                    frag_key[base + (long long)nf * P.tp] = m.j0 + k;
+                    ++nf;
+                    C0 = C1 = C2 = 0.0f;
+                    Tr = 1.0f;
+                }
+                run = true;
+                ++nsamp;
+                float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
+                TFSample c = tf_lookup(s_tf, P, s);
+                float al = sample_alpha(P, c.v.w);
+                float ta = Tr * al;
+                C0 = fmaf(ta, c.v.x, C0);
+                C1 = fmaf(ta, c.v.y, C1);
+                C2 = fmaf(ta, c.v.z, C2);
+                Tr = Tr * (1.0f - al);
+                Tb = Tb * (1.0f - al);
+                if (P.ert_on && 1.0f - Tb > P.ert) break;
+            }
+            if (nf > 0) frag_rgba[base + (long long)(nf - 1) * P.tp] = make_float4(C0, C1, C2, 1.0f - Tr);
+        }
+        for (int d = nf; d < DEEP_LAYERS; ++d) frag_key[base + (long long)d * P.tp] = KEY_EMPTY;
+    }
+    return nsamp;
+}
+
+// MODE: 0 the plain march, 1 with empty-space skipping, 2 deep fragments
+template <typename T, int GL, int MODE>
+__device__ __forceinline__ unsigned long long march_any(const FrameParams& P, const CamBasis* cams,
+                                                        const BrickDev* bricks, const float* scales, const Item& it,
+                                                        long long item, const float4* s_tf, float4* frag_rgba,
+                                                        int* frag_key) {
+    if (MODE == 2) return march_item_deep<T, GL>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
+    return march_item<T, GL, MODE == 1>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
+}
+
+template <typename T, int GL, int MODE>
 __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
                                                    const float* scales, const Item* items, const float4* tf,
                                                    float4* frag_rgba, int* frag_key, Counters* counters) {
@@ -465,7 +549,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis
     __syncthreads();
     const Item it = items[blockIdx.x];
     if (!item_ok(it, P)) return;
-    unsigned long long nsamp = march_item<T, GL, SKIP>(P, cams, bricks, scales, it, blockIdx.x, s_tf, frag_rgba, frag_key);
+    unsigned long long nsamp = march_any<T, GL, MODE>(P, cams, bricks, scales, it, blockIdx.x, s_tf, frag_rgba, frag_key);
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
@@ -473,7 +557,7 @@ __global__ void __launch_bounds__(256) k_march_fwd(FrameParams P, const CamBasis
 // Persistent form: a grid sized to the GPU pulls work items from a counter
 // in the order `sched` gives (brick-major: all cameras' tiles of one brick
 // together, so a brick is read from HBM about once per batch).
-template <typename T, int GL, bool SKIP>
+template <typename T, int GL, int MODE>
 __global__ void __launch_bounds__(256) k_march_fwd_persistent(FrameParams P, const CamBasis* cams,
                                                               const BrickDev* bricks, const float* scales,
                                                               const Item* items, const int* sched, int n_items,
@@ -491,49 +575,51 @@ __global__ void __launch_bounds__(256) k_march_fwd_persistent(FrameParams P, con
         if (i >= n_items) break;
         const int item = sched[i];
         const Item it = items[item];
-        if (item_ok(it, P)) nsamp += march_item<T, GL, SKIP>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
+        if (item_ok(it, P)) nsamp += march_any<T, GL, MODE>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
     }
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
 
-template <typename T, int GL, bool SKIP>
+template <typename T, int GL, int MODE>
 static void fwd_launch_s(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                        const Item* items, int n_items, const float4* tf, float4* frag_rgba, int* frag_key,
                        Counters* counters, const Schedule* sch, cudaStream_t st) {
     size_t smem = sizeof(float4) * P.ntf;
     if (sch) {
         if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_march_fwd_persistent<T, GL, SKIP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(k_march_fwd_persistent<T, GL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         int per_sm = 0, dev = 0, nsm = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_fwd_persistent<T, GL, SKIP>, P.tp, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_fwd_persistent<T, GL, MODE>, P.tp, smem);
         int grid = nsm * (per_sm > 0 ? per_sm : 1);
         if (sch->ctas_per_sm > 0 && sch->ctas_per_sm < per_sm) grid = nsm * sch->ctas_per_sm;
         if (grid > n_items) grid = n_items;
         cudaMemsetAsync(sch->work, 0, sizeof(unsigned int), st);
-        k_march_fwd_persistent<T, GL, SKIP><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched, n_items,
+        k_march_fwd_persistent<T, GL, MODE><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched, n_items,
                                                                   sch->work, tf, frag_rgba, frag_key, counters);
         return;
     }
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_march_fwd<T, GL, SKIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_march_fwd<T, GL, SKIP><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
+        cudaFuncSetAttribute(k_march_fwd<T, GL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_march_fwd<T, GL, MODE><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
                                                             counters);
 }
 
-// empty-space skipping is a template switch: the march without it carries
-// no macro-cell test
+// empty-space skipping and deep fragments are template switches: the plain
+// march carries no macro-cell test
 template <typename T, int GL>
 static void fwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                        const Item* items, int n_items, const float4* tf, float4* frag_rgba, int* frag_key,
                        Counters* counters, const Schedule* sch, cudaStream_t st) {
-    if (P.skip_on)
-        fwd_launch_s<T, GL, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st);
+    if (P.deep > 1)
+        fwd_launch_s<T, GL, 2>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st);
+    else if (P.skip_on)
+        fwd_launch_s<T, GL, 1>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st);
     else
-        fwd_launch_s<T, GL, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st);
+        fwd_launch_s<T, GL, 0>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st);
 }
 
 // ===========================================================================
@@ -987,9 +1073,12 @@ __global__ void __launch_bounds__(256) k_composite_fwd(FrameParams P, float inv_
     tile_pixel(threadIdx.x, P.tw, lx, ly);
     int px = (tile % P.ntx) * P.tw + lx, py = (tile / P.ntx) * P.th + ly;
     if (px >= P.W || py >= P.H) return;
-    long long first = tile_first[ct];
+    long long first_item = tile_first[ct];
     int cnt = tile_count[ct];
-    if (first < 0 || first + cnt > P.items_cap) cnt = 0;    // list overflowed: error bit already set
+    if (first_item < 0 || first_item + cnt > P.items_cap) cnt = 0;    // list overflowed: error bit already set
+    // fragment slots: P.deep layers per item (1 unless deep fragments)
+    const long long first = first_item * P.deep;
+    cnt *= P.deep;
     int t = threadIdx.x;
     SortedFrags s;
     collect_sorted(frag_key, first, cnt, P.tp, t, s);
@@ -1008,7 +1097,7 @@ __global__ void __launch_bounds__(256) k_composite_fwd(FrameParams P, float inv_
                 C2 = fmaf(w, f.z, C2);
                 A = fmaf(w, f.w, A);
                 if (f.w > 0.0f && depth_key == KEY_EMPTY) depth_key = s.key[i];
-                if (ord) ord[i] = (unsigned char)items[first + s.slot[i]].brick;
+                if (ord && i < P.order_stride) ord[i] = (unsigned char)items[first_item + s.slot[i] / P.deep].brick;
             }
         }
     } else {
@@ -1024,7 +1113,7 @@ __global__ void __launch_bounds__(256) k_composite_fwd(FrameParams P, float inv_
             C2 = fmaf(w, f.z, C2);
             A = fmaf(w, f.w, A);
             if (f.w > 0.0f && depth_key == KEY_EMPTY) depth_key = k;
-            if (ord && i < P.order_stride) ord[i] = (unsigned char)items[first + q].brick;
+            if (ord && i < P.order_stride) ord[i] = (unsigned char)items[first_item + q / P.deep].brick;
         }
     }
     if (ord)
@@ -1816,7 +1905,7 @@ __global__ void k_fill_key(int* key, long long n) {
     if (i < n) key[i] = KEY_EMPTY;
 }
 
-__global__ void k_read_frags(FrameParams P, const Item* items, int n_items, int cam, int rank,
+__global__ void k_read_frags(FrameParams P, const Item* items, int n_items, int cam, int rank, int layer,
                              const float4* frag_rgba, const int* frag_key, float4* out_rgba, int* out_key) {
     int i = blockIdx.x;
     if (i >= n_items) return;
@@ -1826,20 +1915,22 @@ __global__ void k_read_frags(FrameParams P, const Item* items, int n_items, int 
     tile_pixel(threadIdx.x, P.tw, lx, ly);
     int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
     if (px >= P.W || py >= P.H) return;
-    long long slot = (long long)i * P.tp + threadIdx.x;
+    long long slot = ((long long)i * P.deep + layer) * P.tp + threadIdx.x;
     long long pix = (long long)py * P.W + px;
     int k = frag_key[slot];
     out_key[pix] = k;
     out_rgba[pix] = k == KEY_EMPTY ? make_float4(0.f, 0.f, 0.f, 0.f) : frag_rgba[slot];
 }
 
-cudaError_t launch_read_frags(const FrameParams& P, const Item* items, int n_items, int cam, int rank,
+cudaError_t launch_read_frags(const FrameParams& P, const Item* items, int n_items, int cam, int rank, int layer,
                               const float4* frag_rgba, const int* frag_key, float4* out_rgba, int* out_key,
                               cudaStream_t st) {
     long long n = (long long)P.W * P.H;
     cudaMemsetAsync(out_rgba, 0, sizeof(float4) * n, st);
     k_fill_key<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out_key, n);
-    if (n_items) k_read_frags<<<n_items, P.tp, 0, st>>>(P, items, n_items, cam, rank, frag_rgba, frag_key, out_rgba, out_key);
+    if (n_items)
+        k_read_frags<<<n_items, P.tp, 0, st>>>(P, items, n_items, cam, rank, layer, frag_rgba, frag_key, out_rgba,
+                                               out_key);
     return cudaGetLastError();
 }
 

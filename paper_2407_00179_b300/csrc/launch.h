@@ -119,7 +119,8 @@ cudaError_t launch_build_quad(int dtype, const void* src, const int s_n[3], void
 size_t cell_bytes(int dtype, const int s_n[3]);
 cudaError_t launch_build_cell(int dtype, const void* src, const int s_n[3], void* dst, cudaStream_t st);
 
-cudaError_t launch_read_frags(const FrameParams& P, const Item* items, int n_items, int cam, int rank,
+// One rank's fragments of one camera, fragment layer `layer` (< P.deep).
+cudaError_t launch_read_frags(const FrameParams& P, const Item* items, int n_items, int cam, int rank, int layer,
                               const float4* frag_rgba, const int* frag_key, float4* out_rgba, int* out_key,
                               cudaStream_t st);
 

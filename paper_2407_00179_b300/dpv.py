@@ -30,6 +30,8 @@ FRAME_QUAD = 64
 FRAME_ISO = 128
 FRAME_ORDERED = 256
 FRAME_SKIP = 512
+FRAME_DEEP = 1024
+DEEP_MAX = 4
 GATHER_FLAGS = {"auto": 0, "cell": FRAME_CELL, "quad": FRAME_QUAD, "linear": FRAME_LINEAR}
 
 
@@ -47,7 +49,7 @@ STATUS = {0: "DPV_OK", 1: "DPV_ERR_INVALID_ARG", 2: "DPV_ERR_STATE", 3: "DPV_ERR
 
 EXPORTS = ["dpvCreateDevice", "dpvSetVolumeGeometry", "dpvCommitBrick", "dpvSetTransferFunction", "dpvSetCameras",
            "dpvSetFrame", "dpvRenderFrame", "dpvFrameReady", "dpvMapFrame", "dpvUnmapFrame", "dpvCopyFrame",
-           "dpvReadFragments", "dpvReadBrick", "dpvMapOrder", "dpvBackward", "dpvGetStats", "dpvResetStats", "dpvSetProfiling", "dpvGetLastError",
+           "dpvReadFragments", "dpvReadDeepFragments", "dpvReadBrick", "dpvMapOrder", "dpvBackward", "dpvGetStats", "dpvResetStats", "dpvSetProfiling", "dpvGetLastError",
            "dpvRelease", "dpvRenderNoAlloc", "dpvAutotune"]
 
 
@@ -129,6 +131,7 @@ def load(path: Optional[str] = None):
         "dpvUnmapFrame": [V, I],
         "dpvCopyFrame": [V, I, V, V],
         "dpvReadFragments": [V, I, I, V, V],
+        "dpvReadDeepFragments": [V, I, I, I, V, V],
         "dpvMapOrder": [V, I, C.POINTER(V), C.POINTER(C.c_int)],
         "dpvReadBrick": [V, I, V, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)],
         "dpvBackward": [V, V, V, V],
@@ -275,24 +278,26 @@ class Device:
     def set_frame(self, width: int, height: int, step_voxels: float = 0.5, sigma_max: float = 8.0, ert: float = 0.0,
                   tile=(0, 0), order: bool = False, staged: bool = False, gather: str = "auto",
                   persistent: bool = False, graph: bool = False, iso: Optional[float] = None,
-                  ordered: bool = False, skip: bool = False):
+                  ordered: bool = False, skip: bool = False, deep: bool = False):
         """gather: "auto" (cell layout where it fits in half of the free
         device memory, else quad), "cell", "quad" or "linear".  iso: render
         iso-surface fragments at that level instead of volume rendering
         (DPV_FRAME_ISO).  ordered: visibility-ordered march with global early
         termination (DPV_FRAME_ORDERED).  skip: empty-space skipping
-        (DPV_FRAME_SKIP)."""
+        (DPV_FRAME_SKIP).  deep: deep fragments (DPV_FRAME_DEEP: skipping
+        splits a brick's segment into up to DEEP_MAX fragments)."""
         if gather not in GATHER_FLAGS:
             raise ValueError("gather must be one of %s" % sorted(GATHER_FLAGS))
         flags = (FRAME_ORDER if order else 0) | (FRAME_STAGED if staged else 0) | GATHER_FLAGS[gather] | (
             FRAME_PERSISTENT if persistent else 0) | (FRAME_GRAPH if graph else 0) | (
-            FRAME_ISO if iso is not None else 0) | (FRAME_ORDERED if ordered else 0) | (FRAME_SKIP if skip else 0)
+            FRAME_ISO if iso is not None else 0) | (FRAME_ORDERED if ordered else 0) | (FRAME_SKIP if skip else 0) | (
+            FRAME_DEEP if deep else 0)
         f = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
                       int(tile[1]), flags, float(iso) if iso is not None else 0.0)
         _check(load().dpvSetFrame(self._h, C.byref(f)))
         self._frame_args = (step_voxels, sigma_max, ert)
         self._frame_kw = {"order": order, "staged": staged, "graph": graph, "iso": iso, "ordered": ordered,
-                          "skip": skip}
+                          "skip": skip, "deep": deep}
         self.width, self.height = int(width), int(height)
 
     # -- rendering ---------------------------------------------------------
@@ -324,10 +329,11 @@ class Device:
         _check(load().dpvCopyFrame(self._h, camera, _ptr(rgba) if rgba is not None else None,
                                    _ptr(depth) if depth is not None else None))
 
-    def read_fragments(self, camera: int, rank: int):
+    def read_fragments(self, camera: int, rank: int, layer: int = 0):
+        """Rank's fragments of one camera (fragment layer `layer` of a deep frame)."""
         rgba = torch.empty((self.height, self.width, 4), dtype=torch.float32, device=self.torch_device)
         key = torch.empty((self.height, self.width), dtype=torch.int32, device=self.torch_device)
-        _check(load().dpvReadFragments(self._h, camera, rank, _ptr(rgba), _ptr(key)))
+        _check(load().dpvReadDeepFragments(self._h, camera, rank, layer, _ptr(rgba), _ptr(key)))
         return rgba, key
 
     def read_brick(self, rank: int):
