@@ -29,6 +29,7 @@ KEY_EMPTY = 2 ** 31 - 1
 FLAG_HIT, FLAG_EXIT_AMBIG, FLAG_OWNER_AMBIG, FLAG_ERT_AMBIG = 1, 2, 4, 8
 FLAG_ISO_AMBIG = 16
 FLAG_MACRO_AMBIG = 32
+FLAG_SHADOW_AMBIG = 64
 ISO_EPS = 5e-5   # iso ambiguity band on s (a rounded sample may cross otherwise)
 
 
@@ -62,6 +63,10 @@ class _Brick(C.Structure):
                 ("scale", C.c_double), ("data", C.c_void_p)]
 
 
+class _Light(C.Structure):
+    _fields_ = [("dir", C.c_double * 3), ("step_voxels", C.c_double), ("ambient", C.c_double)]
+
+
 class _TF(C.Structure):
     _fields_ = [("rgba", C.c_void_p), ("n", C.c_int), ("vmin", C.c_double), ("vmax", C.c_double)]
 
@@ -82,6 +87,8 @@ def lib():
         _lib.orc_render_iso.argtypes = [P, P, C.c_int, P, P, P, P, C.c_double, C.c_double, C.c_int, P, P, P, P, P,
                                         P, P]
         _lib.orc_render_deep.argtypes = [P, C.c_int, P, P, P, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P]
+        _lib.orc_render_shadow.argtypes = [P, P, C.c_int, P, P, P, P, P, C.c_int, P, P, P, P, P, P]
+        _lib.orc_light_transmittance.argtypes = [P, P, C.c_int, P, P, P, P, C.c_int, P, P, P, P]
         _lib.orc_kd_order.argtypes = [C.c_int, P, P, P, P, P, P]
         _lib.orc_kd_order.restype = C.c_int
         _lib.orc_camera_ray.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
@@ -302,6 +309,72 @@ def render_deep(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, de
                           _p(res["rgba"]), _p(res["depth"]), _p(res["frag_rgba"]), _p(res["frag_key"]),
                           _p(res["frag_count"]), _p(res["nsamples"]), _p(res["flags"]))
     return res
+
+
+@dataclass
+class Light:
+    """Directional light: unit direction toward the light, shadow sample
+    spacing h in node units, ambient term k_a."""
+    direction: tuple = (0.0, 0.0, 1.0)
+    step_voxels: float = 1.0
+    ambient: float = 0.25
+
+    def c(self) -> _Light:
+        d = np.asarray(self.direction, np.float64)
+        d = d / np.linalg.norm(d)
+        return _Light((C.c_double * 3)(*d), self.step_voxels, self.ambient)
+
+
+def _source(dims, field, bricks):
+    if (field is None) == (bricks is None):
+        raise ValueError("give exactly one of field and bricks")
+    if bricks is not None:
+        barr, keep = _bricks_c(bricks)
+        return None, len(bricks), barr, keep
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    assert f.shape == (dims[2], dims[1], dims[0])
+    return _p(f), 1, None, f
+
+
+def render_shadow(dims, tf: np.ndarray, cam, frame: Frame, light: Light, field=None, bricks=None, pix=None,
+                  vmin=0.0, vmax=1.0, origin=(0.0, 0.0, 0.0), spacing=None):
+    """FP64 shadowed render: each sample's emission scaled by
+    k_a + (1 - k_a) T_light, T_light the transmittance of its shadow ray
+    toward the directional light.  With `field` the plain definition (no
+    early termination); with `bricks` per-brick fragments (frame.ert per
+    fragment), shadow samples evaluated by their owner bricks, sort-last
+    composite.  Returns rgba, depth, nsamples, nshadow and flags."""
+    g = _grid(dims, origin, spacing)
+    t, tab = _tf(tf, vmin, vmax)
+    cam_c = _camera(cam)
+    fr = frame.c()
+    lc = light.c()
+    f_ptr, K, barr, keep_s = _source(dims, field, bricks)
+    n, pp, keep = _pix(pix, frame)
+    res = {"rgba": np.zeros((n, 4)), "depth": np.zeros(n), "nsamples": np.zeros(n, np.int64),
+           "nshadow": np.zeros(n, np.int64), "flags": np.zeros(n, np.uint8)}
+    lib().orc_render_shadow(C.byref(g), f_ptr, K, barr, C.byref(t), C.byref(cam_c), C.byref(fr), C.byref(lc), n, pp,
+                            _p(res["rgba"]), _p(res["depth"]), _p(res["nsamples"]), _p(res["nshadow"]),
+                            _p(res["flags"]))
+    return res
+
+
+def light_transmittance(dims, tf: np.ndarray, points: np.ndarray, light: Light, sigma_max: float = 8.0,
+                        field=None, bricks=None, vmin=0.0, vmax=1.0, origin=(0.0, 0.0, 0.0), spacing=None):
+    """T_light at node-space points (n, 3); also the shadow sample counts and
+    the face-ambiguity flags."""
+    g = _grid(dims, origin, spacing)
+    t, tab = _tf(tf, vmin, vmax)
+    fr = Frame(1, 1, sigma_max=sigma_max).c()
+    lc = light.c()
+    f_ptr, K, barr, keep_s = _source(dims, field, bricks)
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    T = np.zeros(len(pts))
+    cnt = np.zeros(len(pts), np.int64)
+    amb = np.zeros(len(pts), np.uint8)
+    lib().orc_light_transmittance(C.byref(g), f_ptr, K, barr, C.byref(t), C.byref(fr), C.byref(lc), len(pts),
+                                  _p(pts), _p(T), _p(cnt), _p(amb))
+    return T, cnt, amb
 
 
 def render_ordered(dims, tf: np.ndarray, cam, frame: Frame, field=None, bricks=None, pix=None, vmin=0.0, vmax=1.0,

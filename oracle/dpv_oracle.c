@@ -998,6 +998,186 @@ void orc_render_deep(const orc_grid* g, int K, const orc_brick* bricks, const or
 }
 
 /* ------------------------------------------------------------------------ */
+/* volumetric shadows by ray forwarding                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Readings (the global effect compositing cannot produce, §7 and Fig. 6,
+ * that data-parallel ray tracers get by forwarding ray wave-fronts between
+ * ranks, §2.3; the paper gives no shading equations):
+ *   - one directional light, unit direction L toward the light (node and
+ *     world directions agree: the spacing is uniform);
+ *   - the shadow ray of a sample at node-space point p takes samples at
+ *     p + (i + 1/2) h L, i = 0, 1, ..., while they lie in the volume box
+ *     [0, dims - 1] (the box is convex and p lies in it, so these are the
+ *     first n_s); each attenuates by 1 - alpha_i with
+ *     alpha_i = 1 - exp(-sigma_max a(s_i) h spacing), the same emission-
+ *     absorption model at step h (node units);
+ *   - T_light(p) = prod_i (1 - alpha_i);
+ *   - the sample's emitted colour c becomes c (k_a + (1 - k_a) T_light(p)),
+ *     k_a the ambient term; opacities and the compositing are unchanged;
+ *   - data-parallel form: the primary samples stay with their owner brick
+ *     (per-brick fragments, sort-last composite); each shadow sample is
+ *     evaluated by the brick owning its position, so T_light is the product
+ *     of one partial product per brick the shadow ray crosses (the order
+ *     the bricks take does not change it).
+ * Flag SHADOW_AMBIG: a shadow sample of an evaluated primary sample lies
+ * within 1e-3 node of the box's faces and has alpha > 0 (FP32 positions
+ * may count it otherwise). */
+
+#define ORC_FLAG_SHADOW_AMBIG 64
+
+typedef struct {
+    double dir[3];        /* unit direction toward the light */
+    double step_voxels;   /* h, node units */
+    double ambient;       /* k_a */
+} orc_light;
+
+/* scalar value at node-space point q: the whole field, or the owner brick */
+static double value_at(const orc_grid* g, const float* field, int K, const orc_brick* bricks, const double q[3],
+                       int* hint) {
+    if (field) {
+        int lo[3] = {0, 0, 0};
+        return trilinear(field, ORC_F32, 1.0, lo, g->dims, q, NULL, NULL);
+    }
+    int o = find_owner(g, K, bricks, q, *hint);
+    if (o < 0) o = find_owner(g, K, bricks, q, -1);
+    *hint = o;
+    int bl[3], bn[3];
+    orc_stored_box(g->dims, bricks[o].owned_lo, bricks[o].owned_hi, bl, bn);
+    return trilinear(bricks[o].data, bricks[o].dtype, bricks[o].scale, bl, bn, q, NULL, NULL);
+}
+
+/* signed distance of q to the volume box's faces (negative outside) */
+static double box_margin(const orc_grid* g, const double q[3]) {
+    double m = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        double d0 = q[a], d1 = (g->dims[a] - 1) - q[a];
+        if (d0 < m) m = d0;
+        if (d1 < m) m = d1;
+    }
+    return m;
+}
+
+static double light_transmittance(const orc_grid* g, const float* field, int K, const orc_brick* bricks,
+                                  const orc_tf* tf, const orc_frame* fr, const orc_light* L, const double p[3],
+                                  int* amb, int64_t* count) {
+    double T = 1.0, hw = L->step_voxels * g->spacing;
+    int hint = -1;
+    for (int64_t i = 0;; ++i) {
+        double q[3];
+        for (int a = 0; a < 3; ++a) q[a] = p[a] + (i + 0.5) * L->step_voxels * L->dir[a];
+        double m = box_margin(g, q);
+        if (fabs(m) < 1e-3) {               /* at a face: does counting it matter? */
+            double qc[3], c[3], al;
+            for (int a = 0; a < 3; ++a) qc[a] = q[a] < 0.0 ? 0.0 : q[a] > g->dims[a] - 1 ? g->dims[a] - 1 : q[a];
+            classify(tf, fr, hw, value_at(g, field, K, bricks, qc, &hint), c, &al);
+            if (al > 0.0) *amb = 1;
+        }
+        if (m < 0.0) break;
+        double c[3], al;
+        classify(tf, fr, hw, value_at(g, field, K, bricks, q, &hint), c, &al);
+        T *= 1.0 - al;
+        ++*count;
+    }
+    return T;
+}
+
+/* Shadowed render (readings above).  field != NULL: the plain definition
+ * on the whole float32 field (every sample evaluated from it); else the
+ * partitioned form: per-brick fragments of the owned primary samples with
+ * per-fragment early termination, shadow samples evaluated by their owner
+ * bricks, sort-last composite.  Outputs per listed pixel: rgba, depth,
+ * primary samples evaluated, shadow samples evaluated (for the primary
+ * samples with alpha > 0), flags. */
+void orc_render_shadow(const orc_grid* g, const float* field, int K, const orc_brick* bricks, const orc_tf* tf,
+                       const orc_camera* cam, const orc_frame* fr, const orc_light* L, int npix,
+                       const int32_t* pix, double* rgba, double* depth, int64_t* nsamples, int64_t* nshadow,
+                       uint8_t* flags) {
+    int ert_on = fr->ert > 0.0 && fr->ert < 1.0 && !field;
+    int KK = field ? 1 : K;
+#pragma omp parallel
+    {
+        frag_state* fs = (frag_state*)malloc(sizeof(frag_state) * KK);
+        uint8_t* ord = (uint8_t*)malloc(KK);
+#pragma omp for schedule(dynamic, 4)
+        for (int k = 0; k < npix; ++k) {
+            int p = pix ? pix[k] : k;
+            orc_rayinfo ri;
+            ray_samples(g, cam, fr, p % fr->width, p / fr->width, &ri);
+            int fl = ri.flags, amb = 0, owner = -1, hint = -1;
+            int64_t nsh = 0;
+            for (int b = 0; b < KK; ++b) {
+                fs[b].C[0] = fs[b].C[1] = fs[b].C[2] = 0.0;
+                fs[b].T = 1.0;
+                fs[b].key = ORC_KEY_EMPTY;
+                fs[b].nsamp = 0;
+                fs[b].done = 0;
+            }
+            for (int64_t j = 0; j < ri.n; ++j) {
+                double q[3], tj;
+                sample_point(g, &ri, j, q, &tj);
+                if (field) {
+                    owner = 0;
+                } else {
+                    owner = find_owner(g, K, bricks, q, owner);
+                    if (owner < 0) continue;
+                    if (near_internal_face(g, &bricks[owner], &ri, tj, fr->amb_samples)) fl |= ORC_FLAG_OWNER_AMBIG;
+                }
+                frag_state* f = &fs[owner];
+                if (f->key == ORC_KEY_EMPTY) f->key = j;
+                if (f->done) continue;
+                hint = owner;
+                double s = value_at(g, field, K, bricks, q, &hint);
+                double c[3], al;
+                classify(tf, fr, ri.dt, s, c, &al);
+                if (al > 0.0) {
+                    double Tl = light_transmittance(g, field, K, bricks, tf, fr, L, q, &amb, &nsh);
+                    double w = L->ambient + (1.0 - L->ambient) * Tl;
+                    for (int a = 0; a < 3; ++a) c[a] *= w;
+                }
+                double A_before = 1.0 - f->T;
+                for (int a = 0; a < 3; ++a) f->C[a] += f->T * al * c[a];
+                f->T *= 1.0 - al;
+                f->nsamp++;
+                if (ert_on && 1.0 - f->T > fr->ert) {
+                    f->done = 1;
+                    double m1 = (1.0 - f->T) - fr->ert, m0 = fr->ert - A_before;
+                    if ((m1 < m0 ? m1 : m0) < fr->amb_alpha) fl |= ORC_FLAG_ERT_AMBIG;
+                }
+            }
+            if (amb) fl |= ORC_FLAG_SHADOW_AMBIG;
+            int m = fragment_order(KK, fs, ord);
+            double out[4], dep;
+            composite_pixel(KK, fs, &ri, ord, m, out, &dep);
+            for (int c = 0; c < 4; ++c) rgba[4 * k + c] = out[c];
+            if (depth) depth[k] = dep;
+            int64_t ns = 0;
+            for (int b = 0; b < KK; ++b) ns += fs[b].nsamp;
+            if (nsamples) nsamples[k] = ns;
+            if (nshadow) nshadow[k] = nsh;
+            if (flags) flags[k] = (uint8_t)fl;
+        }
+        free(fs);
+        free(ord);
+    }
+}
+
+/* T_light at arbitrary node-space points (for pins): the field or bricks
+ * as above. */
+void orc_light_transmittance(const orc_grid* g, const float* field, int K, const orc_brick* bricks,
+                             const orc_tf* tf, const orc_frame* fr, const orc_light* L, int n, const double* pts,
+                             double* T, int64_t* count, uint8_t* amb) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < n; ++k) {
+        int a = 0;
+        int64_t c = 0;
+        T[k] = light_transmittance(g, field, K, bricks, tf, fr, L, pts + 3 * k, &a, &c);
+        if (count) count[k] = c;
+        if (amb) amb[k] = (uint8_t)a;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* iso-surface fragments (first hit per brick, depth composite)              */
 /* ------------------------------------------------------------------------ */
 
