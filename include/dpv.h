@@ -157,6 +157,18 @@ typedef struct {
                                       num_ranks x DPV_DEEP_MAX entries per pixel, one brick
                                       id per fragment. */
 #define DPV_DEEP_MAX 4
+#define DPV_FRAME_SHADOW 2048     /* volumetric shadows by ray forwarding: every sample's
+                                      emission is scaled by k_a + (1 - k_a) T_light, T_light
+                                      the transmittance of a shadow ray toward the light of
+                                      dpvSetLight, sampled at p + (i + 1/2) h L inside the
+                                      volume box.  Each brick's samples spawn one wave-front
+                                      of shadow rays; in num_ranks rounds every brick marches
+                                      every wave-front through the samples it owns (a ring
+                                      exchange of full wave-fronts, §2.3), then the shading
+                                      march writes ordinary fragments.  Opacity, keys, depth
+                                      and the composite are those of the sort-last frame.
+                                      Forward only; not with STAGED, ISO, ORDERED, SKIP or
+                                      DEEP.  Needs dpvSetLight. */
 #define DPV_FRAME_ISO 128          /* iso-surface fragments instead of volume rendering
                                       (the paper's z-composited opaque surfaces, §7):
                                       each brick reports the first sample pair (j-1, j)
@@ -211,6 +223,7 @@ typedef struct {
     uint32_t stage_calls[DPV_NUM_STAGES];
     uint64_t kernel_launches;
     uint64_t graph_launches;      /* frames replayed from a CUDA graph since the reset */
+    uint64_t samples_shadow;      /* shadow samples evaluated (DPV_FRAME_SHADOW) */
 } dpv_stats;
 
 /* Create a device for `num_ranks` logical ranks (1..255) on CUDA device
@@ -234,6 +247,12 @@ dpv_status dpvCommitBrick(dpv_device dev, int rank, const dpv_brick_desc* desc);
  * (on_device = 0) or the device; values over [vmin, vmax], vmax > vmin.
  * Copied; visible to the next render. */
 dpv_status dpvSetTransferFunction(dpv_device dev, const float* rgba, int n, float vmin, float vmax, int on_device);
+
+/* Directional light for DPV_FRAME_SHADOW: direction toward the light (any
+ * non-zero length; normalised here), shadow sample spacing h in voxels
+ * (1/64 .. 64), ambient term k_a in [0, 1] (1: no shadows).  Visible to the
+ * next render; DPV_ERR_INVALID_ARG otherwise. */
+dpv_status dpvSetLight(dpv_device dev, const float direction[3], float step_voxels, float ambient);
 
 /* Cameras (host array of n >= 1).  Every render produces one image each. */
 dpv_status dpvSetCameras(dpv_device dev, const dpv_camera* cams, int n);

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -77,6 +78,10 @@ struct dpv_device_t {
     float4* d_tf = nullptr;
     int ntf = 0;
     float vmin = 0.f, vmax = 1.f;
+    bool has_light = false;
+    float light_dir[3] = {0.f, 0.f, 1.f};   // unit, toward the light
+    float light_step = 1.f;                 // h, voxels
+    float light_ambient = 0.25f;            // k_a
 
     std::vector<CamIn> cams;
     CamIn* d_cam_in = nullptr;
@@ -124,6 +129,18 @@ struct dpv_device_t {
     int* d_nb_first = nullptr;          // nranks + 1
     int* d_nb = nullptr;                // nranks * nranks
     long long max_rows = 0;             // most owned (y, z) node rows of a brick
+
+    // shadows by ray forwarding: per slot of the brick-major order its
+    // record count and offset, the wave-fronts' first records, the records
+    int* d_sh_counts = nullptr;
+    long long* d_sh_offsets = nullptr;
+    long long* d_sh_chunks = nullptr;
+    long long* d_sh_total = nullptr;
+    long long* d_rec_first = nullptr;   // nranks + 1
+    size_t sh_slot_cap = 0;
+    float4* d_recs = nullptr;
+    long long rec_cap = 0;
+    long long n_recs = 0;
 
     // persistent schedule (DPV_FRAME_PERSISTENT)
     int* d_sched = nullptr;
@@ -263,6 +280,24 @@ void free_graph(dpv_device dev) {
     dev->graph_failed = false;
 }
 
+void free_shadow(dpv_device dev) {
+    dev_free(dev->d_sh_counts);
+    dev_free(dev->d_sh_offsets);
+    dev_free(dev->d_sh_chunks);
+    dev_free(dev->d_sh_total);
+    dev_free(dev->d_rec_first);
+    dev_free(dev->d_recs);
+    dev->d_sh_counts = nullptr;
+    dev->d_sh_offsets = nullptr;
+    dev->d_sh_chunks = nullptr;
+    dev->d_sh_total = nullptr;
+    dev->d_rec_first = nullptr;
+    dev->d_recs = nullptr;
+    dev->sh_slot_cap = 0;
+    dev->rec_cap = 0;
+    dev->n_recs = 0;
+}
+
 void free_frags(dpv_device dev) {
     dev_free(dev->d_frag_rgba);
     dev_free(dev->d_frag_key);
@@ -343,6 +378,11 @@ dpv_status prepare(dpv_device dev) {
     P.iso_on = (F.flags & DPV_FRAME_ISO) ? 1 : 0;
     P.ordered_on = (F.flags & DPV_FRAME_ORDERED) ? 1 : 0;
     P.skip_on = (F.flags & (DPV_FRAME_SKIP | DPV_FRAME_DEEP)) ? 1 : 0;   // deep fragments skip
+    P.shadow_on = (F.flags & DPV_FRAME_SHADOW) ? 1 : 0;
+    if (P.shadow_on && !dev->has_light) return fail(DPV_ERR_STATE, "DPV_FRAME_SHADOW needs dpvSetLight");
+    for (int a = 0; a < 3; ++a) P.hl[a] = dev->light_step * dev->light_dir[a];
+    P.shadow_dt = dev->light_step * dev->spacing;
+    P.ambient = dev->light_ambient;
     P.iso = F.iso_value;
     P.box_cap = 6144;
     if (const char* env = getenv("DPV_BOX_CAP")) {
@@ -614,6 +654,50 @@ dpv_status prepare(dpv_device dev) {
         if ((s = dev_alloc(dev, (void**)&dev->d_order, nord, "order image"))) return s;
         dev->order_cap = nord;
     }
+    // shadow records: one per primary sample of every brick segment, sized
+    // by one blocking pass over the filled work list
+    if (P.shadow_on) {
+        const size_t slots = (size_t)std::max(1, dev->n_items) * P.tp;
+        if (slots > dev->sh_slot_cap) {
+            free_shadow(dev);
+            if ((s = dev_alloc(dev, (void**)&dev->d_sh_counts, sizeof(int) * slots, "shadow counts"))) return s;
+            if ((s = dev_alloc(dev, (void**)&dev->d_sh_offsets, sizeof(long long) * slots, "shadow offsets")))
+                return s;
+            if ((s = dev_alloc(dev, (void**)&dev->d_sh_chunks,
+                               sizeof(long long) * shadow_chunk_count(P, dev->n_items), "shadow offsets")))
+                return s;
+            if ((s = dev_alloc(dev, (void**)&dev->d_sh_total, sizeof(long long), "shadow offsets"))) return s;
+            if ((s = dev_alloc(dev, (void**)&dev->d_rec_first, sizeof(long long) * (MAX_RANKS + 1), "wave-fronts")))
+                return s;
+            dev->sh_slot_cap = slots;
+        }
+        CK(launch_cull(P, dev->d_cam_in, og, dev->spacing, dev->d_cams, dev->d_camd, dev->d_rays, dev->d_bricks,
+                       dev->d_rects, dev->d_tile_count, dev->d_tile_first, dev->d_items, dev->items_cap,
+                       dev->d_counters, true, dev->stream),
+           "cull (shadow sizing)");
+        CK(launch_schedule(P, dev->d_items, dev->n_items, 1, dev->d_hist, dev->d_offsets, dev->d_cursor,
+                           dev->d_tmp64, dev->d_sched, dev->stream),
+           "schedule (shadow sizing)");
+        CK(launch_shadow_offsets(P, dev->d_cams, dev->d_bricks, dev->d_items, dev->n_items, dev->d_sched,
+                                 dev->d_sh_counts, dev->d_sh_offsets, dev->d_sh_chunks, dev->d_sh_total,
+                                 dev->stream),
+           "shadow sizing");
+        long long total = 0;
+        CK(cudaMemcpyAsync(&total, dev->d_sh_total, sizeof total, cudaMemcpyDeviceToHost, dev->stream),
+           "shadow sizing");
+        CK(cudaStreamSynchronize(dev->stream), "shadow sizing");
+        dev->launches += 14;
+        if (total > dev->rec_cap) {
+            dev_free(dev->d_recs);
+            dev->d_recs = nullptr;
+            dev->rec_cap = 0;
+            if ((s = dev_alloc(dev, (void**)&dev->d_recs, sizeof(float4) * (size_t)std::max(1LL, total),
+                               "shadow rays")))
+                return s;
+            dev->rec_cap = total;
+        }
+        dev->n_recs = total;
+    }
     free_graph(dev);
     dev->dirty = false;
     return DPV_OK;
@@ -636,7 +720,7 @@ dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
                    true, st),
        "cull");
     Schedule sch{dev->d_sched, dev->d_work, 0};
-    if (persistent)
+    if (persistent || P.shadow_on)
         CK(launch_schedule(P, dev->d_items, dev->n_items, 1, dev->d_hist, dev->d_offsets, dev->d_cursor,
                            dev->d_tmp64, dev->d_sched, st),
            "schedule");
@@ -656,7 +740,19 @@ dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
         dev->launches += 6 + 1;
         return DPV_OK;
     }
-    if (iso)
+    if (P.shadow_on) {
+        // shadow rays: records per slot, spawn, the forwarding rounds, the
+        // shading march (fragments as the sort-last march writes them)
+        CK(launch_shadow_offsets(P, dev->d_cams, dev->d_bricks, dev->d_items, dev->n_items, dev->d_sched,
+                                 dev->d_sh_counts, dev->d_sh_offsets, dev->d_sh_chunks, dev->d_sh_total, st),
+           "shadow offsets");
+        CK(launch_shadow_render(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
+                                dev->d_items, dev->n_items, dev->d_sched, dev->d_offsets, dev->d_sh_offsets,
+                                dev->d_sh_total, dev->d_rec_first, dev->n_recs, dev->d_recs, dev->d_tf,
+                                dev->d_frag_rgba, dev->d_frag_key, dev->d_counters, st),
+           "shadow march");
+        dev->launches += 4 + 2 + P.nbricks + 1;
+    } else if (iso)
         CK(launch_iso_fwd(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                           dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_counters,
                           st),
@@ -683,7 +779,7 @@ dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
                                 P.order_stride ? dev->d_order : nullptr, st),
            "composite");
     if (timed) stage_stop(dev, DPV_STAGE_COMPOSITE, t0);
-    dev->launches += 6 + (persistent ? 3 : 0) + (dev->n_items > 0 ? 1 : 0) + 1;
+    dev->launches += 6 + (persistent || P.shadow_on ? 3 : 0) + (dev->n_items > 0 && !P.shadow_on ? 1 : 0) + 1;
     return DPV_OK;
 }
 
@@ -900,6 +996,26 @@ dpv_status dpvSetTransferFunction(dpv_device dev, const float* rgba, int n, floa
     return DPV_OK;
 }
 
+dpv_status dpvSetLight(dpv_device dev, const float direction[3], float step_voxels, float ambient) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!direction) return fail(DPV_ERR_INVALID_ARG, "direction is NULL");
+    const double x = direction[0], y = direction[1], z = direction[2];
+    const double n = std::sqrt(x * x + y * y + z * z);
+    if (!(n > 0.0) || !std::isfinite(n)) return fail(DPV_ERR_INVALID_ARG, "light direction must be finite, non-zero");
+    if (!(step_voxels >= 1.0f / 64.0f && step_voxels <= 64.0f))
+        return fail(DPV_ERR_INVALID_ARG, "shadow step %g not in [1/64, 64] voxels", (double)step_voxels);
+    if (!(ambient >= 0.0f && ambient <= 1.0f)) return fail(DPV_ERR_INVALID_ARG, "ambient not in [0, 1]");
+    dev->light_dir[0] = (float)(x / n);
+    dev->light_dir[1] = (float)(y / n);
+    dev->light_dir[2] = (float)(z / n);
+    dev->light_step = step_voxels;
+    dev->light_ambient = ambient;
+    dev->has_light = true;
+    dev->dirty = true;
+    return DPV_OK;
+}
+
 dpv_status dpvSetCameras(dpv_device dev, const dpv_camera* cams, int n) {
     dpv_status s = check_dev(dev);
     if (s) return s;
@@ -937,6 +1053,9 @@ dpv_status dpvSetFrame(dpv_device dev, const dpv_frame_desc* f) {
         return fail(DPV_ERR_UNSUPPORTED, "empty-space skipping has no staged or iso-surface form");
     if ((f->flags & DPV_FRAME_DEEP) && (f->flags & (DPV_FRAME_STAGED | DPV_FRAME_ISO | DPV_FRAME_ORDERED)))
         return fail(DPV_ERR_UNSUPPORTED, "deep fragments have no staged, iso-surface or ordered form");
+    if ((f->flags & DPV_FRAME_SHADOW) &&
+        (f->flags & (DPV_FRAME_STAGED | DPV_FRAME_ISO | DPV_FRAME_ORDERED | DPV_FRAME_SKIP | DPV_FRAME_DEEP)))
+        return fail(DPV_ERR_UNSUPPORTED, "shadows have no staged, iso-surface, ordered, skipping or deep form");
     if ((f->flags & DPV_FRAME_ISO) && !isfinite(f->iso_value))
         return fail(DPV_ERR_INVALID_ARG, "iso_value must be finite");
     dev->frame = *f;
@@ -1092,6 +1211,7 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
     if (dev->P.iso_on) return fail(DPV_ERR_UNSUPPORTED, "the adjoint is of the volume-rendering mode");
     if (dev->P.ordered_on) return fail(DPV_ERR_UNSUPPORTED, "the adjoint is of the sort-last march");
     if (dev->P.deep > 1) return fail(DPV_ERR_UNSUPPORTED, "the adjoint is of one fragment per brick");
+    if (dev->P.shadow_on) return fail(DPV_ERR_UNSUPPORTED, "the adjoint is of the unshadowed march");
     if (!dL_drgba || !dL_dtf) return fail(DPV_ERR_INVALID_ARG, "gradient pointers NULL");
     DeviceGuard g(dev->cuda_device);
     const FrameParams& P = dev->P;
@@ -1182,6 +1302,7 @@ dpv_status dpvGetStats(dpv_device dev, dpv_stats* out) {
     }
     out->kernel_launches = dev->launches;
     out->graph_launches = dev->graph_launches;
+    out->samples_shadow = c.samples_shadow;
     return DPV_OK;
 }
 
@@ -1292,6 +1413,7 @@ dpv_status dpvRelease(dpv_device dev) {
         }
         dev_free(dev->d_empty);
         dev_free(dev->d_tfz);
+        free_shadow(dev);
         free_schedule(dev);
         free_frags(dev);
         dev_free(dev->d_gface);

@@ -149,6 +149,7 @@ struct Counters {
     unsigned long long n_items;
     unsigned int err;
     unsigned int max_frag;
+    unsigned long long samples_shadow;
 };
 
 // Per-frame constants, passed by value.
@@ -174,6 +175,10 @@ struct FrameParams {
     int ordered_on;    // visibility-ordered march, global early termination
     int skip_on;       // empty-space skipping in the forward march
     int deep;          // fragment layers per work item: 1, or DEEP_LAYERS (deep fragments)
+    int shadow_on;     // volumetric shadows by ray forwarding
+    float hl[3];       // shadow step h L, node units
+    float shadow_dt;   // h in world units (the shadow samples' opacity step)
+    float ambient;     // k_a
     int iso_on;        // iso-surface fragments instead of volume rendering
     float iso;         // their level
     const float4* rays;// per camera and pixel RAY_VECS float4; see k_rays

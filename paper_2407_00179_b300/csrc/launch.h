@@ -66,6 +66,21 @@ cudaError_t launch_build_minmax(int dtype, const void* data, const int s_n[3], f
 cudaError_t launch_classify_empty(int dtype, const FrameParams& P, const BrickDev* bricks, int nbricks,
                                   const float* scales, int max_macro, const float4* tf, int* z, cudaStream_t st);
 
+// Volumetric shadows by ray forwarding (shadow.cu): per slot of the
+// brick-major order its sample count and the exclusive 64-bit offsets of
+// its records (chunk_sums: shadow_chunk_count entries; total: one), then
+// spawn, the K forwarding rounds and the shading march into the fragments.
+size_t shadow_chunk_count(const FrameParams& P, int n_items);
+cudaError_t launch_shadow_offsets(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks,
+                                  const Item* items, int n_items, const int* sched, int* counts, long long* offsets,
+                                  long long* chunk_sums, long long* total, cudaStream_t st);
+cudaError_t launch_shadow_render(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
+                                 const BrickDev* bricks, const float* scales, const Item* items, int n_items,
+                                 const int* sched, const int* item_first, const long long* offsets,
+                                 const long long* total, long long* rec_first, long long max_wave, float4* recs,
+                                 const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
+                                 cudaStream_t st);
+
 // Iso-surface fragments (DPV_FRAME_ISO) and their depth composite.
 cudaError_t launch_iso_fwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                            const BrickDev* bricks, const float* scales, const Item* items, int n_items,

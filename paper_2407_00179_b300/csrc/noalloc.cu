@@ -84,8 +84,8 @@ extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_ca
     if (tw % 8 || th % 4 || tw * th > 256) return na_fail(DPV_ERR_INVALID_ARG, "bad tile size");
     if (((uintptr_t)rgba & 15) || ((uintptr_t)depth & 3)) return na_fail(DPV_ERR_INVALID_ARG, "misaligned output");
     if (!(cam->fovy_deg > 0.0f && cam->fovy_deg < 180.0f)) return na_fail(DPV_ERR_INVALID_ARG, "bad fovy");
-    if (fr->flags & (DPV_FRAME_ISO | DPV_FRAME_ORDERED | DPV_FRAME_SKIP | DPV_FRAME_DEEP))
-        return na_fail(DPV_ERR_UNSUPPORTED, "iso-surface, ordered, skipping and deep frames need dpvRenderFrame");
+    if (fr->flags & (DPV_FRAME_ISO | DPV_FRAME_ORDERED | DPV_FRAME_SKIP | DPV_FRAME_DEEP | DPV_FRAME_SHADOW))
+        return na_fail(DPV_ERR_UNSUPPORTED, "iso-surface, ordered, skipping, deep and shadowed frames need dpvRenderFrame");
 
     // bricks: owned ranges must tile the volume exactly
     std::vector<BrickDev> table(K);

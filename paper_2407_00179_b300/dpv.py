@@ -32,6 +32,7 @@ FRAME_ORDERED = 256
 FRAME_SKIP = 512
 FRAME_DEEP = 1024
 DEEP_MAX = 4
+FRAME_SHADOW = 2048
 GATHER_FLAGS = {"auto": 0, "cell": FRAME_CELL, "quad": FRAME_QUAD, "linear": FRAME_LINEAR}
 
 
@@ -50,7 +51,7 @@ STATUS = {0: "DPV_OK", 1: "DPV_ERR_INVALID_ARG", 2: "DPV_ERR_STATE", 3: "DPV_ERR
 EXPORTS = ["dpvCreateDevice", "dpvSetVolumeGeometry", "dpvCommitBrick", "dpvSetTransferFunction", "dpvSetCameras",
            "dpvSetFrame", "dpvRenderFrame", "dpvFrameReady", "dpvMapFrame", "dpvUnmapFrame", "dpvCopyFrame",
            "dpvReadFragments", "dpvReadDeepFragments", "dpvReadBrick", "dpvMapOrder", "dpvBackward", "dpvGetStats", "dpvResetStats", "dpvSetProfiling", "dpvGetLastError",
-           "dpvRelease", "dpvRenderNoAlloc", "dpvAutotune"]
+           "dpvRelease", "dpvRenderNoAlloc", "dpvAutotune", "dpvSetLight"]
 
 
 class DPVError(RuntimeError):
@@ -97,7 +98,7 @@ class Stats(C.Structure):
     _fields_ = [("samples_forward", C.c_uint64), ("samples_backward", C.c_uint64), ("work_items", C.c_uint64),
                 ("fragment_bytes", C.c_uint64), ("error_flags", C.c_uint32), ("max_fragments", C.c_uint32),
                 ("stage_ms", C.c_double * 5), ("stage_calls", C.c_uint32 * 5), ("kernel_launches", C.c_uint64),
-                ("graph_launches", C.c_uint64)]
+                ("graph_launches", C.c_uint64), ("samples_shadow", C.c_uint64)]
 
 
 _lib = None
@@ -124,6 +125,7 @@ def load(path: Optional[str] = None):
         "dpvCommitBrick": [V, I, C.POINTER(BrickDesc)],
         "dpvSetTransferFunction": [V, V, I, C.c_float, C.c_float, I],
         "dpvSetCameras": [V, C.POINTER(CameraDesc), I],
+        "dpvSetLight": [V, C.POINTER(C.c_float), C.c_float, C.c_float],
         "dpvSetFrame": [V, C.POINTER(FrameDesc)],
         "dpvRenderFrame": [V],
         "dpvFrameReady": [V, I, C.POINTER(C.c_int)],
@@ -266,6 +268,12 @@ class Device:
         self.vmin, self.vmax = vmin, vmax
         self._tf_keep = t
 
+    def set_light(self, direction, step_voxels: float = 1.0, ambient: float = 0.25):
+        """Directional light of DPV_FRAME_SHADOW: direction toward the light,
+        shadow sample spacing in voxels, ambient term k_a."""
+        d = (C.c_float * 3)(*[float(x) for x in direction])
+        _check(load().dpvSetLight(self._h, d, float(step_voxels), float(ambient)))
+
     def set_cameras(self, cams: Iterable):
         cams = list(cams)
         arr = (CameraDesc * len(cams))()
@@ -278,26 +286,28 @@ class Device:
     def set_frame(self, width: int, height: int, step_voxels: float = 0.5, sigma_max: float = 8.0, ert: float = 0.0,
                   tile=(0, 0), order: bool = False, staged: bool = False, gather: str = "auto",
                   persistent: bool = False, graph: bool = False, iso: Optional[float] = None,
-                  ordered: bool = False, skip: bool = False, deep: bool = False):
+                  ordered: bool = False, skip: bool = False, deep: bool = False, shadow: bool = False):
         """gather: "auto" (cell layout where it fits in half of the free
         device memory, else quad), "cell", "quad" or "linear".  iso: render
         iso-surface fragments at that level instead of volume rendering
         (DPV_FRAME_ISO).  ordered: visibility-ordered march with global early
         termination (DPV_FRAME_ORDERED).  skip: empty-space skipping
         (DPV_FRAME_SKIP).  deep: deep fragments (DPV_FRAME_DEEP: skipping
-        splits a brick's segment into up to DEEP_MAX fragments)."""
+        splits a brick's segment into up to DEEP_MAX fragments).  shadow:
+        volumetric shadows by ray forwarding (DPV_FRAME_SHADOW; set_light
+        first)."""
         if gather not in GATHER_FLAGS:
             raise ValueError("gather must be one of %s" % sorted(GATHER_FLAGS))
         flags = (FRAME_ORDER if order else 0) | (FRAME_STAGED if staged else 0) | GATHER_FLAGS[gather] | (
             FRAME_PERSISTENT if persistent else 0) | (FRAME_GRAPH if graph else 0) | (
             FRAME_ISO if iso is not None else 0) | (FRAME_ORDERED if ordered else 0) | (FRAME_SKIP if skip else 0) | (
-            FRAME_DEEP if deep else 0)
+            FRAME_DEEP if deep else 0) | (FRAME_SHADOW if shadow else 0)
         f = FrameDesc(int(width), int(height), float(step_voxels), float(sigma_max), float(ert), int(tile[0]),
                       int(tile[1]), flags, float(iso) if iso is not None else 0.0)
         _check(load().dpvSetFrame(self._h, C.byref(f)))
         self._frame_args = (step_voxels, sigma_max, ert)
         self._frame_kw = {"order": order, "staged": staged, "graph": graph, "iso": iso, "ordered": ordered,
-                          "skip": skip, "deep": deep}
+                          "skip": skip, "deep": deep, "shadow": shadow}
         self.width, self.height = int(width), int(height)
 
     # -- rendering ---------------------------------------------------------
