@@ -63,6 +63,11 @@ CONFIGS = {
     # same frame without skipping
     "mid_ess": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
                     storage="f32", cams="direction", skip=True, tf_cut=0.4),
+    # volumetric shadows by ray forwarding: 256^3 f32, 16 blobs, 2x2x2 bricks,
+    # 512^2, a directional light, one shadow ray per sample at 1 voxel
+    # (forward only); TF transparent below 0.05
+    "shadow": dict(dims=(256, 256, 256), field="diff", splits=(2, 2, 2), ncam=1, width=512, height=512, ert=0.0,
+                   storage="f32", cams="direction", shadow=((-0.4, 0.8, 0.45), 1.0, 0.25), tf_cut=0.05),
     "mid_f16": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
                     storage="f16", cams="direction"),
     # 64^3 f32, 8 blobs, 2x1x1 bricks, 256x256, no ERT
@@ -197,10 +202,15 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
     cam = cams[0]
 
     iso = cfg.get("iso")
+    sh = cfg.get("shadow")
 
     def run(rows):
         pix = np.concatenate([np.arange(W, dtype=np.int32) + W * int(r) for r in rows])
         t = time.perf_counter()
+        if sh is not None:
+            out = oracle.render_shadow(cfg["dims"], tf, cam, fr, oracle.Light(sh[0], step_voxels=sh[1], ambient=sh[2]),
+                                       bricks=bricks, pix=pix)
+            return time.perf_counter() - t, int(out["nsamples"].sum() + out["nshadow"].sum()), len(pix)
         if iso is not None:
             oracle.render_iso(cfg["dims"], tf, cam, fr, iso, bricks=bricks, pix=pix)
             return time.perf_counter() - t, 0, len(pix)
@@ -308,17 +318,20 @@ def run_ours(args, cfg_name, cfg):
     iso = cfg.get("iso")
     ordered = bool(cfg.get("ordered"))
     skip = bool(cfg.get("skip"))
+    shadow = cfg.get("shadow")
+    if shadow is not None:
+        dev.set_light(*shadow)
     dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
-                  tile=(args.tile_w, args.tile_h), iso=iso, ordered=ordered, skip=skip)
+                  tile=(args.tile_w, args.tile_h), iso=iso, ordered=ordered, skip=skip, shadow=shadow is not None)
     tune = None
     if not args.no_autotune:
         tune = dev.autotune(frames=3, cache=args.autotune_cache, key=cfg_name)
         fl = tune["flags"]
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"], tile=tuple(tune["tile"]),
                       gather=dpv.gather_of(fl), persistent=bool(fl & dpv.FRAME_PERSISTENT), iso=iso, ordered=ordered,
-                      skip=skip)
+                      skip=skip, shadow=shadow is not None)
     grad = None
-    if iso is None and not ordered:
+    if iso is None and not ordered and shadow is None:
         # fixed upstream gradient: d/dI of mean (I - I*)^2 with I* from a perturbed TF
         dev.set_tf(torch.from_numpy(inputs.perturb_tf(tf_np, 0)).to(device))
         dev.render()
@@ -368,7 +381,10 @@ def run_ours(args, cfg_name, cfg):
     total_ms = t0.elapsed_time(t1)
     fwd_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
     bwd_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
-    n_fwd = st["samples_forward"] * args.steps          # per step counts are deterministic
+    # samples per step (deterministic); shadowed frames count the shadow
+    # samples the forwarding rounds evaluate too
+    per_step = st["samples_forward"] + (st["samples_shadow"] if shadow is not None else 0)
+    n_fwd = per_step * args.steps
     n_bwd = st["samples_backward"] * args.steps
     launches = st["kernel_launches"]
     frames = ncam * args.steps
@@ -378,7 +394,7 @@ def run_ours(args, cfg_name, cfg):
     bpv = BYTES_PER_VOXEL[cfg["storage"]]
     march_ms = st["stage_ms"]["march"] / max(1, st["stage_calls"]["march"])
     march_bwd_ms = st["stage_ms"]["march_bwd"] / max(1, st["stage_calls"]["march_bwd"])
-    bytes_per_launch = st["samples_forward"] * 8 * bpv
+    bytes_per_launch = per_step * 8 * bpv
     achieved = bytes_per_launch / (march_ms * 1e-3) / 1e9
     bwd_achieved = st["samples_backward"] * (8 * bpv + 8 * 4) / (march_bwd_ms * 1e-3) / 1e9 if grad is not None else 0.0
     peak, peak_kind = _peaks()
@@ -565,7 +581,7 @@ def run_ours(args, cfg_name, cfg):
             dev.copy_frame(c, frame_host[c])
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - w0
-    (e2e_s,), (e2e_n,) = reduce_over_ranks(pg, device, [e2e_s], [st["samples_forward"] * e2e_steps])
+    (e2e_s,), (e2e_n,) = reduce_over_ranks(pg, device, [e2e_s], [per_step * e2e_steps])
     e2e_val = e2e_n / e2e_s / 1e9
     value = n_fwd / (fwd_ms * 1e-3) / 1e9
     line = {
@@ -585,7 +601,8 @@ def run_ours(args, cfg_name, cfg):
                    "cameras_per_gpu": ncam, "image": [W, H], "storage": cfg["storage"], "ert": cfg["ert"],
                    "step_voxels": 0.5, "sigma_max": cfg.get("sigma_max", 8.0), "mode": (
                        "iso-surface" if iso is not None else "ordered" if ordered else "sort-last") + (
-                       ", empty-space skipping" if skip else ""),
+                       ", empty-space skipping" if skip else "") + (
+                       ", shadows by ray forwarding" if shadow is not None else ""),
                    "tile": list(tune["tile"]) if tune else [args.tile_w or 16, args.tile_h or 16],
                    "l2": "inputs larger than L2 (%d MiB volume), no flush" % (
                        np.prod(cfg["dims"]) * bpv // 2 ** 20),
@@ -603,11 +620,16 @@ def run_ours(args, cfg_name, cfg):
                         "samples evaluated up to each brick's first hit / forward time (cull + iso march + depth "
                         "composite); iso-surface frames have no adjoint, a step is the forward frame"
                         if iso is not None else
+                        "primary + shadow samples evaluated / forward time (cull, shadow-ray spawn, %d forwarding "
+                        "rounds, shading march, composite); shadowed frames have no adjoint, a step is the forward "
+                        "frame" % part.num_ranks
+                        if shadow is not None else
                         "samples evaluated up to the global termination / forward time (cull + ordered march); "
                         "ordered frames have no adjoint, a step is the forward frame"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": TRAFFIC.get((cfg_name, "march")),
                      "kernel": ("k_iso_fwd<%s>" if iso is not None else "k_march_ordered<%s>" if ordered
+                                else "k_shadow_round<%s> + k_march_shadowed (march stage)" if shadow is not None
                                 else "k_march_fwd<%s>") % cfg["storage"],
                      "model": "stencil bytes: 8 corners x %d B per evaluated sample" % bpv,
                      "peak_kind": peak_kind},
@@ -631,6 +653,12 @@ def run_ours(args, cfg_name, cfg):
         line["storage_comparison"] = storage_cmp
     if order_cmp:
         line["sort_last_comparison"] = order_cmp
+    if shadow is not None:
+        line["shadow"] = {"light_direction": list(shadow[0]), "shadow_step_voxels": shadow[1], "ambient": shadow[2],
+                          "primary_samples_per_step": st["samples_forward"],
+                          "shadow_samples_per_step": st["samples_shadow"],
+                          "wave_front_rounds": part.num_ranks}
+        line["config"]["tf_transparent_below"] = cfg["tf_cut"]
     if skip_cmp:
         line["skip_comparison"] = skip_cmp
         line["config"]["tf_transparent_below"] = cfg["tf_cut"]

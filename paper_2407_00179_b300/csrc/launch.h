@@ -77,7 +77,7 @@ cudaError_t launch_shadow_offsets(const FrameParams& P, const CamBasis* cams, co
 cudaError_t launch_shadow_render(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                                  const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                                  const int* sched, const int* item_first, const long long* offsets,
-                                 const long long* total, long long* rec_first, long long max_wave, float4* recs,
+                                 const long long* total, long long* rec_first, long long n_recs, float4* recs,
                                  const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
                                  cudaStream_t st);
 

@@ -151,26 +151,30 @@ __device__ __forceinline__ bool owns(const BrickDev& b, const float p[3]) {
     return true;
 }
 
-// Round r: brick (w + r) mod K marches every ray of wave-front w = blockIdx.y
-// through the shadow samples it owns.
+// Round r: brick (w + r) mod K marches every ray of wave-front w through
+// the shadow samples it owns.  One grid covers the records of all
+// wave-fronts evenly (wave-fronts differ in size); a record's wave-front is
+// found in the K + 1 first-record offsets.
 template <typename T, int GL>
 __global__ void __launch_bounds__(256) k_shadow_round(FrameParams P, const BrickDev* bricks, const float* scales,
                                                       const float4* tf, const long long* rec_first, int round,
                                                       float4* recs, Counters* counters) {
     extern __shared__ float4 s_tf[];
+    __shared__ long long s_first[MAX_RANKS + 1];
     for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
+    for (int i = threadIdx.x; i <= P.nbricks; i += blockDim.x) s_first[i] = rec_first[i];
     __syncthreads();
-    const int w = blockIdx.y;
-    const int bi = (w + round) % P.nbricks;
-    const BrickDev b = bricks[bi];
-    const float scale = scales[b.scale_idx];
-    const T* data = (const T*)b.data;
-    const long long r0 = rec_first[w], r1 = rec_first[w + 1];
+    const long long total = s_first[P.nbricks];
     const float hl[3] = {P.hl[0], P.hl[1], P.hl[2]};
-    const int lim[3] = {b.s_n[0] - 2, b.s_n[1] - 2, b.s_n[2] - 2};
     unsigned long long nsamp = 0;
-    for (long long r = r0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; r < r1;
+    int w = 0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < total;
          r += (long long)gridDim.x * blockDim.x) {
+        while (w + 1 < P.nbricks && r >= s_first[w + 1]) ++w;     // records ascend: w only grows
+        const BrickDev& b = bricks[(w + round) % P.nbricks];
+        const float scale = scales[b.scale_idx];
+        const T* data = (const T*)b.data;
+        const int lim[3] = {b.s_n[0] - 2, b.s_n[1] - 2, b.s_n[2] - 2};
         float4 rec = recs[r];
         const float o[3] = {rec.x, rec.y, rec.z};
         // the step interval t (sample i at t = i + 1/2) inside the owned box,
@@ -282,19 +286,17 @@ __global__ void __launch_bounds__(256) k_march_shadowed(FrameParams P, const Cam
 template <typename T, int GL>
 void rounds_and_shade(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                       const Item* items, int n_items, const int* sched, const long long* offsets,
-                      const long long* rec_first, long long max_wave, float4* recs, const float4* tf,
+                      const long long* rec_first, long long n_recs, float4* recs, const float4* tf,
                       float4* frag_rgba, int* frag_key, Counters* counters, cudaStream_t st) {
     const size_t smem = sizeof(float4) * P.ntf;
     if (smem > 48 * 1024) {
         cudaFuncSetAttribute(k_shadow_round<T, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_march_shadowed<T, GL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    // wave-fronts x chunks: about 8 CTAs of 256 per SM over all wave-fronts
-    int per_wave = (int)std::min<long long>((max_wave + 255) / 256, std::max(1, 148 * 8 / std::max(1, P.nbricks)));
-    per_wave = std::max(1, per_wave);
+    // one grid over every wave-front's records: 16 CTAs of 256 per SM
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n_recs + 255) / 256, 148LL * 16));
     for (int r = 0; r < P.nbricks; ++r)
-        k_shadow_round<T, GL><<<dim3(per_wave, P.nbricks), 256, smem, st>>>(P, bricks, scales, tf, rec_first, r,
-                                                                             recs, counters);
+        k_shadow_round<T, GL><<<grid, 256, smem, st>>>(P, bricks, scales, tf, rec_first, r, recs, counters);
     k_march_shadowed<T, GL><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, sched, offsets, recs, tf,
                                                          frag_rgba, frag_key, counters);
 }
@@ -321,7 +323,7 @@ size_t shadow_chunk_count(const FrameParams& P, int n_items) {
 cudaError_t launch_shadow_render(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                                  const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                                  const int* sched, const int* item_first, const long long* offsets,
-                                 const long long* total, long long* rec_first, long long max_wave, float4* recs,
+                                 const long long* total, long long* rec_first, long long n_recs, float4* recs,
                                  const float4* tf, float4* frag_rgba, int* frag_key, Counters* counters,
                                  cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
@@ -329,7 +331,7 @@ cudaError_t launch_shadow_render(int dtype, int gather, const FrameParams& P, co
                                                              rec_first);
     k_shadow_spawn<<<n_items, P.tp, 0, st>>>(P, cams, bricks, items, sched, offsets, recs);
 #define SHADE(T, GL)                                                                                          \
-    rounds_and_shade<T, GL>(P, cams, bricks, scales, items, n_items, sched, offsets, rec_first, max_wave, recs, \
+    rounds_and_shade<T, GL>(P, cams, bricks, scales, items, n_items, sched, offsets, rec_first, n_recs, recs, \
                             tf, frag_rgba, frag_key, counters, st)
 #define SHADE_T(T)                                                                                            \
     (gather == GATHER_CELL ? SHADE(T, GATHER_CELL) : gather == GATHER_QUAD ? SHADE(T, GATHER_QUAD)           \
