@@ -285,6 +285,20 @@ dpv_status dpvUnmapFrame(dpv_device dev, int camera);
  * after the copy has been issued (host destinations: after it completed). */
 dpv_status dpvCopyFrame(dpv_device dev, int camera, float* rgba, float* depth);
 
+/* Asynchronous copy of camera `camera`'s frame (camera = -1: every camera's,
+ * in camera order, contiguous) into caller buffers (host or device; either
+ * pointer may be NULL).  The frame is first copied on the device stream into
+ * one of two device staging slots; a separate copy stream then moves it to
+ * the destination while the device stream goes on with the next render.
+ * Returns at once.  The destination is complete after dpvCopyWait.  A third
+ * copy in flight waits on the device stream until the slot it reuses has
+ * drained.  Destinations in pageable host memory copy synchronously with
+ * respect to the host (CUDA's rule); pinned memory overlaps. */
+dpv_status dpvCopyFrameAsync(dpv_device dev, int camera, float* rgba, float* depth);
+
+/* Block until every copy dpvCopyFrameAsync issued has completed. */
+dpv_status dpvCopyWait(dpv_device dev);
+
 /* Debug/test: write rank `rank`'s fragments for camera `camera` into caller
  * device buffers rgba (height x width x 4, premultiplied) and key (height x
  * width int32; 2^31 - 1 = empty, also for pixels the rank was culled from). */

@@ -151,6 +151,16 @@ struct dpv_device_t {
     unsigned int* d_work = nullptr;
     size_t sched_cap = 0;
 
+    // asynchronous frame copies (dpvCopyFrameAsync): two staging slots,
+    // each the frames of every camera, drained by a copy stream
+    cudaStream_t copy_stream = nullptr;
+    float4* d_stage_rgba[2] = {nullptr, nullptr};
+    float* d_stage_depth[2] = {nullptr, nullptr};
+    size_t stage_cap = 0;               // pixels per slot
+    cudaEvent_t ev_staged[2] = {nullptr, nullptr};
+    cudaEvent_t ev_drained[2] = {nullptr, nullptr};
+    int stage_next = 0;
+
     // CUDA graph of the per-frame launches (DPV_FRAME_GRAPH)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -1153,6 +1163,71 @@ dpv_status dpvCopyFrame(dpv_device dev, int camera, float* rgba, float* depth) {
     return DPV_OK;
 }
 
+dpv_status dpvCopyFrameAsync(dpv_device dev, int camera, float* rgba, float* depth) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!dev->rendered) return fail(DPV_ERR_STATE, "no frame rendered yet");
+    if (camera < -1 || camera >= dev->P.ncam) return fail(DPV_ERR_INVALID_ARG, "camera %d out of range", camera);
+    DeviceGuard g(dev->cuda_device);
+    const size_t per = (size_t)dev->P.W * dev->P.H;
+    const size_t n = camera < 0 ? per * dev->P.ncam : per;
+    const size_t off = camera < 0 ? 0 : per * camera;
+    if (!dev->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&dev->copy_stream, cudaStreamNonBlocking), "copy stream");
+        for (int k = 0; k < 2; ++k) {
+            CK(cudaEventCreateWithFlags(&dev->ev_staged[k], cudaEventDisableTiming), "copy events");
+            CK(cudaEventCreateWithFlags(&dev->ev_drained[k], cudaEventDisableTiming), "copy events");
+        }
+    }
+    if (n > dev->stage_cap) {
+        CK(cudaStreamSynchronize(dev->copy_stream), "copy stream");
+        for (int k = 0; k < 2; ++k) {
+            dev_free(dev->d_stage_rgba[k]);
+            dev_free(dev->d_stage_depth[k]);
+            dev->d_stage_rgba[k] = nullptr;
+            dev->d_stage_depth[k] = nullptr;
+        }
+        dev->stage_cap = 0;
+        for (int k = 0; k < 2; ++k) {
+            if ((s = dev_alloc(dev, (void**)&dev->d_stage_rgba[k], sizeof(float4) * n, "copy staging"))) return s;
+            if ((s = dev_alloc(dev, (void**)&dev->d_stage_depth[k], sizeof(float) * n, "copy staging"))) return s;
+        }
+        dev->stage_cap = n;
+    }
+    const int k = dev->stage_next;
+    dev->stage_next ^= 1;
+    // the slot's previous drain must be done before the device stream
+    // overwrites it; the drain then runs beside the next render
+    CK(cudaStreamWaitEvent(dev->stream, dev->ev_drained[k], 0), "copy order");
+    if (rgba)
+        CK(cudaMemcpyAsync(dev->d_stage_rgba[k], dev->d_out_rgba + off, sizeof(float4) * n, cudaMemcpyDeviceToDevice,
+                           dev->stream),
+           "stage frame");
+    if (depth)
+        CK(cudaMemcpyAsync(dev->d_stage_depth[k], dev->d_out_depth + off, sizeof(float) * n,
+                           cudaMemcpyDeviceToDevice, dev->stream),
+           "stage frame");
+    CK(cudaEventRecord(dev->ev_staged[k], dev->stream), "copy order");
+    CK(cudaStreamWaitEvent(dev->copy_stream, dev->ev_staged[k], 0), "copy order");
+    if (rgba)
+        CK(cudaMemcpyAsync(rgba, dev->d_stage_rgba[k], sizeof(float4) * n, cudaMemcpyDefault, dev->copy_stream),
+           "copy frame");
+    if (depth)
+        CK(cudaMemcpyAsync(depth, dev->d_stage_depth[k], sizeof(float) * n, cudaMemcpyDefault, dev->copy_stream),
+           "copy frame");
+    CK(cudaEventRecord(dev->ev_drained[k], dev->copy_stream), "copy order");
+    return DPV_OK;
+}
+
+dpv_status dpvCopyWait(dpv_device dev) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!dev->copy_stream) return DPV_OK;
+    DeviceGuard g(dev->cuda_device);
+    CK(cudaStreamSynchronize(dev->copy_stream), "copy wait");
+    return DPV_OK;
+}
+
 dpv_status dpvReadDeepFragments(dpv_device dev, int camera, int rank, int layer, float* rgba, int32_t* key) {
     dpv_status s = check_dev(dev);
     if (s) return s;
@@ -1435,6 +1510,16 @@ dpv_status dpvRelease(dpv_device dev) {
         dev_free(dev->d_hist);
         dev_free(dev->d_tmp64);
         free_graph(dev);
+        if (dev->copy_stream) {
+            cudaStreamSynchronize(dev->copy_stream);
+            cudaStreamDestroy(dev->copy_stream);
+        }
+        for (int k = 0; k < 2; ++k) {
+            dev_free(dev->d_stage_rgba[k]);
+            dev_free(dev->d_stage_depth[k]);
+            if (dev->ev_staged[k]) cudaEventDestroy(dev->ev_staged[k]);
+            if (dev->ev_drained[k]) cudaEventDestroy(dev->ev_drained[k]);
+        }
         if (dev->cap_stream) cudaStreamDestroy(dev->cap_stream);
         if (dev->ev_done) cudaEventDestroy(dev->ev_done);
         for (auto& t : dev->pending) {

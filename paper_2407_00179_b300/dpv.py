@@ -51,7 +51,7 @@ STATUS = {0: "DPV_OK", 1: "DPV_ERR_INVALID_ARG", 2: "DPV_ERR_STATE", 3: "DPV_ERR
 EXPORTS = ["dpvCreateDevice", "dpvSetVolumeGeometry", "dpvCommitBrick", "dpvSetTransferFunction", "dpvSetCameras",
            "dpvSetFrame", "dpvRenderFrame", "dpvFrameReady", "dpvMapFrame", "dpvUnmapFrame", "dpvCopyFrame",
            "dpvReadFragments", "dpvReadDeepFragments", "dpvReadBrick", "dpvMapOrder", "dpvBackward", "dpvGetStats", "dpvResetStats", "dpvSetProfiling", "dpvGetLastError",
-           "dpvRelease", "dpvRenderNoAlloc", "dpvAutotune", "dpvSetLight"]
+           "dpvRelease", "dpvRenderNoAlloc", "dpvAutotune", "dpvSetLight", "dpvCopyFrameAsync", "dpvCopyWait"]
 
 
 class DPVError(RuntimeError):
@@ -132,6 +132,8 @@ def load(path: Optional[str] = None):
         "dpvMapFrame": [V, I, C.POINTER(V), C.POINTER(V)],
         "dpvUnmapFrame": [V, I],
         "dpvCopyFrame": [V, I, V, V],
+        "dpvCopyFrameAsync": [V, I, V, V],
+        "dpvCopyWait": [V],
         "dpvReadFragments": [V, I, I, V, V],
         "dpvReadDeepFragments": [V, I, I, I, V, V],
         "dpvMapOrder": [V, I, C.POINTER(V), C.POINTER(C.c_int)],
@@ -338,6 +340,16 @@ class Device:
     def copy_frame(self, camera: int, rgba: Optional[torch.Tensor], depth: Optional[torch.Tensor] = None):
         _check(load().dpvCopyFrame(self._h, camera, _ptr(rgba) if rgba is not None else None,
                                    _ptr(depth) if depth is not None else None))
+
+    def copy_frame_async(self, camera: int, rgba: Optional[torch.Tensor], depth: Optional[torch.Tensor] = None):
+        """Issue the copy of camera's frame (camera -1: all cameras) and
+        return; the destination is complete after copy_wait().  It runs on a
+        copy stream beside the next render (pinned host memory overlaps)."""
+        _check(load().dpvCopyFrameAsync(self._h, camera, _ptr(rgba) if rgba is not None else None,
+                                        _ptr(depth) if depth is not None else None))
+
+    def copy_wait(self):
+        _check(load().dpvCopyWait(self._h))
 
     def read_fragments(self, camera: int, rank: int, layer: int = 0):
         """Rank's fragments of one camera (fragment layer `layer` of a deep frame)."""

@@ -155,5 +155,8 @@ def test_face_buffer_matches_scalar_atomics(monkeypatch, split):
     assert l1 == l0 + 1                      # the gather ran on the face path only
     assert float(dvol0.abs().max()) > 0
     assert torch.allclose(dvol1, dvol0, rtol=1e-5, atol=1e-6 * float(dvol0.abs().max()))
-    assert torch.allclose(dtf1, dtf0, rtol=1e-5, atol=1e-9 * float(dtf0.abs().max()))
+    # TF entries are FP32 shared-memory sums in atomic order before the FP64
+    # table: an entry whose contributions cancel keeps their rounding,
+    # about 1e-7 of the table's largest entry
+    assert torch.allclose(dtf1, dtf0, rtol=1e-5, atol=1e-6 * float(dtf0.abs().max()))
     dev.release()

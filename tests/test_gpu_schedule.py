@@ -106,3 +106,43 @@ def test_autotune_choice_renders_the_same_frame(tmp_path):
     _same_frames(ref, dev2, sc)
     for d in (ref, dev, dev2):
         d.release()
+
+
+def test_async_frame_copies_in_flight():
+    """dpvCopyFrameAsync: frames of successive renders (different TFs)
+    copied to pinned host memory while the next render runs, more copies in
+    flight than staging slots, single cameras and all cameras at once: each
+    destination holds the frame of the render before its copy."""
+    sc = _scene(0)
+    dev = _device(sc)
+    ncam, H, W = len(sc.cams), sc.height, sc.width
+    tfs = [inputs.make_tf(1234), inputs.make_tf(77), inputs.make_tf(5), inputs.make_tf(9)]
+    want, outs = [], []
+    for k, tf in enumerate(tfs):
+        dev.set_tf(torch.from_numpy(tf).cuda())
+        dev.render()
+        if k % 2 == 0:
+            rgba = torch.empty((ncam, H, W, 4), dtype=torch.float32).pin_memory()
+            depth = torch.empty((ncam, H, W), dtype=torch.float32).pin_memory()
+            dev.copy_frame_async(-1, rgba, depth)
+            outs.append((rgba, depth))
+            want.append([t.clone() for c in range(ncam) for t in dev.map_frame(c)])
+        else:
+            rgba = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+            dev.copy_frame_async(ncam - 1, rgba, None)
+            outs.append((rgba, None))
+            want.append([dev.map_frame(ncam - 1)[0].clone()])
+    dev.copy_wait()
+    torch.cuda.synchronize()
+    for k, ((rgba, depth), w) in enumerate(zip(outs, want)):
+        if depth is not None:
+            for c in range(ncam):
+                assert torch.equal(rgba[c], w[2 * c].cpu())
+                assert torch.equal(depth[c], w[2 * c + 1].cpu())
+        else:
+            assert torch.equal(rgba, w[0].cpu())
+    # successive frames differ, so a stale slot would show
+    assert not torch.equal(outs[0][0][ncam - 1], outs[1][0])
+    with pytest.raises(dpv.DPVError, match="INVALID_ARG"):
+        dev.copy_frame_async(ncam, outs[1][0], None)
+    dev.release()
