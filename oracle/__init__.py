@@ -81,7 +81,7 @@ def lib():
         P = C.c_void_p
         _lib.orc_render_full.argtypes = [P, P, P, P, P, C.c_int, P, P, P, P]
         _lib.orc_render_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P, P, P, P, P]
-        _lib.orc_grad_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, C.c_double]
+        _lib.orc_grad_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, C.c_double, P]
         _lib.orc_composite.argtypes = [C.c_int, C.c_int, P, P, P, P]
         _lib.orc_render_ordered.argtypes = [P, P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P]
         _lib.orc_render_iso.argtypes = [P, P, C.c_int, P, P, P, P, C.c_double, C.c_double, C.c_int, P, P, P, P, P,
@@ -444,7 +444,8 @@ KNOT_EPS = 4e-3   # knot ambiguity band, in TF entries (u units)
 
 
 def grad_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, grad_rgba: np.ndarray, pix=None,
-                vmin=0.0, vmax=1.0, want_volume=True, origin=(0.0, 0.0, 0.0), spacing=None, knot_eps=None):
+                vmin=0.0, vmax=1.0, want_volume=True, origin=(0.0, 0.0, 0.0), spacing=None, knot_eps=None,
+                tf_amb=False):
     """FP64 reverse-mode gradient of sum(grad_rgba * image) with respect to the
     TF table (n x 4) and the global field (nz, ny, nx).
 
@@ -453,7 +454,13 @@ def grad_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, gr
     correct gradient may lie from the returned one because samples within
     knot_eps of a TF knot may take either one-sided slope there.  The lerp's
     derivative jumps at such knots, so an s rounded to the other side of one
-    gives the other, equally correct, derivative."""
+    gives the other, equally correct, derivative.
+
+    With tf_amb also returns the TF-coordinate ambiguity of the TF gradient
+    (n x 4): per entry, the sum over samples of du |g| with
+    du = 2^-22 max(u, 1), how far an FP32 u (about three roundings of
+    2^-24 u) may move the split of a sample's value adjoint g between the
+    entries i0 and i0 + 1."""
     g = _grid(dims, origin, spacing)
     t, tab = _tf(tf, vmin, vmax)
     cam_c = _camera(cam)
@@ -465,12 +472,12 @@ def grad_bricks(dims, bricks: List[Brick], tf: np.ndarray, cam, frame: Frame, gr
     dtf = np.zeros((tab.shape[0], 4))
     dvol = np.zeros((dims[2], dims[1], dims[0])) if want_volume else None
     damb = np.zeros((dims[2], dims[1], dims[0])) if knot_eps is not None else None
+    tamb = np.zeros_like(dtf) if tf_amb else None
     lib().orc_grad_bricks(C.byref(g), K, barr, C.byref(t), C.byref(cam_c), C.byref(fr), n, pp, _p(gr), _p(dtf),
                           _p(dvol) if dvol is not None else None, _p(damb) if damb is not None else None,
-                          float(knot_eps or 0.0))
-    if knot_eps is not None:
-        return dtf, dvol, damb
-    return dtf, dvol
+                          float(knot_eps or 0.0), _p(tamb) if tamb is not None else None)
+    out = (dtf, dvol) + ((damb,) if knot_eps is not None else ()) + ((tamb,) if tf_amb else ())
+    return out
 
 
 def composite(frag_rgba: np.ndarray, frag_key: np.ndarray):

@@ -1454,15 +1454,25 @@ static double seg_slope(const orc_tf* tf, int k, int c) {
  * collects, per voxel, |ds-adjoint with the other segment - with the chosen
  * one| times the trilinear weight: how far a correct gradient may lie from
  * dvol.  Both sides of m use the same value adjoints, since the TF value is
- * continuous there. */
+ * continuous there.
+ *
+ * TF-coordinate ambiguity (optional dtf_amb, n x 4, accumulated): a sample
+ * splits its value adjoint g between entries i0 and i0 + 1 with weights
+ * 1 - w and w, w = u - i0.  An FP32 u carries about 3 roundings of 2^-24 u
+ * (the sample value, the scale, the product), so w may move by
+ * du = 2^-22 max(u, 1), which moves each of the two entries by du |g|
+ * (per channel); past a knot the same du moves the sample's weight between
+ * neighbouring entries by the same amount.  dtf_amb sums du |g| over the
+ * samples: how far a correct TF gradient may lie from dtf. */
 void orc_grad_bricks(const orc_grid* g, int K, const orc_brick* bricks, const orc_tf* tf, const orc_camera* cam,
                      const orc_frame* fr, int npix, const int32_t* pix, const double* grad_rgba, double* dtf,
-                     double* dvol, double* damb, double knot_eps) {
+                     double* dvol, double* damb, double knot_eps, double* dtf_amb) {
     int nthreads = 1;
 #ifdef _OPENMP
     nthreads = omp_get_max_threads();
 #endif
     double* dtf_priv = (double*)calloc((size_t)nthreads * tf->n * 4, sizeof(double));
+    double* amb_priv = dtf_amb ? (double*)calloc((size_t)nthreads * tf->n * 4, sizeof(double)) : NULL;
 #pragma omp parallel
     {
         int tid = 0;
@@ -1470,6 +1480,7 @@ void orc_grad_bricks(const orc_grid* g, int K, const orc_brick* bricks, const or
         tid = omp_get_thread_num();
 #endif
         double* my_dtf = dtf_priv + (size_t)tid * tf->n * 4;
+        double* my_amb = amb_priv ? amb_priv + (size_t)tid * tf->n * 4 : NULL;
         frag_state* fs = (frag_state*)malloc(sizeof(frag_state) * K);
         uint8_t* ord = (uint8_t*)malloc(K);
         size_t cap = 1024;
@@ -1573,6 +1584,13 @@ void orc_grad_bricks(const orc_grid* g, int K, const orc_brick* bricks, const or
                         my_dtf[4 * (e->i0 + 1) + c] += e->w * gv[c];
                         gw += gv[c] * (tf->rgba[4 * (e->i0 + 1) + c] - tf->rgba[4 * e->i0 + c]);
                     }
+                    if (my_amb) {
+                        double du = ldexp(e->u > 1.0 ? e->u : 1.0, -22);
+                        for (int c = 0; c < 4; ++c) {
+                            my_amb[4 * e->i0 + c] += du * fabs(gv[c]);
+                            my_amb[4 * (e->i0 + 1) + c] += du * fabs(gv[c]);
+                        }
+                    }
                     double gs = gw * e->duds;
                     double gs_amb = 0.0;
                     if (damb) {
@@ -1622,8 +1640,12 @@ void orc_grad_bricks(const orc_grid* g, int K, const orc_brick* bricks, const or
         free(fs); free(ord); free(tape); free(perm); free(first); free(count); free(bl); free(bn);
     }
     for (int t = 0; t < nthreads; ++t)
-        for (int i = 0; i < tf->n * 4; ++i) dtf[i] += dtf_priv[(size_t)t * tf->n * 4 + i];
+        for (int i = 0; i < tf->n * 4; ++i) {
+            dtf[i] += dtf_priv[(size_t)t * tf->n * 4 + i];
+            if (dtf_amb) dtf_amb[i] += amb_priv[(size_t)t * tf->n * 4 + i];
+        }
     free(dtf_priv);
+    free(amb_priv);
 }
 
 int orc_max_threads(void) {

@@ -127,6 +127,10 @@ def grad_checks(gpu, ref, what, kappa=None, amb=None):
               int((a > 0).sum()),
               ", ".join("gpu %.6e ref %.6e kappa %.1e amb %.1e (|ref|/max %.1e)" % (
                   gpu[big][i], ref[big][i], k[big][i], a[big][i], abs(ref[big][i]) / m) for i in w)))
+    for i in np.flatnonzero(viol.reshape(-1))[:4]:
+        print("  beyond: index %d gpu %.6e ref %.6e bound %.2e (kappa %.1e, |ref|/max %.1e)" % (
+            i, gpu.reshape(-1)[i], ref.reshape(-1)[i], bound.reshape(-1)[i], k.reshape(-1)[i],
+            abs(ref.reshape(-1)[i]) / m))
     return l2, int(viol.sum())
 
 

@@ -150,3 +150,28 @@ def test_knot_ambiguity_covers_the_one_sided_jump(orc):
     # equal corners: s is exact, so it stays on its side of the knot
     _, dv_flat, amb_flat = _knot_problem(orc, above, kinked)
     assert np.abs(dv_flat).max() > 0 and amb_flat.max() == 0.0
+
+
+def test_tf_coordinate_ambiguity_closed_form(orc):
+    """With a two-entry table every sample splits its value adjoint between
+    entries 0 and 1 (u in [0, 1], du = 2^-22); where every adjoint of a
+    channel has one sign (colour channels under a non-negative image
+    gradient: T alpha g >= 0) the ambiguity of each entry is exactly
+    2^-22 |dtf[0] + dtf[1]| of that channel.  It is zero for an untouched
+    entry and never negative."""
+    dims, f, tf, part, cam, W, H, g, _ = _problem(2)
+    fr = orc.Frame(W, H, sigma_max=20.0)
+    bricks = orc.make_bricks(f, part, orc.F32)
+    g = np.abs(g)
+    g[:, 3] = 0.0
+    tf2 = inputs.make_tf(5, n=2)
+    dtf, _, amb = orc.grad_bricks(dims, bricks, tf2, cam, fr, g, want_volume=False, tf_amb=True)
+    for c in range(3):
+        want = 2.0 ** -22 * abs(dtf[0, c] + dtf[1, c])
+        assert want > 0
+        np.testing.assert_allclose(amb[:, c], [want, want], rtol=1e-12)
+    # a 256-entry table: non-negative, zero where no sample reads
+    dtf, _, amb = orc.grad_bricks(dims, bricks, tf, cam, fr, np.abs(g), want_volume=False, tf_amb=True)
+    assert np.all(amb >= 0.0)
+    assert np.all(amb[np.all(dtf == 0.0, axis=1)] == 0.0)
+    assert amb.max() > 0
