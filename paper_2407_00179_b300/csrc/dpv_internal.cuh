@@ -547,17 +547,24 @@ struct MarchState {
 
 // Ray of pixel (px, py) against brick b: its sample range and the local
 // frame.  Returns false when the brick holds no sample of the ray.
-__device__ __forceinline__ bool brick_samples(const FrameParams& P, const CamBasis& cam, int c, const BrickDev& b,
-                                              int px, int py, MarchState& m) {
-    Ray r;
-    load_ray(cam, P, c, px, py, r);
+// The sample range [j0, j1) of ray r in brick b (the range brick_samples
+// uses); false when empty.
+__device__ __forceinline__ bool segment_range(const FrameParams& P, const Ray& r, const BrickDev& b, int& j0,
+                                              int& j1) {
     if (!(r.te < r.tx)) return false;
     float t0 = r.te, t1 = r.tx;
     ray_box(r.o, r.d, r.inv, b.r0, b.r1, b.closed, t0, t1);
     if (!(t0 < t1)) return false;
-    m.j0 = first_sample_at(t0, r.te, P);
-    m.j1 = first_sample_at(t1, r.te, P);
-    if (m.j0 >= m.j1) return false;
+    j0 = first_sample_at(t0, r.te, P);
+    j1 = first_sample_at(t1, r.te, P);
+    return j0 < j1;
+}
+
+__device__ __forceinline__ bool brick_samples(const FrameParams& P, const CamBasis& cam, int c, const BrickDev& b,
+                                              int px, int py, MarchState& m) {
+    Ray r;
+    load_ray(cam, P, c, px, py, r);
+    if (!segment_range(P, r, b, m.j0, m.j1)) return false;
     m.te = r.te;
     // Position of sample j0 in brick-local node coordinates, kept to about
     // one FP32 ulp of the brick-local value: entry point p = p_hi + p_lo,

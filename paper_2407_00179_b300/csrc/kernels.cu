@@ -743,17 +743,23 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
 
 // The work-list slot of the ray's segment with the smallest first sample
 // index above `last` (-1: none), and that index.
+// Only the ray's slab intersection with each candidate brick is needed
+// (the pixel's ray is loaded once per call, not kept live across the
+// march); the sample anchor of brick_samples is computed for the chosen
+// segment alone.
 __device__ __forceinline__ int next_segment(const FrameParams& P, const CamBasis& cam, int c, const BrickDev* bricks,
                                             const Item* items, long long first, int cnt, int px, int py, int last,
                                             int& j0) {
+    Ray r;
+    load_ray(cam, P, c, px, py, r);
     int best = KEY_EMPTY, bs = -1;
     for (int q = 0; q < cnt; ++q) {
         const Item it = items[first + q];
         if (!item_ok(it, P)) continue;
-        MarchState m;
-        if (!brick_samples(P, cam, c, bricks[it.brick], px, py, m)) continue;
-        if (m.j0 > last && m.j0 < best) {
-            best = m.j0;
+        int a, e;
+        if (!segment_range(P, r, bricks[it.brick], a, e)) continue;
+        if (a > last && a < best) {
+            best = a;
             bs = q;
         }
     }
@@ -762,7 +768,7 @@ __device__ __forceinline__ int next_segment(const FrameParams& P, const CamBasis
 }
 
 template <typename T, int GL, bool SKIP>
-__global__ void __launch_bounds__(256, 4) k_march_ordered(FrameParams P, const CamBasis* cams,
+__global__ void __launch_bounds__(256, 5) k_march_ordered(FrameParams P, const CamBasis* cams,
                                                           const BrickDev* bricks, const float* scales,
                                                           const int* tile_first, const int* tile_count,
                                                           const Item* items, const float4* tf, float4* out_rgba,
