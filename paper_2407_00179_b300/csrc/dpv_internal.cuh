@@ -423,6 +423,77 @@ struct Cell<__nv_fp8_e4m3> {
     }
 };
 
+// Raw cell vectors, fetched one sample ahead and decoded at use.
+template <typename T>
+struct CellRaw;
+template <>
+struct CellRaw<float> {
+    float v[8];
+    __device__ __forceinline__ void fetch(const void* base, long long cell) { Cell<float>::load(base, cell, v); }
+    __device__ __forceinline__ void decode(float o[8]) const {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = v[k];
+    }
+};
+template <>
+struct CellRaw<__half> {
+    uint4 w;
+    __device__ __forceinline__ void fetch(const void* base, long long cell) {
+        w = __ldg(reinterpret_cast<const uint4*>(base) + cell);
+    }
+    __device__ __forceinline__ void decode(float v[8]) const {
+        const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = __half2float(__ushort_as_half((unsigned short)(u[k] & 0xffffu)));
+            v[2 * k + 1] = __half2float(__ushort_as_half((unsigned short)(u[k] >> 16)));
+        }
+    }
+};
+template <>
+struct CellRaw<__nv_bfloat16> {
+    uint4 w;
+    __device__ __forceinline__ void fetch(const void* base, long long cell) {
+        w = __ldg(reinterpret_cast<const uint4*>(base) + cell);
+    }
+    __device__ __forceinline__ void decode(float v[8]) const {
+        const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = __uint_as_float(u[k] << 16);
+            v[2 * k + 1] = __uint_as_float(u[k] & 0xffff0000u);
+        }
+    }
+};
+template <>
+struct CellRaw<__nv_fp8_e4m3> {
+    uint2 w;
+    __device__ __forceinline__ void fetch(const void* base, long long cell) {
+        w = __ldg(reinterpret_cast<const uint2*>(base) + cell);
+    }
+    __device__ __forceinline__ void decode(float v[8]) const {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = Quad<__nv_fp8_e4m3>::dec((w.x >> (8 * k)) & 0xffu);
+            v[4 + k] = Quad<__nv_fp8_e4m3>::dec((w.y >> (8 * k)) & 0xffu);
+        }
+    }
+};
+
+// The trilinear interpolant of eight decoded corners (the arithmetic of
+// trilinear(), in the same order).
+template <typename T>
+__device__ __forceinline__ float lerp_cell(const float v[8], float fx, float fy, float fz, float scale) {
+    float x00 = fmaf(fx, v[1] - v[0], v[0]);
+    float x10 = fmaf(fx, v[3] - v[2], v[2]);
+    float x01 = fmaf(fx, v[5] - v[4], v[4]);
+    float x11 = fmaf(fx, v[7] - v[6], v[6]);
+    float y0 = fmaf(fy, x10 - x00, x00);
+    float y1 = fmaf(fy, x11 - x01, x01);
+    float r = fmaf(fz, y1 - y0, y0);
+    return Storage<T>::unit_scale ? r : r * scale;
+}
+
 // The eight corners of the last cell a ray sampled, kept in registers:
 // consecutive samples (step < 1 voxel) mostly stay in the same cell, and a
 // step to the next cell in z shares a face; only what changed is loaded.
