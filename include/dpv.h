@@ -245,7 +245,10 @@ dpv_status dpvCommitBrick(dpv_device dev, int rank, const dpv_brick_desc* desc);
 
 /* Transfer function: n (2..4096) RGBA float entries, x fastest, on the host
  * (on_device = 0) or the device; values over [vmin, vmax], vmax > vmin.
- * Copied; visible to the next render. */
+ * Copied; visible to the next render.  A host table is copied into one of
+ * two pinned staging buffers and uploaded on the device stream: the
+ * caller's buffer may be reused at return and the call does not wait for
+ * the device (only for the upload issued two calls earlier). */
 dpv_status dpvSetTransferFunction(dpv_device dev, const float* rgba, int n, float vmin, float vmax, int on_device);
 
 /* Directional light for DPV_FRAME_SHADOW: direction toward the light (any

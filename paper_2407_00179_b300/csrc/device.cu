@@ -78,6 +78,12 @@ struct dpv_device_t {
     float4* d_tf = nullptr;
     int ntf = 0;
     float vmin = 0.f, vmax = 1.f;
+    // host TF uploads: copied into one of two pinned staging slots, then
+    // uploaded on the device stream (the caller's buffer is free at return
+    // and the host does not wait for the device)
+    float4* h_tf_stage[2] = {nullptr, nullptr};
+    cudaEvent_t ev_tf_stage[2] = {nullptr, nullptr};
+    int tf_stage_next = 0;
     bool has_light = false;
     float light_dir[3] = {0.f, 0.f, 1.f};   // unit, toward the light
     float light_step = 1.f;                 // h, voxels
@@ -996,9 +1002,23 @@ dpv_status dpvSetTransferFunction(dpv_device dev, const float* rgba, int n, floa
         dev->d_tf = nullptr;
         if ((s = dev_alloc(dev, (void**)&dev->d_tf, sizeof(float4) * n, "TF"))) return s;
     }
-    CK(cudaMemcpyAsync(dev->d_tf, rgba, sizeof(float4) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                       dev->stream), "upload TF");
-    if (!on_device) CK(cudaStreamSynchronize(dev->stream), "upload TF");
+    if (on_device) {
+        CK(cudaMemcpyAsync(dev->d_tf, rgba, sizeof(float4) * n, cudaMemcpyDeviceToDevice, dev->stream), "upload TF");
+    } else {
+        const int k = dev->tf_stage_next;
+        dev->tf_stage_next ^= 1;
+        if (!dev->h_tf_stage[k]) {
+            CK(cudaHostAlloc((void**)&dev->h_tf_stage[k], sizeof(float4) * MAX_TF, cudaHostAllocDefault),
+               "TF staging");
+            CK(cudaEventCreateWithFlags(&dev->ev_tf_stage[k], cudaEventDisableTiming), "TF staging");
+        } else {
+            CK(cudaEventSynchronize(dev->ev_tf_stage[k]), "TF staging");   // its last upload has run
+        }
+        memcpy(dev->h_tf_stage[k], rgba, sizeof(float4) * n);
+        CK(cudaMemcpyAsync(dev->d_tf, dev->h_tf_stage[k], sizeof(float4) * n, cudaMemcpyHostToDevice, dev->stream),
+           "upload TF");
+        CK(cudaEventRecord(dev->ev_tf_stage[k], dev->stream), "upload TF");
+    }
     if (n != dev->ntf || vmin != dev->vmin || vmax != dev->vmax) dev->dirty = true;
     dev->ntf = n;
     dev->vmin = vmin;
@@ -1521,6 +1541,13 @@ dpv_status dpvRelease(dpv_device dev) {
             if (dev->ev_drained[k]) cudaEventDestroy(dev->ev_drained[k]);
         }
         if (dev->cap_stream) cudaStreamDestroy(dev->cap_stream);
+        for (int k = 0; k < 2; ++k) {
+            if (dev->ev_tf_stage[k]) {
+                cudaEventSynchronize(dev->ev_tf_stage[k]);
+                cudaEventDestroy(dev->ev_tf_stage[k]);
+            }
+            if (dev->h_tf_stage[k]) cudaFreeHost(dev->h_tf_stage[k]);
+        }
         if (dev->ev_done) cudaEventDestroy(dev->ev_done);
         for (auto& t : dev->pending) {
             cudaEventDestroy(t.a);
