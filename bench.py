@@ -41,6 +41,7 @@ BYTES_PER_VOXEL = {"f32": 4, "f16": 2, "bf16": 2, "fp8": 1}
 # capture of this workload (profiles/ holds the summary and the command);
 # absent where no capture of the current kernel exists
 TRAFFIC = {
+    ("mid", "march"): 4.797e9,        # k_march_fwd<float, cell, 0>: 4.768 GB read + 28.3 MB written
     ("mid", "march_bwd"): 12.36e9,    # k_march_bwd<float, cell> 9.59 GB + k_face_gather 2.77 GB
 }
 
