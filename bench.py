@@ -45,6 +45,18 @@ TRAFFIC = {
     ("mid", "march_bwd"): 12.36e9,    # k_march_bwd<float, cell> 9.59 GB + k_face_gather 2.77 GB
 }
 
+# L1 / L2 sector hit rates of the timed kernels, from the same ncu captures
+HIT_RATES = {
+    ("mid", "march"): (0.544, 0.330),
+    ("mid", "march_bwd"): (None, 0.583),      # the adjoint's L1 rate is dominated by reductions (bypass L1)
+}
+
+# FP32 arithmetic per sample counted in the source (an FMA counts once):
+# forward: position 6, trilinear 14, TF lookup 15, opacity 11, emission-
+# absorption and termination 8; the adjoint adds the recurrence adjoints,
+# the TF-lerp and trilinear-weight gradients and their run sums (about 60).
+FP32_OPS_PER_SAMPLE = {"march": 54, "march_bwd": 114}
+
 CONFIGS = {
     # 512^3 f32, 64 blobs + 3-octave noise, 2x2x2 bricks, 1920x1080, ERT 0.99
     "mid": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
@@ -399,6 +411,36 @@ def run_ours(args, cfg_name, cfg):
     bwd_achieved = st["samples_backward"] * (8 * bpv + 8 * 4) / (march_bwd_ms * 1e-3) / 1e9 if grad is not None else 0.0
     peak, peak_kind = _peaks()
 
+    # compulsory bytes (each stored brick read once + fragment writes), the
+    # DRAM traffic ncu measured, hit rates, and an FP32 ALU ceiling from the
+    # device's SM count and the sampled maximum SM clock
+    brick_bytes = 0
+    for k in range(part.num_ranks):
+        n_nodes = 1
+        for a in range(3):
+            lo = max(int(part.lo[k][a]) - 1, 0)
+            hi = min(int(part.hi[k][a]), cfg["dims"][a] - 1)
+            n_nodes *= hi - lo + 1
+        brick_bytes += n_nodes * bpv
+    nsm = torch.cuda.get_device_properties(device).multi_processor_count
+    tile_px = (tune["tile"][0] * tune["tile"][1]) if tune else (args.tile_w or 16) * (args.tile_h or 16)
+
+    def march_detail(kind, ms, samples, sm_mhz):
+        # fragments written (RGBA + key per slot) by the forward; the adjoint
+        # writes the field gradient (4 B per global node)
+        out = st["work_items"] * tile_px * 20 if kind == "march" else int(np.prod(cfg["dims"])) * 4
+        comp = brick_bytes + out
+        traffic = TRAFFIC.get((cfg_name, kind))
+        hits = HIT_RATES.get((cfg_name, kind), (None, None))
+        alu = (128 * nsm * sm_mhz * 1e6 / FP32_OPS_PER_SAMPLE[kind] / 1e9) if sm_mhz else None
+        rate = samples / (ms * 1e-3) / 1e9
+        return {"compulsory_bytes": comp, "compulsory_frac": comp / (ms * 1e-3) / 1e9 / peak,
+                "dram_traffic_bytes": traffic,
+                "dram_gbs": traffic / (ms * 1e-3) / 1e9 if traffic else None,
+                "l1_hit": hits[0], "l2_hit": hits[1], "fp32_ops_per_sample": FP32_OPS_PER_SAMPLE[kind],
+                "alu_ceiling_gsamples": alu, "alu_frac": rate / alu if alu else None,
+                "alu_basis": "128 FP32 lanes x %d SMs x max SM clock / FP32 ops per sample" % nsm}
+
     # many cameras: the same forward replayed from a CUDA graph, and the
     # cameras rendered as separate float32 per-camera frames for comparison
     batch = None
@@ -634,13 +676,16 @@ def run_ours(args, cfg_name, cfg):
                                 else "k_shadow_round<%s> + k_march_shadowed (march stage)" if shadow is not None
                                 else "k_march_fwd<%s>") % cfg["storage"],
                      "model": "stencil bytes: 8 corners x %d B per evaluated sample" % bpv,
-                     "peak_kind": peak_kind},
+                     "peak_kind": peak_kind,
+                     "detail": march_detail("march", march_ms, per_step, clk.get("sm_max_mhz"))},
         "roofline_backward": ({"bound": "hbm", "achieved": bwd_achieved, "peak": peak, "unit": "GB/s",
                                "frac": bwd_achieved / peak, "traffic": TRAFFIC.get((cfg_name, "march_bwd")),
                                "kernel": "k_march_bwd<%s> (+ k_face_gather)" % cfg["storage"],
                                "model": "stencil bytes: 8 corners x %d B read + 8 x 4 B field-gradient adds per "
                                         "replayed sample" % bpv,
-                               "peak_kind": peak_kind} if grad is not None else None),
+                               "peak_kind": peak_kind,
+                               "detail": march_detail("march_bwd", march_bwd_ms, st["samples_backward"],
+                                                      clk.get("sm_max_mhz"))} if grad is not None else None),
         "e2e": {"value": e2e_val, "unit": "Gsamples/s", "h2d_bytes_per_step": int(tf_np.nbytes),
                 "d2h_bytes_per_step": int(ncam * H * W * 16), "what": "set TF from pinned host, render, copy frames"
                 " to pinned host (asynchronous, overlapping the next render; all copies complete inside the "

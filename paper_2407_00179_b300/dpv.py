@@ -483,6 +483,9 @@ class RenderFunction(torch.autograd.Function):
         return dtf.to(ctx.tf_dtype), dvol, None, None, None
 
 
+DPVRender = RenderFunction
+
+
 def render(device: Device, tf: torch.Tensor, volume: Optional[torch.Tensor] = None, vmin: float = 0.0,
            vmax: float = 1.0) -> torch.Tensor:
     """(ncam, H, W, 4) premultiplied RGBA, differentiable in tf (and volume)."""
