@@ -211,7 +211,12 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
     bricks = oracle.make_bricks(field_np, part, oracle.DTYPE_NAMES[cfg["storage"]])
     fr = oracle.Frame(cfg["width"], cfg["height"], step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"])
     W, H = cfg["width"], cfg["height"]
-    cam = cams[0]
+    # the camera and spacing exactly as the C ABI receives them (float32),
+    # so the oracle's frame is comparable with the GPU's
+    f32 = lambda v: tuple(float(x) for x in np.asarray(v, np.float32))
+    c0 = cams[0]
+    cam = inputs.Camera(f32(c0.eye), f32(c0.center), f32(c0.up), float(np.float32(c0.fovy_deg)))
+    sp = float(np.float32(1.0 / (max(cfg["dims"]) - 1)))
 
     iso = cfg.get("iso")
     sh = cfg.get("shadow")
@@ -221,30 +226,31 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
         t = time.perf_counter()
         if sh is not None:
             out = oracle.render_shadow(cfg["dims"], tf, cam, fr, oracle.Light(sh[0], step_voxels=sh[1], ambient=sh[2]),
-                                       bricks=bricks, pix=pix)
-            return time.perf_counter() - t, int(out["nsamples"].sum() + out["nshadow"].sum()), len(pix)
+                                       bricks=bricks, pix=pix, spacing=sp)
+            return time.perf_counter() - t, int(out["nsamples"].sum() + out["nshadow"].sum()), len(pix), out, pix
         if iso is not None:
-            oracle.render_iso(cfg["dims"], tf, cam, fr, iso, bricks=bricks, pix=pix)
-            return time.perf_counter() - t, 0, len(pix)
+            out = oracle.render_iso(cfg["dims"], tf, cam, fr, iso, bricks=bricks, pix=pix, spacing=sp)
+            return time.perf_counter() - t, 0, len(pix), out, pix
         if cfg.get("ordered"):
-            out = oracle.render_ordered(cfg["dims"], tf, cam, fr, bricks=bricks, pix=pix)
-            return time.perf_counter() - t, int(out["nsamples"].sum()), len(pix)
-        out = oracle.render_bricks(cfg["dims"], bricks, tf, cam, fr, pix=pix)
-        return time.perf_counter() - t, int(out["nsamples"].sum()), len(pix)
+            out = oracle.render_ordered(cfg["dims"], tf, cam, fr, bricks=bricks, pix=pix, spacing=sp)
+            return time.perf_counter() - t, int(out["nsamples"].sum()), len(pix), out, pix
+        out = oracle.render_bricks(cfg["dims"], bricks, tf, cam, fr, pix=pix, spacing=sp)
+        return time.perf_counter() - t, int(out["nsamples"].sum()), len(pix), out, pix
 
     # calibrate on 8 rows spread over the image, then size the sample so the
     # oracle works about budget_s seconds
     cal = np.linspace(0, H - 1, 8).astype(int)
-    dt, ns, npx = run(cal)
+    dt, ns, npx, _, _ = run(cal)
     per_row_s = max(dt, 1e-6) / len(cal)
     nrows = int(min(H, max(8, budget_s / per_row_s)))
     rows = np.linspace(0, H - 1, nrows).astype(int)
-    dt, ns, npx = run(rows)
+    dt, ns, npx, ref_out, ref_pix = run(rows)
+    ref = {"pix": ref_pix, "rgba": ref_out["rgba"], "flags": ref_out["flags"], "order": ref_out.get("order")}
     # one core on a reduced image: rows spread over the frame, about 3 s
     oracle.set_threads(1)
     n1 = int(min(H, max(2, 3.0 / (per_row_s * ncores))))
     rows1 = np.linspace(0, H - 1, n1).astype(int)
-    dt1, ns1, npx1 = run(rows1)
+    dt1, ns1, npx1, _, _ = run(rows1)
     oracle.set_threads(ncores)
     if iso is not None:
         # the iso oracle evaluates every sample of the ray: its rate is in pixels
@@ -253,14 +259,14 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
                     len(rows), H, npx, dt),
                 "one_core": {"value": npx1 / dt1 / 1e6, "unit": "Mpixels/s", "cores": 1,
                              "sample": "%d pixel rows (%d pixels) of camera 0, %.1f s" % (len(rows1), npx1, dt1)},
-                "seconds": dt, "samples": npx, "rows": rows}
+                "seconds": dt, "samples": npx, "rows": rows, "ref": ref}
     return {"value": ns / dt / 1e9, "unit": "Gsamples/s", "cores": ncores, "kind": "oracle",
             "sample": "%d of %d pixel rows (%d pixels, %d samples) of camera 0, FP64, %.1f s" % (
                 len(rows), H, npx, ns, dt),
             "one_core": {"value": ns1 / dt1 / 1e9, "unit": "Gsamples/s", "cores": 1,
                          "sample": "%d pixel rows (%d pixels, %d samples) of camera 0, %.1f s" % (
                              len(rows1), npx1, ns1, dt1)},
-            "seconds": dt, "samples": ns, "rows": rows}
+            "seconds": dt, "samples": ns, "rows": rows, "ref": ref}
 
 
 def run_reference(args, cfg_name, cfg):
@@ -389,6 +395,7 @@ def run_ours(args, cfg_name, cfg):
         pg.barrier()
     clk = clocks.stop()
     st = dev.stats()
+    img0 = dev.map_frame(0)[0].clone()           # camera 0 of the timed frame, for the parity report
     dev.set_profiling(False)
     total_ms = t0.elapsed_time(t1)
     fwd_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
@@ -710,13 +717,38 @@ def run_ours(args, cfg_name, cfg):
     if skip_cmp:
         line["skip_comparison"] = skip_cmp
         line["config"]["tf_transparent_below"] = cfg["tf_cut"]
+    # the per-pixel order of camera 0 (sort-last modes), for the parity report
+    order0 = None
+    if rank == 0 and not args.no_cpu_baseline and iso is None and not ordered and shadow is None:
+        fl = tune["flags"] if tune else 0
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
+                      tile=tuple(tune["tile"]) if tune else (args.tile_w, args.tile_h), gather=dpv.gather_of(fl),
+                      persistent=bool(fl & dpv.FRAME_PERSISTENT), skip=skip, order=True)
+        dev.render()
+        order0 = dev.order(0).reshape(-1, part.num_ranks).cpu().numpy()
     if rank == 0 and not args.no_cpu_baseline:
         try:
             cb = cpu_baseline(cfg_name, cfg, field_host, part, tf_np, cams, budget_s=args.ref_budget)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "one_core")}
         except Exception as e:  # the oracle is a reported baseline, never the product
+            cb = None
             line["cpu_baseline"] = {"value": None, "unit": "Gsamples/s", "cores": None, "kind": "oracle",
                                     "sample": "failed: %s" % e}
+        if cb is not None:
+            # the timed frame against the oracle's frame of the same rows
+            ref = cb["ref"]
+            img = img0.reshape(-1, 4).double().cpu().numpy()[ref["pix"]]
+            ok = (ref["flags"].astype(np.int64) & ~1) == 0     # every ambiguity flag excluded
+            err = np.abs(img - ref["rgba"])[ok]
+            par = {"reference": "FP64 oracle, same stored values, camera 0, the cpu_baseline rows",
+                   "pixels": int(ok.sum()), "flagged": int((~ok).sum()),
+                   "max_abs": float(err.max()) if err.size else None,
+                   "mean_abs": float(err.mean()) if err.size else None,
+                   "max_abs_per_channel": err.max(axis=0).tolist() if err.size else None}
+            if order0 is not None and ref["order"] is not None:
+                o = order0[ref["pix"]]
+                par["order_mismatches"] = int((o[ok] != ref["order"][ok]).any(axis=1).sum())
+            line["parity"] = par
     dev.release()
     if rank == 0:
         print(json.dumps(line), flush=True)
