@@ -741,11 +741,11 @@ __device__ __forceinline__ void tf_flush(TFRun& r, double* s_g) {
 }
 
 // Adjoint of one cell's eight corners, summed in registers while a ray stays
-// in the cell.  a[0..3] are the corners of the cell's lower z face in the
-// order (x,y) (x+1,y) (x,y+1) (x+1,y+1); a[4..7] those of its upper face.
+// in the cell (scalar-atomic path).  a[0..3] are the corners of the cell's
+// lower z face in the order (x,y) (x+1,y) (x,y+1) (x+1,y+1); a[4..7] those of
+// its upper face.
 struct CellRun {
-    long long base = -1;   // the cell: its lower face's index in the face
-                           // buffer, or its (0,0,0) node in the global field
+    long long base = -1;   // the cell's (0,0,0) node in the global field
     float a[8];
 };
 
@@ -763,15 +763,6 @@ __device__ __forceinline__ void cell_flush(CellRun& r, float* dvol, long long sy
     atomicAdd(v + sz + sy + 1, r.a[7]);
 }
 
-// Face form: two 16-byte vector atomics into the face adjoint buffer (laid
-// out like the gather layout: one float4 per cell face, base = the lower
-// face, base + qxy the upper one); k_face_gather later sums each node's four
-// face slots of every brick that stores it.
-__device__ __forceinline__ void cell_flush_faces(CellRun& r, float4* gface, long long qxy) {
-    if (r.base < 0) return;
-    atomicAdd(gface + r.base, make_float4(r.a[0], r.a[1], r.a[2], r.a[3]));
-    atomicAdd(gface + r.base + qxy, make_float4(r.a[4], r.a[5], r.a[6], r.a[7]));
-}
 
 // ---------------------------------------------------------------------------
 // helpers
