@@ -751,6 +751,35 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
     wk.init(b);
     int mlast = -1;
     bool mempty = false;
+    if (GL == GATHER_CELL && !SKIP) {
+        // the next sample's cell in flight during this sample's arithmetic
+        // (as in the sort-last march; interpolation bit-identical)
+        CellRaw<T> raw;
+        int ix, iy, iz;
+        float fx, fy, fz;
+        wk.at(m, 0, ix, iy, iz, fx, fy, fz);
+        raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy);
+        for (int k = 0; k < n; ++k) {
+            float v[8];
+            raw.decode(v);
+            const float cx = fx, cy = fy, cz = fz;
+            if (k + 1 < n) {
+                wk.at(m, k + 1, ix, iy, iz, fx, fy, fz);
+                raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy);
+            }
+            float s = lerp_cell<T>(v, cx, cy, cz, scale);
+            TFSample c = tf_lookup(s_tf, P, s);
+            float al = sample_alpha(P, c.v.w);
+            float ta = Tr * al;
+            C0 = fmaf(ta, c.v.x, C0);
+            C1 = fmaf(ta, c.v.y, C1);
+            C2 = fmaf(ta, c.v.z, C2);
+            Tr = Tr * (1.0f - al);
+            ++nsamp;
+            if (P.ert_on && 1.0f - Tr > P.ert) return true;
+        }
+        return false;
+    }
     for (int k = 0; k < n; ++k) {
         int ix, iy, iz;
         float fx, fy, fz;
@@ -806,8 +835,15 @@ __device__ __forceinline__ int next_segment(const FrameParams& P, const CamBasis
     return bs;
 }
 
+// 4 CTAs per SM (64 registers) for the pipelined cell-layout march, 5 (48
+// registers) for the others: measured best for each
+template <int GL, bool SKIP>
+constexpr int ordered_min_ctas() {
+    return (GL == GATHER_CELL && !SKIP) ? 4 : 5;
+}
+
 template <typename T, int GL, bool SKIP>
-__global__ void __launch_bounds__(256, 5) k_march_ordered(FrameParams P, const CamBasis* cams,
+__global__ void __launch_bounds__(256, ordered_min_ctas<GL, SKIP>()) k_march_ordered(FrameParams P, const CamBasis* cams,
                                                           const BrickDev* bricks, const float* scales,
                                                           const int* tile_first, const int* tile_count,
                                                           const Item* items, const float4* tf, float4* out_rgba,
