@@ -554,6 +554,11 @@ def run_ours(args, cfg_name, cfg):
                      "sort_last_autotune": sl_tune,
                      "ordered_samples_per_step": ord_samples, "speedup_vs_sort_last": sl_ms / (fwd_ms / args.steps),
                      "image_difference_vs_sort_last": {"max": float(d.max()), "mean": float(d.mean())}}
+        # back to the ordered frame for the end-to-end loop
+        fl = tune["flags"] if tune else 0
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
+                      tile=tuple(tune["tile"]) if tune else (args.tile_w, args.tile_h), gather=dpv.gather_of(fl),
+                      persistent=bool(fl & dpv.FRAME_PERSISTENT), ordered=True)
 
     # empty-space skipping beside the same frame without it, in its own best
     # launch form: time, samples evaluated, and the frames (bit-identical)
