@@ -155,8 +155,15 @@ __device__ __forceinline__ bool owns(const BrickDev& b, const float p[3]) {
 // the shadow samples it owns.  One grid covers the records of all
 // wave-fronts evenly (wave-fronts differ in size); a record's wave-front is
 // found in the K + 1 first-record offsets.
+// the pipelined cell-layout round at 4 CTAs per SM (64 registers): 7 %
+// faster than the plain loop at 5
+template <int GL>
+constexpr int shadow_min_ctas() {
+    return GL == GATHER_CELL ? 4 : 1;
+}
+
 template <typename T, int GL>
-__global__ void __launch_bounds__(256) k_shadow_round(FrameParams P, const BrickDev* bricks, const float* scales,
+__global__ void __launch_bounds__(256, shadow_min_ctas<GL>()) k_shadow_round(FrameParams P, const BrickDev* bricks, const float* scales,
                                                       const float4* tf, const long long* rec_first, int round,
                                                       float4* recs, Counters* counters) {
     extern __shared__ float4 s_tf[];
@@ -196,6 +203,72 @@ __global__ void __launch_bounds__(256) k_shadow_round(FrameParams P, const Brick
         float Tl = rec.w;
         CornerCache<T, GL> cc;
         bool any = false;
+        if (GL == GATHER_CELL) {
+            // the owned samples are one contiguous run (each coordinate of
+            // fma(i + 1/2, hL, o) is monotone in i): find its start, then
+            // fetch each next sample's cell while this one's is evaluated
+            int i = i0;
+            float p[3];
+            bool own = false;
+            for (; i <= i1; ++i) {
+                const float ti = (float)i + 0.5f;
+                p[0] = fmaf(ti, hl[0], o[0]);
+                p[1] = fmaf(ti, hl[1], o[1]);
+                p[2] = fmaf(ti, hl[2], o[2]);
+                if (owns(b, p)) {
+                    own = true;
+                    break;
+                }
+            }
+            if (own) {
+                CellRaw<T> raw;
+                int ix, iy, iz;
+                float fx, fy, fz;
+                {
+                    const float qx = p[0] - (float)b.s_lo[0], qy = p[1] - (float)b.s_lo[1], qz = p[2] - (float)b.s_lo[2];
+                    ix = min(max(__float2int_rd(qx), 0), lim[0]);
+                    iy = min(max(__float2int_rd(qy), 0), lim[1]);
+                    iz = min(max(__float2int_rd(qz), 0), lim[2]);
+                    fx = qx - (float)ix;
+                    fy = qy - (float)iy;
+                    fz = qz - (float)iz;
+                }
+                raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy);
+                for (;;) {
+                    float v[8];
+                    raw.decode(v);
+                    const float cx = fx, cy = fy, cz = fz;
+                    bool nown = false;
+                    if (i + 1 <= i1) {
+                        const float tn = (float)(i + 1) + 0.5f;
+                        p[0] = fmaf(tn, hl[0], o[0]);
+                        p[1] = fmaf(tn, hl[1], o[1]);
+                        p[2] = fmaf(tn, hl[2], o[2]);
+                        nown = owns(b, p);
+                        if (nown) {
+                            const float qx = p[0] - (float)b.s_lo[0], qy = p[1] - (float)b.s_lo[1],
+                                        qz = p[2] - (float)b.s_lo[2];
+                            ix = min(max(__float2int_rd(qx), 0), lim[0]);
+                            iy = min(max(__float2int_rd(qy), 0), lim[1]);
+                            iz = min(max(__float2int_rd(qz), 0), lim[2]);
+                            fx = qx - (float)ix;
+                            fy = qy - (float)iy;
+                            fz = qz - (float)iz;
+                            raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy);
+                        }
+                    }
+                    const float s = lerp_cell<T>(v, cx, cy, cz, scale);
+                    const TFSample c = tf_lookup(s_tf, P, s);
+                    const float al = -expm1f(-P.sigma_max * c.v.w * P.shadow_dt);
+                    Tl = Tl * (1.0f - al);
+                    ++nsamp;
+                    if (!nown) break;
+                    ++i;
+                }
+                recs[r].w = Tl;
+            }
+            continue;
+        }
         for (int i = i0; i <= i1; ++i) {
             const float ti = (float)i + 0.5f;
             const float p[3] = {fmaf(ti, hl[0], o[0]), fmaf(ti, hl[1], o[1]), fmaf(ti, hl[2], o[2])};
