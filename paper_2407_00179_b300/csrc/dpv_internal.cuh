@@ -601,6 +601,25 @@ __device__ __forceinline__ TFSample tf_lookup(const float4* tab, const FramePara
     return r;
 }
 
+// The lookup with the segment's slopes b - a per channel (the adjoint's
+// ds term), from the same two entries.
+__device__ __forceinline__ TFSample tf_lookup_slope(const float4* tab, const FrameParams& P, float s, float4& d) {
+    TFSample r;
+    float u = (s - P.vmin) * P.tf_scale;
+    float hi = (float)(P.ntf - 1);
+    r.duds = (s >= P.vmin && s <= P.vmax) ? P.tf_scale : 0.0f;
+    u = fminf(fmaxf(u, 0.0f), hi);
+    r.i0 = min(__float2int_rd(u), P.ntf - 2);
+    r.w = u - (float)r.i0;
+    float4 a = tab[r.i0], b = tab[r.i0 + 1];
+    d = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+    r.v.x = fmaf(r.w, d.x, a.x);
+    r.v.y = fmaf(r.w, d.y, a.y);
+    r.v.z = fmaf(r.w, d.z, a.z);
+    r.v.w = fmaf(r.w, d.w, a.w);
+    return r;
+}
+
 // Opacity of one sample: 1 - exp(-sigma_max * a * dt).
 __device__ __forceinline__ float sample_alpha(const FrameParams& P, float a) {
     return -expm1f(-P.sigma_max * a * P.dt);

@@ -1473,7 +1473,8 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 float fx, fy, fz;
                 wk.at(m, k, ix, iy, iz, fx, fy, fz);
                 float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
-                TFSample c = tf_lookup(s_tf, P, s);
+                float4 dsl;
+                TFSample c = tf_lookup_slope(s_tf, P, s, dsl);
                 float al = sample_alpha(P, c.v.w);
                 float ta = Tr * al;
                 float n0 = fmaf(ta, c.v.x, C0), n1 = fmaf(ta, c.v.y, C1), n2 = fmaf(ta, c.v.z, C2);
@@ -1500,9 +1501,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 tr.a[6] = fmaf(w1, g_b, tr.a[6]);
                 tr.a[7] = fmaf(w1, g_a, tr.a[7]);
                 if ((FACE || dvol) && c.duds != 0.0f) {
-                    float4 ta0 = s_tf[c.i0], ta1 = s_tf[c.i0 + 1];
-                    float gs = (g_r * (ta1.x - ta0.x) + g_g * (ta1.y - ta0.y) + g_b * (ta1.z - ta0.z) +
-                                g_a * (ta1.w - ta0.w)) * c.duds * gscale;
+                    float gs = (g_r * dsl.x + g_g * dsl.y + g_b * dsl.z + g_a * dsl.w) * c.duds * gscale;
                     if (FACE && gs != 0.0f) {
                         // straight into the face buffer, two vector reductions per
                         // sample: cheaper than a register run per cell, whose
