@@ -42,7 +42,6 @@ BYTES_PER_VOXEL = {"f32": 4, "f16": 2, "bf16": 2, "fp8": 1}
 # absent where no capture of the current kernel exists
 TRAFFIC = {
     ("mid", "march"): 4.797e9,        # k_march_fwd<float, cell, 0>: 4.768 GB read + 28.3 MB written
-    ("mid", "march_bwd"): 12.16e9,    # k_march_bwd<float, cell, face> 9.39 GB + k_face_gather 2.77 GB
 }
 
 # L1 / L2 sector hit rates of the timed kernels, from the same ncu captures
