@@ -146,3 +146,34 @@ def test_async_frame_copies_in_flight():
     with pytest.raises(dpv.DPVError, match="INVALID_ARG"):
         dev.copy_frame_async(ncam, outs[1][0], None)
     dev.release()
+
+
+@pytest.mark.parametrize("mode", ["skip", "deep", "shadow"])
+def test_graph_replay_of_the_extended_modes(mode):
+    """Skipping, deep fragments and shadows replayed from a CUDA graph give
+    the direct launches' frames bit for bit, also after a TF update (the
+    skipping classification and the shadows read the new table)."""
+    sc = _scene(1)
+    kw = {"skip": dict(skip=True), "deep": dict(deep=True), "shadow": dict(shadow=True)}[mode]
+    tfs = [inputs.make_tf(1234, transparent_below=0.3), inputs.make_tf(55, transparent_below=0.2)]
+    frames = []
+    for graph in (False, True):
+        dev = scenes.gpu_device(sc, order=False)
+        if mode == "shadow":
+            dev.set_light((0.3, 0.8, 0.5), 1.0, 0.25)
+        dev.set_frame(sc.width, sc.height, step_voxels=sc.step, sigma_max=sc.sigma_max, ert=sc.ert, tile=sc.tile,
+                      graph=graph, **kw)
+        out = []
+        for tf in tfs:
+            dev.set_tf(torch.from_numpy(tf).cuda())
+            for _ in range(2):
+                dev.render()
+            out.append([t.clone() for c in range(len(sc.cams)) for t in dev.map_frame(c)])
+        if graph:
+            assert dev.stats()["graph_launches"] > 0
+        frames.append(out)
+        dev.release()
+    for a, b in zip(frames[0], frames[1]):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    assert not torch.equal(frames[0][0][0], frames[0][1][0])      # the TF update changed the frame
