@@ -1401,7 +1401,8 @@ cudaError_t launch_composite_bwd(const FrameParams& P, const int* tile_first, co
 //
 // Accumulation: consecutive samples of a ray usually fall in the same TF
 // segment, so each thread sums its TF gradient in registers while the
-// segment stays the same and flushes on change.  Nearby rays share TF
+// segment stays the same and flushes on change; a step to the neighbouring
+// segment keeps the sums of the entry the two segments share.  Nearby rays share TF
 // segments, so a single shared table would serialise the flushes of a warp
 // on the same addresses; the CTA keeps `ncopy` FP32 copies of the TF
 // gradient table (bwd_tf_copies), lane l writing copy l % ncopy (copies
@@ -1486,10 +1487,30 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 float g_r = G.x * ta, g_g = G.y * ta, g_b = G.z * ta;
                 float g_a = gal * P.sigma_max * P.dt * om;
                 if (c.i0 != tr.i0) {
-                    tf_flush_f(tr, my_tab);
-                    tr.i0 = c.i0;
+                    if (tr.i0 >= 0 && c.i0 == tr.i0 + 1) {
+                        // the next segment shares entry i0 + 1: keep its sums
+                        float* e = my_tab + 4 * tr.i0;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) tr.a[q] = 0.0f;
+                        for (int q = 0; q < 4; ++q) {
+                            if (tr.a[q] != 0.0f) atomicAdd(e + q, tr.a[q]);
+                            tr.a[q] = tr.a[q + 4];
+                            tr.a[q + 4] = 0.0f;
+                        }
+                    } else if (tr.i0 >= 0 && c.i0 == tr.i0 - 1) {
+                        // the previous segment shares entry i0
+                        float* e = my_tab + 4 * (tr.i0 + 1);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            if (tr.a[q + 4] != 0.0f) atomicAdd(e + q, tr.a[q + 4]);
+                            tr.a[q + 4] = tr.a[q];
+                            tr.a[q] = 0.0f;
+                        }
+                    } else {
+                        tf_flush_f(tr, my_tab);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) tr.a[q] = 0.0f;
+                    }
+                    tr.i0 = c.i0;
                 }
                 float w1 = c.w, w0 = 1.0f - c.w;
                 tr.a[0] = fmaf(w0, g_r, tr.a[0]);
