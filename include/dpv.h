@@ -332,7 +332,11 @@ dpv_status dpvMapOrder(dpv_device dev, int camera, const uint8_t** order, int* s
  * with respect to the field values (a ghost copy's share goes to its global
  * node), or NULL.  Both outputs are zeroed by the call.  Uses the fragments
  * of the last render: call it before the next render.  Asynchronous on the
- * device stream. */
+ * device stream.  The field gradient goes through a face adjoint buffer
+ * (one float4 per cell face of every brick) that the first call allocates,
+ * up to half of the free device memory, and keeps until release. Where
+ * not all bricks fit at once, they are replayed in groups of consecutive
+ * ranks, two launches per group. */
 dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, float* dL_dvol);
 
 /* Counters (synchronises the device stream). */

@@ -128,6 +128,8 @@ struct dpv_device_t {
     float4* d_gface = nullptr;
     size_t gface_cap = 0;               // slots allocated
     size_t gface_slots = 0;             // slots the current bricks need
+    size_t gface_tried = 0;             // slots asked for at the last allocation
+    std::vector<size_t> gface_off_h;    // first slot of each brick (nranks + 1)
     unsigned char* d_empty = nullptr;   // macro-cell transparency of every brick
     size_t empty_cap = 0;
     int* d_tfz = nullptr;               // TF opaque-entry prefix counts (MAX_TF)
@@ -440,9 +442,11 @@ dpv_status prepare(dpv_device dev) {
         size_t off = 0;
         long long mo = 0;
         std::vector<int> first(dev->nranks + 1, 0), nb;
+        dev->gface_off_h.assign(dev->nranks + 1, 0);
         for (int k = 0; k < dev->nranks; ++k) {
             const HostBrick& h = dev->bricks[k];
             table[k].gface_off = (long long)off;
+            dev->gface_off_h[k] = off;
             off += face_slots(h.s_n);
             mo = std::max(mo, (long long)(h.hi[1] - h.lo[1]) * (h.hi[2] - h.lo[2]));
             first[k] = (int)nb.size();
@@ -456,6 +460,7 @@ dpv_status prepare(dpv_device dev) {
             }
         }
         first[dev->nranks] = (int)nb.size();
+        dev->gface_off_h[dev->nranks] = off;
         dev->gface_slots = off;
         dev->max_rows = mo;
         if (!dev->d_nb_first) {
@@ -1315,29 +1320,52 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
             return s;
     }
     CK(cudaMemsetAsync(dL_dtf, 0, sizeof(double) * 4 * dev->ntf, dev->stream), "zero dtf");
-    // field gradient: through the face adjoint buffer (two vector atomics per
-    // cell flush, then one gather that writes every node) where it fits in
-    // half of the free device memory; DPV_FACE_GRAD=0 selects the scalar
-    // atomics into the field instead
+    // field gradient: through the face adjoint buffer (two vector reductions
+    // per sample, then a gather that writes every node) where the slots of
+    // the largest brick fit in half of the free device memory.  Where the
+    // whole buffer does not fit, the bricks are taken in groups of
+    // consecutive ranks whose slots fit: each group's items are replayed,
+    // then its slots are gathered and added into the field.
+    // DPV_FACE_GRAD=0 selects the scalar atomics into the field instead;
+    // DPV_FACE_GROUP=n takes at most n bricks per group.
     const bool staged = (dev->frame.flags & DPV_FRAME_STAGED) != 0;
     bool faces = dL_dvol && !staged && dev->gface_slots > 0;
     if (faces) {
         if (const char* env = getenv("DPV_FACE_GRAD")) faces = atoi(env) != 0;
     }
-    if (faces && dev->gface_cap < dev->gface_slots) {
+    const size_t want = dev->gface_slots;
+    int group_max = dev->nranks;
+    if (const char* env = getenv("DPV_FACE_GROUP")) {
+        int v = atoi(env);
+        if (v > 0 && v < group_max) group_max = v;
+    }
+    size_t max_brick = 0;
+    for (int k = 0; k < dev->nranks; ++k)
+        max_brick = std::max(max_brick, dev->gface_off_h[k + 1] - dev->gface_off_h[k]);
+    if (faces && dev->gface_cap < want && dev->gface_tried != want) {
         dev_free(dev->d_gface);
         dev->d_gface = nullptr;
         dev->gface_cap = 0;
+        dev->gface_tried = want;
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
-        if (dev->gface_slots * sizeof(float4) <= free_b / 2 &&
-            cudaMalloc((void**)&dev->d_gface, dev->gface_slots * sizeof(float4)) == cudaSuccess)
-            dev->gface_cap = dev->gface_slots;
+        size_t n = std::min(want, free_b / 2 / sizeof(float4));
+        if (n >= max_brick && cudaMalloc((void**)&dev->d_gface, n * sizeof(float4)) == cudaSuccess)
+            dev->gface_cap = n;
         else
             cudaGetLastError();
     }
-    faces = faces && dev->d_gface && dev->gface_cap >= dev->gface_slots;
-    if (faces)
+    faces = faces && dev->d_gface && dev->gface_cap >= max_brick;
+    // groups [grp[i], grp[i + 1]) of consecutive ranks
+    std::vector<int> grp{0};
+    if (faces) {
+        for (int k = 0; k < dev->nranks; ++k)
+            if (dev->gface_off_h[k + 1] - dev->gface_off_h[grp.back()] > dev->gface_cap || k - grp.back() >= group_max)
+                grp.push_back(k);
+    }
+    grp.push_back(dev->nranks);
+    const int ngroups = (int)grp.size() - 1;
+    if (faces && ngroups == 1)
         CK(cudaMemsetAsync(dev->d_gface, 0, dev->gface_slots * sizeof(float4), dev->stream), "zero face buffer");
     else if (dL_dvol)
         CK(cudaMemsetAsync(dL_dvol, 0, sizeof(float) * (size_t)dev->dims[0] * dev->dims[1] * dev->dims[2], dev->stream),
@@ -1351,25 +1379,38 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
     t0 = stage_start(dev);
     const bool persistent = (dev->frame.flags & DPV_FRAME_PERSISTENT) != 0;
     Schedule sch{dev->d_sched, dev->d_work, 0};   // the pull order built by the render
-    if (!staged) {
+    if (!staged && faces) {
+        for (int g = 0; g < ngroups; ++g) {
+            const FaceGroup fg{grp[g], grp[g + 1], (long long)dev->gface_off_h[grp[g]]};
+            if (ngroups > 1)
+                CK(cudaMemsetAsync(dev->d_gface, 0,
+                                   (dev->gface_off_h[fg.k1] - dev->gface_off_h[fg.k0]) * sizeof(float4), dev->stream),
+                   "zero face buffer");
+            CK(launch_march_bwd(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
+                                dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key,
+                                dev->d_frag_grad, dL_dtf, nullptr, dev->d_gface, dev->d_counters, dev->stream,
+                                persistent ? &sch : nullptr, &fg),
+               "march backward");
+            CK(launch_face_gather(dev->d_bricks, dev->nranks, dev->d_nb_first, dev->d_nb, dev->max_rows,
+                                  dev->d_gface, dev->dims, dL_dvol, dev->stream, ngroups > 1 ? &fg : nullptr),
+               "face gather");
+        }
+        dev->launches += ngroups * ((dev->n_items > 0 ? 1 : 0) + (dev->max_rows > 0 ? 1 : 0));
+    } else if (!staged) {
         CK(launch_march_bwd(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                             dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key,
-                            dev->d_frag_grad, dL_dtf, faces ? nullptr : dL_dvol, faces ? dev->d_gface : nullptr,
-                            dev->d_counters, dev->stream, persistent ? &sch : nullptr),
+                            dev->d_frag_grad, dL_dtf, dL_dvol, nullptr, dev->d_counters, dev->stream,
+                            persistent ? &sch : nullptr),
            "march backward");
-        if (faces) {
-            CK(launch_face_gather(dev->d_bricks, dev->nranks, dev->d_nb_first, dev->d_nb, dev->max_rows,
-                                  dev->d_gface, dev->dims, dL_dvol, dev->stream),
-               "face gather");
-            dev->launches += 1;
-        }
+        dev->launches += dev->n_items > 0 ? 1 : 0;
     } else
         CK(launch_march_bwd_staged(dev->bricks[0].dtype, P, dev->d_cams, dev->d_bricks, dev->d_scales, dev->d_items,
                                    dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key, dev->d_frag_grad,
                                    dL_dtf, dL_dvol, dev->d_counters, dev->stream),
            "march backward");
     stage_stop(dev, DPV_STAGE_MARCH_BWD, t0);
-    dev->launches += 1 + (dev->n_items > 0 ? 1 : 0);
+    if (staged) dev->launches += dev->n_items > 0 ? 1 : 0;
+    dev->launches += 1;   // the compositor's adjoint
     return DPV_OK;
 }
 

@@ -1443,7 +1443,8 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                                                        const BrickDev* bricks, const float* scales, const Item& it,
                                                        long long item, const float4* s_tf, float* my_tab,
                                                        const float4* frag_rgba, const int* frag_key,
-                                                       const float4* frag_grad, float* dvol, float4* gface) {
+                                                       const float4* frag_grad, float* dvol, float4* gface,
+                                                       long long gbase) {
     const BrickDev b = bricks[it.brick];
     const CamBasis cam = cams[it.cam];
     const float scale = scales[b.scale_idx];
@@ -1527,7 +1528,8 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                         // straight into the face buffer, two vector reductions per
                         // sample: cheaper than a register run per cell, whose
                         // eight accumulators cost the loop registers
-                        const long long gb = b.gface_off + (long long)iz * b.qxy + (long long)iy * b.qx + ix;
+                        const long long gb =
+                            b.gface_off - gbase + (long long)iz * b.qxy + (long long)iy * b.qx + ix;
                         float ax = 1.0f - fx, ay = 1.0f - fy, az = 1.0f - fz;
                         float gyz0 = gs * ay * az, gyz1 = gs * fy * az, gyz2 = gs * ay * fz, gyz3 = gs * fy * fz;
                         atomicAdd(gface + gb, make_float4(gyz0 * ax, gyz0 * fx, gyz1 * ax, gyz1 * fx));
@@ -1571,8 +1573,11 @@ __global__ void __launch_bounds__(256, 3) k_march_bwd(FrameParams P, const CamBa
                                                    const float* scales, const Item* items, const float4* tf,
                                                    const float4* frag_rgba, const int* frag_key,
                                                    const float4* frag_grad, int ncopy, double* dtf, float* dvol,
-                                                   float4* gface, Counters* counters) {
+                                                   float4* gface, FaceGroup fg, Counters* counters) {
     extern __shared__ float4 s_mem[];
+    const Item it = items[blockIdx.x];
+    // an item of a brick outside the face group: the whole CTA leaves
+    if (FACE && (it.brick < fg.k0 || it.brick >= fg.k1)) return;
     float4* s_tf = s_mem;
     float* s_g = (float*)(s_mem + P.ntf);
     const int stride = 4 * P.ntf + 1;
@@ -1580,11 +1585,10 @@ __global__ void __launch_bounds__(256, 3) k_march_bwd(FrameParams P, const CamBa
     for (int i = threadIdx.x; i < ncopy * stride; i += blockDim.x) s_g[i] = 0.0f;
     __syncthreads();
     float* my_tab = s_g + (threadIdx.x % ncopy) * stride;
-    const Item it = items[blockIdx.x];
     unsigned long long nsamp = 0;
     if (item_ok(it, P))
         nsamp = bwd_item<T, GL, FACE>(P, cams, bricks, scales, it, blockIdx.x, s_tf, my_tab, frag_rgba, frag_key,
-                                  frag_grad, dvol, gface);
+                                  frag_grad, dvol, gface, fg.base);
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
     __syncthreads();
@@ -1604,7 +1608,8 @@ __global__ void __launch_bounds__(256, 3) k_march_bwd_persistent(FrameParams P, 
                                                               unsigned int* work, const float4* tf,
                                                               const float4* frag_rgba, const int* frag_key,
                                                               const float4* frag_grad, int ncopy, double* dtf,
-                                                              float* dvol, float4* gface, Counters* counters) {
+                                                              float* dvol, float4* gface, FaceGroup fg,
+                                                              Counters* counters) {
     extern __shared__ float4 s_mem[];
     __shared__ int s_next;
     float4* s_tf = s_mem;
@@ -1622,9 +1627,9 @@ __global__ void __launch_bounds__(256, 3) k_march_bwd_persistent(FrameParams P, 
         if (i >= n_items) break;
         const int item = sched[i];
         const Item it = items[item];
-        if (item_ok(it, P))
+        if (item_ok(it, P) && (!FACE || (it.brick >= fg.k0 && it.brick < fg.k1)))
             nsamp += bwd_item<T, GL, FACE>(P, cams, bricks, scales, it, item, s_tf, my_tab, frag_rgba, frag_key,
-                                       frag_grad, dvol, gface);
+                                       frag_grad, dvol, gface, fg.base);
     }
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
@@ -1640,7 +1645,7 @@ template <typename T, int GL, bool FACE>
 static void bwd_launch_f(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                          const Item* items, int n_items, const float4* tf, const float4* frag_rgba,
                          const int* frag_key, const float4* frag_grad, double* dtf, float* dvol, float4* gface,
-                         Counters* counters, const Schedule* sch, cudaStream_t st) {
+                         FaceGroup fg, Counters* counters, const Schedule* sch, cudaStream_t st) {
     int ncopy = bwd_tf_copies(P.ntf);
     size_t smem = sizeof(float4) * P.ntf + sizeof(float) * (size_t)ncopy * (4 * P.ntf + 1);
     if (sch) {
@@ -1656,44 +1661,45 @@ static void bwd_launch_f(const FrameParams& P, const CamBasis* cams, const Brick
         cudaMemsetAsync(sch->work, 0, sizeof(unsigned int), st);
         k_march_bwd_persistent<T, GL, FACE><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched,
                                                                   n_items, sch->work, tf, frag_rgba, frag_key,
-                                                                  frag_grad, ncopy, dtf, dvol, gface, counters);
+                                                                  frag_grad, ncopy, dtf, dvol, gface, fg, counters);
         return;
     }
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_march_bwd<T, GL, FACE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_march_bwd<T, GL, FACE><<<n_items, P.tp, smem, st>>>(P, cams, bricks, scales, items, tf, frag_rgba, frag_key,
-                                                            frag_grad, ncopy, dtf, dvol, gface, counters);
+                                                            frag_grad, ncopy, dtf, dvol, gface, fg, counters);
 }
 
 // the face-buffer path and the scalar-atomic path are separate instances
 template <typename T, int GL>
 static void bwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                        const Item* items, int n_items, const float4* tf, const float4* frag_rgba, const int* frag_key,
-                       const float4* frag_grad, double* dtf, float* dvol, float4* gface, Counters* counters,
-                       const Schedule* sch, cudaStream_t st) {
+                       const float4* frag_grad, double* dtf, float* dvol, float4* gface, FaceGroup fg,
+                       Counters* counters, const Schedule* sch, cudaStream_t st) {
     if (gface)
         bwd_launch_f<T, GL, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf,
-                                  dvol, gface, counters, sch, st);
+                                  dvol, gface, fg, counters, sch, st);
     else
         bwd_launch_f<T, GL, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf,
-                                   dvol, gface, counters, sch, st);
+                                   dvol, gface, fg, counters, sch, st);
 }
 
 cudaError_t launch_march_bwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, const float4* frag_rgba, const int* frag_key,
                              const float4* frag_grad, double* dtf, float* dvol, float4* gface,
-                             Counters* counters, cudaStream_t st, const Schedule* sch) {
+                             Counters* counters, cudaStream_t st, const Schedule* sch, const FaceGroup* fgp) {
     if (n_items == 0) return cudaSuccess;
+    const FaceGroup fg = fgp ? *fgp : FaceGroup{0, P.nbricks, 0};
 #define BWD(T)                                                                                                  \
     (gather == GATHER_CELL                                                                                          \
          ? bwd_launch<T, GATHER_CELL>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad,   \
-                                      dtf, dvol, gface, counters, sch, st)                                          \
+                                      dtf, dvol, gface, fg, counters, sch, st)                                      \
      : gather == GATHER_QUAD                                                                                        \
          ? bwd_launch<T, GATHER_QUAD>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad,   \
-                                      dtf, dvol, gface, counters, sch, st)                                          \
+                                      dtf, dvol, gface, fg, counters, sch, st)                                      \
          : bwd_launch<T, GATHER_LINEAR>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, \
-                                        dtf, dvol, gface, counters, sch, st))
+                                        dtf, dvol, gface, fg, counters, sch, st))
     switch (dtype) {
         case 0: BWD(float); break;
         case 1: BWD(__half); break;
@@ -1929,19 +1935,28 @@ size_t face_slots(const int s_n[3]) { return (size_t)(s_n[0] - 1) * (s_n[1] - 1)
 constexpr int GR = 4;
 
 __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, const int* nb_first, const int* nb,
-                                                     const float4* gface, int dims0, int dims1, float* dvol) {
+                                                     const float4* gface, int dims0, int dims1, float* dvol,
+                                                     FaceGroup fg, int add) {
     const int o = blockIdx.y;
+    const int j0 = nb_first[o], j1 = nb_first[o + 1];
+    // with a group: the owner's own slots count if it is in the group; an
+    // owner outside it gathers only where a group brick stores its nodes
+    const bool own = o >= fg.k0 && o < fg.k1;
+    if (!own) {
+        bool any = false;
+        for (int j = j0 + 1; j < j1; ++j) any = any || (nb[j] >= fg.k0 && nb[j] < fg.k1);
+        if (!any) return;
+    }
     const BrickDev bo = bricks[o];
     const int nx = bo.o_hi[0] - bo.o_lo[0], ny = bo.o_hi[1] - bo.o_lo[1], nz = bo.o_hi[2] - bo.o_lo[2];
     const int ngy = (ny + GR - 1) / GR;
     const int ngroups = ngy * nz;
-    const int j0 = nb_first[o], j1 = nb_first[o + 1];
     const int lane = threadIdx.x & 31;
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
         const int yy0 = (grp % ngy) * GR, zz = grp / ngy;
         const int gy0 = bo.o_lo[1] + yy0, gz = bo.o_lo[2] + zz;
         const int ly0 = gy0 - bo.s_lo[1], lz = gz - bo.s_lo[2];
-        const float4* F = gface + bo.gface_off + (long long)lz * bo.qxy;
+        const long long fo = bo.gface_off - fg.base + (long long)lz * bo.qxy;   // read only if own
         // block-uniform trip count: the shuffles below need every lane
         for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
             const int xo = x0 + threadIdx.x;
@@ -1955,8 +1970,8 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
 #pragma unroll
             for (int k = 0; k <= GR; ++k) {
                 const int fy = ly0 - 1 + k;
-                const bool ok = act && xr && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
-                A[k] = ok ? F[(long long)fy * bo.qx + lx] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool ok = own && act && xr && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
+                A[k] = ok ? gface[fo + (long long)fy * bo.qx + lx] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
             for (int k = 0; k <= GR; ++k) {
@@ -1967,8 +1982,9 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
 #pragma unroll
                 for (int k = 0; k <= GR; ++k) {
                     const int fy = ly0 - 1 + k;
-                    const bool ok = act && xl && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
-                    const float4 q = ok ? F[(long long)fy * bo.qx + lx - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const bool ok = own && act && xl && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
+                    const float4 q =
+                        ok ? gface[fo + (long long)fy * bo.qx + lx - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
                     Ly[k] = q.y;
                     Lw[k] = q.w;
                 }
@@ -1983,12 +1999,15 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
                 float v = A[k + 1].x + Ly[k + 1] + A[k].z + Lw[k];
                 // ghost copies in other bricks exist only for nodes on the
                 // owned box's surface
-                if (yy == 0 || yy == ny - 1 || zz == 0 || zz == nz - 1 || xo == 0 || xo == nx - 1) {
+                const bool surface = yy == 0 || yy == ny - 1 || zz == 0 || zz == nz - 1 || xo == 0 || xo == nx - 1;
+                if (!own && !surface) continue;
+                if (surface) {
                     for (int j = j0 + 1; j < j1; ++j) {
+                        if (nb[j] < fg.k0 || nb[j] >= fg.k1) continue;
                         const BrickDev& b = bricks[nb[j]];
                         const int mx = gx - b.s_lo[0], my = gy - b.s_lo[1], mz = gz - b.s_lo[2];
                         if (mx < 0 || my < 0 || mz < 0 || mx >= b.s_n[0] || my >= b.s_n[1] || mz >= b.s_n[2]) continue;
-                        const float4* G = gface + b.gface_off + (long long)mz * b.qxy;
+                        const float4* G = gface + (b.gface_off - fg.base) + (long long)mz * b.qxy;
                         const bool bxl = mx >= 1, bxr = mx <= b.s_n[0] - 2, byl = my >= 1, byr = my <= b.s_n[1] - 2;
                         const long long q0 = (long long)my * b.qx, q1 = q0 - b.qx;
                         if (bxr && byr) v += G[q0 + mx].x;
@@ -1997,7 +2016,11 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
                         if (bxl && byl) v += G[q1 + mx - 1].w;
                     }
                 }
-                dvol[((long long)gz * dims1 + gy) * dims0 + gx] = v;
+                float* dst = dvol + ((long long)gz * dims1 + gy) * dims0 + gx;
+                if (add)
+                    *dst += v;
+                else
+                    *dst = v;
             }
         }
     }
@@ -2005,12 +2028,13 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
 
 cudaError_t launch_face_gather(const BrickDev* bricks, int nbricks, const int* nb_first, const int* nb,
                                long long max_rows, const float4* gface, const int dims[3], float* dvol,
-                               cudaStream_t st) {
+                               cudaStream_t st, const FaceGroup* fgp) {
     if (nbricks <= 0 || max_rows <= 0) return cudaSuccess;
+    const FaceGroup fg = fgp ? *fgp : FaceGroup{0, nbricks, 0};
     long long groups = (max_rows + GR - 1) / GR;
     long long bx = groups < 4096 ? groups : 4096;
     dim3 grid((unsigned)bx, (unsigned)nbricks);
-    k_face_gather<<<grid, 128, 0, st>>>(bricks, nb_first, nb, gface, dims[0], dims[1], dvol);
+    k_face_gather<<<grid, 128, 0, st>>>(bricks, nb_first, nb, gface, dims[0], dims[1], dvol, fg, fgp ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,14 @@ struct CommitArgs {
 };
 
 // Persistent launches: the order in which CTAs pull work items.
+// A group of consecutive bricks [k0, k1) whose face adjoint slots sit in the
+// buffer from slot `base` (the first slot of brick k0) on: the adjoint
+// replays only the group's items, and the gather adds the group's slots.
+struct FaceGroup {
+    int k0, k1;
+    long long base;
+};
+
 struct Schedule {
     const int* sched;        // pull index -> work item
     unsigned int* work;      // pull counter (reset by the launcher)
@@ -114,17 +122,21 @@ cudaError_t launch_march_bwd(int dtype, int gather, const FrameParams& P, const 
                              const BrickDev* bricks, const float* scales, const Item* items, int n_items,
                              const float4* tf, const float4* frag_rgba, const int* frag_key,
                              const float4* frag_grad, double* dtf, float* dvol, float4* gface,
-                             Counters* counters, cudaStream_t st, const Schedule* sch = nullptr);
+                             Counters* counters, cudaStream_t st, const Schedule* sch = nullptr,
+                             const FaceGroup* fg = nullptr);
 
 // Face adjoint buffer (kernels.cu): float4 slots it needs for a brick (one
 // per cell face, as the gather layout), and the pass that turns the buffer
 // into the global field gradient: every owned node of every brick is
 // written once (no zeroing needed) with the sum of its face slots over the
 // bricks in its owner's neighbour list nb[nb_first[o] .. nb_first[o+1]).
+// With a group `fg`, only the group's bricks' slots are summed, and they are
+// added to the field (zeroed before the first group) at the nodes the group
+// stores.
 size_t face_slots(const int s_n[3]);
 cudaError_t launch_face_gather(const BrickDev* bricks, int nbricks, const int* nb_first, const int* nb,
                                long long max_rows, const float4* gface, const int dims[3], float* dvol,
-                               cudaStream_t st);
+                               cudaStream_t st, const FaceGroup* fg = nullptr);
 
 // Gather layout of a brick (kernels.cu): bytes it needs, and its build from
 // the stored nodes.

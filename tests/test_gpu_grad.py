@@ -162,6 +162,40 @@ def test_face_buffer_matches_scalar_atomics(monkeypatch, split):
     dev.release()
 
 
+@pytest.mark.parametrize("split", ["regular", "kd"])
+def test_face_buffer_in_brick_groups(monkeypatch, split):
+    """Where the face buffer does not fit, the adjoint takes the bricks in
+    groups: it replays one group's items into the buffer, gathers the
+    group's slots and adds them into the field, then takes the next group.
+    Forced here with at most n bricks per group: the field and TF gradients
+    equal the one-buffer pass up to atomic summation order, and each extra
+    group costs one replay and one gather launch."""
+    dims = (40, 36, 32)
+    cams = inputs.sphere_cameras(dims, 2, seed=4)
+    kw = dict(splits=(2, 2, 2)) if split == "regular" else dict(kd=7)
+    sc = scenes.make(dims, nblobs=10, cams=cams, width=48, height=40, **kw)
+    K = sc.part.num_ranks
+    dev = scenes.gpu_device(sc, order=False)
+    dev.render()
+    g = torch.from_numpy(inputs.rng(2, inputs.STREAM_GRAD).normal(size=(len(sc.cams), sc.height, sc.width, 4))
+                         .astype(np.float32)).cuda()
+    monkeypatch.delenv("DPV_FACE_GRAD", raising=False)
+    monkeypatch.delenv("DPV_FACE_GROUP", raising=False)
+    dev.reset_stats()
+    dtf0, dvol0 = dev.backward(g)
+    l0 = dev.stats()["kernel_launches"]
+    assert float(dvol0.abs().max()) > 0
+    for n in (1, 3):
+        monkeypatch.setenv("DPV_FACE_GROUP", str(n))
+        dev.reset_stats()
+        dtf, dvol = dev.backward(g)
+        groups = -(-K // n)
+        assert dev.stats()["kernel_launches"] == l0 + 2 * (groups - 1)
+        assert torch.allclose(dvol, dvol0, rtol=1e-5, atol=1e-6 * float(dvol0.abs().max()))
+        assert torch.allclose(dtf, dtf0, rtol=1e-5, atol=1e-6 * float(dtf0.abs().max()))
+    dev.release()
+
+
 def test_adjoint_run_to_run_spread():
     """The forward has no atomics and is bit-deterministic (test_gpu_parity);
     the adjoint sums with FP32 atomics in whatever order the hardware takes,
