@@ -167,6 +167,52 @@ def test_large_full_size_reduced_precision(orc, storage):
     dev.release()
 
 
+def test_large_adjoint_in_brick_groups(monkeypatch):
+    """2048^3 fp8, 64 bricks, 8 cameras at 3840x2160: the face adjoint buffer
+    for all bricks would need 138 GB, so the adjoint runs it over groups of
+    bricks (more than one group here).  Its field gradient equals the one
+    through scalar atomics into the field (another summation order) on 4 M
+    seeded nodes plus every node of the planes on both sides of each brick
+    boundary in x, where the groups' ghost copies meet; the TF gradients
+    agree too."""
+    cfg = bench.CONFIGS["large_fp8"]
+    field = bench._field(cfg, "cuda")
+    part = bench._partition(cfg)
+    cams = [scenes.f32_camera(c) for c in bench._cameras(cfg)]
+    dev = _bench_device(cfg, field, part, cams)
+    del field
+    torch.cuda.empty_cache()
+    H, W = cfg["height"], cfg["width"]
+    g = torch.from_numpy(inputs.rng(5, inputs.STREAM_GRAD).normal(size=(len(cams), H, W, 4)).astype(np.float32)).cuda()
+    nx, ny, nz = cfg["dims"]
+    idx = torch.from_numpy(inputs.rng(6, inputs.STREAM_SELECT).integers(0, nx * ny * nz, size=4 << 20)).cuda()
+    cuts = sorted({int(v) for lo, hi in zip(part.lo, part.hi) for v in (lo[0] - 1, lo[0], hi[0] - 1, hi[0])
+                   if 0 <= v < nx})
+    monkeypatch.delenv("DPV_FACE_GRAD", raising=False)
+    monkeypatch.delenv("DPV_FACE_GROUP", raising=False)
+    out = []
+    for scalar in (False, True):
+        if scalar:
+            monkeypatch.setenv("DPV_FACE_GRAD", "0")
+        dev.reset_stats()
+        dtf, dvol = dev.backward(g)
+        launches = dev.stats()["kernel_launches"]
+        flat = dvol.reshape(-1)
+        out.append((dtf.cpu().numpy(), flat[idx].cpu().numpy(), dvol[:, :, cuts].cpu().numpy(), launches))
+        del dvol, flat
+        torch.cuda.empty_cache()
+    (tf_g, s_g, c_g, l_g), (tf_s, s_s, c_s, l_s) = out
+    groups = (l_g - 1) // 2
+    print("large fp8 adjoint: %d face-buffer groups" % groups)
+    assert groups > 1 and l_s == 2
+    for a, b in ((s_g, s_s), (c_g, c_s)):
+        m = float(np.abs(b).max())
+        assert m > 0
+        np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-5 * m)
+    np.testing.assert_allclose(tf_g, tf_s, rtol=1e-4, atol=1e-6 * float(np.abs(tf_s).max()))
+    dev.release()
+
+
 def _diff_inputs():
     cfg = bench.CONFIGS["diff"]
     field = bench._field(cfg, "cuda")
