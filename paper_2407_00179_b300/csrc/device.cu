@@ -1359,9 +1359,10 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
     // groups [grp[i], grp[i + 1]) of consecutive ranks
     std::vector<int> grp{0};
     if (faces) {
-        for (int k = 0; k < dev->nranks; ++k)
-            if (dev->gface_off_h[k + 1] - dev->gface_off_h[grp.back()] > dev->gface_cap || k - grp.back() >= group_max)
-                grp.push_back(k);
+        for (int k = 0; k < dev->nranks; ++k) {
+            const bool full = dev->gface_off_h[k + 1] - dev->gface_off_h[grp.back()] > dev->gface_cap;
+            if (full || k - grp.back() >= group_max) grp.push_back(k);
+        }
     }
     grp.push_back(dev->nranks);
     const int ngroups = (int)grp.size() - 1;
