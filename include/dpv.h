@@ -334,9 +334,12 @@ dpv_status dpvMapOrder(dpv_device dev, int camera, const uint8_t** order, int* s
  * of the last render: call it before the next render.  Asynchronous on the
  * device stream.  The field gradient goes through a face adjoint buffer
  * (one float4 per cell face of every brick) that the first call allocates,
- * up to half of the free device memory, and keeps until release. Where
- * not all bricks fit at once, they are replayed in groups of consecutive
- * ranks, two launches per group. */
+ * up to half of the free device memory, and keeps until release (it is not
+ * tried again until the bricks' sizes change). Where not all bricks fit at
+ * once, they are replayed in groups of consecutive ranks, two launches per
+ * group. Where not even one brick fits, the field gradient goes with scalar
+ * atomics straight into dL_dvol. Environment (tests): DPV_FACE_GRAD=0 takes
+ * the scalar atomics; DPV_FACE_GROUP=n puts at most n bricks in a group. */
 dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, float* dL_dvol);
 
 /* Counters (synchronises the device stream). */
