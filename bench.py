@@ -44,13 +44,13 @@ TRAFFIC = {
     # the autotuner picks the per-item or the persistent form of the same
     # per-item code; their DRAM traffic is within 3 % (persistent 4.93 GB)
     ("mid", "march"): 4.818e9,        # k_march_fwd<float, cell, 0>: 4.790 GB read + 28.7 MB written
-    ("mid", "march_bwd"): 12.67e9,    # k_march_bwd<float, cell, face> 9.90 GB + k_face_gather 2.77 GB
+    ("mid", "march_bwd"): 12.37e9,    # k_march_bwd<float, cell, face> 9.60 GB + k_face_gather 2.77 GB
 }
 
 # L1 / L2 sector hit rates of the timed kernels, from the same ncu captures
 HIT_RATES = {
     ("mid", "march"): (0.538, 0.333),
-    ("mid", "march_bwd"): (None, 0.585),      # the adjoint's L1 rate counts its reductions, which bypass L1
+    ("mid", "march_bwd"): (0.542, 0.538),     # L1: global loads only (the reductions bypass L1)
 }
 
 # FP32 arithmetic per sample counted in the source (an FMA counts once):

@@ -1405,7 +1405,7 @@ cudaError_t launch_composite_bwd(const FrameParams& P, const int* tile_first, co
 // segment keeps the sums of the entry the two segments share.  Nearby rays share TF
 // segments, so a single shared table would serialise the flushes of a warp
 // on the same addresses; the CTA keeps `ncopy` FP32 copies of the TF
-// gradient table (bwd_tf_copies), lane l writing copy l % ncopy (copies
+// gradient table (bwd_tf_copies; the copy of a lane: tf_copy) (copies
 // offset by one float so equal entries of different copies sit in different
 // banks).  At the end the copies are summed and added to the global FP64
 // table once per touched entry.  The voxel gradient goes, per sample, as two
@@ -1428,11 +1428,22 @@ __device__ __forceinline__ void tf_flush_f(TFRunF& r, float* tab) {
 }
 
 // Copies of the FP32 TF gradient table per CTA: as many as fit in 64 KB of
-// shared memory, at most 16 (lanes l and l + 16 of a warp, two pixel rows
-// apart, share one), so that three CTAs still fit on an SM.
+// shared memory, at most 8 (the four lanes of a warp's pixel column share
+// one).  Shared memory and L1 share each SM's 256 KB and registers hold the
+// kernel to three CTAs per SM either way: at 256 entries, 8 copies leave
+// the gather about 140 KB of L1 instead of about 45 KB with 16 copies
+// (measured at mid: 7.61 -> 6.72 ms; 4 copies 6.81, 2 copies 7.16).
 int bwd_tf_copies(int ntf) {
     int c = 65536 / (16 * ntf);
-    return c < 1 ? 1 : (c > 16 ? 16 : c);
+    return c < 1 ? 1 : (c > 8 ? 8 : c);
+}
+
+// The copy a thread flushes into.  A warp covers an 8 x 4 pixel block (lane
+// = x + 8 y), and neighbouring rays tend to hit the same TF entries, so the
+// lanes that share a copy lie on a diagonal, (x + 2 y) mod ncopy, rather
+// than in one column (x mod ncopy): 6.72 -> 6.54 ms at mid with 8 copies.
+__device__ __forceinline__ int tf_copy(int tid, int ncopy) {
+    return ((tid & 7) + 2 * ((tid >> 3) & 3)) % ncopy;
 }
 
 // One work item of the adjoint: replay each thread's fragment and
@@ -1584,7 +1595,7 @@ __global__ void __launch_bounds__(256, 3) k_march_bwd(FrameParams P, const CamBa
     for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
     for (int i = threadIdx.x; i < ncopy * stride; i += blockDim.x) s_g[i] = 0.0f;
     __syncthreads();
-    float* my_tab = s_g + (threadIdx.x % ncopy) * stride;
+    float* my_tab = s_g + tf_copy(threadIdx.x, ncopy) * stride;
     unsigned long long nsamp = 0;
     if (item_ok(it, P))
         nsamp = bwd_item<T, GL, FACE>(P, cams, bricks, scales, it, blockIdx.x, s_tf, my_tab, frag_rgba, frag_key,
@@ -1617,7 +1628,7 @@ __global__ void __launch_bounds__(256, 3) k_march_bwd_persistent(FrameParams P, 
     const int stride = 4 * P.ntf + 1;
     for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
     for (int i = threadIdx.x; i < ncopy * stride; i += blockDim.x) s_g[i] = 0.0f;
-    float* my_tab = s_g + (threadIdx.x % ncopy) * stride;
+    float* my_tab = s_g + tf_copy(threadIdx.x, ncopy) * stride;
     unsigned long long nsamp = 0;
     for (;;) {
         __syncthreads();
