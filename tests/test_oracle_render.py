@@ -1,6 +1,7 @@
 """Oracle pins for the forward render.
 
-* camera convention: geometric properties of the rays;
+* camera convention: geometric properties of the rays, and the rays of
+  the OpenGL look-at / perspective unprojection;
 * closed form 1 (constant slab): A = 1 - exp(-sigma d), C = c A;
 * closed form 2 (linear extinction): the midpoint samples integrate a linear
   sigma exactly, on axis-aligned and oblique rays;
@@ -55,6 +56,69 @@ def test_camera_rays_geometry(orc):
     # horizontal field of view scales with the aspect ratio W / H
     _, d = orc.camera_ray(cam, W, H, W - 1, 3)
     assert abs(math.atan2(d @ r, d @ f) - math.atan(((W - 0.5) / W * 2 - 1) * W / H * math.tan(math.radians(20)))) < 1e-14
+
+
+def _gl_look_at(eye, center, up):
+    """The viewing matrix of the fixed-function OpenGL look-at (world to eye
+    coordinates, the eye looking down -z), as its reference page defines it."""
+    f = np.asarray(center, np.float64) - np.asarray(eye, np.float64)
+    f /= np.linalg.norm(f)
+    s = np.cross(f, np.asarray(up, np.float64))
+    s /= np.linalg.norm(s)
+    u = np.cross(s, f)
+    m = np.eye(4)
+    m[0, :3], m[1, :3], m[2, :3] = s, u, -f
+    t = np.eye(4)
+    t[:3, 3] = -np.asarray(eye, np.float64)
+    return m @ t
+
+
+def _gl_perspective(fovy_deg, aspect, near, far):
+    """The fixed-function OpenGL perspective projection (eye to clip
+    coordinates), as its reference page defines it."""
+    f = 1.0 / math.tan(math.radians(fovy_deg) / 2.0)
+    p = np.zeros((4, 4))
+    p[0, 0] = f / aspect
+    p[1, 1] = f
+    p[2, 2] = (far + near) / (near - far)
+    p[2, 3] = 2.0 * far * near / (near - far)
+    p[3, 2] = -1.0
+    return p
+
+
+def _gl_unproject(win, inv_pv, W, H):
+    """Window coordinates (x, y from the lower-left corner, depth in [0, 1])
+    to world coordinates through the inverse of projection x view."""
+    ndc = np.array([2.0 * win[0] / W - 1.0, 2.0 * win[1] / H - 1.0, 2.0 * win[2] - 1.0, 1.0])
+    w = inv_pv @ ndc
+    return w[:3] / w[3]
+
+
+@pytest.mark.parametrize("W,H", [(9, 7), (64, 36), (5, 11)])
+def test_camera_rays_match_the_gl_unprojection(orc, W, H):
+    """The camera convention pinned to a textbook one: the OpenGL look-at
+    and perspective matrices (vertical field of view, aspect W / H), whose
+    window origin is the lower-left corner.  A pixel centre unprojected at
+    the near and the far plane gives a segment; its direction, and the eye
+    as its origin, equal the oracle's ray for that pixel.  A transposed
+    basis, a flipped row order, a half-angle slip or the aspect on the wrong
+    axis fails here."""
+    rng = inputs.rng(11, inputs.STREAM_SELECT)
+    for trial in range(6):
+        eye = rng.normal(size=3) * 3.0
+        center = rng.normal(size=3) * 0.5
+        up = rng.normal(size=3)
+        fovy = float(rng.uniform(15.0, 80.0))
+        cam = inputs.Camera(tuple(eye), tuple(center), tuple(up), fovy)
+        inv_pv = np.linalg.inv(_gl_perspective(fovy, W / H, 0.5, 50.0) @ _gl_look_at(eye, center, up))
+        for px, py in [(0, 0), (W - 1, H - 1), (W // 2, 0), (1, H - 2), (W - 1, 0)]:
+            a = _gl_unproject((px + 0.5, py + 0.5, 0.0), inv_pv, W, H)
+            b = _gl_unproject((px + 0.5, py + 0.5, 1.0), inv_pv, W, H)
+            ref = (b - a) / np.linalg.norm(b - a)
+            o, d = orc.camera_ray(cam, W, H, px, py)
+            np.testing.assert_allclose(d, ref, atol=1e-9)
+            # the segment lies on the ray from the eye
+            np.testing.assert_allclose(np.cross(a - np.asarray(o), d), 0.0, atol=1e-8)
 
 
 # --------------------------------------------------------------------------
