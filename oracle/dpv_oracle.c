@@ -24,8 +24,9 @@
  * decoded per access and never copied into an FP64 array.
  *
  * Parity status: every function below is pinned by a CPU test against a
- * closed form, an invariant, a library routine or brute force, except the
- * camera convention, which is pinned only by geometric properties.
+ * closed form, an invariant, a library routine or brute force.  The camera
+ * convention (the paper fixes none) is pinned by geometric properties and
+ * by the OpenGL look-at / perspective unprojection of each pixel centre.
  */
 #include <math.h>
 #include <stdint.h>
