@@ -10,6 +10,7 @@ is in the C file.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -33,13 +34,22 @@ FLAG_SHADOW_AMBIG = 64
 ISO_EPS = 5e-5   # iso ambiguity band on s (a rounded sample may cross otherwise)
 
 
+_CFLAGS = ["-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math",
+           "-ffp-contract=off"]
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle C source (gcc, the flags of build()) into `out`."""
+    tmp = out + ".tmp.%d" % os.getpid()
+    subprocess.check_call(["gcc", *_CFLAGS, "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc, -O2, OpenMP) if missing or stale."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-fPIC", "-shared",
-                               "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+        compile_source(_SRC, _LIB)
     return _LIB
 
 
@@ -74,33 +84,50 @@ class _TF(C.Structure):
 _lib = None
 
 
+def _configure(l):
+    P = C.c_void_p
+    l.orc_render_full.argtypes = [P, P, P, P, P, C.c_int, P, P, P, P]
+    l.orc_render_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P, P, P, P, P]
+    l.orc_grad_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, C.c_double, P]
+    l.orc_composite.argtypes = [C.c_int, C.c_int, P, P, P, P]
+    l.orc_render_ordered.argtypes = [P, P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P]
+    l.orc_render_iso.argtypes = [P, P, C.c_int, P, P, P, P, C.c_double, C.c_double, C.c_int, P, P, P, P, P,
+                                 P, P]
+    l.orc_render_deep.argtypes = [P, C.c_int, P, P, P, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P]
+    l.orc_render_shadow.argtypes = [P, P, C.c_int, P, P, P, P, P, C.c_int, P, P, P, P, P, P]
+    l.orc_light_transmittance.argtypes = [P, P, C.c_int, P, P, P, P, C.c_int, P, P, P, P]
+    l.orc_kd_order.argtypes = [C.c_int, P, P, P, P, P, P]
+    l.orc_kd_order.restype = C.c_int
+    l.orc_camera_ray.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
+    l.orc_brick_scale.argtypes = [P, C.c_int64, C.c_int]
+    l.orc_brick_scale.restype = C.c_float
+    l.orc_quantize.argtypes = [P, C.c_int64, C.c_int, C.c_float, P]
+    l.orc_dequantize.argtypes = [P, C.c_int64, C.c_int, C.c_double, P]
+    l.orc_stored_box.argtypes = [P, P, P, P, P]
+    l.orc_extract_brick.argtypes = [P, P, P, P, P]
+    l.orc_max_threads.restype = C.c_int
+    l.orc_set_threads.argtypes = [C.c_int]
+    return l
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        P = C.c_void_p
-        _lib.orc_render_full.argtypes = [P, P, P, P, P, C.c_int, P, P, P, P]
-        _lib.orc_render_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P, P, P, P, P]
-        _lib.orc_grad_bricks.argtypes = [P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, C.c_double, P]
-        _lib.orc_composite.argtypes = [C.c_int, C.c_int, P, P, P, P]
-        _lib.orc_render_ordered.argtypes = [P, P, C.c_int, P, P, P, P, C.c_int, P, P, P, P, P, P]
-        _lib.orc_render_iso.argtypes = [P, P, C.c_int, P, P, P, P, C.c_double, C.c_double, C.c_int, P, P, P, P, P,
-                                        P, P]
-        _lib.orc_render_deep.argtypes = [P, C.c_int, P, P, P, P, C.c_int, C.c_int, P, P, P, P, P, P, P, P]
-        _lib.orc_render_shadow.argtypes = [P, P, C.c_int, P, P, P, P, P, C.c_int, P, P, P, P, P, P]
-        _lib.orc_light_transmittance.argtypes = [P, P, C.c_int, P, P, P, P, C.c_int, P, P, P, P]
-        _lib.orc_kd_order.argtypes = [C.c_int, P, P, P, P, P, P]
-        _lib.orc_kd_order.restype = C.c_int
-        _lib.orc_camera_ray.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
-        _lib.orc_brick_scale.argtypes = [P, C.c_int64, C.c_int]
-        _lib.orc_brick_scale.restype = C.c_float
-        _lib.orc_quantize.argtypes = [P, C.c_int64, C.c_int, C.c_float, P]
-        _lib.orc_dequantize.argtypes = [P, C.c_int64, C.c_int, C.c_double, P]
-        _lib.orc_stored_box.argtypes = [P, P, P, P, P]
-        _lib.orc_extract_brick.argtypes = [P, P, P, P, P]
-        _lib.orc_max_threads.restype = C.c_int
-        _lib.orc_set_threads.argtypes = [C.c_int]
+        _lib = _configure(C.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Run every wrapper against another build of an oracle source (the
+    tests compile copies with a planted mistake to show that a pin fails)."""
+    global _lib
+    prev = lib()
+    _lib = _configure(C.CDLL(path))
+    try:
+        yield _lib
+    finally:
+        _lib = prev
 
 
 def _p(a: np.ndarray):
