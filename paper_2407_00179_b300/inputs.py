@@ -259,6 +259,15 @@ def make_tf(seed: int = 1234, n: int = 256, n_ctrl: int = 8, transparent_below: 
     return tab.astype(np.float32)
 
 
+def linear_tf(n: int = 256) -> np.ndarray:
+    """RGBA table of n entries whose every channel is linear in s (no kink
+    between the end entries): r = 0.2 + 0.6 s, g = 0.8 - 0.5 s,
+    b = 0.3 + 0.4 s, alpha = 0.05 + 0.6 s.  Returns (n, 4) f32."""
+    xs = np.arange(n, dtype=np.float64) / (n - 1)
+    tab = np.stack([0.2 + 0.6 * xs, 0.8 - 0.5 * xs, 0.3 + 0.4 * xs, 0.05 + 0.6 * xs], -1)
+    return tab.astype(np.float32)
+
+
 def perturb_tf(tf: np.ndarray, seed: int = 0, sigma: float = 0.05) -> np.ndarray:
     """Target table for the differentiable workload: clamp(TF + N(0, sigma^2))."""
     g = rng(seed, STREAM_TF_PERTURB)

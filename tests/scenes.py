@@ -120,6 +120,16 @@ def grad_checks(gpu, ref, what, kappa=None, amb=None):
     k = np.zeros_like(ref) if kappa is None else kappa
     bound = 1e-3 * np.abs(ref) + 3.0 * k + a
     viol = big & (err > bound)
+    # entries that need the kappa allowance: beyond 1e-3 |ref| + amb, within
+    # the full bound; and the distribution of |gpu - ref| / kappa over them
+    need = big & (err > 1e-3 * np.abs(ref) + a) & ~viol
+    if need.any():
+        r = (err[need] - 1e-3 * np.abs(ref[need]) - a[need]) / np.maximum(k[need], 1e-300)
+        print("%s: %d of %d entries use the kappa allowance; (|gpu - ref| - 1e-3|ref| - amb) / kappa: "
+              "median %.2f, 90th pct %.2f, max %.2f" % (what, need.sum(), big.sum(), np.median(r),
+                                                         np.percentile(r, 90), r.max()))
+    else:
+        print("%s: no entry uses the kappa allowance" % what)
     w = np.argsort(rel)[-3:]
     print("%s: max rel %.2e (over %d entries), rel L2 %.2e (raw %.2e), %d beyond 1e-3|ref| + 3 kappa + amb "
           "(%d entries with amb > 0); worst: %s" % (

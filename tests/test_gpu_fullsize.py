@@ -69,7 +69,7 @@ def _check_camera(orc, dev, ci, cfg, bricks, tf, cam, pix, tol=TOL):
     rgba, _ = dev.map_frame(ci)
     img = rgba.reshape(-1, 4)[torch.from_numpy(pix).long().cuda()].double().cpu().numpy()
     ex = _ambiguous(orc, ref)
-    assert ex.mean() < 0.35
+    assert ex.mean() < 0.05, ex.mean()    # measured 1.1 % (mid) to 2.2 % (2048^3)
     err = np.abs(img - ref["rgba"])[~ex]
     assert err.max() <= tol, err.max()
     order = dev.order(ci).reshape(-1, dev.num_ranks)[torch.from_numpy(pix).long().cuda()].cpu().numpy()
@@ -264,6 +264,67 @@ def test_diff_full_size_gradient(orc):
     l2b, vb = scenes.grad_checks(dvol.double().cpu().numpy(), rvol, "diff full size dL/dvolume", kvol, avol)
     assert l2a <= 1e-4 and l2b <= 1e-4, (l2a, l2b)
     assert va == 0 and vb == 0, (va, vb)
+    dev.release()
+
+
+def test_diff_full_size_gradient_kink_free(orc):
+    """The adjoint of the full differentiable workload (32 views at 512x512,
+    8 bricks of a 256^3 float32 field, the 1/16 pixel subsample of every
+    view) with a TF whose channels are linear in s: no interior knot, so no
+    knot ambiguity.  Both gradients must meet the plain bar, with no
+    allowance of any kind: relative L2 <= 1e-4 and, on entries above 1e-3 of
+    the largest, |gpu - ref| <= 1e-3 |ref|.  The eye-perturbation spread
+    kappa is computed only to report how the errors compare with it."""
+    cfg, field, part, cams, _, _ = _diff_inputs()
+    tf = inputs.linear_tf(256)
+    tf_t = inputs.perturb_tf(tf, seed=0, sigma=0.05)
+    W, H = cfg["width"], cfg["height"]
+    dev = _bench_device(cfg, field, part, cams)
+    dev.set_tf(torch.from_numpy(tf).cuda())
+    dev.render()
+    f = field.cpu().numpy()
+    bricks = orc.make_bricks(f, part, orc.F32)
+    fr = orc.Frame(W, H, step_voxels=0.5, sigma_max=8.0, ert=cfg["ert"])
+    pix = inputs.pixel_subsample(W, H, SUB)
+    sp = _spacing(cfg)
+    N = len(cams) * W * H * 4
+    g = np.zeros((len(cams), H * W, 4), np.float32)
+    rtf, rvol, avol, ktf, kvol = 0.0, 0.0, 0.0, 0.0, 0.0
+    for ci, cam in enumerate(cams):
+        ref = orc.render_bricks(cfg["dims"], bricks, tf, cam, fr, pix=pix, spacing=sp)
+        tgt = orc.render_bricks(cfg["dims"], bricks, tf_t, cam, fr, pix=pix, spacing=sp)
+        gi = (2.0 / N) * (ref["rgba"] - tgt["rgba"])
+        gi[_ambiguous(orc, ref)] = 0.0
+        gi = gi.astype(np.float32)
+        g[ci, pix] = gi
+        gi = gi.astype(np.float64)
+        a, b, amb = orc.grad_bricks(cfg["dims"], bricks, tf, cam, fr, gi, pix=pix, spacing=sp, knot_eps=orc.KNOT_EPS)
+        rtf, rvol, avol = rtf + a, rvol + b, avol + amb
+        for eps in (1e-7, -1e-7):
+            pa, pb = orc.grad_bricks(cfg["dims"], bricks, tf, scenes.perturbed_eye(cam, eps), fr, gi, pix=pix,
+                                     spacing=sp)
+            ktf = np.maximum(ktf, np.abs(pa - a))
+            kvol = np.maximum(kvol, np.abs(pb - b))
+    # a linear TF has no interior knot: the oracle sees no knot ambiguity
+    # beyond the float32 rounding of the table (slopes equal to ~1e-7)
+    assert float(np.abs(avol).max()) <= 1e-5 * float(np.abs(rvol).max())
+    dtf, dvol = dev.backward(torch.from_numpy(g.reshape(len(cams), H, W, 4)).cuda())
+    assert dev.stats()["error_flags"] == 0
+    gtf, gvol = dtf.cpu().numpy(), dvol.double().cpu().numpy()
+    for name, gpu, ref, kap in (("dL/dTF", gtf, rtf, ktf), ("dL/dvolume", gvol, rvol, kvol)):
+        m = np.abs(ref).max()
+        big = np.abs(ref) > 1e-3 * m
+        err = np.abs(gpu - ref)
+        l2 = np.linalg.norm(gpu - ref) / np.linalg.norm(ref)
+        rel = err[big] / np.abs(ref[big])
+        over = big & (err > 1e-3 * np.abs(ref))
+        ratio = err[big] / np.maximum(kap[big], 1e-300)
+        print("kink-free diff %s: rel L2 %.2e, max rel %.2e over %d entries, %d beyond 1e-3|ref|; "
+              "|gpu - ref| / kappa: median %.2f, 99th pct %.2f, max %.2f" % (
+                  name, l2, rel.max(), big.sum(), over.sum(), np.median(ratio), np.percentile(ratio, 99),
+                  ratio.max()))
+        assert l2 <= 1e-4, (name, l2)
+        assert not over.any(), (name, int(over.sum()), float(rel.max()))
     dev.release()
 
 

@@ -113,6 +113,39 @@ def test_fragments_keys_and_order_bitexact(orc):
     dev.release()
 
 
+def test_mapped_fragments_match_oracle(orc):
+    """dpvMapFragments: each rank's fragment image of each camera, mapped as
+    a device-owned block (RGBA then keys), equals the oracle's fragments
+    (keys bit-exact, RGBA within the tolerance on unflagged pixels) and the
+    copy dpvReadFragments makes; unmapping releases it."""
+    dims = (44, 40, 36)
+    sc = scenes.make(dims, kd=5, cams=inputs.orbit_cameras(dims, 2, seed=3), width=72, height=56)
+    dev = _render(sc)
+    for ci, cam in enumerate(sc.cams):
+        ref = scenes.o_bricks(orc, sc, cam)
+        ex = _excluded(ref["flags"], ["exit", "owner"])
+        assert ex.mean() < 0.05
+        for k in range(sc.part.num_ranks):
+            rgba, key = dev.map_fragments(ci, k)
+            torch.cuda.synchronize()
+            r2, k2 = dev.read_fragments(ci, k)
+            assert torch.equal(key, k2) and torch.equal(rgba, r2)
+            key = key.cpu().numpy().reshape(-1)
+            rgba = rgba.double().cpu().numpy().reshape(-1, 4)
+            np.testing.assert_array_equal(key[~ex], ref["frag_key"][~ex, k])
+            ne = (key != dpv.KEY_EMPTY) & ~ex
+            if ne.any():
+                assert np.abs(rgba[ne] - ref["frag_rgba"][ne, k]).max() <= TOL
+            dev.unmap_fragments(ci, k)
+    with pytest.raises(dpv.DPVError) as e:
+        dev.unmap_fragments(0, 0)
+    assert e.value.status == 2
+    with pytest.raises(dpv.DPVError) as e:
+        dev.map_fragments(0, sc.part.num_ranks)
+    assert e.value.status == 1
+    dev.release()
+
+
 def test_single_rank_composite_is_identity():
     sc = scenes.make((40, 33, 27), splits=(1, 1, 1), width=61, height=47)
     dev = _render(sc)
@@ -191,7 +224,7 @@ def test_early_termination_per_fragment(orc):
     ex = _excluded(ref["flags"], ["exit", "ert", "owner"])
     print("excluded: exit %.3f ert %.3f owner %.3f" % tuple(_excluded(ref["flags"], [w]).mean()
                                                            for w in ("exit", "ert", "owner")))
-    assert ex.mean() < 0.35
+    assert ex.mean() < 0.05, ex.mean()
     assert np.abs(img - ref["rgba"])[~ex].max() <= TOL
     # the fragments did terminate early
     sc0 = scenes.make((48, 40, 44), splits=(2, 2, 2), width=80, height=64, sigma_max=40.0)
