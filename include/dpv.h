@@ -228,12 +228,19 @@ typedef struct {
 
 /* Create a device for `num_ranks` logical ranks (1..255) on CUDA device
  * `cuda_device`, issuing all work on `cuda_stream` (a cudaStream_t; NULL =
- * the legacy default stream).  The stream must outlive the device. */
+ * the legacy default stream).  The stream must outlive the device.
+ * Paper: every rank creates the data-parallel device together (§3.3, §2.3);
+ * here one handle stands for all logical ranks.  *out is written only on
+ * success; DPV_ERR_INVALID_ARG for a bad rank count, device or NULL out,
+ * DPV_ERR_CUDA if the device cannot be set up. */
 dpv_status dpvCreateDevice(int num_ranks, int cuda_device, void* cuda_stream, dpv_device* out);
 
 /* Global node grid: dims[a] >= 2 nodes per axis, world origin of node 0 and
  * isotropic spacing > 0.  Must be set before bricks are committed; setting
- * it again discards all bricks. */
+ * it again discards all bricks.  Paper: the world is one jointly defined
+ * entity whose parts the ranks own (§1, §3.1.1 ANARIWorld is global); the
+ * grid is the frame of reference of every rank's part.  Host arrays, read
+ * during the call.  DPV_ERR_INVALID_ARG for dims < 2 or spacing <= 0. */
 dpv_status dpvSetVolumeGeometry(dpv_device dev, const int dims[3], const float origin[3], float spacing);
 
 /* Commit rank `rank`'s brick (copies, see dpv_brick_desc).  Ranks commit
@@ -248,19 +255,35 @@ dpv_status dpvCommitBrick(dpv_device dev, int rank, const dpv_brick_desc* desc);
  * Copied; visible to the next render.  A host table is copied into one of
  * two pinned staging buffers and uploaded on the device stream: the
  * caller's buffer may be reused at return and the call does not wait for
- * the device (only for the upload issued two calls earlier). */
+ * the device (only for the upload issued two calls earlier).  A device
+ * table is copied on the device stream.  Paper: renderer and camera
+ * parameters are identical on every rank (§3.1.1); the table is the
+ * renderer's classification.  `on_device` has no counterpart in the call
+ * shape of the paper: it says where `rgba` lives so a render loop can
+ * feed a table it keeps on the GPU.  DPV_ERR_INVALID_ARG for NULL rgba, n
+ * out of range or vmax <= vmin. */
 dpv_status dpvSetTransferFunction(dpv_device dev, const float* rgba, int n, float vmin, float vmax, int on_device);
 
 /* Directional light for DPV_FRAME_SHADOW: direction toward the light (any
  * non-zero length; normalised here), shadow sample spacing h in voxels
  * (1/64 .. 64), ambient term k_a in [0, 1] (1: no shadows).  Visible to the
- * next render; DPV_ERR_INVALID_ARG otherwise. */
+ * next render; DPV_ERR_INVALID_ARG otherwise.  Paper: shadows are the
+ * global effect the paper says compositing cannot give and ray forwarding
+ * between ranks can (§2.2, §7); the light is a renderer parameter and so
+ * globally consistent (§3.1.1). */
 dpv_status dpvSetLight(dpv_device dev, const float direction[3], float step_voxels, float ambient);
 
-/* Cameras (host array of n >= 1).  Every render produces one image each. */
+/* Cameras (host array of n >= 1, read during the call).  Every render
+ * produces one image each.  Paper: the camera is globally consistent, set
+ * identically on every rank (§3.1.1); several cameras form one batch.
+ * DPV_ERR_INVALID_ARG for NULL, n < 1, fovy outside (0, 180), eye equal to
+ * center or up parallel to the view direction. */
 dpv_status dpvSetCameras(dpv_device dev, const dpv_camera* cams, int n);
 
-/* Frame parameters (host struct). */
+/* Frame parameters (host struct, read during the call).  Paper: the frame
+ * is a global object whose parameters match on every rank (§3.1.1).
+ * DPV_ERR_INVALID_ARG for a non-positive size or step, a tile that is not
+ * a multiple of 8 x 4 or above 256 pixels, or conflicting flags. */
 dpv_status dpvSetFrame(dpv_device dev, const dpv_frame_desc* desc);
 
 /* Render one frame for every camera: cull, brick ray-march and sort-last
@@ -272,20 +295,29 @@ dpv_status dpvSetFrame(dpv_device dev, const dpv_frame_desc* desc);
 dpv_status dpvRenderFrame(dpv_device dev);
 
 /* Frame completion: wait = 1 blocks until the last render has finished
- * (ANARI_WAIT); wait = 0 only polls (ANARI_NO_WAIT).  *ready = 1 when done. */
+ * (ANARI_WAIT); wait = 0 only polls (ANARI_NO_WAIT).  *ready = 1 when done.
+ * Paper: the property query of a frame synchronises with WAIT and may
+ * return at once with NO_WAIT (§3.2).  DPV_ERR_INVALID_ARG for NULL ready;
+ * DPV_ERR_CUDA if the render failed on the device. */
 dpv_status dpvFrameReady(dpv_device dev, int wait, int* ready);
 
 /* Device pointers to camera `camera`'s composited frame: rgba = height x
  * width x 4 floats (premultiplied, row 0 at the bottom), depth = height x
  * width floats (t of the first sample of the first fragment with non-zero
  * opacity, +inf if none).  Device-owned, valid until the next render or
- * release; read them on the device stream or after dpvFrameReady. */
+ * release; read them on the device stream or after dpvFrameReady.  Paper:
+ * the final frame is mapped on rank 0 with the ordinary map call (§3.1.3);
+ * here the one device holds it.  Unmap releases nothing (the buffers are
+ * the device's) and only checks the camera index.  DPV_ERR_STATE before
+ * the first render, DPV_ERR_INVALID_ARG for a camera out of range. */
 dpv_status dpvMapFrame(dpv_device dev, int camera, const float** rgba, const float** depth);
 dpv_status dpvUnmapFrame(dpv_device dev, int camera);
 
 /* Copy camera `camera`'s frame into caller buffers (device or host
  * pointers; either may be NULL), ordered on the device stream.  Returns
- * after the copy has been issued (host destinations: after it completed). */
+ * after the copy has been issued (host destinations: after it completed).
+ * Paper: the final frame is delivered on rank 0 (§3.1.3); this is the map
+ * followed by a copy.  DPV_ERR_STATE / DPV_ERR_INVALID_ARG as dpvMapFrame. */
 dpv_status dpvCopyFrame(dpv_device dev, int camera, float* rgba, float* depth);
 
 /* Asynchronous copy of camera `camera`'s frame (camera = -1: every camera's,
@@ -296,35 +328,73 @@ dpv_status dpvCopyFrame(dpv_device dev, int camera, float* rgba, float* depth);
  * Returns at once.  The destination is complete after dpvCopyWait.  A third
  * copy in flight waits on the device stream until the slot it reuses has
  * drained.  Destinations in pageable host memory copy synchronously with
- * respect to the host (CUDA's rule); pinned memory overlaps. */
+ * respect to the host (CUDA's rule); pinned memory overlaps.  Paper: frame
+ * delivery on rank 0 (§3.1.3) under ANARI's asynchronous rendering (§3.2);
+ * overlapping the copy with the next render has no counterpart there. */
 dpv_status dpvCopyFrameAsync(dpv_device dev, int camera, float* rgba, float* depth);
 
-/* Block until every copy dpvCopyFrameAsync issued has completed. */
+/* Block until every copy dpvCopyFrameAsync issued has completed (the wait
+ * of the asynchronous delivery above; no counterpart in the paper). */
 dpv_status dpvCopyWait(dpv_device dev);
+
+/* Map rank `rank`'s fragments of camera `camera` from the last render.
+ * *frag points to a device-owned block: height x width float4 (the
+ * fragments' premultiplied RGBA, x fastest, row 0 at the bottom), followed
+ * at byte offset 16 x width x height by height x width int32 keys (the
+ * global index of the fragment's first sample; 2^31 - 1 = empty, also for
+ * pixels the rank was culled from).  The block is filled on the device
+ * stream by this call (read it on that stream or after dpvFrameReady) and
+ * stays allocated until dpvUnmapFragments for the same camera and rank, or
+ * release; a later render does not refresh it (map again).  Layer 0 of a
+ * DPV_FRAME_DEEP frame (dpvReadDeepFragments reads the others).  Paper:
+ * each rank's fragment image is the compositor's per-rank input (§5.1.1),
+ * and mapping gives read access to device-held pixels (§3.1.3).
+ * DPV_ERR_STATE before the first render, DPV_ERR_INVALID_ARG for a camera
+ * or rank out of range or NULL frag, DPV_ERR_OUT_OF_MEMORY if the block
+ * cannot be allocated. */
+dpv_status dpvMapFragments(dpv_device dev, int camera, int rank, const void** frag);
+
+/* Release the block dpvMapFragments returned for (camera, rank); waits for
+ * the device stream first.  Paper: the unmap that ends a map (§3.1.3).
+ * DPV_ERR_STATE if that pair is not mapped. */
+dpv_status dpvUnmapFragments(dpv_device dev, int camera, int rank);
 
 /* Debug/test: write rank `rank`'s fragments for camera `camera` into caller
  * device buffers rgba (height x width x 4, premultiplied) and key (height x
- * width int32; 2^31 - 1 = empty, also for pixels the rank was culled from). */
+ * width int32; 2^31 - 1 = empty, also for pixels the rank was culled from);
+ * the copy form of dpvMapFragments (§5.1.1: a rank's fragments).
+ * DPV_ERR_STATE before the first render, DPV_ERR_INVALID_ARG for a camera
+ * or rank out of range or a NULL buffer. */
 dpv_status dpvReadFragments(dpv_device dev, int camera, int rank, float* rgba, int32_t* key);
 
 /* Debug/test: as dpvReadFragments, for fragment layer `layer` of a frame
  * rendered with DPV_FRAME_DEEP (0 <= layer < DPV_DEEP_MAX; layers past a
  * pixel's fragment count read as empty).  Without DPV_FRAME_DEEP only layer 0
- * exists.  DPV_ERR_INVALID_ARG for a layer out of range. */
+ * exists.  Paper: several fragments per pixel from one rank, the general
+ * input of the compositor (§2.1, §5.1.1).  DPV_ERR_INVALID_ARG for a layer
+ * out of range. */
 dpv_status dpvReadDeepFragments(dpv_device dev, int camera, int rank, int layer, float* rgba, int32_t* key);
 
 /* Debug/test: copy rank `rank`'s stored nodes (owned + ghost box, x
  * fastest, in the storage format) to the caller's device buffer `dst` (NULL
  * to skip) and return the box and the rank's decode scale (synchronises the
- * device stream).  stored_lo/stored_dims/scale may be NULL. */
+ * device stream).  stored_lo/stored_dims/scale may be NULL.  Paper: the
+ * rank's locally defined data (§3.1.2) as committed, ghost layer included
+ * (§1).  DPV_ERR_STATE if the rank has not committed. */
 dpv_status dpvReadBrick(dpv_device dev, int rank, void* dst, int stored_lo[3], int stored_dims[3], float* scale);
 
 /* Debug/test (needs DPV_FRAME_ORDER): device pointer to camera `camera`'s
  * order image: height x width x stride bytes, the ranks of the pixel's
- * non-empty fragments front to back, then 0xFF. */
+ * non-empty fragments front to back, then 0xFF.  Paper: the compositor
+ * sorts each pixel's fragments by depth (§5.1.1); this is that order.
+ * DPV_ERR_STATE without DPV_FRAME_ORDER, DPV_ERR_INVALID_ARG for a camera
+ * out of range. */
 dpv_status dpvMapOrder(dpv_device dev, int camera, const uint8_t** order, int* stride);
 
-/* Adjoint of the last render.  dL_drgba: device array cameras x height x
+/* Adjoint of the last render (the differentiable form: no counterpart in
+ * the paper, whose renderer is forward only; the operations it inverts are
+ * the ray-march of one rank's part and the sort-last composite, §2.1,
+ * §5.1.1).  dL_drgba: device array cameras x height x
  * width x 4 floats (gradient of the loss with respect to the composited
  * premultiplied RGBA).  dL_dtf: device array n x 4 doubles, overwritten with
  * the gradient with respect to the TF entries.  dL_dvol: device array of the
@@ -342,7 +412,8 @@ dpv_status dpvMapOrder(dpv_device dev, int camera, const uint8_t** order, int* s
  * the scalar atomics; DPV_FACE_GROUP=n puts at most n bricks in a group. */
 dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, float* dL_dvol);
 
-/* Counters (synchronises the device stream). */
+/* Counters (synchronises the device stream).  Tracing has no counterpart
+ * in the paper.  DPV_ERR_INVALID_ARG for NULL out. */
 dpv_status dpvGetStats(dpv_device dev, dpv_stats* out);
 
 /* Result of dpvAutotune. */
@@ -360,13 +431,16 @@ typedef struct {
  * `frames` frames each after one warm-up frame, and keep the fastest in the
  * device's frame parameters (other flags are kept).  Needs a renderable
  * device; blocks the host until done; the last rendered frame is the best
- * candidate's. */
+ * candidate's.  Launch forms have no counterpart in the paper (its device
+ * implementation is left to the vendor, §3.2). */
 dpv_status dpvAutotune(dpv_device dev, int frames, dpv_tune_result* out);
 
-/* Clear the accumulated stage times and the launch count. */
+/* Clear the accumulated stage times and the launch count (tracing: no
+ * counterpart in the paper). */
 dpv_status dpvResetStats(dpv_device dev);
 
-/* Turn per-stage CUDA-event timing on (1) or off (0). */
+/* Turn per-stage CUDA-event timing on (1) or off (0) (tracing: no
+ * counterpart in the paper). */
 dpv_status dpvSetProfiling(dpv_device dev, int enable);
 
 /* One rank's brick for dpvRenderNoAlloc: a device pointer to the nodes the
@@ -380,8 +454,9 @@ typedef struct {
 } dpv_noalloc_brick;
 
 /* Everything dpvRenderNoAlloc reads: the grid, the ranks' bricks (host
- * array of num_ranks entries, all in `storage`), and the transfer function
- * (device pointer, tf_n RGBA floats). */
+ * array of num_ranks entries, all in `storage`, read during the call), and
+ * the transfer function (device pointer, 16-byte aligned, tf_n RGBA
+ * floats). */
 typedef struct {
     int dims[3];
     float origin[3];
@@ -413,13 +488,19 @@ typedef struct {
  * same array, so calls that overlap on the GPU -- on different streams or
  * from different host threads -- race and must be serialised by the caller.
  * It marches the linear gather layout and ignores the layout, staged,
- * persistent and graph bits of frame->flags; DPV_FRAME_ISO, DPV_FRAME_ORDERED
- * and DPV_FRAME_SKIP return DPV_ERR_UNSUPPORTED (they need device state).
+ * persistent and graph bits of frame->flags; DPV_FRAME_ISO,
+ * DPV_FRAME_ORDERED, DPV_FRAME_SKIP, DPV_FRAME_DEEP, DPV_FRAME_SHADOW and
+ * DPV_FRAME_ORDER return DPV_ERR_UNSUPPORTED (they need device state).
+ * Cameras are checked as dpvSetCameras checks them.  Its small host tables
+ * (brick table, scales, camera) travel to the device as kernel parameters,
+ * so the call reads none of the caller's host memory after it returns.
  * Asynchronous: returns once the work is queued. */
 dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* scene, const dpv_camera* camera, const dpv_frame_desc* frame,
                             float* rgba, float* depth, void* cuda_stream);
 
-/* Message of the last failed call on this host thread ("" if none). */
+/* Message of the last failed call on this host thread ("" if none).  Error
+ * reporting through status codes and messages has no counterpart in the
+ * paper. */
 const char* dpvGetLastError(void);
 
 /* Release the device and all its memory (§3.2: lock step).  NULL is OK. */

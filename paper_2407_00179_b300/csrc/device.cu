@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -58,6 +59,15 @@ const int kElemSize[4] = {4, 2, 2, 1};
 }  // namespace
 
 void dpv::set_last_error(const char* msg) { g_last_error = msg; }
+
+const char* dpv::camera_problem(const dpv_camera& c) {
+    float fx = c.center[0] - c.eye[0], fy = c.center[1] - c.eye[1], fz = c.center[2] - c.eye[2];
+    float cx = fy * c.up[2] - fz * c.up[1], cy = fz * c.up[0] - fx * c.up[2], cz = fx * c.up[1] - fy * c.up[0];
+    if (fx * fx + fy * fy + fz * fz == 0.0f) return "eye == center";
+    if (cx * cx + cy * cy + cz * cz == 0.0f) return "up parallel to view";
+    if (!(c.fovy_deg > 0.0f && c.fovy_deg < 180.0f)) return "fovy";
+    return nullptr;
+}
 
 struct dpv_device_t {
     int nranks = 0;
@@ -186,6 +196,14 @@ struct dpv_device_t {
     uint32_t stage_calls[DPV_NUM_STAGES] = {0};
     uint64_t launches = 0;
     uint64_t graph_launches = 0;
+
+    // mapped fragment images (dpvMapFragments): per (camera, rank) a
+    // device-owned block of width x height float4 RGBA then int32 keys
+    struct FragMap {
+        void* ptr;
+        size_t bytes;
+    };
+    std::map<long long, FragMap> frag_maps;
 };
 
 namespace {
@@ -1058,11 +1076,7 @@ dpv_status dpvSetCameras(dpv_device dev, const dpv_camera* cams, int n) {
     std::vector<CamIn> v(n);
     for (int i = 0; i < n; ++i) {
         const dpv_camera& c = cams[i];
-        float fx = c.center[0] - c.eye[0], fy = c.center[1] - c.eye[1], fz = c.center[2] - c.eye[2];
-        float cx = fy * c.up[2] - fz * c.up[1], cy = fz * c.up[0] - fx * c.up[2], cz = fx * c.up[1] - fy * c.up[0];
-        if (fx * fx + fy * fy + fz * fz == 0.0f) return fail(DPV_ERR_INVALID_ARG, "camera %d: eye == center", i);
-        if (cx * cx + cy * cy + cz * cz == 0.0f) return fail(DPV_ERR_INVALID_ARG, "camera %d: up parallel to view", i);
-        if (!(c.fovy_deg > 0.0f && c.fovy_deg < 180.0f)) return fail(DPV_ERR_INVALID_ARG, "camera %d: fovy", i);
+        if (const char* why = camera_problem(c)) return fail(DPV_ERR_INVALID_ARG, "camera %d: %s", i, why);
         memcpy(&v[i], &c, sizeof(CamIn));
     }
     dev->cams.swap(v);
@@ -1271,6 +1285,52 @@ dpv_status dpvReadDeepFragments(dpv_device dev, int camera, int rank, int layer,
 
 dpv_status dpvReadFragments(dpv_device dev, int camera, int rank, float* rgba, int32_t* key) {
     return dpvReadDeepFragments(dev, camera, rank, 0, rgba, key);
+}
+
+dpv_status dpvMapFragments(dpv_device dev, int camera, int rank, const void** frag) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    if (!dev->rendered) return fail(DPV_ERR_STATE, "no frame rendered yet");
+    if (camera < 0 || camera >= dev->P.ncam) return fail(DPV_ERR_INVALID_ARG, "camera %d out of range", camera);
+    if (rank < 0 || rank >= dev->nranks) return fail(DPV_ERR_INVALID_ARG, "rank %d out of range", rank);
+    if (!frag) return fail(DPV_ERR_INVALID_ARG, "frag is NULL");
+    DeviceGuard g(dev->cuda_device);
+    const size_t npix = (size_t)dev->P.W * dev->P.H;
+    const size_t bytes = npix * (sizeof(float4) + sizeof(int32_t));
+    const long long key = (long long)camera * (MAX_RANKS + 1) + rank;
+    auto it = dev->frag_maps.find(key);
+    if (it != dev->frag_maps.end() && it->second.bytes != bytes) {
+        CK(cudaStreamSynchronize(dev->stream), "remap fragments");
+        dev_free(it->second.ptr);
+        dev->frag_maps.erase(it);
+        it = dev->frag_maps.end();
+    }
+    if (it == dev->frag_maps.end()) {
+        void* p = nullptr;
+        if ((s = dev_alloc(dev, &p, bytes, "mapped fragments"))) return s;
+        it = dev->frag_maps.emplace(key, dpv_device_t::FragMap{p, bytes}).first;
+    }
+    float4* rgba = (float4*)it->second.ptr;
+    int* keys = (int*)(rgba + npix);
+    CK(launch_read_frags(dev->P, dev->d_items, dev->n_items, camera, rank, 0, dev->d_frag_rgba, dev->d_frag_key,
+                         rgba, keys, dev->stream),
+       "map fragments");
+    *frag = it->second.ptr;
+    return DPV_OK;
+}
+
+dpv_status dpvUnmapFragments(dpv_device dev, int camera, int rank) {
+    dpv_status s = check_dev(dev);
+    if (s) return s;
+    const long long key = (long long)camera * (MAX_RANKS + 1) + rank;
+    auto it = dev->frag_maps.find(key);
+    if (it == dev->frag_maps.end())
+        return fail(DPV_ERR_STATE, "fragments of camera %d, rank %d are not mapped", camera, rank);
+    DeviceGuard g(dev->cuda_device);
+    CK(cudaStreamSynchronize(dev->stream), "unmap fragments");
+    dev_free(it->second.ptr);
+    dev->frag_maps.erase(it);
+    return DPV_OK;
 }
 
 dpv_status dpvReadBrick(dpv_device dev, int rank, void* dst, int stored_lo[3], int stored_dims[3], float* scale) {
@@ -1567,6 +1627,8 @@ dpv_status dpvRelease(dpv_device dev) {
         dev_free(dev->d_out_rgba);
         dev_free(dev->d_out_depth);
         dev_free(dev->d_order);
+        for (auto& m : dev->frag_maps) dev_free(m.second.ptr);
+        dev->frag_maps.clear();
         dev_free(dev->d_counters);
         dev_free(dev->d_sched);
         dev_free(dev->d_hist);

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/dpv.h"
 #include "dpv_internal.cuh"
 
 namespace dpv {
@@ -45,6 +46,10 @@ cudaError_t launch_schedule(const FrameParams& P, const Item* items, int n_items
 
 // Message returned by dpvGetLastError() on this host thread.
 void set_last_error(const char* msg);
+
+// Why a camera cannot be used (eye == center, up parallel to the view
+// direction, fovy outside (0, 180)), or nullptr if it can.
+const char* camera_problem(const dpv_camera& c);
 
 cudaError_t launch_commit(const CommitArgs& a, int storage, int src_is_f32, float given_scale, unsigned int* d_tmp,
                           float* d_scale, void* dst, cudaStream_t st);

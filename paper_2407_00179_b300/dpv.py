@@ -50,7 +50,7 @@ STATUS = {0: "DPV_OK", 1: "DPV_ERR_INVALID_ARG", 2: "DPV_ERR_STATE", 3: "DPV_ERR
 
 EXPORTS = ["dpvCreateDevice", "dpvSetVolumeGeometry", "dpvCommitBrick", "dpvSetTransferFunction", "dpvSetCameras",
            "dpvSetFrame", "dpvRenderFrame", "dpvFrameReady", "dpvMapFrame", "dpvUnmapFrame", "dpvCopyFrame",
-           "dpvReadFragments", "dpvReadDeepFragments", "dpvReadBrick", "dpvMapOrder", "dpvBackward", "dpvGetStats", "dpvResetStats", "dpvSetProfiling", "dpvGetLastError",
+           "dpvMapFragments", "dpvUnmapFragments", "dpvReadFragments", "dpvReadDeepFragments", "dpvReadBrick", "dpvMapOrder", "dpvBackward", "dpvGetStats", "dpvResetStats", "dpvSetProfiling", "dpvGetLastError",
            "dpvRelease", "dpvRenderNoAlloc", "dpvAutotune", "dpvSetLight", "dpvCopyFrameAsync", "dpvCopyWait"]
 
 
@@ -134,6 +134,8 @@ def load(path: Optional[str] = None):
         "dpvCopyFrame": [V, I, V, V],
         "dpvCopyFrameAsync": [V, I, V, V],
         "dpvCopyWait": [V],
+        "dpvMapFragments": [V, I, I, C.POINTER(V)],
+        "dpvUnmapFragments": [V, I, I],
         "dpvReadFragments": [V, I, I, V, V],
         "dpvReadDeepFragments": [V, I, I, I, V, V],
         "dpvMapOrder": [V, I, C.POINTER(V), C.POINTER(C.c_int)],
@@ -178,6 +180,14 @@ def _ptr(t: torch.Tensor) -> int:
     return t.data_ptr()
 
 
+def _stamp(t):
+    """Identity of a field's contents: storage address, in-place version,
+    shape and device of a tensor (None for other arrays)."""
+    if isinstance(t, torch.Tensor):
+        return (t.data_ptr(), t._version, tuple(t.shape), str(t.device), t.dtype)
+    return None
+
+
 class Device:
     """One data-parallel rendering device (all logical ranks on one GPU)."""
 
@@ -195,6 +205,7 @@ class Device:
         self.width = self.height = 0
         self.ntf = 0
         self._keep = []
+        self._committed = None
 
     # -- lifecycle ---------------------------------------------------------
     def release(self):
@@ -221,6 +232,7 @@ class Device:
         o = (C.c_float * 3)(*[float(x) for x in origin])
         _check(load().dpvSetVolumeGeometry(self._h, d, o, float(sp)))
         self.dims = tuple(int(x) for x in dims)
+        self._committed = None        # a new grid discards every brick
 
     def commit_brick(self, rank: int, lo: Sequence[int], hi: Sequence[int], data, storage: str = "f32",
                      scale: float = 0.0, data_lo: Sequence[int] = (0, 0, 0)):
@@ -245,6 +257,7 @@ class Device:
                 raise TypeError("data must be float32 or %s" % TORCH_STORAGE[st])
             shape = tuple(t.shape)
             keep = t
+        self._committed = None        # no longer the bricks of one known field
         desc = BrickDesc((C.c_int * 3)(*[int(x) for x in lo]), (C.c_int * 3)(*[int(x) for x in hi]), st,
                          float(scale), src, ptr, (C.c_int * 3)(*[int(x) for x in data_lo]),
                          (C.c_int * 3)(int(shape[2]), int(shape[1]), int(shape[0])), on_dev)
@@ -253,9 +266,29 @@ class Device:
         del keep
 
     def commit_partition(self, field, partition, storage: str = "f32", scale: float = 0.0):
-        """Commit every rank's brick out of one global field."""
+        """Commit every rank's brick out of one global field.  The device
+        remembers which tensor (and which in-place version of it) the bricks
+        came from, so that render() can tell whether a volume it is handed
+        is still what the bricks hold."""
         for k in range(partition.num_ranks):
             self.commit_brick(k, partition.lo[k], partition.hi[k], field, storage, scale)
+        self._committed = (partition, storage, scale, _stamp(field))
+
+    def ensure_volume(self, volume: torch.Tensor) -> bool:
+        """Make the committed bricks those of `volume`: if the bricks were
+        committed from another tensor, or from this one before an in-place
+        change, commit `volume` again with the same partition, storage and
+        scale.  Returns True when it re-committed.  Raises if the bricks were
+        not committed from one field by commit_partition (the device cannot
+        know which field they are)."""
+        c = getattr(self, "_committed", None)
+        if c is None:
+            raise ValueError("the bricks were not committed from one field with commit_partition: the device "
+                             "cannot tie them to `volume`")
+        if c[3] == _stamp(volume):
+            return False
+        self.commit_partition(volume.detach(), c[0], c[1], c[2])
+        return True
 
     def set_tf(self, table, vmin: float = 0.0, vmax: float = 1.0):
         if isinstance(table, np.ndarray):
@@ -350,6 +383,20 @@ class Device:
 
     def copy_wait(self):
         _check(load().dpvCopyWait(self._h))
+
+    def map_fragments(self, camera: int, rank: int):
+        """Zero-copy views of rank's fragments of one camera (dpvMapFragments):
+        rgba (H, W, 4) premultiplied and key (H, W) int32 (KEY_EMPTY = none),
+        valid until unmap_fragments(camera, rank) or release."""
+        p = C.c_void_p()
+        _check(load().dpvMapFragments(self._h, camera, rank, C.byref(p)))
+        npix = self.height * self.width
+        rgba = _wrap(p.value, (self.height, self.width, 4), torch.float32, self.torch_device)
+        key = _wrap(p.value + 16 * npix, (self.height, self.width), torch.int32, self.torch_device)
+        return rgba, key
+
+    def unmap_fragments(self, camera: int, rank: int):
+        _check(load().dpvUnmapFragments(self._h, camera, rank))
 
     def read_fragments(self, camera: int, rank: int, layer: int = 0):
         """Rank's fragments of one camera (fragment layer `layer` of a deep frame)."""
@@ -463,12 +510,17 @@ def render_noalloc(dims: Sequence[int], bricks, storage: str, tf: torch.Tensor, 
 
 class RenderFunction(torch.autograd.Function):
     """Differentiable render: images of all cameras as a function of the TF
-    table and (for the gradient) the global field the bricks were committed
-    from.  The forward uploads `tf` and renders; the backward runs the
-    library's adjoint (compositor + ray-march replay)."""
+    table and (for the gradient) the global field `volume`.  The forward
+    uploads `tf`, makes the committed bricks those of `volume` (committing
+    it again if the bricks came from another tensor or from an older
+    in-place version of this one), and renders; the backward runs the
+    library's adjoint (compositor + ray-march replay), whose field gradient
+    is then the gradient for `volume` as it was at the forward."""
 
     @staticmethod
     def forward(ctx, tf: torch.Tensor, volume: Optional[torch.Tensor], device: Device, vmin: float, vmax: float):
+        if volume is not None:
+            device.ensure_volume(volume)
         device.set_tf(tf, vmin, vmax)
         device.render()
         rgba, _ = device.frames()

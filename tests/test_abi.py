@@ -31,6 +31,39 @@ def test_exports_every_declared_symbol(lib):
     assert sorted(names) == sorted(dpv.EXPORTS)
 
 
+# The calls of the boundary the scope table fixes (device creation, per-rank
+# commit, globally consistent TF / cameras / frame, collaborative render,
+# frame ready, frame and fragment maps, order map, backward, last error,
+# release): every one is declared and exported.
+SCOPE_CALLS = ["dpvCreateDevice", "dpvSetVolumeGeometry", "dpvCommitBrick", "dpvSetTransferFunction",
+               "dpvSetCameras", "dpvSetFrame", "dpvRenderFrame", "dpvFrameReady", "dpvMapFrame", "dpvUnmapFrame",
+               "dpvMapFragments", "dpvMapOrder", "dpvBackward", "dpvGetLastError", "dpvRelease"]
+
+
+def test_exports_every_scope_call(lib):
+    names = _declared()
+    for n in SCOPE_CALLS:
+        assert n in names, n
+        assert hasattr(lib, n), n
+
+
+def test_every_declaration_cites_or_disclaims_a_passage():
+    """Each declaration's comment names the passage of the paper it follows
+    (a section sign) or says the paper has no counterpart."""
+    src = open(os.path.join(ROOT, "include", "dpv.h")).read()
+    body = src[src.index("typedef struct dpv_device_t"):]
+    missing = []
+    for m in re.finditer(r"^\s*(?:dpv_status|const char\*)\s+(dpv\w+)\s*\(", body, re.M):
+        # the comment block(s) right above the declaration (a pair such as
+        # map / unmap may share one)
+        before = body[:m.start()]
+        cstart = before.rfind("/*")
+        comment = re.sub(r"\s*\n\s*\*?\s*", " ", before[cstart:])
+        if "§" not in comment and "no counterpart" not in comment and "not in the paper" not in comment:
+            missing.append(m.group(1))
+    assert not missing, missing
+
+
 def test_null_and_bad_arguments(lib):
     assert lib.dpvRelease(None) == 0
     h = C.c_void_p()
