@@ -64,6 +64,32 @@ dpv_status scratch_address(int device, unsigned char** out) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// The call's small host tables (brick table, scales, camera) reach the
+// device as kernel parameters, under 4 KB per launch, instead of copies
+// from host memory: nothing reads the host memory behind them after the
+// call returns, and nothing needs a staging buffer.
+struct Words {
+    unsigned n;
+    unsigned w[1000];
+};
+
+__global__ void k_put_words(Words b, unsigned* dst) {
+    for (unsigned i = threadIdx.x; i < b.n; i += blockDim.x) dst[i] = b.w[i];
+}
+
+cudaError_t put_words(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    const unsigned* s = (const unsigned*)src;
+    unsigned* d = (unsigned*)dst;
+    size_t n = bytes / 4;
+    Words b;
+    for (size_t i = 0; i < n; i += 1000) {
+        b.n = (unsigned)(n - i < 1000 ? n - i : 1000);
+        memcpy(b.w, s + i, 4 * (size_t)b.n);
+        k_put_words<<<1, 256, 0, st>>>(b, d + i);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_camera* cam, const dpv_frame_desc* fr,
@@ -83,9 +109,18 @@ extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_ca
     int tw = fr->tile_w > 0 ? fr->tile_w : 16, th = fr->tile_h > 0 ? fr->tile_h : 16;
     if (tw % 8 || th % 4 || tw * th > 256) return na_fail(DPV_ERR_INVALID_ARG, "bad tile size");
     if (((uintptr_t)rgba & 15) || ((uintptr_t)depth & 3)) return na_fail(DPV_ERR_INVALID_ARG, "misaligned output");
-    if (!(cam->fovy_deg > 0.0f && cam->fovy_deg < 180.0f)) return na_fail(DPV_ERR_INVALID_ARG, "bad fovy");
-    if (fr->flags & (DPV_FRAME_ISO | DPV_FRAME_ORDERED | DPV_FRAME_SKIP | DPV_FRAME_DEEP | DPV_FRAME_SHADOW))
-        return na_fail(DPV_ERR_UNSUPPORTED, "iso-surface, ordered, skipping, deep and shadowed frames need dpvRenderFrame");
+    // the march reads the table as float4
+    if ((uintptr_t)sc->tf_rgba & 15)
+        return na_fail(DPV_ERR_INVALID_ARG, "transfer function not 16-byte aligned");
+    if (const char* why = camera_problem(*cam)) {
+        std::string m = std::string("camera: ") + why;
+        return na_fail(DPV_ERR_INVALID_ARG, m.c_str());
+    }
+    if (fr->flags & (DPV_FRAME_ISO | DPV_FRAME_ORDERED | DPV_FRAME_SKIP | DPV_FRAME_DEEP | DPV_FRAME_SHADOW |
+                     DPV_FRAME_ORDER))
+        return na_fail(DPV_ERR_UNSUPPORTED,
+                       "iso-surface, ordered, skipping, deep and shadowed frames and the order image need "
+                       "dpvRenderFrame");
 
     // bricks: owned ranges must tile the volume exactly
     std::vector<BrickDev> table(K);
@@ -218,9 +253,10 @@ extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_ca
         cudaError_t e_ = (x);                                            \
         if (e_ != cudaSuccess) return na_fail(DPV_ERR_CUDA, cudaGetErrorString(e_)); \
     } while (0)
-    NA_CK(cudaMemcpyAsync(d_table, table.data(), sizeof(BrickDev) * K, cudaMemcpyHostToDevice, st));
-    NA_CK(cudaMemcpyAsync(d_scales, scales.data(), sizeof(float) * K, cudaMemcpyHostToDevice, st));
-    NA_CK(cudaMemcpyAsync(d_camin, &ci, sizeof ci, cudaMemcpyHostToDevice, st));
+    static_assert(sizeof(BrickDev) % 4 == 0 && sizeof(CamIn) % 4 == 0, "tables travel as 32-bit words");
+    NA_CK(put_words(d_table, table.data(), sizeof(BrickDev) * K, st));
+    NA_CK(put_words(d_scales, scales.data(), sizeof(float) * K, st));
+    NA_CK(put_words(d_camin, &ci, sizeof ci, st));
     // the array keeps the previous call's contents: clear the counters and
     // mark every work-list entry invalid before the cull fills it
     NA_CK(cudaMemsetAsync(d_counters, 0, sizeof(Counters), st));

@@ -130,6 +130,42 @@ def test_autograd_matches_direct_backward():
     dev.release()
 
 
+def test_autograd_volume_follows_the_tensor():
+    """The field handed to the autograd render is the field rendered and
+    differentiated: a tensor changed in place after the commit (or another
+    tensor) is committed again before the render, so the image and both
+    gradients equal those of a device committed from the changed values;
+    an unchanged tensor is not committed again; bricks not committed from
+    one field cannot be tied to a volume and the render refuses."""
+    sc = _scene()
+    dev = scenes.gpu_device(sc, order=False)
+    vol = torch.from_numpy(sc.field).cuda()
+    dev.commit_partition(vol, sc.part, "f32")
+    assert not dev.ensure_volume(vol)
+    with torch.no_grad():
+        vol.mul_(0.7).add_(0.1)                 # in place: the bricks are stale now
+    vol.requires_grad_(True)
+    tf = torch.from_numpy(sc.tf).cuda().requires_grad_(True)
+    img = dpv.render(dev, tf, vol)
+    w = torch.randn(img.shape, generator=torch.Generator().manual_seed(4)).cuda()
+    (img * w).sum().backward()
+    ref = scenes.gpu_device(sc, order=False)
+    ref.commit_partition(vol.detach().clone(), sc.part, "f32")
+    ref.render()
+    assert torch.equal(img.detach(), ref.frames()[0])
+    dtf, dvol = ref.backward(w)
+    assert torch.allclose(tf.grad.double(), dtf, rtol=1e-4, atol=1e-7 * float(dtf.abs().max()))
+    assert torch.allclose(vol.grad, dvol, rtol=1e-4, atol=1e-6 * float(dvol.abs().max()))
+    # the same tensor, unchanged: no new commit
+    assert not dev.ensure_volume(vol)
+    # bricks committed one by one from a box each: not one known field
+    dev.commit_brick(0, sc.part.lo[0], sc.part.hi[0], vol.detach())
+    with pytest.raises(ValueError):
+        dpv.render(dev, tf, vol)
+    dev.release()
+    ref.release()
+
+
 @pytest.mark.parametrize("split", ["regular", "kd"])
 def test_face_buffer_matches_scalar_atomics(monkeypatch, split):
     """The field gradient through the face adjoint buffer (vector atomics per
