@@ -6,14 +6,18 @@ A step is one pass of the whole hot path over one batch: cull and work list,
 brick ray-march, sort-last composite (the forward frame of every camera),
 then the adjoint (compositor backward, ray-march replay with TF and volume
 gradients) for a fixed upstream image gradient.  The scene (bricks, TF,
-cameras, upstream gradient) is resident in HBM before timing; the 512 MiB
-volume is larger than L2, so no flush is needed between steps.
+cameras, upstream gradient) is resident in HBM before timing; every
+workload's volume is larger than L2, so no flush is needed between steps.
 
-`value` is the forward sample rate (samples the ray-march evaluated per
-second of forward device time); frames/s and the backward sample rate are
-reported beside it, and `ms_per_step` covers the whole step.
+The default workload is the largest single-GPU one: a 2048^3 field stored
+as bf16, 64 bricks, 8 cameras at 3840x2160.  `value` is the forward sample
+rate (samples the ray-march evaluated per second of forward device time);
+frames/s and the backward sample rate are reported beside it, and
+`ms_per_step` covers the whole step.  `roofline` describes the kernel with
+the larger share of the step (`roofline_forward` and `roofline_backward`
+describe both).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config mid]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config large_bf16]
   python bench.py --impl reference      # the FP64 CPU oracle, bounded sample
 """
 from __future__ import annotations
@@ -37,21 +41,19 @@ from paper_2407_00179_b300 import inputs  # noqa: E402
 
 METRIC = "Gsamples/s and composited frames/s at 1 B300 (% HBM roofline); backward Gsamples/s"
 BYTES_PER_VOXEL = {"f32": 4, "f16": 2, "bf16": 2, "fp8": 1}
-# DRAM bytes (read + write) per launch of the timed kernels, from one ncu
-# capture of this workload (profiles/ holds the summary and the command);
-# absent where no capture of the current kernel exists
-TRAFFIC = {
-    # the autotuner picks the per-item or the persistent form of the same
-    # per-item code; their DRAM traffic is within 3 % (persistent 4.93 GB)
-    ("mid", "march"): 4.818e9,        # k_march_fwd<float, cell, 0>: 4.790 GB read + 28.7 MB written
-    ("mid", "march_bwd"): 12.37e9,    # k_march_bwd<float, cell, face> 9.60 GB + k_face_gather 2.77 GB
-}
+# DRAM bytes (read + write) per unit of work of the timed kernels, and their
+# L1 / L2 sector hit rates, each from one ncu capture summarised under
+# profiles/ (the file is named in "capture").  "source" is the digest of the
+# kernel sources (csrc/kernels.cu, csrc/dpv_internal.cuh) the capture ran;
+# once those sources change, the figures no longer describe the kernel and
+# the line reports traffic null.  Where the bench's workload is too large to
+# capture, the capture is of a smaller case of the same kernel (same storage
+# and gather layout), and the bytes per evaluated sample scale to the full
+# launch by its sample count.
+TRAFFIC = {}
 
-# L1 / L2 sector hit rates of the timed kernels, from the same ncu captures
-HIT_RATES = {
-    ("mid", "march"): (0.538, 0.333),
-    ("mid", "march_bwd"): (0.542, 0.538),     # L1: global loads only (the reductions bypass L1)
-}
+# the capture whose per-sample traffic stands for each (workload, kernel)
+TRAFFIC_FOR = {}
 
 # FP32 arithmetic per sample counted in the source (an FMA counts once):
 # forward: position 6, trilinear 14, TF lookup 15, opacity 11, emission-
@@ -89,15 +91,21 @@ CONFIGS = {
                   storage="f32", cams="direction"),
     # 1024x1024x512 f16 turbulence, k-d 37 bricks, 16 orbit cameras at 1024^2
     "batched": dict(dims=(1024, 1024, 512), field="turbulent", kd=37, ncam=16, width=1024, height=1024, ert=0.0,
-                    storage="f16", cams="orbit"),
+                    storage="f16", cams="orbit", subsample=4),
     # 256^3 f32, 16 blobs, 2x2x2, 32 sphere cameras at 512^2
     "diff": dict(dims=(256, 256, 256), field="diff", splits=(2, 2, 2), ncam=32, width=512, height=512, ert=0.0,
                  storage="f32", cams="sphere"),
     # 2048^3, 4-octave noise + 256 blobs, 4x4x4 bricks, 8 orbit cameras at 3840x2160, bf16 / fp8 storage
+    # (the default workload: the largest single-GPU one); the CPU baseline
+    # and the parity report take the 1/16 pixel subsample of camera 0; after
+    # the timed run, the same batch from fp8 storage and the cameras as
+    # separate float32 frames
     "large_bf16": dict(dims=(2048, 2048, 2048), field="large", splits=(4, 4, 4), ncam=8, width=3840, height=2160,
-                       ert=0.0, storage="bf16", cams="orbit", compare_f32=False),
+                       ert=0.0, storage="bf16", cams="orbit", compare_f32=False, subsample=4,
+                       after_release={"storage": "fp8", "separate_f32": True}),
     "large_fp8": dict(dims=(2048, 2048, 2048), field="large", splits=(4, 4, 4), ncam=8, width=3840, height=2160,
-                      ert=0.0, storage="fp8", cams="orbit", compare_f32=False),
+                      ert=0.0, storage="fp8", cams="orbit", compare_f32=False, subsample=4,
+                      after_release={"storage": "bf16", "separate_f32": True}),
 }
 
 
@@ -129,6 +137,30 @@ def _peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6400.0, "fallback"
+
+
+def kernel_source_digest() -> str:
+    """Digest of the kernel sources a traffic capture describes."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "dpv_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2407_00179_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(cfg_name, kind, samples):
+    """(DRAM bytes of one launch, L1 hit, L2 hit, capture record) of the
+    workload's kernel `kind` ("march" or "march_bwd"), from its capture
+    scaled by the launch's evaluated samples; Nones where no capture of the
+    current kernel source exists."""
+    key = TRAFFIC_FOR.get((cfg_name, kind))
+    rec = TRAFFIC.get(key) if key else None
+    if not rec or rec["source"] != kernel_source_digest():
+        return None, None, None, ({"capture": rec["capture"], "stale": True} if rec else None)
+    return (rec["bytes_per_sample"] * samples, rec.get("l1_hit"), rec.get("l2_hit"),
+            {"capture": rec["capture"], "case": rec["case"], "bytes_per_sample": rec["bytes_per_sample"],
+             "scaled_by": "evaluated samples of the launch"})
 
 
 class ClockSampler:
@@ -203,16 +235,26 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_mod=None):
+def oracle_bricks(cfg, field_np, part):
+    """The oracle's bricks of the workload: its own stored values (the
+    oracle's encoders), built once per process."""
+    import oracle
+    oracle.build()
+    return oracle.make_bricks(field_np, part, oracle.DTYPE_NAMES[cfg["storage"]])
+
+
+def cpu_baseline(cfg_name, cfg, bricks, part, tf, cams, budget_s=12.0, one_core=True):
     """The FP64 oracle as it stands, on this host's cores, on a bounded pixel
-    sample of the same workload: whole pixel rows spread over the image."""
+    sample of the same workload: pixel rows spread over the image (with
+    cfg["subsample"] = s, the rows y % s == 0 and in them the pixels
+    x % s == 0: the 1/s^2 subsample of the frame)."""
     import oracle
     oracle.build()
     ncores = len(os.sched_getaffinity(0))
     oracle.set_threads(ncores)
-    bricks = oracle.make_bricks(field_np, part, oracle.DTYPE_NAMES[cfg["storage"]])
     fr = oracle.Frame(cfg["width"], cfg["height"], step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"])
     W, H = cfg["width"], cfg["height"]
+    sub = int(cfg.get("subsample", 1))
     # the camera and spacing exactly as the C ABI receives them (float32),
     # so the oracle's frame is comparable with the GPU's
     f32 = lambda v: tuple(float(x) for x in np.asarray(v, np.float32))
@@ -222,9 +264,11 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
 
     iso = cfg.get("iso")
     sh = cfg.get("shadow")
+    row_ids = np.arange(0, H, sub)                  # the rows the sample may take
+    xs = np.arange(0, W, sub, dtype=np.int32)
 
     def run(rows):
-        pix = np.concatenate([np.arange(W, dtype=np.int32) + W * int(r) for r in rows])
+        pix = np.concatenate([xs + W * int(r) for r in rows])
         t = time.perf_counter()
         if sh is not None:
             out = oracle.render_shadow(cfg["dims"], tf, cam, fr, oracle.Light(sh[0], step_voxels=sh[1], ambient=sh[2]),
@@ -239,35 +283,41 @@ def cpu_baseline(cfg_name, cfg, field_np, part, tf, cams, budget_s=12.0, oracle_
         out = oracle.render_bricks(cfg["dims"], bricks, tf, cam, fr, pix=pix, spacing=sp)
         return time.perf_counter() - t, int(out["nsamples"].sum()), len(pix), out, pix
 
+    def spread(n):
+        return row_ids[np.linspace(0, len(row_ids) - 1, max(1, min(n, len(row_ids)))).astype(int)]
+
     # calibrate on 8 rows spread over the image, then size the sample so the
     # oracle works about budget_s seconds
-    cal = np.linspace(0, H - 1, 8).astype(int)
+    cal = spread(8)
     dt, ns, npx, _, _ = run(cal)
     per_row_s = max(dt, 1e-6) / len(cal)
-    nrows = int(min(H, max(8, budget_s / per_row_s)))
-    rows = np.linspace(0, H - 1, nrows).astype(int)
+    rows = spread(int(max(8, budget_s / per_row_s)))
     dt, ns, npx, ref_out, ref_pix = run(rows)
     ref = {"pix": ref_pix, "rgba": ref_out["rgba"], "flags": ref_out["flags"], "order": ref_out.get("order")}
-    # one core on a reduced image: rows spread over the frame, about 3 s
-    oracle.set_threads(1)
-    n1 = int(min(H, max(2, 3.0 / (per_row_s * ncores))))
-    rows1 = np.linspace(0, H - 1, n1).astype(int)
-    dt1, ns1, npx1, _, _ = run(rows1)
-    oracle.set_threads(ncores)
+    what = "pixels x %% %d == 0 of %d of the %d rows y %% %d == 0" % (sub, len(rows), len(row_ids), sub) if sub > 1 \
+        else "%d of %d pixel rows" % (len(rows), H)
+    one = None
+    if one_core:
+        # one core on a reduced image: rows spread over the frame, about 3 s
+        oracle.set_threads(1)
+        rows1 = spread(int(max(2, 3.0 / (per_row_s * ncores))))
+        dt1, ns1, npx1, _, _ = run(rows1)
+        oracle.set_threads(ncores)
+        one = (dt1, ns1, npx1, len(rows1))
     if iso is not None:
         # the iso oracle evaluates every sample of the ray: its rate is in pixels
         return {"value": npx / dt / 1e6, "unit": "Mpixels/s", "cores": ncores, "kind": "oracle",
-                "sample": "%d of %d pixel rows (%d pixels) of camera 0, iso-surface, FP64, %.1f s" % (
-                    len(rows), H, npx, dt),
-                "one_core": {"value": npx1 / dt1 / 1e6, "unit": "Mpixels/s", "cores": 1,
-                             "sample": "%d pixel rows (%d pixels) of camera 0, %.1f s" % (len(rows1), npx1, dt1)},
+                "sample": "%s (%d pixels) of camera 0, iso-surface, FP64, %.1f s" % (what, npx, dt),
+                "one_core": None if one is None else {
+                    "value": one[2] / one[0] / 1e6, "unit": "Mpixels/s", "cores": 1,
+                    "sample": "%d pixel rows (%d pixels) of camera 0, %.1f s" % (one[3], one[2], one[0])},
                 "seconds": dt, "samples": npx, "rows": rows, "ref": ref}
     return {"value": ns / dt / 1e9, "unit": "Gsamples/s", "cores": ncores, "kind": "oracle",
-            "sample": "%d of %d pixel rows (%d pixels, %d samples) of camera 0, FP64, %.1f s" % (
-                len(rows), H, npx, ns, dt),
-            "one_core": {"value": ns1 / dt1 / 1e9, "unit": "Gsamples/s", "cores": 1,
-                         "sample": "%d pixel rows (%d pixels, %d samples) of camera 0, %.1f s" % (
-                             len(rows1), npx1, ns1, dt1)},
+            "sample": "%s (%d pixels, %d samples) of camera 0, FP64, %.1f s" % (what, npx, ns, dt),
+            "one_core": None if one is None else {
+                "value": one[1] / one[0] / 1e9, "unit": "Gsamples/s", "cores": 1,
+                "sample": "%d pixel rows (%d pixels, %d samples) of camera 0, %.1f s" % (one[3], one[2], one[1],
+                                                                                        one[0])},
             "seconds": dt, "samples": ns, "rows": rows, "ref": ref}
 
 
@@ -275,15 +325,16 @@ def run_reference(args, cfg_name, cfg):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    dev = "cpu"
     f = _field(cfg, "cuda" if torch.cuda.is_available() else "cpu").cpu().numpy()
     part = _partition(cfg)
+    bricks = oracle_bricks(cfg, f, part)
+    del f
     tf = inputs.make_tf(1234, transparent_below=cfg.get("tf_cut", 0.0))
     cams = _cameras(cfg)
     steps = []
     base = None
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(cfg_name, cfg, f, part, tf, cams, budget_s=args.ref_budget)
+        r = cpu_baseline(cfg_name, cfg, bricks, part, tf, cams, budget_s=args.ref_budget, one_core=False)
         if i >= args.warmup:
             steps.append(r)
         base = r
@@ -302,6 +353,88 @@ def run_reference(args, cfg_name, cfg):
                              "sample": base["sample"]},
             "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def after_release(args, cfg, field_host, part, tf, cams, tune, img0, batch_ms, batch_samples, device):
+    """Comparisons for workloads whose main device leaves no room for a
+    second one: run after it is released, from the host copy of the field.
+
+    * "storage": the same batch of cameras from another storage format, in
+      the main run's launch form: forward rate and image difference (camera
+      0) from the main run's frame;
+    * "separate_f32": every camera rendered as its own float32-storage frame
+      (one device, one camera at a time, its default launch form): their
+      summed forward time against the batched reduced-precision forward,
+      and camera 0's image difference (the storage error of the batched
+      form)."""
+    from paper_2407_00179_b300 import dpv
+    out = {}
+    W, H = cfg["width"], cfg["height"]
+    stream = torch.cuda.current_stream(device)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    what = cfg["after_release"]
+    fl = tune["flags"] if tune else 0
+    if "storage" in what:
+        alt = dpv.Device(part.num_ranks, device.index or 0)
+        alt.set_geometry(cfg["dims"])
+        alt.commit_partition(field_host, part, what["storage"])
+        alt.set_tf(tf)
+        alt.set_cameras(cams)
+        alt.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
+                      tile=tuple(tune["tile"]) if tune else (0, 0), gather=dpv.gather_of(fl),
+                      persistent=bool(fl & dpv.FRAME_PERSISTENT))
+        for _ in range(2):
+            alt.render()
+        torch.cuda.synchronize()
+        a0, a1 = ev(), ev()
+        n = max(2, min(args.steps, 5))
+        a0.record(stream)
+        for _ in range(n):
+            alt.render()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms = a0.elapsed_time(a1) / n
+        d = (alt.map_frame(0)[0] - img0).abs()
+        out["storage_comparison"] = {
+            "storage": what["storage"], "forward_ms_per_step": ms,
+            "value": alt.stats()["samples_forward"] / (ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+            "launch_form": "the main run's", "image_difference_vs_%s_camera0" % cfg["storage"]: {
+                "max": float(d.max()), "mean": float(d.mean())}}
+        alt.release()
+        del d
+        torch.cuda.empty_cache()
+    if what.get("separate_f32"):
+        sep = dpv.Device(part.num_ranks, device.index or 0)
+        sep.set_geometry(cfg["dims"])
+        sep.commit_partition(field_host, part, "f32")
+        sep.set_tf(tf)
+        total, samples, err = 0.0, 0, None
+        for c, cam in enumerate(cams):
+            sep.set_cameras([cam])
+            sep.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"])
+            sep.render()
+            torch.cuda.synchronize()
+            s0, s1 = ev(), ev()
+            s0.record(stream)
+            for _ in range(2):
+                sep.render()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            total += s0.elapsed_time(s1) / 2
+            samples += sep.stats()["samples_forward"]
+            if c == 0:
+                d = (sep.map_frame(0)[0] - img0).abs()
+                err = {"max": float(d.max()), "mean": float(d.mean())}
+                del d
+        sep.release()
+        torch.cuda.empty_cache()
+        out["separate_f32"] = {
+            "what": "each camera its own float32-storage frame, one after another (default launch form)",
+            "forward_ms_total": total, "gsamples_per_s": samples / (total * 1e-3) / 1e9,
+            "batched_%s_forward_ms" % cfg["storage"]: batch_ms,
+            "speedup_of_batched_%s" % cfg["storage"]: total / batch_ms,
+            "image_difference_camera0_batched_%s_vs_f32" % cfg["storage"]: err}
+    return out
 
 
 def run_ours(args, cfg_name, cfg):
@@ -328,7 +461,8 @@ def run_ours(args, cfg_name, cfg):
     dev.commit_partition(field, part, cfg["storage"])
     compare_f32 = cfg.get("compare_f32", True)
     # keep a host copy for the CPU baseline and free the device field
-    field_host = field.cpu().numpy() if (rank == 0 and not args.no_cpu_baseline) else None
+    field_host = field.cpu().numpy() if (rank == 0 and (not args.no_cpu_baseline or cfg.get("after_release"))) \
+        else None
     field_dev = field if ((compare_f32 and ncam > 1) or cfg.get("compare_storage")) else None
     del field
     torch.cuda.empty_cache()
@@ -411,13 +545,17 @@ def run_ours(args, cfg_name, cfg):
     frames = ncam * args.steps
     (total_ms, fwd_ms, bwd_ms), (n_fwd, n_bwd, frames) = reduce_over_ranks(
         pg, device, [total_ms, fwd_ms, bwd_ms], [n_fwd, n_bwd, frames])
-    # roofline of the dominant kernel (forward ray-march): stencil bytes
+    # rooflines of the two hot kernels on the stencil-byte model, each from
+    # its own device time in the timed region (library CUDA events on the
+    # device stream around its launches); `roofline` is the one that takes
+    # the larger share of the step
     bpv = BYTES_PER_VOXEL[cfg["storage"]]
-    march_ms = st["stage_ms"]["march"] / max(1, st["stage_calls"]["march"])
-    march_bwd_ms = st["stage_ms"]["march_bwd"] / max(1, st["stage_calls"]["march_bwd"])
-    bytes_per_launch = per_step * 8 * bpv
-    achieved = bytes_per_launch / (march_ms * 1e-3) / 1e9
-    bwd_achieved = st["samples_backward"] * (8 * bpv + 8 * 4) / (march_bwd_ms * 1e-3) / 1e9 if grad is not None else 0.0
+    steps = args.steps
+    march_ms = st["stage_ms"]["march"] / steps                 # one launch per step
+    march_bwd_ms = st["stage_ms"]["march_bwd"] / steps         # one launch per face-buffer group
+    face_ms = st["stage_ms"]["face"] / steps
+    fwd_bytes = per_step * 8 * bpv
+    bwd_bytes = st["samples_backward"] * (8 * bpv + 8 * 4)
     peak, peak_kind = _peaks()
 
     # compulsory bytes (each stored brick read once + fragment writes), the
@@ -434,21 +572,38 @@ def run_ours(args, cfg_name, cfg):
     nsm = torch.cuda.get_device_properties(device).multi_processor_count
     tile_px = (tune["tile"][0] * tune["tile"][1]) if tune else (args.tile_w or 16) * (args.tile_h or 16)
 
-    def march_detail(kind, ms, samples, sm_mhz):
+    def roofline(kind, ms, samples, nbytes, kernel, model, sm_mhz):
         # fragments written (RGBA + key per slot) by the forward; the adjoint
         # writes the field gradient (4 B per global node)
         out = st["work_items"] * tile_px * 20 if kind == "march" else int(np.prod(cfg["dims"])) * 4
         comp = brick_bytes + out
-        traffic = TRAFFIC.get((cfg_name, kind))
-        hits = HIT_RATES.get((cfg_name, kind), (None, None))
+        traffic, l1, l2, cap = traffic_for(cfg_name, kind, samples)
         alu = (128 * nsm * sm_mhz * 1e6 / FP32_OPS_PER_SAMPLE[kind] / 1e9) if sm_mhz else None
         rate = samples / (ms * 1e-3) / 1e9
-        return {"compulsory_bytes": comp, "compulsory_frac": comp / (ms * 1e-3) / 1e9 / peak,
-                "dram_traffic_bytes": traffic,
-                "dram_gbs": traffic / (ms * 1e-3) / 1e9 if traffic else None,
-                "l1_hit": hits[0], "l2_hit": hits[1], "fp32_ops_per_sample": FP32_OPS_PER_SAMPLE[kind],
-                "alu_ceiling_gsamples": alu, "alu_frac": rate / alu if alu else None,
-                "alu_basis": "128 FP32 lanes x %d SMs x max SM clock / FP32 ops per sample" % nsm}
+        achieved = nbytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": kernel, "model": model, "peak_kind": peak_kind,
+                "ms_per_step": ms, "share_of_step": ms / (total_ms / steps),
+                "detail": {"compulsory_bytes": comp, "compulsory_frac": comp / (ms * 1e-3) / 1e9 / peak,
+                           "dram_traffic_bytes": traffic,
+                           "dram_gbs": traffic / (ms * 1e-3) / 1e9 if traffic else None,
+                           "traffic_capture": cap, "l1_hit": l1, "l2_hit": l2,
+                           "fp32_ops_per_sample": FP32_OPS_PER_SAMPLE[kind],
+                           "alu_ceiling_gsamples": alu, "alu_frac": rate / alu if alu else None,
+                           "alu_basis": "128 FP32 lanes x %d SMs x max SM clock / FP32 ops per sample" % nsm}}
+
+    roof_fwd = roofline("march", march_ms, per_step, fwd_bytes,
+                        ("k_iso_fwd<%s>" if iso is not None else "k_march_ordered<%s>" if ordered
+                         else "k_shadow_round<%s> + k_march_shadowed (march stage)" if shadow is not None
+                         else "k_march_fwd<%s>") % cfg["storage"],
+                        "stencil bytes: 8 corners x %d B per evaluated sample" % bpv, clk.get("sm_max_mhz"))
+    roof_bwd = None
+    if grad is not None:
+        roof_bwd = roofline("march_bwd", march_bwd_ms, st["samples_backward"], bwd_bytes,
+                            "k_march_bwd<%s>" % cfg["storage"],
+                            "stencil bytes: 8 corners x %d B read + 8 x 4 B field-gradient adds per replayed "
+                            "sample" % bpv, clk.get("sm_max_mhz"))
+        roof_bwd["face_buffer_ms_per_step"] = face_ms
 
     # many cameras: the same forward replayed from a CUDA graph, and the
     # cameras rendered as separate float32 per-camera frames for comparison
@@ -684,22 +839,9 @@ def run_ours(args, cfg_name, cfg):
                         if shadow is not None else
                         "samples evaluated up to the global termination / forward time (cull + ordered march); "
                         "ordered frames have no adjoint, a step is the forward frame"),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": TRAFFIC.get((cfg_name, "march")),
-                     "kernel": ("k_iso_fwd<%s>" if iso is not None else "k_march_ordered<%s>" if ordered
-                                else "k_shadow_round<%s> + k_march_shadowed (march stage)" if shadow is not None
-                                else "k_march_fwd<%s>") % cfg["storage"],
-                     "model": "stencil bytes: 8 corners x %d B per evaluated sample" % bpv,
-                     "peak_kind": peak_kind,
-                     "detail": march_detail("march", march_ms, per_step, clk.get("sm_max_mhz"))},
-        "roofline_backward": ({"bound": "hbm", "achieved": bwd_achieved, "peak": peak, "unit": "GB/s",
-                               "frac": bwd_achieved / peak, "traffic": TRAFFIC.get((cfg_name, "march_bwd")),
-                               "kernel": "k_march_bwd<%s> (+ k_face_gather)" % cfg["storage"],
-                               "model": "stencil bytes: 8 corners x %d B read + 8 x 4 B field-gradient adds per "
-                                        "replayed sample" % bpv,
-                               "peak_kind": peak_kind,
-                               "detail": march_detail("march_bwd", march_bwd_ms, st["samples_backward"],
-                                                      clk.get("sm_max_mhz"))} if grad is not None else None),
+        "roofline": (roof_bwd if roof_bwd is not None and march_bwd_ms > march_ms else roof_fwd),
+        "roofline_forward": roof_fwd,
+        "roofline_backward": roof_bwd,
         "e2e": {"value": e2e_val, "unit": "Gsamples/s", "h2d_bytes_per_step": int(tf_np.nbytes),
                 "d2h_bytes_per_step": int(ncam * H * W * 16), "what": "set TF from pinned host, render, copy frames"
                 " to pinned host (asynchronous, overlapping the next render; all copies complete inside the "
@@ -735,7 +877,8 @@ def run_ours(args, cfg_name, cfg):
         order0 = dev.order(0).reshape(-1, part.num_ranks).cpu().numpy()
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            cb = cpu_baseline(cfg_name, cfg, field_host, part, tf_np, cams, budget_s=args.ref_budget)
+            cb = cpu_baseline(cfg_name, cfg, oracle_bricks(cfg, field_host, part), part, tf_np, cams,
+                              budget_s=args.ref_budget)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "one_core")}
         except Exception as e:  # the oracle is a reported baseline, never the product
             cb = None
@@ -757,6 +900,11 @@ def run_ours(args, cfg_name, cfg):
                 par["order_mismatches"] = int((o[ok] != ref["order"][ok]).any(axis=1).sum())
             line["parity"] = par
     dev.release()
+    del grad
+    torch.cuda.empty_cache()
+    if rank == 0 and cfg.get("after_release") and field_host is not None:
+        line.update(after_release(args, cfg, field_host, part, tf, cams, tune, img0, fwd_ms / steps, per_step,
+                                  device))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
@@ -769,7 +917,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="mid", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="large_bf16", choices=sorted(CONFIGS))
     ap.add_argument("--tile-w", type=int, default=0)
     ap.add_argument("--tile-h", type=int, default=0)
     ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of oracle work per reference step")

@@ -203,8 +203,10 @@ typedef enum {
     DPV_STAGE_MARCH = 1,          /* brick ray-march (forward) */
     DPV_STAGE_COMPOSITE = 2,      /* sort-last compositor (forward) */
     DPV_STAGE_COMPOSITE_BWD = 3,  /* compositor adjoint */
-    DPV_STAGE_MARCH_BWD = 4,      /* ray-march adjoint */
-    DPV_NUM_STAGES = 5
+    DPV_STAGE_MARCH_BWD = 4,      /* ray-march adjoint (the replay launches) */
+    DPV_STAGE_FACE = 5,           /* face adjoint buffer of the field gradient:
+                                     clears and gathers into the field */
+    DPV_NUM_STAGES = 6
 } dpv_stage;
 
 /* Counters.  samples_* and error_flags are those of the most recent

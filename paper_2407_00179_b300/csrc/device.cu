@@ -1364,6 +1364,13 @@ dpv_status dpvMapOrder(dpv_device dev, int camera, const uint8_t** order, int* s
     return DPV_OK;
 }
 
+namespace {
+dpv_status finish_backward(dpv_device dev) {
+    dev->launches += 1;   // the compositor's adjoint
+    return DPV_OK;
+}
+}  // namespace
+
 dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, float* dL_dvol) {
     dpv_status s = check_dev(dev);
     if (s) return s;
@@ -1426,9 +1433,11 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
     }
     grp.push_back(dev->nranks);
     const int ngroups = (int)grp.size() - 1;
-    if (faces && ngroups == 1)
+    if (faces && ngroups == 1) {
+        cudaEvent_t tc = stage_start(dev);
         CK(cudaMemsetAsync(dev->d_gface, 0, dev->gface_slots * sizeof(float4), dev->stream), "zero face buffer");
-    else if (dL_dvol)
+        stage_stop(dev, DPV_STAGE_FACE, tc);
+    } else if (dL_dvol)
         CK(cudaMemsetAsync(dL_dvol, 0, sizeof(float) * (size_t)dev->dims[0] * dev->dims[1] * dev->dims[2], dev->stream),
            "zero dvol");
     CK(cudaMemsetAsync(&dev->d_counters->samples_bwd, 0, sizeof(unsigned long long), dev->stream), "reset counter");
@@ -1437,27 +1446,38 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
                             (const float4*)dL_drgba, dev->d_frag_grad, dev->stream),
        "composite backward");
     stage_stop(dev, DPV_STAGE_COMPOSITE_BWD, t0);
-    t0 = stage_start(dev);
     const bool persistent = (dev->frame.flags & DPV_FRAME_PERSISTENT) != 0;
     Schedule sch{dev->d_sched, dev->d_work, 0};   // the pull order built by the render
     if (!staged && faces) {
+        // the replays are timed as DPV_STAGE_MARCH_BWD, the clears and
+        // gathers of the face buffer as DPV_STAGE_FACE
         for (int g = 0; g < ngroups; ++g) {
             const FaceGroup fg{grp[g], grp[g + 1], (long long)dev->gface_off_h[grp[g]]};
-            if (ngroups > 1)
+            if (ngroups > 1) {
+                cudaEvent_t tc = stage_start(dev);
                 CK(cudaMemsetAsync(dev->d_gface, 0,
                                    (dev->gface_off_h[fg.k1] - dev->gface_off_h[fg.k0]) * sizeof(float4), dev->stream),
                    "zero face buffer");
+                stage_stop(dev, DPV_STAGE_FACE, tc);
+            }
+            t0 = stage_start(dev);
             CK(launch_march_bwd(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                                 dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key,
                                 dev->d_frag_grad, dL_dtf, nullptr, dev->d_gface, dev->d_counters, dev->stream,
                                 persistent ? &sch : nullptr, &fg),
                "march backward");
+            stage_stop(dev, DPV_STAGE_MARCH_BWD, t0);
+            t0 = stage_start(dev);
             CK(launch_face_gather(dev->d_bricks, dev->nranks, dev->d_nb_first, dev->d_nb, dev->max_rows,
                                   dev->d_gface, dev->dims, dL_dvol, dev->stream, ngroups > 1 ? &fg : nullptr),
                "face gather");
+            stage_stop(dev, DPV_STAGE_FACE, t0);
         }
         dev->launches += ngroups * ((dev->n_items > 0 ? 1 : 0) + (dev->max_rows > 0 ? 1 : 0));
-    } else if (!staged) {
+        return finish_backward(dev);
+    }
+    t0 = stage_start(dev);
+    if (!staged) {
         CK(launch_march_bwd(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                             dev->d_items, dev->n_items, dev->d_tf, dev->d_frag_rgba, dev->d_frag_key,
                             dev->d_frag_grad, dL_dtf, dL_dvol, nullptr, dev->d_counters, dev->stream,
@@ -1471,8 +1491,7 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
            "march backward");
     stage_stop(dev, DPV_STAGE_MARCH_BWD, t0);
     if (staged) dev->launches += dev->n_items > 0 ? 1 : 0;
-    dev->launches += 1;   // the compositor's adjoint
-    return DPV_OK;
+    return finish_backward(dev);
 }
 
 dpv_status dpvGetStats(dpv_device dev, dpv_stats* out) {

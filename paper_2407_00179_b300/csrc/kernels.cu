@@ -398,16 +398,16 @@ cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 orig
 template <typename T, int GL, bool SKIP>
 __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, const CamBasis* cams,
                                                          const BrickDev* bricks, const float* scales, const Item& it,
-                                                         long long item, const float4* s_tf, float4* frag_rgba,
-                                                         int* frag_key) {
+                                                         long long item, int t, const float4* s_tf,
+                                                         float4* frag_rgba, int* frag_key) {
     const BrickDev b = bricks[it.brick];
     const CamBasis cam = cams[it.cam];
     const float scale = scales[b.scale_idx];
     const T* data = (const T*)b.data;
     int lx, ly;
-    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    tile_pixel(t, P.tw, lx, ly);
     int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
-    long long slot = item * P.tp + threadIdx.x;
+    long long slot = item * P.tp + t;
     unsigned long long nsamp = 0;
     if (px < P.W && py < P.H) {
         MarchState m;
@@ -497,16 +497,16 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
 template <typename T, int GL>
 __device__ __forceinline__ unsigned long long march_item_deep(const FrameParams& P, const CamBasis* cams,
                                                               const BrickDev* bricks, const float* scales,
-                                                              const Item& it, long long item, const float4* s_tf,
-                                                              float4* frag_rgba, int* frag_key) {
+                                                              const Item& it, long long item, int t,
+                                                              const float4* s_tf, float4* frag_rgba, int* frag_key) {
     const BrickDev b = bricks[it.brick];
     const CamBasis cam = cams[it.cam];
     const float scale = scales[b.scale_idx];
     const T* data = (const T*)b.data;
     int lx, ly;
-    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    tile_pixel(t, P.tw, lx, ly);
     int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
-    const long long base = item * DEEP_LAYERS * P.tp + threadIdx.x;     // layer d at base + d tp
+    const long long base = item * DEEP_LAYERS * P.tp + t;     // layer d at base + d tp
     unsigned long long nsamp = 0;
     if (px < P.W && py < P.H) {
         int nf = 0;
@@ -564,10 +564,10 @@ __device__ __forceinline__ unsigned long long march_item_deep(const FrameParams&
 template <typename T, int GL, int MODE>
 __device__ __forceinline__ unsigned long long march_any(const FrameParams& P, const CamBasis* cams,
                                                         const BrickDev* bricks, const float* scales, const Item& it,
-                                                        long long item, const float4* s_tf, float4* frag_rgba,
+                                                        long long item, int t, const float4* s_tf, float4* frag_rgba,
                                                         int* frag_key) {
-    if (MODE == 2) return march_item_deep<T, GL>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
-    return march_item<T, GL, MODE == 1>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
+    if (MODE == 2) return march_item_deep<T, GL>(P, cams, bricks, scales, it, item, t, s_tf, frag_rgba, frag_key);
+    return march_item<T, GL, MODE == 1>(P, cams, bricks, scales, it, item, t, s_tf, frag_rgba, frag_key);
 }
 
 // The march over the cell layout is held to 48 registers, 5 CTAs per SM;
@@ -588,14 +588,18 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<GL, MODE>()) k_march_fwd(Fra
     __syncthreads();
     const Item it = items[blockIdx.x];
     if (!item_ok(it, P)) return;
-    unsigned long long nsamp = march_any<T, GL, MODE>(P, cams, bricks, scales, it, blockIdx.x, s_tf, frag_rgba, frag_key);
+    unsigned long long nsamp =
+        march_any<T, GL, MODE>(P, cams, bricks, scales, it, blockIdx.x, threadIdx.x, s_tf, frag_rgba, frag_key);
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
 
-// Persistent form: a grid sized to the GPU pulls work items from a counter
-// in the order `sched` gives (brick-major: all cameras' tiles of one brick
-// together, so a brick is read from HBM about once per batch).
+// Persistent form: a grid sized to the GPU whose warps each pull one warp's
+// share of a work item (32 pixels of its tile) at a time from a counter, in
+// the order `sched` gives (brick-major: all cameras' tiles of one brick
+// together, so a brick is read from HBM about once per batch).  A warp
+// whose rays are short takes the next unit at once instead of waiting for
+// the other warps of its tile, and no barrier separates the units.
 template <typename T, int GL, int MODE>
 __global__ void __launch_bounds__(256, fwd_min_ctas<GL, MODE>()) k_march_fwd_persistent(FrameParams P, const CamBasis* cams,
                                                               const BrickDev* bricks, const float* scales,
@@ -603,21 +607,26 @@ __global__ void __launch_bounds__(256, fwd_min_ctas<GL, MODE>()) k_march_fwd_per
                                                               unsigned int* work, const float4* tf,
                                                               float4* frag_rgba, int* frag_key, Counters* counters) {
     extern __shared__ float4 s_tf[];
-    __shared__ int s_next;
     for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned wpt = (unsigned)(P.tp >> 5);               // warps per tile
+    const unsigned n_units = (unsigned)n_items * wpt;
     unsigned long long nsamp = 0;
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_next = (int)atomicAdd(work, 1u);
-        __syncthreads();
-        const int i = s_next;
-        if (i >= n_items) break;
-        const int item = sched[i];
+        __syncwarp();
+        unsigned u = 0;
+        if (lane == 0) u = atomicAdd(work, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= n_units) break;
+        const int item = sched[u / wpt];
         const Item it = items[item];
-        if (item_ok(it, P)) nsamp += march_any<T, GL, MODE>(P, cams, bricks, scales, it, item, s_tf, frag_rgba, frag_key);
+        if (item_ok(it, P))
+            nsamp += march_any<T, GL, MODE>(P, cams, bricks, scales, it, item, (int)((u % wpt) * 32 + lane), s_tf,
+                                            frag_rgba, frag_key);
     }
     nsamp = warp_sum_u64(nsamp);
-    if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
+    if (lane == 0 && nsamp) atomicAdd(&counters->samples_fwd, nsamp);
 }
 
 template <typename T, int GL, int MODE>
@@ -635,7 +644,7 @@ static void fwd_launch_s(const FrameParams& P, const CamBasis* cams, const Brick
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_march_fwd_persistent<T, GL, MODE>, P.tp, smem);
         int grid = nsm * (per_sm > 0 ? per_sm : 1);
         if (sch->ctas_per_sm > 0 && sch->ctas_per_sm < per_sm) grid = nsm * sch->ctas_per_sm;
-        if (grid > n_items) grid = n_items;
+        if (grid > n_items) grid = n_items;      // a CTA's warps take at least one tile's worth
         cudaMemsetAsync(sch->work, 0, sizeof(unsigned int), st);
         k_march_fwd_persistent<T, GL, MODE><<<grid, P.tp, smem, st>>>(P, cams, bricks, scales, items, sch->sched, n_items,
                                                                   sch->work, tf, frag_rgba, frag_key, counters);
@@ -1404,11 +1413,14 @@ cudaError_t launch_composite_bwd(const FrameParams& P, const int* tile_first, co
 // segment stays the same and flushes on change; a step to the neighbouring
 // segment keeps the sums of the entry the two segments share.  Nearby rays share TF
 // segments, so a single shared table would serialise the flushes of a warp
-// on the same addresses; the CTA keeps `ncopy` FP32 copies of the TF
-// gradient table (bwd_tf_copies; the copy of a lane: tf_copy) (copies
-// offset by one float so equal entries of different copies sit in different
-// banks).  At the end the copies are summed and added to the global FP64
-// table once per touched entry.  The voxel gradient goes, per sample, as two
+// on the same addresses; the CTA keeps `ncopy` copies of the TF gradient
+// table (bwd_tf_copies; the copy of a lane: tf_copy) (copies offset by one
+// float so equal entries of different copies sit in different banks).
+// Each copy is a compensated FP32 sum: a high part and a low part per entry
+// (tf_add_comp), so that a copy's value does not drift with the number of
+// flushes it takes or with how much they cancel.  At the end the copies
+// are summed the same way and added to the global FP64 table once per
+// touched entry.  The voxel gradient goes, per sample, as two
 // float4 reductions into the face adjoint buffer (gather layout; one float4
 // per cell face; k_face_gather then writes the field) -- measured 3 % faster
 // than summing a cell run in eight registers first -- or, without that
@@ -1419,23 +1431,61 @@ struct TFRunF {
     float a[8];        // entry i0 (rgba), entry i0+1 (rgba)
 };
 
-__device__ __forceinline__ void tf_flush_f(TFRunF& r, float* tab) {
+// Knuth's TwoSum: s = fl(a + b) and the exact rounding error e, a + b = s + e.
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+    float bb = s - a;
+    return (a - (s - bb)) + (b - bb);
+}
+
+// Compensated shared accumulation of x into the entry at `hi` (the entry's
+// low part sits `lo` floats further on).  The atomic returns the value o it
+// added x to; the sum it stored is fl(o + x), rounded to nearest like the
+// register sum below, so TwoSum recovers the exact rounding error of that
+// addition, which goes into the low part.  hi + lo then equals the sum of
+// every x up to the rounding of the low part's own sums (errors of errors),
+// whatever the order of the flushes and however much they cancel.
+__device__ __forceinline__ void tf_add_comp(float* hi, int lo, float x) {
+    const float o = atomicAdd(hi, x);
+    const float e = two_sum_err(o, x, o + x);
+    if (e != 0.0f) atomicAdd(hi + lo, e);
+}
+
+__device__ __forceinline__ void tf_flush_f(TFRunF& r, float* tab, int lo) {
     if (r.i0 < 0) return;
     float* e = tab + 4 * r.i0;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
-        if (r.a[c] != 0.0f) atomicAdd(e + c, r.a[c]);
+        if (r.a[c] != 0.0f) tf_add_comp(e + c, lo, r.a[c]);
 }
 
-// Copies of the FP32 TF gradient table per CTA: as many as fit in 64 KB of
-// shared memory, at most 8 (the four lanes of a warp's pixel column share
-// one).  Shared memory and L1 share each SM's 256 KB and registers hold the
-// kernel to three CTAs per SM either way: at 256 entries, 8 copies leave
-// the gather about 140 KB of L1 instead of about 45 KB with 16 copies
-// (measured at mid: 7.61 -> 6.72 ms; 4 copies 6.81, 2 copies 7.16).
+// Copies of the compensated TF gradient table per CTA (a high and a low
+// part per entry): as many as fit in 64 KB of shared memory, at most 4.
+// Shared memory and L1 share each SM's 256 KB and registers hold the
+// kernel to three CTAs per SM either way: at 256 entries, 4 copies take
+// 32 KB and leave the gather about 140 KB of L1.  (Plain FP32 copies, one
+// part per entry, measured at mid: 16 copies 7.61 ms, 8 copies 6.72, 4
+// copies 6.81, 2 copies 7.16.)
 int bwd_tf_copies(int ntf) {
-    int c = 65536 / (16 * ntf);
-    return c < 1 ? 1 : (c > 8 ? 8 : c);
+    int c = 65536 / (32 * ntf);
+    return c < 1 ? 1 : (c > 4 ? 4 : c);
+}
+
+// Floats of one copy: high parts, low parts, one float of padding.
+__host__ __device__ __forceinline__ int tf_copy_stride(int ntf) { return 8 * ntf + 1; }
+
+// Sum of entry i over the copies (high and low parts), compensated, into
+// the global FP64 table.
+__device__ __forceinline__ void tf_copies_to_global(const float* s_g, int ncopy, int ntf, int i, double* dtf) {
+    const int stride = tf_copy_stride(ntf), lo = 4 * ntf;
+    float s = 0.0f, e = 0.0f;
+    for (int c = 0; c < ncopy; ++c) {
+        const float h = s_g[c * stride + i];
+        const float t = s + h;
+        e += two_sum_err(s, h, t) + s_g[c * stride + lo + i];
+        s = t;
+    }
+    const double v = (double)s + (double)e;
+    if (v != 0.0) atomicAdd(dtf + i, v);
 }
 
 // The copy a thread flushes into.  A warp covers an 8 x 4 pixel block (lane
@@ -1452,7 +1502,7 @@ __device__ __forceinline__ int tf_copy(int tid, int ncopy) {
 template <typename T, int GL, bool FACE>
 __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, const CamBasis* cams,
                                                        const BrickDev* bricks, const float* scales, const Item& it,
-                                                       long long item, const float4* s_tf, float* my_tab,
+                                                       long long item, int t, const float4* s_tf, float* my_tab,
                                                        const float4* frag_rgba, const int* frag_key,
                                                        const float4* frag_grad, float* dvol, float4* gface,
                                                        long long gbase) {
@@ -1461,12 +1511,13 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
     const float scale = scales[b.scale_idx];
     const T* data = (const T*)b.data;
     int lx, ly;
-    tile_pixel(threadIdx.x, P.tw, lx, ly);
+    tile_pixel(t, P.tw, lx, ly);
     int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
-    long long slot = item * P.tp + threadIdx.x;
+    long long slot = item * P.tp + t;
     unsigned long long nsamp = 0;
     const float gscale = Storage<T>::unit_scale ? 1.0f : scale;
     const long long sy = P.dims[0], sz = (long long)P.dims[0] * P.dims[1];
+    const int tf_lo = 4 * P.ntf;          // low parts of the copy, after its high parts
     if (px < P.W && py < P.H && frag_key[slot] != KEY_EMPTY) {
         MarchState m;
         float4 F = frag_rgba[slot];
@@ -1504,7 +1555,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                         float* e = my_tab + 4 * tr.i0;
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            if (tr.a[q] != 0.0f) atomicAdd(e + q, tr.a[q]);
+                            if (tr.a[q] != 0.0f) tf_add_comp(e + q, tf_lo, tr.a[q]);
                             tr.a[q] = tr.a[q + 4];
                             tr.a[q + 4] = 0.0f;
                         }
@@ -1513,12 +1564,12 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                         float* e = my_tab + 4 * (tr.i0 + 1);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            if (tr.a[q + 4] != 0.0f) atomicAdd(e + q, tr.a[q + 4]);
+                            if (tr.a[q + 4] != 0.0f) tf_add_comp(e + q, tf_lo, tr.a[q + 4]);
                             tr.a[q + 4] = tr.a[q];
                             tr.a[q] = 0.0f;
                         }
                     } else {
-                        tf_flush_f(tr, my_tab);
+                        tf_flush_f(tr, my_tab, tf_lo);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) tr.a[q] = 0.0f;
                     }
@@ -1572,7 +1623,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 ++nsamp;
                 if (P.ert_on && 1.0f - Tr > P.ert) break;
             }
-            tf_flush_f(tr, my_tab);
+            tf_flush_f(tr, my_tab, tf_lo);
             if (!FACE && dvol) cell_flush(cr, dvol, sy, sz);
         }
     }
@@ -1591,27 +1642,26 @@ __global__ void __launch_bounds__(256, 3) k_march_bwd(FrameParams P, const CamBa
     if (FACE && (it.brick < fg.k0 || it.brick >= fg.k1)) return;
     float4* s_tf = s_mem;
     float* s_g = (float*)(s_mem + P.ntf);
-    const int stride = 4 * P.ntf + 1;
+    const int stride = tf_copy_stride(P.ntf);
     for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
     for (int i = threadIdx.x; i < ncopy * stride; i += blockDim.x) s_g[i] = 0.0f;
     __syncthreads();
     float* my_tab = s_g + tf_copy(threadIdx.x, ncopy) * stride;
     unsigned long long nsamp = 0;
     if (item_ok(it, P))
-        nsamp = bwd_item<T, GL, FACE>(P, cams, bricks, scales, it, blockIdx.x, s_tf, my_tab, frag_rgba, frag_key,
-                                  frag_grad, dvol, gface, fg.base);
+        nsamp = bwd_item<T, GL, FACE>(P, cams, bricks, scales, it, blockIdx.x, threadIdx.x, s_tf, my_tab, frag_rgba,
+                                      frag_key, frag_grad, dvol, gface, fg.base);
     nsamp = warp_sum_u64(nsamp);
     if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) {
-        float v = 0.0f;
-        for (int c = 0; c < ncopy; ++c) v += s_g[c * stride + i];
-        if (v != 0.0f) atomicAdd(dtf + i, (double)v);
-    }
+    for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) tf_copies_to_global(s_g, ncopy, P.ntf, i, dtf);
 }
 
-// Persistent adjoint: items pulled in schedule order; each CTA's TF tables
-// are added to the global table once, after its last item.
+// Persistent adjoint: each warp pulls one warp's share of a work item (32
+// pixels of its tile) at a time, in schedule order; a warp whose rays are
+// short takes the next unit at once, with no barrier between units.  Each
+// CTA's TF tables are added to the global table once, after its warps have
+// run out of units.
 template <typename T, int GL, bool FACE>
 __global__ void __launch_bounds__(256, 3) k_march_bwd_persistent(FrameParams P, const CamBasis* cams,
                                                               const BrickDev* bricks, const float* scales,
@@ -1622,34 +1672,33 @@ __global__ void __launch_bounds__(256, 3) k_march_bwd_persistent(FrameParams P, 
                                                               float* dvol, float4* gface, FaceGroup fg,
                                                               Counters* counters) {
     extern __shared__ float4 s_mem[];
-    __shared__ int s_next;
     float4* s_tf = s_mem;
     float* s_g = (float*)(s_mem + P.ntf);
-    const int stride = 4 * P.ntf + 1;
+    const int stride = tf_copy_stride(P.ntf);
     for (int i = threadIdx.x; i < P.ntf; i += blockDim.x) s_tf[i] = tf[i];
     for (int i = threadIdx.x; i < ncopy * stride; i += blockDim.x) s_g[i] = 0.0f;
+    __syncthreads();
     float* my_tab = s_g + tf_copy(threadIdx.x, ncopy) * stride;
+    const int lane = threadIdx.x & 31;
+    const unsigned wpt = (unsigned)(P.tp >> 5);               // warps per tile
+    const unsigned n_units = (unsigned)n_items * wpt;
     unsigned long long nsamp = 0;
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_next = (int)atomicAdd(work, 1u);
-        __syncthreads();
-        const int i = s_next;
-        if (i >= n_items) break;
-        const int item = sched[i];
+        __syncwarp();
+        unsigned u = 0;
+        if (lane == 0) u = atomicAdd(work, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= n_units) break;
+        const int item = sched[u / wpt];
         const Item it = items[item];
         if (item_ok(it, P) && (!FACE || (it.brick >= fg.k0 && it.brick < fg.k1)))
-            nsamp += bwd_item<T, GL, FACE>(P, cams, bricks, scales, it, item, s_tf, my_tab, frag_rgba, frag_key,
-                                       frag_grad, dvol, gface, fg.base);
+            nsamp += bwd_item<T, GL, FACE>(P, cams, bricks, scales, it, item, (int)((u % wpt) * 32 + lane), s_tf,
+                                           my_tab, frag_rgba, frag_key, frag_grad, dvol, gface, fg.base);
     }
     nsamp = warp_sum_u64(nsamp);
-    if ((threadIdx.x & 31) == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
+    if (lane == 0 && nsamp) atomicAdd(&counters->samples_bwd, nsamp);
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) {
-        float v = 0.0f;
-        for (int c = 0; c < ncopy; ++c) v += s_g[c * stride + i];
-        if (v != 0.0f) atomicAdd(dtf + i, (double)v);
-    }
+    for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) tf_copies_to_global(s_g, ncopy, P.ntf, i, dtf);
 }
 
 template <typename T, int GL, bool FACE>
@@ -1658,7 +1707,7 @@ static void bwd_launch_f(const FrameParams& P, const CamBasis* cams, const Brick
                          const int* frag_key, const float4* frag_grad, double* dtf, float* dvol, float4* gface,
                          FaceGroup fg, Counters* counters, const Schedule* sch, cudaStream_t st) {
     int ncopy = bwd_tf_copies(P.ntf);
-    size_t smem = sizeof(float4) * P.ntf + sizeof(float) * (size_t)ncopy * (4 * P.ntf + 1);
+    size_t smem = sizeof(float4) * P.ntf + sizeof(float) * (size_t)ncopy * tf_copy_stride(P.ntf);
     if (sch) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_march_bwd_persistent<T, GL, FACE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -91,13 +91,13 @@ class NoAllocScene(C.Structure):
                 ("vmin", C.c_float), ("vmax", C.c_float)]
 
 
-STAGES = ["cull", "march", "composite", "composite_bwd", "march_bwd"]
+STAGES = ["cull", "march", "composite", "composite_bwd", "march_bwd", "face"]
 
 
 class Stats(C.Structure):
     _fields_ = [("samples_forward", C.c_uint64), ("samples_backward", C.c_uint64), ("work_items", C.c_uint64),
                 ("fragment_bytes", C.c_uint64), ("error_flags", C.c_uint32), ("max_fragments", C.c_uint32),
-                ("stage_ms", C.c_double * 5), ("stage_calls", C.c_uint32 * 5), ("kernel_launches", C.c_uint64),
+                ("stage_ms", C.c_double * 6), ("stage_calls", C.c_uint32 * 6), ("kernel_launches", C.c_uint64),
                 ("graph_launches", C.c_uint64), ("samples_shadow", C.c_uint64)]
 
 

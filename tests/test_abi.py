@@ -80,7 +80,7 @@ def test_struct_layouts_match_header():
     assert C.sizeof(dpv.BrickDesc) == 4 * 9 + 4 + 8 + 4 * 7 + 4
     assert C.sizeof(dpv.CameraDesc) == 40
     assert C.sizeof(dpv.FrameDesc) == 36
-    assert C.sizeof(dpv.Stats) == 40 + 8 * 5 + 4 * 5 + 4 + 8 + 8 + 8
+    assert C.sizeof(dpv.Stats) == 40 + 8 * 6 + 4 * 6 + 8 + 8 + 8
 
 
 def test_no_gpu_fails_loudly(lib):

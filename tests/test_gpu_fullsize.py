@@ -209,7 +209,7 @@ def test_large_adjoint_in_brick_groups(monkeypatch):
         m = float(np.abs(b).max())
         assert m > 0
         np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-5 * m)
-    np.testing.assert_allclose(tf_g, tf_s, rtol=1e-4, atol=1e-6 * float(np.abs(tf_s).max()))
+    np.testing.assert_allclose(tf_g, tf_s, rtol=0, atol=1e-9 * float(np.abs(tf_s).max()))
     dev.release()
 
 
@@ -323,6 +323,12 @@ def test_diff_full_size_gradient_kink_free(orc):
               "|gpu - ref| / kappa: median %.2f, 99th pct %.2f, max %.2f" % (
                   name, l2, rel.max(), big.sum(), over.sum(), np.median(ratio), np.percentile(ratio, 99),
                   ratio.max()))
+        for idx in np.argwhere(over)[:10]:
+            t = tuple(int(v) for v in idx)
+            print("  beyond: %s gpu %.6e ref %.6e rel %.2e |ref|/max %.2e kappa %.2e%s" % (
+                t, gpu[t], ref[t], abs(gpu[t] - ref[t]) / abs(ref[t]), abs(ref[t]) / m, kap[t],
+                "" if len(t) < 3 else " field %.4f; brick-face distance %s" % (
+                    f[t], [min(abs(c - b) for b in (127, 128, 129)) for c in t])))
         assert l2 <= 1e-4, (name, l2)
         assert not over.any(), (name, int(over.sum()), float(rel.max()))
     dev.release()

@@ -34,7 +34,7 @@ def _scene(domain, storage="f32", ert=0.0, ncam=2):
     vmin, vmax = domain
     w = vmax - vmin
     f = sc.field.astype(np.float64)
-    f = (f - f.min()) / (f.max() - f.min())
+    f = np.cbrt((f - f.min()) / (f.max() - f.min()))      # about 15 % of the nodes on each clamped side
     sc.field = (vmin - 0.5 * w + 2.0 * w * f).astype(np.float32)
     return sc
 
@@ -55,7 +55,7 @@ def _sides(sc, domain):
 @pytest.mark.parametrize("domain", DOMAINS)
 def test_forward_non_unit_domain(orc, domain, storage):
     sc = _scene(domain, storage=storage)
-    assert _sides(sc, domain).min() > 0.05
+    assert _sides(sc, domain).min() > 0.1
     dev = _device(sc, domain)
     dev.render()
     bricks = scenes.oracle_bricks(orc, sc)
