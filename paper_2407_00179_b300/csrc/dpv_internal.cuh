@@ -620,9 +620,26 @@ __device__ __forceinline__ TFSample tf_lookup_slope(const float4* tab, const Fra
     return r;
 }
 
+// Opacity 1 - exp(-x) of optical depth x.  For |x| < 1/16 (every sample at
+// the usual step and sigma_max: x = sigma_max a dt is about 0.008 at 512^3
+// and 0.002 at 2048^3) the Taylor series of 1 - exp(-x) to x^5, in Horner
+// form: the truncation is below x^6 / 720 (1.4e-9 relative at the edge of
+// the range, below one FP32 rounding), at a third of the instructions of
+// the library's expm1f, which takes the other samples.
+__device__ __forceinline__ float opacity(float x) {
+    if (fabsf(x) < 0.0625f) {
+        float q = fmaf(-x, 1.0f / 120.0f, 1.0f / 24.0f);
+        q = fmaf(-x, q, 1.0f / 6.0f);
+        q = fmaf(-x, q, 0.5f);
+        q = fmaf(-x, q, 1.0f);
+        return x * q;
+    }
+    return -expm1f(-x);
+}
+
 // Opacity of one sample: 1 - exp(-sigma_max * a * dt).
 __device__ __forceinline__ float sample_alpha(const FrameParams& P, float a) {
-    return -expm1f(-P.sigma_max * a * P.dt);
+    return opacity(P.sigma_max * a * P.dt);
 }
 
 // ---------------------------------------------------------------------------

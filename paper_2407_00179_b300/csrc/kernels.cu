@@ -1496,6 +1496,16 @@ __device__ __forceinline__ int tf_copy(int tid, int ncopy) {
     return ((tid & 7) + 2 * ((tid >> 3) & 3)) % ncopy;
 }
 
+// Face-buffer form of the field gradient: per sample (two vector
+// reductions each), or per run of samples in one cell (kFaceRuns).
+constexpr bool kFaceRuns = false;
+
+__device__ __forceinline__ void face_flush(CellRun& r, float4* gface, int qxy) {
+    if (r.base < 0) return;
+    atomicAdd(gface + r.base, make_float4(r.a[0], r.a[1], r.a[2], r.a[3]));
+    atomicAdd(gface + r.base + qxy, make_float4(r.a[4], r.a[5], r.a[6], r.a[7]));
+}
+
 // One work item of the adjoint: replay each thread's fragment and
 // accumulate its TF gradient into `my_tab` (a shared copy) and its voxel
 // gradient into the global field.  Returns the samples replayed.
@@ -1514,7 +1524,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
     tile_pixel(t, P.tw, lx, ly);
     int px = (it.tile % P.ntx) * P.tw + lx, py = (it.tile / P.ntx) * P.th + ly;
     long long slot = item * P.tp + t;
-    unsigned long long nsamp = 0;
+    unsigned nsamp = 0;
     const float gscale = Storage<T>::unit_scale ? 1.0f : scale;
     const long long sy = P.dims[0], sz = (long long)P.dims[0] * P.dims[1];
     const int tf_lo = 4 * P.ntf;          // low parts of the copy, after its high parts
@@ -1524,7 +1534,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
         float4 G = frag_grad[slot];
         if (brick_samples(P, cam, it.cam, b, px, py, m) && (G.x != 0.f || G.y != 0.f || G.z != 0.f || G.w != 0.f)) {
             float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.0f;
-            float Tend = 1.0f - F.w;
+            const float GwT = G.w * (1.0f - F.w);     // G_a (1 - A): the only use of G_a and A below
             int n = m.j1 - m.j0;
             TFRunF tr;
             CellRun cr;
@@ -1543,12 +1553,15 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 float ta = Tr * al;
                 float n0 = fmaf(ta, c.v.x, C0), n1 = fmaf(ta, c.v.y, C1), n2 = fmaf(ta, c.v.z, C2);
                 float om = 1.0f - al;
-                float inv1ma = om > 0.0f ? 1.0f / om : 0.0f;
+                // dL/dalpha times dalpha/dsigma = dt (1 - alpha), with (1 - alpha)
+                // multiplied into the bracket: no division by 1 - alpha
+                //   dL/dsigma = dt (sum_c G_c (T c_c (1 - alpha) - S_c) + G_a (1 - A))
                 float S0 = F.x - n0, S1 = F.y - n1, S2 = F.z - n2;
-                float gal = G.x * (Tr * c.v.x - S0 * inv1ma) + G.y * (Tr * c.v.y - S1 * inv1ma) +
-                            G.z * (Tr * c.v.z - S2 * inv1ma) + G.w * Tend * inv1ma;
+                float Tom = Tr * om;
+                float gal = G.x * fmaf(Tom, c.v.x, -S0) + G.y * fmaf(Tom, c.v.y, -S1) + G.z * fmaf(Tom, c.v.z, -S2) +
+                            GwT;
                 float g_r = G.x * ta, g_g = G.y * ta, g_b = G.z * ta;
-                float g_a = gal * P.sigma_max * P.dt * om;
+                float g_a = gal * (P.sigma_max * P.dt);
                 if (c.i0 != tr.i0) {
                     if (tr.i0 >= 0 && c.i0 == tr.i0 + 1) {
                         // the next segment shares entry i0 + 1: keep its sums
@@ -1586,7 +1599,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 tr.a[7] = fmaf(w1, g_a, tr.a[7]);
                 if ((FACE || dvol) && c.duds != 0.0f) {
                     float gs = (g_r * dsl.x + g_g * dsl.y + g_b * dsl.z + g_a * dsl.w) * c.duds * gscale;
-                    if (FACE && gs != 0.0f) {
+                    if (FACE && gs != 0.0f && !kFaceRuns) {
                         // straight into the face buffer, two vector reductions per
                         // sample: cheaper than a register run per cell, whose
                         // eight accumulators cost the loop registers
@@ -1596,6 +1609,28 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                         float gyz0 = gs * ay * az, gyz1 = gs * fy * az, gyz2 = gs * ay * fz, gyz3 = gs * fy * fz;
                         atomicAdd(gface + gb, make_float4(gyz0 * ax, gyz0 * fx, gyz1 * ax, gyz1 * fx));
                         atomicAdd(gface + gb + b.qxy, make_float4(gyz2 * ax, gyz2 * fx, gyz3 * ax, gyz3 * fx));
+                    } else if (FACE && gs != 0.0f) {
+                        // a run per cell: the eight corner sums stay in registers
+                        // while the ray stays in the cell, then go to the face
+                        // buffer as two vector reductions
+                        const long long gb =
+                            b.gface_off - gbase + (long long)iz * b.qxy + (long long)iy * b.qx + ix;
+                        if (gb != cr.base) {
+                            face_flush(cr, gface, b.qxy);
+                            cr.base = gb;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) cr.a[q] = 0.0f;
+                        }
+                        float ax = 1.0f - fx, ay = 1.0f - fy, az = 1.0f - fz;
+                        float gyz0 = gs * ay * az, gyz1 = gs * fy * az, gyz2 = gs * ay * fz, gyz3 = gs * fy * fz;
+                        cr.a[0] = fmaf(gyz0, ax, cr.a[0]);
+                        cr.a[1] = fmaf(gyz0, fx, cr.a[1]);
+                        cr.a[2] = fmaf(gyz1, ax, cr.a[2]);
+                        cr.a[3] = fmaf(gyz1, fx, cr.a[3]);
+                        cr.a[4] = fmaf(gyz2, ax, cr.a[4]);
+                        cr.a[5] = fmaf(gyz2, fx, cr.a[5]);
+                        cr.a[6] = fmaf(gyz3, ax, cr.a[6]);
+                        cr.a[7] = fmaf(gyz3, fx, cr.a[7]);
                     } else if (!FACE && gs != 0.0f) {
                         long long gb = gofs + (long long)iz * sz + (long long)iy * sy + ix;
                         if (gb != cr.base) {
@@ -1620,11 +1655,15 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 C1 = n1;
                 C2 = n2;
                 Tr = Tr * (1.0f - al);
-                ++nsamp;
-                if (P.ert_on && 1.0f - Tr > P.ert) break;
+                if (P.ert_on && 1.0f - Tr > P.ert) {
+                    n = k + 1;                          // the samples replayed
+                    break;
+                }
             }
+            nsamp = (unsigned)n;
             tf_flush_f(tr, my_tab, tf_lo);
             if (!FACE && dvol) cell_flush(cr, dvol, sy, sz);
+            if (FACE && kFaceRuns) face_flush(cr, gface, b.qxy);
         }
     }
     return nsamp;

@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256, shadow_min_ctas<GL>()) k_shadow_round(Fra
                     }
                     const float s = lerp_cell<T>(v, cx, cy, cz, scale);
                     const TFSample c = tf_lookup(s_tf, P, s);
-                    const float al = -expm1f(-P.sigma_max * c.v.w * P.shadow_dt);
+                    const float al = opacity(P.sigma_max * c.v.w * P.shadow_dt);
                     Tl = Tl * (1.0f - al);
                     ++nsamp;
                     if (!nown) break;
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(256, shadow_min_ctas<GL>()) k_shadow_round(Fra
             }
             const float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
             const TFSample c = tf_lookup(s_tf, P, s);
-            const float al = -expm1f(-P.sigma_max * c.v.w * P.shadow_dt);
+            const float al = opacity(P.sigma_max * c.v.w * P.shadow_dt);
             Tl = Tl * (1.0f - al);
             any = true;
             ++nsamp;

@@ -457,12 +457,15 @@ __global__ void __launch_bounds__(256) k_march_bwd_staged(FrameParams P, const C
         float ta = Tr * al;
         float n0 = fmaf(ta, c.v.x, C0), n1 = fmaf(ta, c.v.y, C1), n2 = fmaf(ta, c.v.z, C2);
         float om = 1.0f - al;
-        float inv1ma = om > 0.0f ? 1.0f / om : 0.0f;
+        // dL/dalpha times dalpha/dsigma = dt (1 - alpha), with (1 - alpha)
+        // multiplied into the bracket: no division by 1 - alpha
+        //   dL/dsigma = dt (sum_c G_c (T c_c (1 - alpha) - S_c) + G_a (1 - A))
         float S0 = F.x - n0, S1 = F.y - n1, S2 = F.z - n2;
-        float gal = G.x * (Tr * c.v.x - S0 * inv1ma) + G.y * (Tr * c.v.y - S1 * inv1ma) +
-                    G.z * (Tr * c.v.z - S2 * inv1ma) + G.w * Tend * inv1ma;
+        float Tom = Tr * om;
+        float gal = G.x * fmaf(Tom, c.v.x, -S0) + G.y * fmaf(Tom, c.v.y, -S1) + G.z * fmaf(Tom, c.v.z, -S2) +
+                    G.w * Tend;
         float g_r = G.x * ta, g_g = G.y * ta, g_b = G.z * ta;
-        float g_a = gal * P.sigma_max * P.dt * om;
+        float g_a = gal * (P.sigma_max * P.dt);
         if (c.i0 != tr.i0) {
             tf_flush(tr, s_g);
             tr.i0 = c.i0;
