@@ -410,8 +410,11 @@ dpv_status dpvMapOrder(dpv_device dev, int camera, const uint8_t** order, int* s
  * tried again until the bricks' sizes change). Where not all bricks fit at
  * once, they are replayed in groups of consecutive ranks, two launches per
  * group. Where not even one brick fits, the field gradient goes with scalar
- * atomics straight into dL_dvol. Environment (tests): DPV_FACE_GRAD=0 takes
- * the scalar atomics; DPV_FACE_GROUP=n puts at most n bricks in a group. */
+ * atomics straight into dL_dvol.  Where a brick's slots are far larger
+ * than L2 (over 8x), each thread sums the samples it takes in one cell in
+ * registers before reducing into the buffer.  Environment (tests):
+ * DPV_FACE_GRAD=0 takes the scalar atomics; DPV_FACE_GROUP=n puts at most n
+ * bricks in a group; DPV_FACE_RUNS=0/1 turns the per-cell sums off or on. */
 dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, float* dL_dvol);
 
 /* Counters (synchronises the device stream).  Tracing has no counterpart

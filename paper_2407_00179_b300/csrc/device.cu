@@ -1433,6 +1433,12 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
     }
     grp.push_back(dev->nranks);
     const int ngroups = (int)grp.size() - 1;
+    // cell runs before the face reductions where a brick's slots are far
+    // larger than L2 (the reductions then mostly go to DRAM)
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev->cuda_device);
+    int runs = max_brick * sizeof(float4) > 8 * (size_t)l2 ? 1 : 0;
+    if (const char* env = getenv("DPV_FACE_RUNS")) runs = atoi(env) != 0;
     if (faces && ngroups == 1) {
         cudaEvent_t tc = stage_start(dev);
         CK(cudaMemsetAsync(dev->d_gface, 0, dev->gface_slots * sizeof(float4), dev->stream), "zero face buffer");
@@ -1452,7 +1458,7 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
         // the replays are timed as DPV_STAGE_MARCH_BWD, the clears and
         // gathers of the face buffer as DPV_STAGE_FACE
         for (int g = 0; g < ngroups; ++g) {
-            const FaceGroup fg{grp[g], grp[g + 1], (long long)dev->gface_off_h[grp[g]]};
+            const FaceGroup fg{grp[g], grp[g + 1], (long long)dev->gface_off_h[grp[g]], runs};
             if (ngroups > 1) {
                 cudaEvent_t tc = stage_start(dev);
                 CK(cudaMemsetAsync(dev->d_gface, 0,

@@ -480,6 +480,38 @@ struct CellRaw<__nv_fp8_e4m3> {
     }
 };
 
+// Raw face vectors of one cell in the quad layout (lower face, upper face),
+// fetched one sample ahead and decoded at use.
+template <typename T>
+struct QuadRaw {
+    typename Quad<T>::W lo, hi;
+    __device__ __forceinline__ void fetch(const void* base, long long face, int qxy) {
+        const typename Quad<T>::W* q = reinterpret_cast<const typename Quad<T>::W*>(base) + face;
+        lo = __ldg(q);
+        hi = __ldg(q + qxy);
+    }
+    __device__ __forceinline__ void decode(float v[8]) const {
+        Quad<T>::unpack(lo, v[0], v[1], v[2], v[3]);
+        Quad<T>::unpack(hi, v[4], v[5], v[6], v[7]);
+    }
+};
+
+// The raw gather of the layouts that fetch one sample ahead.
+template <typename T, int GL>
+struct GatherRaw;
+template <typename T>
+struct GatherRaw<T, GATHER_CELL> {
+    CellRaw<T> r;
+    __device__ __forceinline__ void fetch(const void* base, long long cell, int) { r.fetch(base, cell); }
+    __device__ __forceinline__ void decode(float v[8]) const { r.decode(v); }
+};
+template <typename T>
+struct GatherRaw<T, GATHER_QUAD> {
+    QuadRaw<T> r;
+    __device__ __forceinline__ void fetch(const void* base, long long face, int qxy) { r.fetch(base, face, qxy); }
+    __device__ __forceinline__ void decode(float v[8]) const { r.decode(v); }
+};
+
 // The trilinear interpolant of eight decoded corners (the arithmetic of
 // trilinear(), in the same order).
 template <typename T>

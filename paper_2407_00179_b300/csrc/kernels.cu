@@ -420,22 +420,22 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
             wk.init(b);
             int mlast = -1;
             bool mempty = false;
-            if (GL == GATHER_CELL && !SKIP && n > 0) {
-                // the next sample's cell is fetched before this one's
-                // arithmetic, so its load overlaps the current sample's
-                // work; the interpolation is trilinear()'s, bit for bit
-                CellRaw<T> raw;
+            if ((GL == GATHER_CELL || GL == GATHER_QUAD) && !SKIP && n > 0) {
+                // the next sample's cell (or its two faces) is fetched before
+                // this one's arithmetic, so its load overlaps the current
+                // sample's work; the interpolation is trilinear()'s, bit for bit
+                GatherRaw<T, GL == GATHER_CELL ? GATHER_CELL : GATHER_QUAD> raw;
                 int ix, iy, iz;
                 float fx, fy, fz;
                 wk.at(m, 0, ix, iy, iz, fx, fy, fz);
-                raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy);
+                raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy, b.qxy);
                 for (; k < n; ++k) {
                     float v[8];
                     raw.decode(v);
                     const float cx = fx, cy = fy, cz = fz;
                     if (k + 1 < n) {
                         wk.at(m, k + 1, ix, iy, iz, fx, fy, fz);
-                        raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy);
+                        raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy, b.qxy);
                     }
                     ++nsamp;
                     float s = lerp_cell<T>(v, cx, cy, cz, scale);
@@ -1496,9 +1496,13 @@ __device__ __forceinline__ int tf_copy(int tid, int ncopy) {
     return ((tid & 7) + 2 * ((tid >> 3) & 3)) % ncopy;
 }
 
-// Face-buffer form of the field gradient: per sample (two vector
-// reductions each), or per run of samples in one cell (kFaceRuns).
-constexpr bool kFaceRuns = false;
+// Forms of the field gradient (template parameter FACE): 0 scalar atomics
+// into the field (cell runs of eight registers); 1 the face buffer, two
+// vector reductions per sample; 2 the face buffer, one pair of vector
+// reductions per run of samples in one cell.  Per sample is faster where
+// the reductions mostly hit L2 (bricks of 257^3: 1.7 % at 512^3); per run
+// where they go to DRAM (bricks of 513^3 at 2048^3: 11.6 % faster), since
+// a run halves them (about two samples per cell at half-voxel steps).
 
 __device__ __forceinline__ void face_flush(CellRun& r, float4* gface, int qxy) {
     if (r.base < 0) return;
@@ -1509,7 +1513,7 @@ __device__ __forceinline__ void face_flush(CellRun& r, float4* gface, int qxy) {
 // One work item of the adjoint: replay each thread's fragment and
 // accumulate its TF gradient into `my_tab` (a shared copy) and its voxel
 // gradient into the global field.  Returns the samples replayed.
-template <typename T, int GL, bool FACE>
+template <typename T, int GL, int FACE>
 __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, const CamBasis* cams,
                                                        const BrickDev* bricks, const float* scales, const Item& it,
                                                        long long item, int t, const float4* s_tf, float* my_tab,
@@ -1599,7 +1603,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 tr.a[7] = fmaf(w1, g_a, tr.a[7]);
                 if ((FACE || dvol) && c.duds != 0.0f) {
                     float gs = (g_r * dsl.x + g_g * dsl.y + g_b * dsl.z + g_a * dsl.w) * c.duds * gscale;
-                    if (FACE && gs != 0.0f && !kFaceRuns) {
+                    if (FACE == 1 && gs != 0.0f) {
                         // straight into the face buffer, two vector reductions per
                         // sample: cheaper than a register run per cell, whose
                         // eight accumulators cost the loop registers
@@ -1609,7 +1613,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                         float gyz0 = gs * ay * az, gyz1 = gs * fy * az, gyz2 = gs * ay * fz, gyz3 = gs * fy * fz;
                         atomicAdd(gface + gb, make_float4(gyz0 * ax, gyz0 * fx, gyz1 * ax, gyz1 * fx));
                         atomicAdd(gface + gb + b.qxy, make_float4(gyz2 * ax, gyz2 * fx, gyz3 * ax, gyz3 * fx));
-                    } else if (FACE && gs != 0.0f) {
+                    } else if (FACE == 2 && gs != 0.0f) {
                         // a run per cell: the eight corner sums stay in registers
                         // while the ray stays in the cell, then go to the face
                         // buffer as two vector reductions
@@ -1663,13 +1667,13 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
             nsamp = (unsigned)n;
             tf_flush_f(tr, my_tab, tf_lo);
             if (!FACE && dvol) cell_flush(cr, dvol, sy, sz);
-            if (FACE && kFaceRuns) face_flush(cr, gface, b.qxy);
+            if (FACE == 2) face_flush(cr, gface, b.qxy);
         }
     }
     return nsamp;
 }
 
-template <typename T, int GL, bool FACE>
+template <typename T, int GL, int FACE>
 __global__ void __launch_bounds__(256, 3) k_march_bwd(FrameParams P, const CamBasis* cams, const BrickDev* bricks,
                                                    const float* scales, const Item* items, const float4* tf,
                                                    const float4* frag_rgba, const int* frag_key,
@@ -1701,7 +1705,7 @@ __global__ void __launch_bounds__(256, 3) k_march_bwd(FrameParams P, const CamBa
 // short takes the next unit at once, with no barrier between units.  Each
 // CTA's TF tables are added to the global table once, after its warps have
 // run out of units.
-template <typename T, int GL, bool FACE>
+template <typename T, int GL, int FACE>
 __global__ void __launch_bounds__(256, 3) k_march_bwd_persistent(FrameParams P, const CamBasis* cams,
                                                               const BrickDev* bricks, const float* scales,
                                                               const Item* items, const int* sched, int n_items,
@@ -1740,7 +1744,7 @@ __global__ void __launch_bounds__(256, 3) k_march_bwd_persistent(FrameParams P, 
     for (int i = threadIdx.x; i < 4 * P.ntf; i += blockDim.x) tf_copies_to_global(s_g, ncopy, P.ntf, i, dtf);
 }
 
-template <typename T, int GL, bool FACE>
+template <typename T, int GL, int FACE>
 static void bwd_launch_f(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                          const Item* items, int n_items, const float4* tf, const float4* frag_rgba,
                          const int* frag_key, const float4* frag_grad, double* dtf, float* dvol, float4* gface,
@@ -1775,12 +1779,15 @@ static void bwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDe
                        const Item* items, int n_items, const float4* tf, const float4* frag_rgba, const int* frag_key,
                        const float4* frag_grad, double* dtf, float* dvol, float4* gface, FaceGroup fg,
                        Counters* counters, const Schedule* sch, cudaStream_t st) {
-    if (gface)
-        bwd_launch_f<T, GL, true>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf,
-                                  dvol, gface, fg, counters, sch, st);
+    if (gface && fg.runs)
+        bwd_launch_f<T, GL, 2>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol,
+                               gface, fg, counters, sch, st);
+    else if (gface)
+        bwd_launch_f<T, GL, 1>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol,
+                               gface, fg, counters, sch, st);
     else
-        bwd_launch_f<T, GL, false>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf,
-                                   dvol, gface, fg, counters, sch, st);
+        bwd_launch_f<T, GL, 0>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad, dtf, dvol,
+                               gface, fg, counters, sch, st);
 }
 
 cudaError_t launch_march_bwd(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
@@ -1789,7 +1796,7 @@ cudaError_t launch_march_bwd(int dtype, int gather, const FrameParams& P, const 
                              const float4* frag_grad, double* dtf, float* dvol, float4* gface,
                              Counters* counters, cudaStream_t st, const Schedule* sch, const FaceGroup* fgp) {
     if (n_items == 0) return cudaSuccess;
-    const FaceGroup fg = fgp ? *fgp : FaceGroup{0, P.nbricks, 0};
+    const FaceGroup fg = fgp ? *fgp : FaceGroup{0, P.nbricks, 0, 0};
 #define BWD(T)                                                                                                  \
     (gather == GATHER_CELL                                                                                          \
          ? bwd_launch<T, GATHER_CELL>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, frag_grad,   \
@@ -2129,7 +2136,7 @@ cudaError_t launch_face_gather(const BrickDev* bricks, int nbricks, const int* n
                                long long max_rows, const float4* gface, const int dims[3], float* dvol,
                                cudaStream_t st, const FaceGroup* fgp) {
     if (nbricks <= 0 || max_rows <= 0) return cudaSuccess;
-    const FaceGroup fg = fgp ? *fgp : FaceGroup{0, nbricks, 0};
+    const FaceGroup fg = fgp ? *fgp : FaceGroup{0, nbricks, 0, 0};
     long long groups = (max_rows + GR - 1) / GR;
     long long bx = groups < 4096 ? groups : 4096;
     dim3 grid((unsigned)bx, (unsigned)nbricks);

@@ -30,6 +30,7 @@ struct CommitArgs {
 struct FaceGroup {
     int k0, k1;
     long long base;
+    int runs;                // 1: the adjoint sums a cell run in registers before its reductions
 };
 
 struct Schedule {

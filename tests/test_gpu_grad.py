@@ -224,12 +224,15 @@ def test_autograd_volume_follows_the_tensor():
     ref.release()
 
 
+@pytest.mark.parametrize("runs", ["0", "1"])
 @pytest.mark.parametrize("split", ["regular", "kd"])
-def test_face_buffer_matches_scalar_atomics(monkeypatch, split):
+def test_face_buffer_matches_scalar_atomics(monkeypatch, split, runs):
     """The field gradient through the face adjoint buffer (vector atomics per
     cell face, then a gather over every brick storing a node) equals the one
     through scalar atomics into the field, up to atomic summation order; on
-    a regular and an uneven k-d partition, ghost copies included."""
+    a regular and an uneven k-d partition, ghost copies included; with the
+    reductions per sample and per run of samples in one cell."""
+    monkeypatch.setenv("DPV_FACE_RUNS", runs)
     dims = (40, 36, 32)
     cams = inputs.sphere_cameras(dims, 2, seed=4)
     kw = dict(splits=(2, 2, 2)) if split == "regular" else dict(kd=7)
