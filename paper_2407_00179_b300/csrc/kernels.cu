@@ -1620,10 +1620,29 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                         const long long gb =
                             b.gface_off - gbase + (long long)iz * b.qxy + (long long)iy * b.qx + ix;
                         if (gb != cr.base) {
-                            face_flush(cr, gface, b.qxy);
-                            cr.base = gb;
+                            if (cr.base >= 0 && gb == cr.base + b.qxy) {
+                                // one cell up in z: the old upper face is the new
+                                // lower face; only the old lower face leaves
+                                atomicAdd(gface + cr.base, make_float4(cr.a[0], cr.a[1], cr.a[2], cr.a[3]));
 #pragma unroll
-                            for (int q = 0; q < 8; ++q) cr.a[q] = 0.0f;
+                                for (int q = 0; q < 4; ++q) {
+                                    cr.a[q] = cr.a[q + 4];
+                                    cr.a[q + 4] = 0.0f;
+                                }
+                            } else if (cr.base >= 0 && gb == cr.base - b.qxy) {
+                                // one cell down in z: the old lower face is the new upper face
+                                atomicAdd(gface + cr.base + b.qxy, make_float4(cr.a[4], cr.a[5], cr.a[6], cr.a[7]));
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    cr.a[q + 4] = cr.a[q];
+                                    cr.a[q] = 0.0f;
+                                }
+                            } else {
+                                face_flush(cr, gface, b.qxy);
+#pragma unroll
+                                for (int q = 0; q < 8; ++q) cr.a[q] = 0.0f;
+                            }
+                            cr.base = gb;
                         }
                         float ax = 1.0f - fx, ay = 1.0f - fy, az = 1.0f - fz;
                         float gyz0 = gs * ay * az, gyz1 = gs * fy * az, gyz2 = gs * ay * fz, gyz3 = gs * fy * fz;
@@ -2057,7 +2076,6 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
     const int nx = bo.o_hi[0] - bo.o_lo[0], ny = bo.o_hi[1] - bo.o_lo[1], nz = bo.o_hi[2] - bo.o_lo[2];
     const int ngy = (ny + GR - 1) / GR;
     const int ngroups = ngy * nz;
-    const int lane = threadIdx.x & 31;
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
         const int yy0 = (grp % ngy) * GR, zz = grp / ngy;
         const int gy0 = bo.o_lo[1] + yy0, gz = bo.o_lo[2] + zz;
@@ -2069,31 +2087,21 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
             const bool act = xo < nx;
             const int gx = bo.o_lo[0] + xo, lx = gx - bo.s_lo[0];
             const bool xl = lx >= 1, xr = lx <= bo.s_n[0] - 2;
-            // face rows ly0 - 1 + k, k = 0 .. GR: this node's face and, from
-            // lane - 1 (the node at x - 1), the face to its left
+            // face rows ly0 - 1 + k, k = 0 .. GR: this node's face A and the
+            // face to its left L (loaded by this thread too: the left
+            // neighbour's load brings the line into L1, and no lane waits
+            // on a divergent reload at the warp's edge)
             float4 A[GR + 1];
             float Ly[GR + 1], Lw[GR + 1];
 #pragma unroll
             for (int k = 0; k <= GR; ++k) {
                 const int fy = ly0 - 1 + k;
-                const bool ok = own && act && xr && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
-                A[k] = ok ? gface[fo + (long long)fy * bo.qx + lx] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int k = 0; k <= GR; ++k) {
-                Ly[k] = __shfl_up_sync(0xffffffffu, A[k].y, 1);
-                Lw[k] = __shfl_up_sync(0xffffffffu, A[k].w, 1);
-            }
-            if (lane == 0 || xo == 0) {
-#pragma unroll
-                for (int k = 0; k <= GR; ++k) {
-                    const int fy = ly0 - 1 + k;
-                    const bool ok = own && act && xl && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
-                    const float4 q =
-                        ok ? gface[fo + (long long)fy * bo.qx + lx - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    Ly[k] = q.y;
-                    Lw[k] = q.w;
-                }
+                const bool row = own && act && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
+                const float4* f = gface + fo + (long long)fy * bo.qx + lx;
+                A[k] = row && xr ? f[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 q = row && xl ? f[-1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                Ly[k] = q.y;
+                Lw[k] = q.w;
             }
 #pragma unroll
             for (int k = 0; k < GR; ++k) {
