@@ -1504,10 +1504,23 @@ __device__ __forceinline__ int tf_copy(int tid, int ncopy) {
 // where they go to DRAM (bricks of 513^3 at 2048^3: 11.6 % faster), since
 // a run halves them (about two samples per cell at half-voxel steps).
 
+// The face buffer interleaves pairs of z layers: face (x, y, z) of a brick
+// is slot ((z / 2) qxy + y qx + x) 2 + z % 2, so the lower and upper faces
+// of a cell at even z share one 32-byte sector (one DRAM read-modify-write
+// instead of two where the reductions miss L2).  A brick's slot count is
+// even, so a slot's parity is its face's z parity.
+__device__ __forceinline__ long long face_slot(const BrickDev& b, int x, int y, int z) {
+    return ((long long)(z >> 1) * b.qxy + (long long)y * b.qx + x) * 2 + (z & 1);
+}
+// The upper face of the cell whose lower face is slot s.
+__device__ __forceinline__ long long face_above(long long s, int qxy) {
+    return (s & 1) ? s + 2 * (long long)qxy - 1 : s + 1;
+}
+
 __device__ __forceinline__ void face_flush(CellRun& r, float4* gface, int qxy) {
     if (r.base < 0) return;
     atomicAdd(gface + r.base, make_float4(r.a[0], r.a[1], r.a[2], r.a[3]));
-    atomicAdd(gface + r.base + qxy, make_float4(r.a[4], r.a[5], r.a[6], r.a[7]));
+    atomicAdd(gface + face_above(r.base, qxy), make_float4(r.a[4], r.a[5], r.a[6], r.a[7]));
 }
 
 // One work item of the adjoint: replay each thread's fragment and
@@ -1607,20 +1620,19 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                         // straight into the face buffer, two vector reductions per
                         // sample: cheaper than a register run per cell, whose
                         // eight accumulators cost the loop registers
-                        const long long gb =
-                            b.gface_off - gbase + (long long)iz * b.qxy + (long long)iy * b.qx + ix;
+                        const long long gb = b.gface_off - gbase + face_slot(b, ix, iy, iz);
                         float ax = 1.0f - fx, ay = 1.0f - fy, az = 1.0f - fz;
                         float gyz0 = gs * ay * az, gyz1 = gs * fy * az, gyz2 = gs * ay * fz, gyz3 = gs * fy * fz;
                         atomicAdd(gface + gb, make_float4(gyz0 * ax, gyz0 * fx, gyz1 * ax, gyz1 * fx));
-                        atomicAdd(gface + gb + b.qxy, make_float4(gyz2 * ax, gyz2 * fx, gyz3 * ax, gyz3 * fx));
+                        atomicAdd(gface + face_above(gb, b.qxy),
+                                  make_float4(gyz2 * ax, gyz2 * fx, gyz3 * ax, gyz3 * fx));
                     } else if (FACE == 2 && gs != 0.0f) {
                         // a run per cell: the eight corner sums stay in registers
                         // while the ray stays in the cell, then go to the face
                         // buffer as two vector reductions
-                        const long long gb =
-                            b.gface_off - gbase + (long long)iz * b.qxy + (long long)iy * b.qx + ix;
+                        const long long gb = b.gface_off - gbase + face_slot(b, ix, iy, iz);
                         if (gb != cr.base) {
-                            if (cr.base >= 0 && gb == cr.base + b.qxy) {
+                            if (cr.base >= 0 && gb == face_above(cr.base, b.qxy)) {
                                 // one cell up in z: the old upper face is the new
                                 // lower face; only the old lower face leaves
                                 atomicAdd(gface + cr.base, make_float4(cr.a[0], cr.a[1], cr.a[2], cr.a[3]));
@@ -1629,9 +1641,10 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                                     cr.a[q] = cr.a[q + 4];
                                     cr.a[q + 4] = 0.0f;
                                 }
-                            } else if (cr.base >= 0 && gb == cr.base - b.qxy) {
+                            } else if (cr.base >= 0 && face_above(gb, b.qxy) == cr.base) {
                                 // one cell down in z: the old lower face is the new upper face
-                                atomicAdd(gface + cr.base + b.qxy, make_float4(cr.a[4], cr.a[5], cr.a[6], cr.a[7]));
+                                atomicAdd(gface + face_above(cr.base, b.qxy),
+                                          make_float4(cr.a[4], cr.a[5], cr.a[6], cr.a[7]));
 #pragma unroll
                                 for (int q = 0; q < 4; ++q) {
                                     cr.a[q + 4] = cr.a[q];
@@ -2053,7 +2066,7 @@ cudaError_t launch_classify_empty(int dtype, const FrameParams& P, const BrickDe
 // is the sum of those slots over every brick storing a copy of it (its owner
 // and the bricks whose ghost layer holds it), added in neighbour-list order.
 
-size_t face_slots(const int s_n[3]) { return (size_t)(s_n[0] - 1) * (s_n[1] - 1) * s_n[2]; }
+size_t face_slots(const int s_n[3]) { return (size_t)(s_n[0] - 1) * (s_n[1] - 1) * (s_n[2] + (s_n[2] & 1)); }
 
 // Rows of nodes a thread gathers at once (face rows ly - 1 .. ly + GR - 1
 // are loaded together, each once, so their latencies overlap).
@@ -2076,11 +2089,14 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
     const int nx = bo.o_hi[0] - bo.o_lo[0], ny = bo.o_hi[1] - bo.o_lo[1], nz = bo.o_hi[2] - bo.o_lo[2];
     const int ngy = (ny + GR - 1) / GR;
     const int ngroups = ngy * nz;
+    // z fastest: the two layers that share the face buffer's sectors are
+    // read by neighbouring groups, close in time
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int yy0 = (grp % ngy) * GR, zz = grp / ngy;
+        const int yy0 = (grp / nz) * GR, zz = grp % nz;
         const int gy0 = bo.o_lo[1] + yy0, gz = bo.o_lo[2] + zz;
         const int ly0 = gy0 - bo.s_lo[1], lz = gz - bo.s_lo[2];
-        const long long fo = bo.gface_off - fg.base + (long long)lz * bo.qxy;   // read only if own
+        // slot of face (0, 0, lz): face (x, y, lz) is at fo + 2 (y qx + x)
+        const long long fo = bo.gface_off - fg.base + face_slot(bo, 0, 0, lz);   // read only if own
         // block-uniform trip count: the shuffles below need every lane
         for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
             const int xo = x0 + threadIdx.x;
@@ -2097,9 +2113,9 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
             for (int k = 0; k <= GR; ++k) {
                 const int fy = ly0 - 1 + k;
                 const bool row = own && act && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
-                const float4* f = gface + fo + (long long)fy * bo.qx + lx;
+                const float4* f = gface + fo + 2 * ((long long)fy * bo.qx + lx);
                 A[k] = row && xr ? f[0] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 q = row && xl ? f[-1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 q = row && xl ? f[-2] : make_float4(0.f, 0.f, 0.f, 0.f);
                 Ly[k] = q.y;
                 Lw[k] = q.w;
             }
@@ -2121,13 +2137,13 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
                         const BrickDev& b = bricks[nb[j]];
                         const int mx = gx - b.s_lo[0], my = gy - b.s_lo[1], mz = gz - b.s_lo[2];
                         if (mx < 0 || my < 0 || mz < 0 || mx >= b.s_n[0] || my >= b.s_n[1] || mz >= b.s_n[2]) continue;
-                        const float4* G = gface + (b.gface_off - fg.base) + (long long)mz * b.qxy;
+                        const float4* G = gface + (b.gface_off - fg.base) + face_slot(b, 0, 0, mz);
                         const bool bxl = mx >= 1, bxr = mx <= b.s_n[0] - 2, byl = my >= 1, byr = my <= b.s_n[1] - 2;
-                        const long long q0 = (long long)my * b.qx, q1 = q0 - b.qx;
-                        if (bxr && byr) v += G[q0 + mx].x;
-                        if (bxl && byr) v += G[q0 + mx - 1].y;
-                        if (bxr && byl) v += G[q1 + mx].z;
-                        if (bxl && byl) v += G[q1 + mx - 1].w;
+                        const long long q0 = 2 * ((long long)my * b.qx + mx), q1 = q0 - 2 * (long long)b.qx;
+                        if (bxr && byr) v += G[q0].x;
+                        if (bxl && byr) v += G[q0 - 2].y;
+                        if (bxr && byl) v += G[q1].z;
+                        if (bxl && byl) v += G[q1 - 2].w;
                     }
                 }
                 float* dst = dvol + ((long long)gz * dims1 + gy) * dims0 + gx;
