@@ -480,15 +480,59 @@ struct CellRaw<__nv_fp8_e4m3> {
     }
 };
 
+// The quad layout interleaves pairs of z layers: face (x, y, z) is vector
+// ((z / 2) qxy + y qx + x) 2 + z % 2, so a cell at even z finds its lower
+// and upper faces side by side (one aligned load of both, one sector);
+// at odd z they are its pair's second and the next pair's first face.
+__device__ __forceinline__ long long quad_slot(const BrickDev& b, int x, int y, int z) {
+    return ((long long)(z >> 1) * b.qxy + (long long)y * b.qx + x) * 2 + (z & 1);
+}
+
+// Both faces of a pair in one load.
+template <typename T>
+struct QuadPair;
+template <>
+struct QuadPair<float> {
+    static __device__ __forceinline__ void load(const float4* p, float4& lo, float4& hi) {
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+            : "l"(p));
+    }
+};
+template <typename H>
+struct QuadPair16 {
+    static __device__ __forceinline__ void load(const uint2* p, uint2& lo, uint2& hi) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
+        lo = make_uint2(w.x, w.y);
+        hi = make_uint2(w.z, w.w);
+    }
+};
+template <>
+struct QuadPair<__half> : QuadPair16<__half> {};
+template <>
+struct QuadPair<__nv_bfloat16> : QuadPair16<__nv_bfloat16> {};
+template <>
+struct QuadPair<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ void load(const unsigned* p, unsigned& lo, unsigned& hi) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
+        lo = w.x;
+        hi = w.y;
+    }
+};
+
 // Raw face vectors of one cell in the quad layout (lower face, upper face),
 // fetched one sample ahead and decoded at use.
 template <typename T>
 struct QuadRaw {
     typename Quad<T>::W lo, hi;
-    __device__ __forceinline__ void fetch(const void* base, long long face, int qxy) {
-        const typename Quad<T>::W* q = reinterpret_cast<const typename Quad<T>::W*>(base) + face;
-        lo = __ldg(q);
-        hi = __ldg(q + qxy);
+    __device__ __forceinline__ void fetch(const BrickDev& b, int x, int y, int z) {
+        const typename Quad<T>::W* q = reinterpret_cast<const typename Quad<T>::W*>(b.gather) + quad_slot(b, x, y, z);
+        if (!(z & 1)) {
+            QuadPair<T>::load(q, lo, hi);
+        } else {
+            lo = __ldg(q);
+            hi = __ldg(q + 2 * (long long)b.qxy - 1);
+        }
     }
     __device__ __forceinline__ void decode(float v[8]) const {
         Quad<T>::unpack(lo, v[0], v[1], v[2], v[3]);
@@ -502,13 +546,15 @@ struct GatherRaw;
 template <typename T>
 struct GatherRaw<T, GATHER_CELL> {
     CellRaw<T> r;
-    __device__ __forceinline__ void fetch(const void* base, long long cell, int) { r.fetch(base, cell); }
+    __device__ __forceinline__ void fetch(const BrickDev& b, int x, int y, int z) {
+        r.fetch(b.gather, (long long)x + (long long)y * b.qx + (long long)z * b.qxy);
+    }
     __device__ __forceinline__ void decode(float v[8]) const { r.decode(v); }
 };
 template <typename T>
 struct GatherRaw<T, GATHER_QUAD> {
     QuadRaw<T> r;
-    __device__ __forceinline__ void fetch(const void* base, long long face, int qxy) { r.fetch(base, face, qxy); }
+    __device__ __forceinline__ void fetch(const BrickDev& b, int x, int y, int z) { r.fetch(b, x, y, z); }
     __device__ __forceinline__ void decode(float v[8]) const { r.decode(v); }
 };
 
@@ -540,7 +586,7 @@ struct CornerCache {
                                          float& d, float& e) const {
         if (G == GATHER_QUAD) {
             using W = typename Quad<T>::W;
-            const W* q = reinterpret_cast<const W*>(b.gather) + (x + y * b.qx + z * b.qxy);
+            const W* q = reinterpret_cast<const W*>(b.gather) + quad_slot(b, x, y, z);
             Quad<T>::unpack(__ldg(q), a, c, d, e);
         } else {
             const T* p = data + (x + y * b.sx + z * b.sxy);

@@ -428,14 +428,14 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                 int ix, iy, iz;
                 float fx, fy, fz;
                 wk.at(m, 0, ix, iy, iz, fx, fy, fz);
-                raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy, b.qxy);
+                raw.fetch(b, ix, iy, iz);
                 for (; k < n; ++k) {
                     float v[8];
                     raw.decode(v);
                     const float cx = fx, cy = fy, cz = fz;
                     if (k + 1 < n) {
                         wk.at(m, k + 1, ix, iy, iz, fx, fy, fz);
-                        raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy, b.qxy);
+                        raw.fetch(b, ix, iy, iz);
                     }
                     ++nsamp;
                     float s = lerp_cell<T>(v, cx, cy, cz, scale);
@@ -1860,6 +1860,8 @@ __global__ void k_build_quad(const T* src, int sx, int sy, int sz, typename Quad
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         long long z = i / qxy, r = i - z * qxy, y = r / qx, x = r - y * qx;
         long long o = (z * sy + y) * sx + x;
+        // interleaved pairs of z layers (quad_slot)
+        const long long slot = ((z >> 1) * qxy + r) * 2 + (z & 1);
         W w;
         if constexpr (sizeof(T) == 4) {
             const float* f = (const float*)src;
@@ -1871,12 +1873,12 @@ __global__ void k_build_quad(const T* src, int sx, int sy, int sz, typename Quad
             const unsigned char* c = (const unsigned char*)src;
             w = (unsigned)c[o] | ((unsigned)c[o + 1] << 8) | ((unsigned)c[o + sx] << 16) | ((unsigned)c[o + sx + 1] << 24);
         }
-        dst[i] = w;
+        dst[slot] = w;
     }
 }
 
 size_t quad_bytes(int dtype, const int s_n[3]) {
-    size_t cells = (size_t)(s_n[0] - 1) * (s_n[1] - 1) * s_n[2];
+    size_t cells = (size_t)(s_n[0] - 1) * (s_n[1] - 1) * (s_n[2] + (s_n[2] & 1));   // z padded to pairs
     static const size_t w[4] = {16, 8, 8, 4};
     return cells * w[dtype];
 }
