@@ -1559,11 +1559,39 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
             CornerCache<T, GL> cc;
             SampleWalker wk;
             wk.init(b);
+            // narrow quad layouts fetch the next sample's faces one sample
+            // ahead (their raw vectors take four registers); the
+            // interpolation is trilinear()'s, bit for bit
+            constexpr bool ahead = GL == GATHER_QUAD && sizeof(T) <= 2;
+            GatherRaw<T, GATHER_QUAD> raw;
+            int nix = 0, niy = 0, niz = 0;
+            float nfx = 0.f, nfy = 0.f, nfz = 0.f;
+            if (ahead && n > 0) {
+                wk.at(m, 0, nix, niy, niz, nfx, nfy, nfz);
+                raw.fetch(b, nix, niy, niz);
+            }
             for (int k = 0; k < n; ++k) {
                 int ix, iy, iz;
                 float fx, fy, fz;
-                wk.at(m, k, ix, iy, iz, fx, fy, fz);
-                float s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
+                float s;
+                if (ahead) {
+                    ix = nix;
+                    iy = niy;
+                    iz = niz;
+                    fx = nfx;
+                    fy = nfy;
+                    fz = nfz;
+                    float v[8];
+                    raw.decode(v);
+                    if (k + 1 < n) {
+                        wk.at(m, k + 1, nix, niy, niz, nfx, nfy, nfz);
+                        raw.fetch(b, nix, niy, niz);
+                    }
+                    s = lerp_cell<T>(v, fx, fy, fz, scale);
+                } else {
+                    wk.at(m, k, ix, iy, iz, fx, fy, fz);
+                    s = trilinear<T, GL>(b, data, scale, cc, ix, iy, iz, fx, fy, fz);
+                }
                 float4 dsl;
                 TFSample c = tf_lookup_slope(s_tf, P, s, dsl);
                 float al = sample_alpha(P, c.v.w);
