@@ -484,8 +484,14 @@ struct CellRaw<__nv_fp8_e4m3> {
 // ((z / 2) qxy + y qx + x) 2 + z % 2, so a cell at even z finds its lower
 // and upper faces side by side (one aligned load of both, one sector);
 // at odd z they are its pair's second and the next pair's first face.
-__device__ __forceinline__ long long quad_slot(const BrickDev& b, int x, int y, int z) {
-    return ((long long)(z >> 1) * b.qxy + (long long)y * b.qx + x) * 2 + (z & 1);
+// (32-bit arithmetic: a brick holds under 2^31 nodes, so under 2^32 slots.)
+__device__ __forceinline__ unsigned quad_slot(const BrickDev& b, int x, int y, int z) {
+    return ((unsigned)(z >> 1) * (unsigned)b.qxy + (unsigned)y * (unsigned)b.qx + (unsigned)x) * 2u + (unsigned)(z & 1);
+}
+
+// Cell index of the cell layout (under 2^31 cells per brick).
+__device__ __forceinline__ unsigned cell_slot(const BrickDev& b, int x, int y, int z) {
+    return (unsigned)z * (unsigned)b.qxy + (unsigned)y * (unsigned)b.qx + (unsigned)x;
 }
 
 // Both faces of a pair in one load.
@@ -531,7 +537,7 @@ struct QuadRaw {
             QuadPair<T>::load(q, lo, hi);
         } else {
             lo = __ldg(q);
-            hi = __ldg(q + 2 * (long long)b.qxy - 1);
+            hi = __ldg(q + (2u * (unsigned)b.qxy - 1u));
         }
     }
     __device__ __forceinline__ void decode(float v[8]) const {
@@ -546,9 +552,7 @@ struct GatherRaw;
 template <typename T>
 struct GatherRaw<T, GATHER_CELL> {
     CellRaw<T> r;
-    __device__ __forceinline__ void fetch(const BrickDev& b, int x, int y, int z) {
-        r.fetch(b.gather, (long long)x + (long long)y * b.qx + (long long)z * b.qxy);
-    }
+    __device__ __forceinline__ void fetch(const BrickDev& b, int x, int y, int z) { r.fetch(b.gather, cell_slot(b, x, y, z)); }
     __device__ __forceinline__ void decode(float v[8]) const { r.decode(v); }
 };
 template <typename T>
@@ -632,7 +636,7 @@ template <typename T, int G>
 __device__ __forceinline__ float trilinear(const BrickDev& b, const T* data, float scale, CornerCache<T, G>& cc,
                                            int ix, int iy, int iz, float fx, float fy, float fz) {
     if (G == GATHER_CELL) {
-        Cell<T>::load(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy, cc.v);
+        Cell<T>::load(b.gather, cell_slot(b, ix, iy, iz), cc.v);
     } else if (G == GATHER_QUAD) {
         // two vector loads: cheaper than the cache's divergent reuse tests
         cc.face(b, data, ix, iy, iz, cc.v[0], cc.v[1], cc.v[2], cc.v[3]);

@@ -437,7 +437,6 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                         wk.at(m, k + 1, ix, iy, iz, fx, fy, fz);
                         raw.fetch(b, ix, iy, iz);
                     }
-                    ++nsamp;
                     float s = lerp_cell<T>(v, cx, cy, cz, scale);
                     TFSample c = tf_lookup(s_tf, P, s);
                     float al = sample_alpha(P, c.v.w);
@@ -446,8 +445,12 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                     C1 = fmaf(ta, c.v.y, C1);
                     C2 = fmaf(ta, c.v.z, C2);
                     Tr = Tr * (1.0f - al);
-                    if (P.ert_on && 1.0f - Tr > P.ert) break;
+                    if (P.ert_on && 1.0f - Tr > P.ert) {
+                        ++k;
+                        break;
+                    }
                 }
+                nsamp += (unsigned)k;        // the samples evaluated
                 n = 0;
             }
             for (; k < n; ++k) {
@@ -767,14 +770,14 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
         int ix, iy, iz;
         float fx, fy, fz;
         wk.at(m, 0, ix, iy, iz, fx, fy, fz);
-        raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy);
+        raw.fetch(b.gather, cell_slot(b, ix, iy, iz));
         for (int k = 0; k < n; ++k) {
             float v[8];
             raw.decode(v);
             const float cx = fx, cy = fy, cz = fz;
             if (k + 1 < n) {
                 wk.at(m, k + 1, ix, iy, iz, fx, fy, fz);
-                raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy);
+                raw.fetch(b.gather, cell_slot(b, ix, iy, iz));
             }
             float s = lerp_cell<T>(v, cx, cy, cz, scale);
             TFSample c = tf_lookup(s_tf, P, s);

@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256, shadow_min_ctas<GL>()) k_shadow_round(Fra
                     fy = qy - (float)iy;
                     fz = qz - (float)iz;
                 }
-                raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy);
+                raw.fetch(b.gather, cell_slot(b, ix, iy, iz));
                 for (;;) {
                     float v[8];
                     raw.decode(v);
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256, shadow_min_ctas<GL>()) k_shadow_round(Fra
                             fx = qx - (float)ix;
                             fy = qy - (float)iy;
                             fz = qz - (float)iz;
-                            raw.fetch(b.gather, (long long)ix + (long long)iy * b.qx + (long long)iz * b.qxy);
+                            raw.fetch(b.gather, cell_slot(b, ix, iy, iz));
                         }
                     }
                     const float s = lerp_cell<T>(v, cx, cy, cz, scale);
