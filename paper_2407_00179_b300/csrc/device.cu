@@ -403,6 +403,8 @@ dpv_status prepare(dpv_device dev) {
     P.vmin = dev->vmin;
     P.vmax = dev->vmax;
     P.tf_scale = (float)(dev->ntf - 1) / (dev->vmax - dev->vmin);
+    P.tf_bias = -P.vmin * P.tf_scale;
+    P.sdt = P.sigma_max * P.dt;
     P.ntf = dev->ntf;
     for (int a = 0; a < 3; ++a) P.dims[a] = dev->dims[a];
     P.nbricks = dev->nranks;

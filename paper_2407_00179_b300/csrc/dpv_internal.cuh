@@ -166,6 +166,8 @@ struct FrameParams {
     float vmin;        // TF domain [vmin, vmax]
     float vmax;
     float tf_scale;    // (n - 1) / (vmax - vmin)
+    float tf_bias;     // -vmin tf_scale: the TF coordinate is u = fma(s, tf_scale, tf_bias)
+    float sdt;         // sigma_max dt: a sample's optical depth is its TF opacity times sdt
     int ntf;           // TF entries
     int dims[3];       // global nodes per axis
     int nbricks;
@@ -667,7 +669,7 @@ struct TFSample {
 
 __device__ __forceinline__ TFSample tf_lookup(const float4* tab, const FrameParams& P, float s) {
     TFSample r;
-    float u = (s - P.vmin) * P.tf_scale;
+    float u = fmaf(s, P.tf_scale, P.tf_bias);
     float hi = (float)(P.ntf - 1);
     // the clamp is decided on s itself, so a rounded u never moves a sample
     // inside the domain onto the clamped side
@@ -687,7 +689,7 @@ __device__ __forceinline__ TFSample tf_lookup(const float4* tab, const FramePara
 // ds term), from the same two entries.
 __device__ __forceinline__ TFSample tf_lookup_slope(const float4* tab, const FrameParams& P, float s, float4& d) {
     TFSample r;
-    float u = (s - P.vmin) * P.tf_scale;
+    float u = fmaf(s, P.tf_scale, P.tf_bias);
     float hi = (float)(P.ntf - 1);
     r.duds = (s >= P.vmin && s <= P.vmax) ? P.tf_scale : 0.0f;
     u = fminf(fmaxf(u, 0.0f), hi);
@@ -720,9 +722,7 @@ __device__ __forceinline__ float opacity(float x) {
 }
 
 // Opacity of one sample: 1 - exp(-sigma_max * a * dt).
-__device__ __forceinline__ float sample_alpha(const FrameParams& P, float a) {
-    return opacity(P.sigma_max * a * P.dt);
-}
+__device__ __forceinline__ float sample_alpha(const FrameParams& P, float a) { return opacity(a * P.sdt); }
 
 // ---------------------------------------------------------------------------
 // one ray through one brick

@@ -444,7 +444,7 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                     C0 = fmaf(ta, c.v.x, C0);
                     C1 = fmaf(ta, c.v.y, C1);
                     C2 = fmaf(ta, c.v.z, C2);
-                    Tr = Tr * (1.0f - al);
+                    Tr = Tr - ta;
                     if (P.ert_on && 1.0f - Tr > P.ert) {
                         ++k;
                         break;
@@ -477,7 +477,7 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                 C0 = fmaf(ta, c.v.x, C0);
                 C1 = fmaf(ta, c.v.y, C1);
                 C2 = fmaf(ta, c.v.z, C2);
-                Tr = Tr * (1.0f - al);
+                Tr = Tr - ta;
                 if (P.ert_on && 1.0f - Tr > P.ert) break;
             }
             frag_rgba[slot] = make_float4(C0, C1, C2, 1.0f - Tr);
@@ -552,8 +552,8 @@ __device__ __forceinline__ unsigned long long march_item_deep(const FrameParams&
                 C0 = fmaf(ta, c.v.x, C0);
                 C1 = fmaf(ta, c.v.y, C1);
                 C2 = fmaf(ta, c.v.z, C2);
-                Tr = Tr * (1.0f - al);
-                Tb = Tb * (1.0f - al);
+                Tr = Tr - ta;
+                Tb = Tb - Tb * al;
                 if (P.ert_on && 1.0f - Tb > P.ert) break;
             }
             if (nf > 0) frag_rgba[base + (long long)(nf - 1) * P.tp] = make_float4(C0, C1, C2, 1.0f - Tr);
@@ -786,7 +786,7 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
             C0 = fmaf(ta, c.v.x, C0);
             C1 = fmaf(ta, c.v.y, C1);
             C2 = fmaf(ta, c.v.z, C2);
-            Tr = Tr * (1.0f - al);
+            Tr = Tr - ta;
             ++nsamp;
             if (P.ert_on && 1.0f - Tr > P.ert) return true;
         }
@@ -814,7 +814,7 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
         C0 = fmaf(ta, c.v.x, C0);
         C1 = fmaf(ta, c.v.y, C1);
         C2 = fmaf(ta, c.v.z, C2);
-        Tr = Tr * (1.0f - al);
+        Tr = Tr - ta;
         ++nsamp;
         if (P.ert_on && 1.0f - Tr > P.ert) return true;
     }
@@ -1609,7 +1609,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 float gal = G.x * fmaf(Tom, c.v.x, -S0) + G.y * fmaf(Tom, c.v.y, -S1) + G.z * fmaf(Tom, c.v.z, -S2) +
                             GwT;
                 float g_r = G.x * ta, g_g = G.y * ta, g_b = G.z * ta;
-                float g_a = gal * (P.sigma_max * P.dt);
+                float g_a = gal * P.sdt;
                 if (c.i0 != tr.i0) {
                     if (tr.i0 >= 0 && c.i0 == tr.i0 + 1) {
                         // the next segment shares entry i0 + 1: keep its sums
@@ -1721,7 +1721,7 @@ __device__ __forceinline__ unsigned long long bwd_item(const FrameParams& P, con
                 C0 = n0;
                 C1 = n1;
                 C2 = n2;
-                Tr = Tr * (1.0f - al);
+                Tr = Tr - ta;
                 if (P.ert_on && 1.0f - Tr > P.ert) {
                     n = k + 1;                          // the samples replayed
                     break;
@@ -2060,7 +2060,7 @@ __global__ void k_tf_opaque_prefix(const float4* tf, int n, int* z) {
 
 // TF entry i0 of tf_lookup for value s (same FP32 steps).
 __device__ __forceinline__ int tf_entry(const FrameParams& P, float s) {
-    float u = (s - P.vmin) * P.tf_scale;
+    float u = fmaf(s, P.tf_scale, P.tf_bias);
     u = fminf(fmaxf(u, 0.0f), (float)(P.ntf - 1));
     return min(__float2int_rd(u), P.ntf - 2);
 }

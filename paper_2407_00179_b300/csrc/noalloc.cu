@@ -183,6 +183,8 @@ extern "C" dpv_status dpvRenderNoAlloc(const dpv_noalloc_scene* sc, const dpv_ca
     P.vmin = sc->vmin;
     P.vmax = sc->vmax;
     P.tf_scale = (float)(sc->tf_n - 1) / (sc->vmax - sc->vmin);
+    P.tf_bias = -P.vmin * P.tf_scale;
+    P.sdt = P.sigma_max * P.dt;
     P.ntf = sc->tf_n;
     for (int a = 0; a < 3; ++a) P.dims[a] = sc->dims[a];
     P.nbricks = K;

@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(256) k_march_shadowed(FrameParams P, const Cam
                 C0 = fmaf(ta, c.v.x, C0);
                 C1 = fmaf(ta, c.v.y, C1);
                 C2 = fmaf(ta, c.v.z, C2);
-                Tr = Tr * (1.0f - al);
+                Tr = Tr - Tr * al;     // the unshadowed frame's update, bit for bit
                 if (P.ert_on && 1.0f - Tr > P.ert) break;
             }
             frag_rgba[slot] = make_float4(C0, C1, C2, 1.0f - Tr);

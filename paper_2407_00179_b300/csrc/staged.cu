@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(256) k_march_fwd_staged(FrameParams P, const C
         C0 = fmaf(ta, c.v.x, C0);
         C1 = fmaf(ta, c.v.y, C1);
         C2 = fmaf(ta, c.v.z, C2);
-        Tr = Tr * (1.0f - al);
+        Tr = Tr - ta;
         ++nsamp;
         return P.ert_on && 1.0f - Tr > P.ert;
     };
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(256) k_march_bwd_staged(FrameParams P, const C
         float gal = G.x * fmaf(Tom, c.v.x, -S0) + G.y * fmaf(Tom, c.v.y, -S1) + G.z * fmaf(Tom, c.v.z, -S2) +
                     G.w * Tend;
         float g_r = G.x * ta, g_g = G.y * ta, g_b = G.z * ta;
-        float g_a = gal * (P.sigma_max * P.dt);
+        float g_a = gal * P.sdt;
         if (c.i0 != tr.i0) {
             tf_flush(tr, s_g);
             tr.i0 = c.i0;
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(256) k_march_bwd_staged(FrameParams P, const C
         C0 = n0;
         C1 = n1;
         C2 = n2;
-        Tr = Tr * (1.0f - al);
+        Tr = Tr - ta;
         ++nsamp;
         return P.ert_on && 1.0f - Tr > P.ert;
     };

@@ -96,15 +96,15 @@ def o_full(orc, sc: Scene, cam, field=None, **kw):
 
 def grad_checks(gpu, ref, what, kappa=None, amb=None):
     """Gradient bar: relative L2 <= 1e-4, and on entries above 1e-3 of
-    the largest, |gpu - ref| <= 1e-3 |ref| + 3 kappa + amb.
+    the largest, |gpu - ref| <= 1e-3 |ref| + 2 kappa + amb.
 
     kappa is how much the FP64 oracle's own answer moves when the eye is
     perturbed by 1e-7 relative (about one FP32 rounding of the ray
     geometry).  Entries that are sums of large cancelling terms are only
     determined to that level once the geometry is rounded to FP32, whatever
-    the arithmetic after it; the FP32 path rounds the geometry in three
-    independent places (eye in node coordinates, ray direction, per-brick
-    sample anchor), hence 3 kappa.
+    the arithmetic after it.  Measured over every gradient test: at most 3
+    entries of a test need the allowance at all, and the largest needs
+    1.01 kappa beyond 1e-3 |ref| + amb; 2 kappa keeps a margin of two.
 
     amb is the oracle's knot ambiguity of a field gradient: where a sample
     lies within rounding of a TF knot whose slope changes, either one-sided
@@ -118,7 +118,7 @@ def grad_checks(gpu, ref, what, kappa=None, amb=None):
     a = np.zeros_like(ref) if amb is None else amb
     l2 = np.linalg.norm(np.maximum(err - a, 0.0)) / np.linalg.norm(ref)
     k = np.zeros_like(ref) if kappa is None else kappa
-    bound = 1e-3 * np.abs(ref) + 3.0 * k + a
+    bound = 1e-3 * np.abs(ref) + 2.0 * k + a
     viol = big & (err > bound)
     # entries that need the kappa allowance: beyond 1e-3 |ref| + amb, within
     # the full bound; and the distribution of |gpu - ref| / kappa over them
@@ -131,7 +131,7 @@ def grad_checks(gpu, ref, what, kappa=None, amb=None):
     else:
         print("%s: no entry uses the kappa allowance" % what)
     w = np.argsort(rel)[-3:]
-    print("%s: max rel %.2e (over %d entries), rel L2 %.2e (raw %.2e), %d beyond 1e-3|ref| + 3 kappa + amb "
+    print("%s: max rel %.2e (over %d entries), rel L2 %.2e (raw %.2e), %d beyond 1e-3|ref| + 2 kappa + amb "
           "(%d entries with amb > 0); worst: %s" % (
               what, rel.max(), big.sum(), l2, np.linalg.norm(gpu - ref) / np.linalg.norm(ref), viol.sum(),
               int((a > 0).sum()),
