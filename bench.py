@@ -50,10 +50,35 @@ BYTES_PER_VOXEL = {"f32": 4, "f16": 2, "bf16": 2, "fp8": 1}
 # capture, the capture is of a smaller case of the same kernel (same storage
 # and gather layout), and the bytes per evaluated sample scale to the full
 # launch by its sample count.
-TRAFFIC = {}
+TRAFFIC = {
+    # one-pass captures (time, DRAM read, DRAM write) of the bench's own
+    # timed steps at full size: 3 steps, 4.7465e10 samples each
+    "large_bf16_fwd": {"bytes_per_sample": 12.834, "l1_hit": None, "l2_hit": None,
+                       "capture": "profiles/bench_large_bf16_launch_list.md",
+                       "case": "2048^3 bf16, 64 bricks, 8 x 3840x2160, quad layout, persistent, 8x32 tiles "
+                               "(the bench's timed steps)",
+                       "source": "d19eea9ba3c9f227"},
+    "large_bf16_bwd": {"bytes_per_sample": 54.823, "l1_hit": None, "l2_hit": None,
+                       "capture": "profiles/bench_large_bf16_launch_list.md",
+                       "case": "2048^3 bf16, the same steps; two replay launches per step (face-buffer groups)",
+                       "source": "d19eea9ba3c9f227"},
+    # mid: the bench's timed steps (3 steps, 3.7027e8 samples each)
+    "mid_fwd": {"bytes_per_sample": 14.203, "l1_hit": None, "l2_hit": None,
+                "capture": "profiles/bench_mid_launch_list.md",
+                "case": "512^3 f32, 8 bricks, 1920x1080, cell layout, persistent, 64x4 tiles (the bench's timed steps)",
+                "source": "d19eea9ba3c9f227"},
+    "mid_bwd": {"bytes_per_sample": 30.281, "l1_hit": None, "l2_hit": None,
+                "capture": "profiles/bench_mid_launch_list.md",
+                "case": "512^3 f32, the same steps", "source": "d19eea9ba3c9f227"},
+}
 
 # the capture whose per-sample traffic stands for each (workload, kernel)
-TRAFFIC_FOR = {}
+TRAFFIC_FOR = {
+    ("large_bf16", "march"): "large_bf16_fwd",
+    ("large_bf16", "march_bwd"): "large_bf16_bwd",
+    ("mid", "march"): "mid_fwd",
+    ("mid", "march_bwd"): "mid_bwd",
+}
 
 # FP32 arithmetic per sample counted in the source (an FMA counts once):
 # forward: position 6, trilinear 14, TF lookup 15, opacity 11, emission-
@@ -86,6 +111,11 @@ CONFIGS = {
                    storage="f32", cams="direction", shadow=((-0.4, 0.8, 0.45), 1.0, 0.25), tf_cut=0.05),
     "mid_f16": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=1, width=1920, height=1080, ert=0.99,
                     storage="f16", cams="direction"),
+    # the 2048^3 workload's kernels on a case small enough for a full ncu
+    # capture: 512^3 bf16 (a 2 GB quad layout), 2x2x2 bricks, 2 orbit cameras
+    # at 1920x1080, no early termination
+    "mid_bf16": dict(dims=(512, 512, 512), field="mid", splits=(2, 2, 2), ncam=2, width=1920, height=1080, ert=0.0,
+                     storage="bf16", cams="orbit", compare_f32=False),
     # 64^3 f32, 8 blobs, 2x1x1 bricks, 256x256, no ERT
     "small": dict(dims=(64, 64, 64), field="small", splits=(2, 1, 1), ncam=1, width=256, height=256, ert=0.0,
                   storage="f32", cams="direction"),
@@ -478,7 +508,17 @@ def run_ours(args, cfg_name, cfg):
     dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"],
                   tile=(args.tile_w, args.tile_h), iso=iso, ordered=ordered, skip=skip, shadow=shadow is not None)
     tune = None
-    if not args.no_autotune:
+    if args.gather:
+        # a fixed launch form instead of the autotuner's choice, recorded as
+        # the choice so that every later frame of the run keeps it
+        tune = {"tile": [args.tile_w or 16, args.tile_h or 16],
+                "flags": dpv.GATHER_FLAGS[args.gather] | (dpv.FRAME_PERSISTENT if args.persistent else 0),
+                "ms": None, "candidates": 0, "cached": False, "fixed": True}
+        fl = tune["flags"]
+        dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"], tile=tuple(tune["tile"]),
+                      gather=args.gather, persistent=args.persistent, iso=iso, ordered=ordered, skip=skip,
+                      shadow=shadow is not None)
+    elif not args.no_autotune:
         tune = dev.autotune(frames=3, cache=args.autotune_cache, key=cfg_name)
         fl = tune["flags"]
         dev.set_frame(W, H, step_voxels=0.5, sigma_max=cfg.get("sigma_max", 8.0), ert=cfg["ert"], tile=tuple(tune["tile"]),
@@ -925,6 +965,9 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=12.0, help="seconds of oracle work per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--gather", default=None, choices=["cell", "quad", "linear"],
+                    help="fixed gather layout (with --tile-w/--tile-h, --persistent) instead of the autotuner's choice")
+    ap.add_argument("--persistent", action="store_true", help="with --gather: the persistent launch form")
     ap.add_argument("--autotune-cache", default=None,
                     help="JSON file: reuse the stored launch choice for this workload and GPU, else tune and store it")
     args = ap.parse_args()
