@@ -120,7 +120,10 @@ typedef struct {
 #define DPV_FRAME_LINEAR 4         /* gather the 8 corners from the stored nodes */
 #define DPV_FRAME_PERSISTENT 8     /* persistent ray-march: a grid sized to the GPU pulls
                                       work items from a counter in brick-major order (all
-                                      cameras' tiles of one brick together) */
+                                      cameras' tiles of one brick together).  With
+                                      DPV_FRAME_ORDERED: warps pull 32 pixels at a time and a
+                                      lane whose ray has finished takes the next pixel (ray
+                                      refill); the same frame, bit for bit */
 #define DPV_FRAME_GRAPH 16         /* replay the frame's launches from a CUDA graph
                                       captured at the first render after a change (not
                                       while profiling is on) */

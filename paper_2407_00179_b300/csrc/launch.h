@@ -70,7 +70,8 @@ cudaError_t launch_march_fwd(int dtype, int gather, const FrameParams& P, const 
 cudaError_t launch_march_ordered(int dtype, int gather, const FrameParams& P, const CamBasis* cams,
                                  const BrickDev* bricks, const float* scales, const int* tile_first,
                                  const int* tile_count, const Item* items, const float4* tf, float4* out_rgba,
-                                 float* out_depth, unsigned char* order, Counters* counters, cudaStream_t st);
+                                 float* out_depth, unsigned char* order, Counters* counters, unsigned int* work,
+                                 cudaStream_t st);
 
 // Empty-space skipping (DPV_FRAME_SKIP): macro-cells a brick needs, their
 // value ranges (built per committed brick), and the per-render transparency
