@@ -121,9 +121,8 @@ typedef struct {
 #define DPV_FRAME_PERSISTENT 8     /* persistent ray-march: a grid sized to the GPU pulls
                                       work items from a counter in brick-major order (all
                                       cameras' tiles of one brick together).  With
-                                      DPV_FRAME_ORDERED: warps pull 32 pixels at a time and a
-                                      lane whose ray has finished takes the next pixel (ray
-                                      refill); the same frame, bit for bit */
+                                      DPV_FRAME_ORDERED: warps pull 32 pixels (a warp's share
+                                      of a tile) at a time; the same frame, bit for bit */
 #define DPV_FRAME_GRAPH 16         /* replay the frame's launches from a CUDA graph
                                       captured at the first render after a change (not
                                       while profiling is on) */
@@ -491,8 +490,7 @@ typedef struct {
  * exits.  A frame needs about width x height x (80 + 20 x num_ranks) bytes
  * of it (e.g. 512 x 512 with 8 ranks); larger requests fail with
  * DPV_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address, so that first call should come before any stream capture
- * on that device.  Every call reuses the
+ * device address (cudaGetSymbolAddress) and keeps it.  Every call reuses the
  * same array, so calls that overlap on the GPU -- on different streams or
  * from different host threads -- race and must be serialised by the caller.
  * It marches the linear gather layout and ignores the layout, staged,

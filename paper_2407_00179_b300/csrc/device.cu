@@ -773,12 +773,12 @@ dpv_status enqueue_render(dpv_device dev, cudaStream_t st, bool timed) {
     t0 = timed ? stage_start(dev) : nullptr;
     if (ordered) {
         // march and composite in one launch: the frame is written directly
-        // (persistent with ray refill when DPV_FRAME_PERSISTENT is set)
-        const bool refill = (dev->frame.flags & DPV_FRAME_PERSISTENT) != 0;
+        // (the persistent form when DPV_FRAME_PERSISTENT is set)
+        const bool pers_ord = (dev->frame.flags & DPV_FRAME_PERSISTENT) != 0;
         CK(launch_march_ordered(dev->bricks[0].dtype, dev->gather, P, dev->d_cams, dev->d_bricks, dev->d_scales,
                                 dev->d_tile_first, dev->d_tile_count, dev->d_items, dev->d_tf, dev->d_out_rgba,
                                 dev->d_out_depth, P.order_stride ? dev->d_order : nullptr, dev->d_counters,
-                                refill ? dev->d_work : nullptr, st),
+                                pers_ord ? dev->d_work : nullptr, st),
            "ordered march");
         if (timed) stage_stop(dev, DPV_STAGE_MARCH, t0);
         dev->launches += 6 + 1;

@@ -685,6 +685,27 @@ __device__ __forceinline__ TFSample tf_lookup(const float4* tab, const FramePara
     return r;
 }
 
+// The lookup of tf_lookup, with the two entries of the last interval kept
+// in registers: consecutive samples of a ray often fall in the same
+// interval, and then no shared-memory load is needed.  Same arithmetic.
+struct TFCache {
+    int i = -1;
+    float4 a, b;
+    __device__ __forceinline__ float4 lookup(const float4* tab, const FrameParams& P, float s) {
+        float u = fmaf(s, P.tf_scale, P.tf_bias);
+        u = fminf(fmaxf(u, 0.0f), (float)(P.ntf - 1));
+        const int i0 = min(__float2int_rd(u), P.ntf - 2);
+        const float w = u - (float)i0;
+        if (i0 != i) {
+            i = i0;
+            a = tab[i0];
+            b = tab[i0 + 1];
+        }
+        return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y), fmaf(w, b.z - a.z, a.z),
+                           fmaf(w, b.w - a.w, a.w));
+    }
+};
+
 // The lookup with the segment's slopes b - a per channel (the adjoint's
 // ds term), from the same two entries.
 __device__ __forceinline__ TFSample tf_lookup_slope(const float4* tab, const FrameParams& P, float s, float4& d) {

@@ -429,6 +429,7 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                 float fx, fy, fz;
                 wk.at(m, 0, ix, iy, iz, fx, fy, fz);
                 raw.fetch(b, ix, iy, iz);
+                TFCache tfc;
                 for (; k < n; ++k) {
                     float v[8];
                     raw.decode(v);
@@ -438,12 +439,12 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                         raw.fetch(b, ix, iy, iz);
                     }
                     float s = lerp_cell<T>(v, cx, cy, cz, scale);
-                    TFSample c = tf_lookup(s_tf, P, s);
-                    float al = sample_alpha(P, c.v.w);
+                    const float4 c = tfc.lookup(s_tf, P, s);
+                    float al = sample_alpha(P, c.w);
                     float ta = Tr * al;
-                    C0 = fmaf(ta, c.v.x, C0);
-                    C1 = fmaf(ta, c.v.y, C1);
-                    C2 = fmaf(ta, c.v.z, C2);
+                    C0 = fmaf(ta, c.x, C0);
+                    C1 = fmaf(ta, c.y, C1);
+                    C2 = fmaf(ta, c.z, C2);
                     Tr = Tr - ta;
                     if (P.ert_on && 1.0f - Tr > P.ert) {
                         ++k;
@@ -576,10 +577,11 @@ __device__ __forceinline__ unsigned long long march_any(const FrameParams& P, co
 // The march over the cell layout is held to 48 registers, 5 CTAs per SM;
 // its plain form keeps the next sample's cell in flight (software
 // pipelining): more loads in flight per SM, measured 5 % faster than 4 CTAs
-// at 52 registers.
+// at 52 registers.  The others at 64 registers, 4 CTAs per SM (the quad
+// march with its kept TF entries: 7 % faster than at 67 registers, 3 CTAs).
 template <int GL, int MODE>
 constexpr int fwd_min_ctas() {
-    return GL == GATHER_CELL ? 5 : 1;
+    return GL == GATHER_CELL ? 5 : 4;
 }
 
 template <typename T, int GL, int MODE>

@@ -45,7 +45,6 @@ dpv_status na_fail(dpv_status s, const char* msg) {
 // Device address of the scratch array on the current device, looked up on
 // the first call on each device (with that device current) and cached; the
 // host-side name of the array is only a host stand-in, not a device address.
-// That first call should therefore come before any stream capture.
 dpv_status scratch_address(int device, unsigned char** out) {
     if (device < 0 || device >= kMaxDevices) return na_fail(DPV_ERR_UNSUPPORTED, "device index too large");
     std::lock_guard<std::mutex> lock(g_mu);

@@ -152,12 +152,12 @@ def _ordered_outputs(sc, gather, skip, order, persistent):
 
 
 @pytest.mark.parametrize("i", range(len(CASES)))
-def test_refill_form_is_bit_identical(i):
-    """The persistent form with ray refill (DPV_FRAME_PERSISTENT) writes the
-    per-tile form's colour, depth and order map bit for bit and evaluates
-    the same samples: every layout, with and without empty-space skipping,
-    with and without the order map (a terminated ray still lists the
-    segments behind it)."""
+def test_persistent_form_is_bit_identical(i):
+    """The persistent form (DPV_FRAME_PERSISTENT: warps pull 32 pixels at a
+    time) writes the per-tile form's colour, depth and order map bit for bit
+    and evaluates the same samples: every layout, with and without
+    empty-space skipping, with and without the order map (a terminated ray
+    still lists the segments behind it)."""
     sc = _scene(i)
     for gather in ("cell", "quad", "linear"):
         for skip, order in ((False, False), (True, False), (False, True)):
@@ -168,3 +168,34 @@ def test_refill_form_is_bit_identical(i):
                 assert torch.equal(a, b), (gather, skip, order)
             for a, b in zip(oa, ob):
                 assert torch.equal(a, b), (gather, skip, order)
+
+
+def test_long_work_lists_scan_the_list(orc):
+    """Tile lists longer than the per-ray entry cache (16 items) take the
+    scanning selection: one 16x16 tile that sees the whole of a 40-brick k-d
+    partition (a wide field of view), both launch forms and every layout bit
+    for bit, and the frame against the oracle."""
+    dims = (64, 60, 56)
+    c = inputs.camera_from_direction(dims, (1.0, 0.7, 0.5))
+    cam = inputs.Camera(c.eye, c.center, c.up, 100.0)
+    sc = scenes.make(dims, kd=40, cams=[cam], nblobs=10, seed=3, width=16, height=16, tile=(16, 16),
+                     sigma_max=60.0, ert=0.95)
+    dev = _device(sc)
+    st = dev.stats()
+    assert st["work_items"] > 16                        # the one tile's list
+    dev.release()
+    ref_frames = None
+    for gather in ("cell", "quad", "linear"):
+        for persistent in (False, True):
+            f, _, n = _ordered_outputs(sc, gather, False, False, persistent=persistent)
+            if ref_frames is None:
+                ref_frames, ref_n = f, n
+            assert n == ref_n
+            for a, b in zip(f, ref_frames):
+                assert torch.equal(a, b), (gather, persistent)
+    ref = orc.render_ordered(sc.dims, sc.tf, sc.cams[0], scenes.oracle_frame(orc, sc),
+                             bricks=scenes.oracle_bricks(orc, sc), spacing=sc.spacing)
+    rgba = ref_frames[0][:sc.width * sc.height * 4].reshape(-1, 4).double().cpu().numpy()
+    ok = (ref["flags"] & (scenes.FLAG["exit"] | scenes.FLAG["ert"])) == 0
+    assert ok.mean() > 0.8 and ref["rgba"][:, 3].max() > 0.3
+    assert np.abs(rgba - ref["rgba"])[ok].max() <= TOL
