@@ -484,8 +484,8 @@ struct CellRaw<__nv_fp8_e4m3> {
 
 // The quad layout interleaves pairs of z layers: face (x, y, z) is vector
 // ((z / 2) qxy + y qx + x) 2 + z % 2, so a cell at even z finds its lower
-// and upper faces side by side (one aligned load of both, one sector);
-// at odd z they are its pair's second and the next pair's first face.
+// and upper faces side by side (one sector); at odd z they are its pair's
+// second and the next pair's first face.
 // (32-bit arithmetic: a brick holds under 2^31 nodes, so under 2^32 slots.)
 __device__ __forceinline__ unsigned quad_slot(const BrickDev& b, int x, int y, int z) {
     return ((unsigned)(z >> 1) * (unsigned)b.qxy + (unsigned)y * (unsigned)b.qx + (unsigned)x) * 2u + (unsigned)(z & 1);
@@ -496,51 +496,19 @@ __device__ __forceinline__ unsigned cell_slot(const BrickDev& b, int x, int y, i
     return (unsigned)z * (unsigned)b.qxy + (unsigned)y * (unsigned)b.qx + (unsigned)x;
 }
 
-// Both faces of a pair in one load.
-template <typename T>
-struct QuadPair;
-template <>
-struct QuadPair<float> {
-    static __device__ __forceinline__ void load(const float4* p, float4& lo, float4& hi) {
-        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
-            : "l"(p));
-    }
-};
-template <typename H>
-struct QuadPair16 {
-    static __device__ __forceinline__ void load(const uint2* p, uint2& lo, uint2& hi) {
-        const uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
-        lo = make_uint2(w.x, w.y);
-        hi = make_uint2(w.z, w.w);
-    }
-};
-template <>
-struct QuadPair<__half> : QuadPair16<__half> {};
-template <>
-struct QuadPair<__nv_bfloat16> : QuadPair16<__nv_bfloat16> {};
-template <>
-struct QuadPair<__nv_fp8_e4m3> {
-    static __device__ __forceinline__ void load(const unsigned* p, unsigned& lo, unsigned& hi) {
-        const uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
-        lo = w.x;
-        hi = w.y;
-    }
-};
-
 // Raw face vectors of one cell in the quad layout (lower face, upper face),
-// fetched one sample ahead and decoded at use.
+// fetched one sample ahead and decoded at use.  Two loads for every cell,
+// with no branch on the parity of z: at even z the upper face is the next
+// slot of the same pair (the same sector), at odd z it is the lower face of
+// the next pair.  Measured faster than one pair-wide load at even z behind
+// a branch (lanes of a warp differ in z parity): bf16 +6 %, f32 +15 %.
 template <typename T>
 struct QuadRaw {
     typename Quad<T>::W lo, hi;
     __device__ __forceinline__ void fetch(const BrickDev& b, int x, int y, int z) {
         const typename Quad<T>::W* q = reinterpret_cast<const typename Quad<T>::W*>(b.gather) + quad_slot(b, x, y, z);
-        if (!(z & 1)) {
-            QuadPair<T>::load(q, lo, hi);
-        } else {
-            lo = __ldg(q);
-            hi = __ldg(q + (2u * (unsigned)b.qxy - 1u));
-        }
+        lo = __ldg(q);
+        hi = __ldg(q + ((z & 1) ? (2u * (unsigned)b.qxy - 1u) : 1u));
     }
     __device__ __forceinline__ void decode(float v[8]) const {
         Quad<T>::unpack(lo, v[0], v[1], v[2], v[3]);
