@@ -530,6 +530,17 @@ dpv_status prepare(dpv_device dev) {
         }
     }
     dev->gather = kind;
+    // the forward's quad gather uses pair-wide loads where a brick's layout
+    // is far larger than L2 (its faces then come from DRAM): more than 4 L2
+    P.quad_pair = 0;
+    if (kind == GATHER_QUAD) {
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev->cuda_device);
+        size_t biggest = 0;
+        for (int k = 0; k < dev->nranks; ++k)
+            biggest = std::max(biggest, quad_bytes(dev->bricks[k].dtype, dev->bricks[k].s_n));
+        P.quad_pair = biggest > 4 * (size_t)l2 ? 1 : 0;
+    }
     // empty-space skipping: per-brick macro-cell value ranges (once per
     // committed brick) and one transparency byte per macro-cell
     for (int k = 0; k < dev->nranks; ++k) {

@@ -176,6 +176,7 @@ struct FrameParams {
     int box_cap;       // floats of shared memory per slab box (staged march)
     int ordered_on;    // visibility-ordered march, global early termination
     int skip_on;       // empty-space skipping in the forward march
+    int quad_pair;     // forward quad gather: pair-wide loads (layouts far larger than L2)
     int deep;          // fragment layers per work item: 1, or DEEP_LAYERS (deep fragments)
     int shadow_on;     // volumetric shadows by ray forwarding
     float hl[3];       // shadow step h L, node units
@@ -484,8 +485,8 @@ struct CellRaw<__nv_fp8_e4m3> {
 
 // The quad layout interleaves pairs of z layers: face (x, y, z) is vector
 // ((z / 2) qxy + y qx + x) 2 + z % 2, so a cell at even z finds its lower
-// and upper faces side by side (one sector); at odd z they are its pair's
-// second and the next pair's first face.
+// and upper faces side by side (one sector, or one load of both); at odd z
+// they are its pair's second and the next pair's first face.
 // (32-bit arithmetic: a brick holds under 2^31 nodes, so under 2^32 slots.)
 __device__ __forceinline__ unsigned quad_slot(const BrickDev& b, int x, int y, int z) {
     return ((unsigned)(z >> 1) * (unsigned)b.qxy + (unsigned)y * (unsigned)b.qx + (unsigned)x) * 2u + (unsigned)(z & 1);
@@ -496,19 +497,59 @@ __device__ __forceinline__ unsigned cell_slot(const BrickDev& b, int x, int y, i
     return (unsigned)z * (unsigned)b.qxy + (unsigned)y * (unsigned)b.qx + (unsigned)x;
 }
 
-// Raw face vectors of one cell in the quad layout (lower face, upper face),
-// fetched one sample ahead and decoded at use.  Two loads for every cell,
-// with no branch on the parity of z: at even z the upper face is the next
-// slot of the same pair (the same sector), at odd z it is the lower face of
-// the next pair.  Measured faster than one pair-wide load at even z behind
-// a branch (lanes of a warp differ in z parity): bf16 +6 %, f32 +15 %.
+// Both faces of a pair in one load.
 template <typename T>
+struct QuadPair;
+template <>
+struct QuadPair<float> {
+    static __device__ __forceinline__ void load(const float4* p, float4& lo, float4& hi) {
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+            : "l"(p));
+    }
+};
+template <typename H>
+struct QuadPair16 {
+    static __device__ __forceinline__ void load(const uint2* p, uint2& lo, uint2& hi) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(p));
+        lo = make_uint2(w.x, w.y);
+        hi = make_uint2(w.z, w.w);
+    }
+};
+template <>
+struct QuadPair<__half> : QuadPair16<__half> {};
+template <>
+struct QuadPair<__nv_bfloat16> : QuadPair16<__nv_bfloat16> {};
+template <>
+struct QuadPair<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ void load(const unsigned* p, unsigned& lo, unsigned& hi) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2*>(p));
+        lo = w.x;
+        hi = w.y;
+    }
+};
+
+// Raw face vectors of one cell in the quad layout (lower face, upper face),
+// fetched one sample ahead and decoded at use.  At even z the upper face is
+// the next slot of the same pair (the same sector), at odd z the lower face
+// of the next pair.  By default two loads for every cell, with no branch on
+// the parity of z (lanes of a warp differ in it); with PAIR one pair-wide
+// load at even z behind that branch.  Measured: where the layout is served
+// from L1/L2 (512^3) the branch-free form is faster (forward bf16 +6 %, f32
+// +15 %); where every sample's faces come from DRAM (2048^3 bf16) the
+// pair-wide load is (forward 195.6 against 199.0 ms), and the adjoint
+// prefers the branch-free form at both sizes (2048^3: 746.7 against 756.8 ms).
+template <typename T, bool PAIR = false>
 struct QuadRaw {
     typename Quad<T>::W lo, hi;
     __device__ __forceinline__ void fetch(const BrickDev& b, int x, int y, int z) {
         const typename Quad<T>::W* q = reinterpret_cast<const typename Quad<T>::W*>(b.gather) + quad_slot(b, x, y, z);
-        lo = __ldg(q);
-        hi = __ldg(q + ((z & 1) ? (2u * (unsigned)b.qxy - 1u) : 1u));
+        if (PAIR && !(z & 1)) {
+            QuadPair<T>::load(q, lo, hi);
+        } else {
+            lo = __ldg(q);
+            hi = __ldg(q + ((z & 1) ? (2u * (unsigned)b.qxy - 1u) : 1u));
+        }
     }
     __device__ __forceinline__ void decode(float v[8]) const {
         Quad<T>::unpack(lo, v[0], v[1], v[2], v[3]);
@@ -516,18 +557,19 @@ struct QuadRaw {
     }
 };
 
-// The raw gather of the layouts that fetch one sample ahead.
-template <typename T, int GL>
+// The raw gather of the layouts that fetch one sample ahead (PAIR: the
+// quad layout's pair-wide load at even z).
+template <typename T, int GL, bool PAIR = false>
 struct GatherRaw;
-template <typename T>
-struct GatherRaw<T, GATHER_CELL> {
+template <typename T, bool PAIR>
+struct GatherRaw<T, GATHER_CELL, PAIR> {
     CellRaw<T> r;
     __device__ __forceinline__ void fetch(const BrickDev& b, int x, int y, int z) { r.fetch(b.gather, cell_slot(b, x, y, z)); }
     __device__ __forceinline__ void decode(float v[8]) const { r.decode(v); }
 };
-template <typename T>
-struct GatherRaw<T, GATHER_QUAD> {
-    QuadRaw<T> r;
+template <typename T, bool PAIR>
+struct GatherRaw<T, GATHER_QUAD, PAIR> {
+    QuadRaw<T, PAIR> r;
     __device__ __forceinline__ void fetch(const BrickDev& b, int x, int y, int z) { r.fetch(b, x, y, z); }
     __device__ __forceinline__ void decode(float v[8]) const { r.decode(v); }
 };

@@ -395,7 +395,7 @@ cudaError_t launch_cull(const FrameParams& P, const CamIn* d_cam_in, float3 orig
 // One work item: every thread marches its pixel's ray through the item's
 // brick and writes the fragment to slot `item * tile_pixels + thread`.
 // Returns the samples this thread evaluated.
-template <typename T, int GL, bool SKIP>
+template <typename T, int GL, bool SKIP, bool PAIR = false>
 __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, const CamBasis* cams,
                                                          const BrickDev* bricks, const float* scales, const Item& it,
                                                          long long item, int t, const float4* s_tf,
@@ -424,7 +424,7 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                 // the next sample's cell (or its two faces) is fetched before
                 // this one's arithmetic, so its load overlaps the current
                 // sample's work; the interpolation is trilinear()'s, bit for bit
-                GatherRaw<T, GL == GATHER_CELL ? GATHER_CELL : GATHER_QUAD> raw;
+                GatherRaw<T, GL == GATHER_CELL ? GATHER_CELL : GATHER_QUAD, PAIR> raw;
                 int ix, iy, iz;
                 float fx, fy, fz;
                 wk.at(m, 0, ix, iy, iz, fx, fy, fz);
@@ -564,14 +564,15 @@ __device__ __forceinline__ unsigned long long march_item_deep(const FrameParams&
     return nsamp;
 }
 
-// MODE: 0 the plain march, 1 with empty-space skipping, 2 deep fragments
+// MODE: 0 the plain march, 1 with empty-space skipping, 2 deep fragments,
+// 3 the plain march with the quad layout's pair-wide loads
 template <typename T, int GL, int MODE>
 __device__ __forceinline__ unsigned long long march_any(const FrameParams& P, const CamBasis* cams,
                                                         const BrickDev* bricks, const float* scales, const Item& it,
                                                         long long item, int t, const float4* s_tf, float4* frag_rgba,
                                                         int* frag_key) {
     if (MODE == 2) return march_item_deep<T, GL>(P, cams, bricks, scales, it, item, t, s_tf, frag_rgba, frag_key);
-    return march_item<T, GL, MODE == 1>(P, cams, bricks, scales, it, item, t, s_tf, frag_rgba, frag_key);
+    return march_item<T, GL, MODE == 1, MODE == 3>(P, cams, bricks, scales, it, item, t, s_tf, frag_rgba, frag_key);
 }
 
 // The march over the cell layout is held to 48 registers, 5 CTAs per SM;
@@ -667,12 +668,20 @@ template <typename T, int GL>
 static void fwd_launch(const FrameParams& P, const CamBasis* cams, const BrickDev* bricks, const float* scales,
                        const Item* items, int n_items, const float4* tf, float4* frag_rgba, int* frag_key,
                        Counters* counters, const Schedule* sch, cudaStream_t st) {
-    if (P.deep > 1)
+    if (P.deep > 1) {
         fwd_launch_s<T, GL, 2>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st);
-    else if (P.skip_on)
+    } else if (P.skip_on) {
         fwd_launch_s<T, GL, 1>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st);
-    else
+    } else {
+        if constexpr (GL == GATHER_QUAD) {
+            if (P.quad_pair) {
+                fwd_launch_s<T, GL, 3>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters,
+                                       sch, st);
+                return;
+            }
+        }
         fwd_launch_s<T, GL, 0>(P, cams, bricks, scales, items, n_items, tf, frag_rgba, frag_key, counters, sch, st);
+    }
 }
 
 // ===========================================================================
