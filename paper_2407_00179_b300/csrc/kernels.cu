@@ -1891,8 +1891,11 @@ size_t face_slots(const int s_n[3]) { return (size_t)(s_n[0] - 1) * (s_n[1] - 1)
 
 // Rows of nodes a thread gathers at once (face rows ly - 1 .. ly + GR - 1
 // are loaded together, each once, so their latencies overlap).
-constexpr int GR = 4;
+constexpr int GR = 2;
 
+// A thread takes one x column of GR node rows in both layers of a pair of z
+// layers (2p, 2p + 1): their face slots are adjacent in the buffer, so each
+// of its loads uses the whole 32-byte sector it brings in.
 __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, const int* nb_first, const int* nb,
                                                      const float4* gface, int dims0, int dims1, float* dvol,
                                                      FaceGroup fg, int add) {
@@ -1909,69 +1912,83 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
     const BrickDev bo = bricks[o];
     const int nx = bo.o_hi[0] - bo.o_lo[0], ny = bo.o_hi[1] - bo.o_lo[1], nz = bo.o_hi[2] - bo.o_lo[2];
     const int ngy = (ny + GR - 1) / GR;
-    const int ngroups = ngy * nz;
-    // z fastest: the two layers that share the face buffer's sectors are
-    // read by neighbouring groups, close in time
+    // local z of the owned layers: lz0 .. lz0 + nz - 1, spanning the layer
+    // pairs p0 .. p0 + npairs - 1 (a pair's layer outside them is skipped;
+    // its slots are in the brick's range, the slot count being even)
+    const int lz0 = bo.o_lo[2] - bo.s_lo[2];
+    const int p0 = lz0 >> 1, npairs = ((lz0 + nz - 1) >> 1) - p0 + 1;
+    const int ngroups = ngy * npairs;
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int yy0 = (grp / nz) * GR, zz = grp % nz;
-        const int gy0 = bo.o_lo[1] + yy0, gz = bo.o_lo[2] + zz;
-        const int ly0 = gy0 - bo.s_lo[1], lz = gz - bo.s_lo[2];
-        // slot of face (0, 0, lz): face (x, y, lz) is at fo + 2 (y qx + x)
-        const long long fo = bo.gface_off - fg.base + face_slot(bo, 0, 0, lz);   // read only if own
-        // block-uniform trip count: the shuffles below need every lane
+        const int yy0 = (grp / npairs) * GR, p = p0 + grp % npairs;
+        const int gy0 = bo.o_lo[1] + yy0;
+        const int ly0 = gy0 - bo.s_lo[1];
+        // slot of face (0, 0, 2p): face (x, y, 2p + h) is at fo + 2 (y qx + x) + h
+        const long long fo = bo.gface_off - fg.base + face_slot(bo, 0, 0, 2 * p);   // read only if own
+        // block-uniform trip count
         for (int x0 = 0; x0 < nx; x0 += blockDim.x) {
             const int xo = x0 + threadIdx.x;
             const bool act = xo < nx;
             const int gx = bo.o_lo[0] + xo, lx = gx - bo.s_lo[0];
             const bool xl = lx >= 1, xr = lx <= bo.s_n[0] - 2;
-            // face rows ly0 - 1 + k, k = 0 .. GR: this node's face A and the
-            // face to its left L (loaded by this thread too: the left
-            // neighbour's load brings the line into L1, and no lane waits
-            // on a divergent reload at the warp's edge)
-            float4 A[GR + 1];
-            float Ly[GR + 1], Lw[GR + 1];
+            // face rows ly0 - 1 + k, k = 0 .. GR, both layers: this node's
+            // face A and the face to its left (loaded by this thread too: the
+            // left neighbour's load brings the line into L1)
+            float4 A[GR + 1][2];
+            float Ly[GR + 1][2], Lw[GR + 1][2];
 #pragma unroll
             for (int k = 0; k <= GR; ++k) {
                 const int fy = ly0 - 1 + k;
                 const bool row = own && act && fy >= 0 && fy <= bo.s_n[1] - 2 && yy0 - 1 + k < ny;
                 const float4* f = gface + fo + 2 * ((long long)fy * bo.qx + lx);
-                A[k] = row && xr ? f[0] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 q = row && xl ? f[-2] : make_float4(0.f, 0.f, 0.f, 0.f);
-                Ly[k] = q.y;
-                Lw[k] = q.w;
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    A[k][h] = row && xr ? f[h] : z4;
+                    const float4 q = row && xl ? f[h - 2] : z4;
+                    Ly[k][h] = q.y;
+                    Lw[k][h] = q.w;
+                }
             }
 #pragma unroll
-            for (int k = 0; k < GR; ++k) {
-                const int yy = yy0 + k;
-                if (!act || yy >= ny) continue;
-                const int gy = gy0 + k;
-                // node row ly0 + k: corner (0,0) of face row k+1, (1,0) of its
-                // left face, (0,1) of face row k, (1,1) of its left face
-                float v = A[k + 1].x + Ly[k + 1] + A[k].z + Lw[k];
-                // ghost copies in other bricks exist only for nodes on the
-                // owned box's surface
-                const bool surface = yy == 0 || yy == ny - 1 || zz == 0 || zz == nz - 1 || xo == 0 || xo == nx - 1;
-                if (!own && !surface) continue;
-                if (surface) {
-                    for (int j = j0 + 1; j < j1; ++j) {
-                        if (nb[j] < fg.k0 || nb[j] >= fg.k1) continue;
-                        const BrickDev& b = bricks[nb[j]];
-                        const int mx = gx - b.s_lo[0], my = gy - b.s_lo[1], mz = gz - b.s_lo[2];
-                        if (mx < 0 || my < 0 || mz < 0 || mx >= b.s_n[0] || my >= b.s_n[1] || mz >= b.s_n[2]) continue;
-                        const float4* G = gface + (b.gface_off - fg.base) + face_slot(b, 0, 0, mz);
-                        const bool bxl = mx >= 1, bxr = mx <= b.s_n[0] - 2, byl = my >= 1, byr = my <= b.s_n[1] - 2;
-                        const long long q0 = 2 * ((long long)my * b.qx + mx), q1 = q0 - 2 * (long long)b.qx;
-                        if (bxr && byr) v += G[q0].x;
-                        if (bxl && byr) v += G[q0 - 2].y;
-                        if (bxr && byl) v += G[q1].z;
-                        if (bxl && byl) v += G[q1 - 2].w;
+            for (int h = 0; h < 2; ++h) {
+                const int zz = 2 * p + h - lz0;
+                if (zz < 0 || zz >= nz) continue;
+                const int gz = bo.o_lo[2] + zz;
+#pragma unroll
+                for (int k = 0; k < GR; ++k) {
+                    const int yy = yy0 + k;
+                    if (!act || yy >= ny) continue;
+                    const int gy = gy0 + k;
+                    // node row ly0 + k: corner (0,0) of face row k+1, (1,0) of its
+                    // left face, (0,1) of face row k, (1,1) of its left face
+                    float v = A[k + 1][h].x + Ly[k + 1][h] + A[k][h].z + Lw[k][h];
+                    // ghost copies in other bricks exist only for nodes on the
+                    // owned box's surface
+                    const bool surface =
+                        yy == 0 || yy == ny - 1 || zz == 0 || zz == nz - 1 || xo == 0 || xo == nx - 1;
+                    if (!own && !surface) continue;
+                    if (surface) {
+                        for (int j = j0 + 1; j < j1; ++j) {
+                            if (nb[j] < fg.k0 || nb[j] >= fg.k1) continue;
+                            const BrickDev& b = bricks[nb[j]];
+                            const int mx = gx - b.s_lo[0], my = gy - b.s_lo[1], mz = gz - b.s_lo[2];
+                            if (mx < 0 || my < 0 || mz < 0 || mx >= b.s_n[0] || my >= b.s_n[1] || mz >= b.s_n[2])
+                                continue;
+                            const float4* G = gface + (b.gface_off - fg.base) + face_slot(b, 0, 0, mz);
+                            const bool bxl = mx >= 1, bxr = mx <= b.s_n[0] - 2, byl = my >= 1, byr = my <= b.s_n[1] - 2;
+                            const long long q0 = 2 * ((long long)my * b.qx + mx), q1 = q0 - 2 * (long long)b.qx;
+                            if (bxr && byr) v += G[q0].x;
+                            if (bxl && byr) v += G[q0 - 2].y;
+                            if (bxr && byl) v += G[q1].z;
+                            if (bxl && byl) v += G[q1 - 2].w;
+                        }
                     }
+                    float* dst = dvol + ((long long)gz * dims1 + gy) * dims0 + gx;
+                    if (add)
+                        *dst += v;
+                    else
+                        *dst = v;
                 }
-                float* dst = dvol + ((long long)gz * dims1 + gy) * dims0 + gx;
-                if (add)
-                    *dst += v;
-                else
-                    *dst = v;
             }
         }
     }
