@@ -695,12 +695,17 @@ __device__ __forceinline__ TFSample tf_lookup(const float4* tab, const FramePara
     return r;
 }
 
-// The lookup of tf_lookup, with the two entries of the last interval kept
-// in registers: consecutive samples of a ray often fall in the same
-// interval, and then no shared-memory load is needed.  Same arithmetic.
+// The lookup of tf_lookup, with the last interval's entries kept in
+// registers: consecutive samples of a ray often fall in the same interval,
+// and then no shared-memory load is needed.  SLOPE keeps the left entry and
+// the slope b - a instead of both entries, so the subtraction is not
+// repeated either: measured faster on the quad layout (2048^3 bf16 +1.2 %,
+// fp8 +1.8 %) and slower on the cell layout's 48-register march (512^3 f32
+// -5 %).  Same arithmetic either way.
+template <bool SLOPE>
 struct TFCache {
     int i = -1;
-    float4 a, b;
+    float4 a, b;       // entry i and, with SLOPE, b - a; else entry i + 1
     __device__ __forceinline__ float4 lookup(const float4* tab, const FrameParams& P, float s) {
         float u = fmaf(s, P.tf_scale, P.tf_bias);
         u = fminf(fmaxf(u, 0.0f), (float)(P.ntf - 1));
@@ -710,7 +715,9 @@ struct TFCache {
             i = i0;
             a = tab[i0];
             b = tab[i0 + 1];
+            if (SLOPE) b = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
         }
+        if (SLOPE) return make_float4(fmaf(w, b.x, a.x), fmaf(w, b.y, a.y), fmaf(w, b.z, a.z), fmaf(w, b.w, a.w));
         return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y), fmaf(w, b.z - a.z, a.z),
                            fmaf(w, b.w - a.w, a.w));
     }

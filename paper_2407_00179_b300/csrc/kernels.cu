@@ -429,7 +429,7 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                 float fx, fy, fz;
                 wk.at(m, 0, ix, iy, iz, fx, fy, fz);
                 raw.fetch(b, ix, iy, iz);
-                TFCache tfc;
+                TFCache<GL == GATHER_QUAD> tfc;
                 for (; k < n; ++k) {
                     float v[8];
                     raw.decode(v);

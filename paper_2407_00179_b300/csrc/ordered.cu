@@ -42,7 +42,7 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
         // arithmetic and the TF entries kept across an interval, as in the
         // sort-last march (interpolation and lookup bit-identical)
         GatherRaw<T, GL == GATHER_CELL ? GATHER_CELL : GATHER_QUAD> raw;
-        TFCache tfc;
+        TFCache<GL == GATHER_QUAD> tfc;
         int ix, iy, iz;
         float fx, fy, fz;
         wk.at(m, 0, ix, iy, iz, fx, fy, fz);
