@@ -1250,15 +1250,17 @@ __device__ __forceinline__ void tf_flush_f(TFRunF& r, float* tab, int lo) {
 }
 
 // Copies of the compensated TF gradient table per CTA (a high and a low
-// part per entry): as many as fit in 64 KB of shared memory, at most 4.
+// part per entry): as many as fit in 64 KB of shared memory, at most 6.
 // Shared memory and L1 share each SM's 256 KB and registers hold the
-// kernel to three CTAs per SM either way: at 256 entries, 4 copies take
-// 32 KB and leave the gather about 140 KB of L1.  (Plain FP32 copies, one
-// part per entry, measured at mid: 16 copies 7.61 ms, 8 copies 6.72, 4
-// copies 6.81, 2 copies 7.16.)
+// kernel to three CTAs per SM either way: at 256 entries, 6 copies take
+// 48 KB per CTA.  Measured (replay, 256 entries): 512^3 f32 one camera
+// 2 copies 7.86 ms, 4 copies 6.83, 6 copies 6.66, 8 copies 7.01; 512^3 bf16
+// two cameras 12.6, 10.83, 10.57, 10.70 ms.  (Plain FP32 copies, one part
+// per entry, at 512^3 f32: 16 copies 7.61 ms, 8 copies 6.72, 4 copies 6.81,
+// 2 copies 7.16.)
 int bwd_tf_copies(int ntf) {
     int c = 65536 / (32 * ntf);
-    return c < 1 ? 1 : (c > 4 ? 4 : c);
+    return c < 1 ? 1 : (c > 6 ? 6 : c);
 }
 
 // Floats of one copy: high parts, low parts, one float of padding.
