@@ -834,13 +834,25 @@ struct SampleWalker {
         lim[2] = b.s_n[2] - 2;
     }
 
+    // RELU: the clamp to [0, lim] as one max(min(i, lim), 0) call (lim >= 0),
+    // the same integers; measured faster in the pipelined forward marches
+    // (2048^3 quad: bf16 +1.3 %, fp8 +2.3 %; 512^3 f16 cell +4.7 %) except
+    // the float32 cell march, whose 48 registers then spill more (-15 %),
+    // and no faster in the adjoint
+    template <bool RELU = false>
     __device__ __forceinline__ void at(const MarchState& m, int k, int& ix, int& iy, int& iz, float& fx, float& fy,
                                        float& fz) const {
         const float fk = (float)k;
         float qx = fmaf(fk, m.st[0], m.q0[0]), qy = fmaf(fk, m.st[1], m.q0[1]), qz = fmaf(fk, m.st[2], m.q0[2]);
-        ix = min(max(__float2int_rd(qx), 0), lim[0]);
-        iy = min(max(__float2int_rd(qy), 0), lim[1]);
-        iz = min(max(__float2int_rd(qz), 0), lim[2]);
+        if (RELU) {
+            ix = __vimin_s32_relu(__float2int_rd(qx), lim[0]);
+            iy = __vimin_s32_relu(__float2int_rd(qy), lim[1]);
+            iz = __vimin_s32_relu(__float2int_rd(qz), lim[2]);
+        } else {
+            ix = min(max(__float2int_rd(qx), 0), lim[0]);
+            iy = min(max(__float2int_rd(qy), 0), lim[1]);
+            iz = min(max(__float2int_rd(qz), 0), lim[2]);
+        }
         fx = qx - (float)ix;
         fy = qy - (float)iy;
         fz = qz - (float)iz;

@@ -435,7 +435,7 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                     raw.decode(v);
                     const float cx = fx, cy = fy, cz = fz;
                     if (k + 1 < n) {
-                        wk.at(m, k + 1, ix, iy, iz, fx, fy, fz);
+                        wk.at<!(GL == GATHER_CELL && sizeof(T) == 4)>(m, k + 1, ix, iy, iz, fx, fy, fz);
                         raw.fetch(b, ix, iy, iz);
                     }
                     float s = lerp_cell<T>(v, cx, cy, cz, scale);

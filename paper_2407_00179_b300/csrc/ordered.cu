@@ -54,7 +54,7 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
             raw.decode(v);
             const float cx = fx, cy = fy, cz = fz;
             if (k + 1 < n) {
-                wk.at(m, k + 1, ix, iy, iz, fx, fy, fz);
+                wk.template at<!(GL == GATHER_CELL && sizeof(T) == 4)>(m, k + 1, ix, iy, iz, fx, fy, fz);
                 raw.fetch(b, ix, iy, iz);
             }
             float s = lerp_cell<T>(v, cx, cy, cz, scale);
