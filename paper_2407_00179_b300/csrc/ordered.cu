@@ -49,14 +49,7 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
         raw.fetch(b, ix, iy, iz);
         int k = 0;
         bool stop = false;
-        for (; k < n; ++k) {
-            float v[8];
-            raw.decode(v);
-            const float cx = fx, cy = fy, cz = fz;
-            if (k + 1 < n) {
-                wk.template at<!(GL == GATHER_CELL && sizeof(T) == 4)>(m, k + 1, ix, iy, iz, fx, fy, fz);
-                raw.fetch(b, ix, iy, iz);
-            }
+        auto shade = [&](const float v[8], float cx, float cy, float cz) {
             float s = lerp_cell<T>(v, cx, cy, cz, scale);
             const float4 c = tfc.lookup(s_tf, P, s);
             float al = sample_alpha(P, c.w);
@@ -65,11 +58,27 @@ __device__ __forceinline__ bool march_segment(const FrameParams& P, const BrickD
             C1 = fmaf(ta, c.y, C1);
             C2 = fmaf(ta, c.z, C2);
             Tr = Tr - ta;
-            if (P.ert_on && 1.0f - Tr > P.ert) {
+            return P.ert_on && 1.0f - Tr > P.ert;
+        };
+        // the last sample after the loop, which then tests no bound for
+        // the look-ahead (as in the sort-last march)
+        for (; k + 1 < n; ++k) {
+            float v[8];
+            raw.decode(v);
+            const float cx = fx, cy = fy, cz = fz;
+            wk.template at<!(GL == GATHER_CELL && sizeof(T) == 4)>(m, k + 1, ix, iy, iz, fx, fy, fz);
+            raw.fetch(b, ix, iy, iz);
+            if (shade(v, cx, cy, cz)) {
                 ++k;
                 stop = true;
                 break;
             }
+        }
+        if (!stop && n > 0) {
+            float v[8];
+            raw.decode(v);
+            stop = shade(v, fx, fy, fz);
+            ++k;
         }
         nsamp += (unsigned)k;
         return stop;
