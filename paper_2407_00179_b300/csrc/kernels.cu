@@ -1250,17 +1250,21 @@ __device__ __forceinline__ void tf_flush_f(TFRunF& r, float* tab, int lo) {
 }
 
 // Copies of the compensated TF gradient table per CTA (a high and a low
-// part per entry): as many as fit in 64 KB of shared memory, at most 6.
+// part per entry): as many as fit in 64 KB of shared memory, at most `cap`.
 // Shared memory and L1 share each SM's 256 KB and registers hold the
-// kernel to three CTAs per SM either way: at 256 entries, 6 copies take
-// 48 KB per CTA.  Measured (replay, 256 entries): 512^3 f32 one camera
-// 2 copies 7.86 ms, 4 copies 6.83, 6 copies 6.66, 8 copies 7.01; 512^3 bf16
-// two cameras 12.6, 10.83, 10.57, 10.70 ms.  (Plain FP32 copies, one part
-// per entry, at 512^3 f32: 16 copies 7.61 ms, 8 copies 6.72, 4 copies 6.81,
-// 2 copies 7.16.)
-int bwd_tf_copies(int ntf) {
+// kernel to three CTAs per SM either way: at 256 entries a copy takes 8 KB.
+// Where the face reductions mostly hit L2 (per-sample reductions), the
+// shared-memory atomics bound the replay and more copies pay; where they go
+// to DRAM (cell runs), the replay is bound by them and L1 for the gather
+// pays.  Measured (replay, 256 entries): 512^3 f32 one camera 2 copies
+// 7.86 ms, 4 copies 6.83, 6 copies 6.66, 8 copies 7.01; 512^3 bf16 two
+// cameras 12.6, 10.83, 10.57, 10.70 ms; 2048^3 bf16 (cell runs) 1 copy
+// 770.8 ms, 2 760.4, 3 751.2, 4 748.4, 6 779.5.  (Plain FP32 copies, one
+// part per entry, at 512^3 f32: 16 copies 7.61 ms, 8 copies 6.72, 4 copies
+// 6.81, 2 copies 7.16.)
+int bwd_tf_copies(int ntf, int cap) {
     int c = 65536 / (32 * ntf);
-    return c < 1 ? 1 : (c > 6 ? 6 : c);
+    return c < 1 ? 1 : (c > cap ? cap : c);
 }
 
 // Floats of one copy: high parts, low parts, one float of padding.
@@ -1602,7 +1606,7 @@ static void bwd_launch_f(const FrameParams& P, const CamBasis* cams, const Brick
                          const Item* items, int n_items, const float4* tf, const float4* frag_rgba,
                          const int* frag_key, const float4* frag_grad, double* dtf, float* dvol, float4* gface,
                          FaceGroup fg, Counters* counters, const Schedule* sch, cudaStream_t st) {
-    int ncopy = bwd_tf_copies(P.ntf);
+    int ncopy = bwd_tf_copies(P.ntf, FACE == 1 ? 6 : 4);
     size_t smem = sizeof(float4) * P.ntf + sizeof(float) * (size_t)ncopy * tf_copy_stride(P.ntf);
     if (sch) {
         if (smem > 48 * 1024)
