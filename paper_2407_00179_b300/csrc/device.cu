@@ -1459,9 +1459,12 @@ dpv_status dpvBackward(dpv_device dev, const float* dL_drgba, double* dL_dtf, fl
         cudaEvent_t tc = stage_start(dev);
         CK(cudaMemsetAsync(dev->d_gface, 0, dev->gface_slots * sizeof(float4), dev->stream), "zero face buffer");
         stage_stop(dev, DPV_STAGE_FACE, tc);
-    } else if (dL_dvol)
+    } else if (dL_dvol && !faces) {
+        // the scalar atomics add into the field; the face-buffer groups'
+        // gathers store each node in the first group that reaches it
         CK(cudaMemsetAsync(dL_dvol, 0, sizeof(float) * (size_t)dev->dims[0] * dev->dims[1] * dev->dims[2], dev->stream),
            "zero dvol");
+    }
     CK(cudaMemsetAsync(&dev->d_counters->samples_bwd, 0, sizeof(unsigned long long), dev->stream), "reset counter");
     cudaEvent_t t0 = stage_start(dev);
     CK(launch_composite_bwd(P, dev->d_tile_first, dev->d_tile_count, dev->d_frag_rgba, dev->d_frag_key,

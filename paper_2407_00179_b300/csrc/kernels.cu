@@ -1924,8 +1924,10 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
     const int lz0 = bo.o_lo[2] - bo.s_lo[2];
     const int p0 = lz0 >> 1, npairs = ((lz0 + nz - 1) >> 1) - p0 + 1;
     const int ngroups = ngy * npairs;
+    // row groups fastest: neighbouring groups share a face row, which the
+    // second one then finds in L2
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int yy0 = (grp / npairs) * GR, p = p0 + grp % npairs;
+        const int p = p0 + grp / ngy, yy0 = (grp % ngy) * GR;
         const int gy0 = bo.o_lo[1] + yy0;
         const int ly0 = gy0 - bo.s_lo[1];
         // slot of face (0, 0, 2p): face (x, y, 2p + h) is at fo + 2 (y qx + x) + h
@@ -1973,13 +1975,21 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
                     const bool surface =
                         yy == 0 || yy == ny - 1 || zz == 0 || zz == nz - 1 || xo == 0 || xo == nx - 1;
                     if (!own && !surface) continue;
+                    // the first pass to reach the node stores it, later passes
+                    // add: groups are consecutive rank ranges taken in order,
+                    // so the first is the group of the lowest rank storing it
+                    bool first = o >= fg.k0;
                     if (surface) {
                         for (int j = j0 + 1; j < j1; ++j) {
-                            if (nb[j] < fg.k0 || nb[j] >= fg.k1) continue;
+                            if (nb[j] >= fg.k1) continue;
                             const BrickDev& b = bricks[nb[j]];
                             const int mx = gx - b.s_lo[0], my = gy - b.s_lo[1], mz = gz - b.s_lo[2];
                             if (mx < 0 || my < 0 || mz < 0 || mx >= b.s_n[0] || my >= b.s_n[1] || mz >= b.s_n[2])
                                 continue;
+                            if (nb[j] < fg.k0) {
+                                first = false;          // an earlier group stores it too
+                                continue;
+                            }
                             const float4* G = gface + (b.gface_off - fg.base) + face_slot(b, 0, 0, mz);
                             const bool bxl = mx >= 1, bxr = mx <= b.s_n[0] - 2, byl = my >= 1, byr = my <= b.s_n[1] - 2;
                             const long long q0 = 2 * ((long long)my * b.qx + mx), q1 = q0 - 2 * (long long)b.qx;
@@ -1990,7 +2000,7 @@ __global__ void __launch_bounds__(128) k_face_gather(const BrickDev* bricks, con
                         }
                     }
                     float* dst = dvol + ((long long)gz * dims1 + gy) * dims0 + gx;
-                    if (add)
+                    if (add && !first)
                         *dst += v;
                     else
                         *dst = v;

@@ -137,9 +137,10 @@ cudaError_t launch_march_bwd(int dtype, int gather, const FrameParams& P, const 
 // into the global field gradient: every owned node of every brick is
 // written once (no zeroing needed) with the sum of its face slots over the
 // bricks in its owner's neighbour list nb[nb_first[o] .. nb_first[o+1]).
-// With a group `fg`, only the group's bricks' slots are summed, and they are
-// added to the field (zeroed before the first group) at the nodes the group
-// stores.
+// With a group `fg`, only the group's bricks' slots are summed, at the nodes
+// the group stores: the first group to reach a node (the group of the lowest
+// rank storing it; groups are consecutive rank ranges taken in order) stores
+// the sum, later groups add theirs, so the field needs no zeroing either.
 size_t face_slots(const int s_n[3]);
 cudaError_t launch_face_gather(const BrickDev* bricks, int nbricks, const int* nb_first, const int* nb,
                                long long max_rows, const float4* gface, const int dims[3], float* dvol,
