@@ -699,9 +699,19 @@ __device__ __forceinline__ TFSample tf_lookup(const float4* tab, const FramePara
 // registers: consecutive samples of a ray often fall in the same interval,
 // and then no shared-memory load is needed.  SLOPE keeps the left entry and
 // the slope b - a instead of both entries, so the subtraction is not
-// repeated either: measured faster on the quad layout (2048^3 bf16 +1.2 %,
-// fp8 +1.8 %) and slower on the cell layout's 48-register march (512^3 f32
-// -5 %).  Same arithmetic either way.
+// repeated either (the ordered march's quad form; on the sort-last quad
+// march at 4 CTAs per SM it measured 2048^3 bf16 +1.2 %, fp8 +1.8 %, but the
+// uncached lookup at 5 CTAs beats both); on the cell layout's 48-register
+// march the slope form measured 5 % slower than both entries.  Same
+// arithmetic either way.
+// The plain lookup with the TFCache interface (no registers kept: the
+// pipelined quad march, whose occupancy the kept entries would cost).
+struct TFNoCache {
+    __device__ __forceinline__ float4 lookup(const float4* tab, const FrameParams& P, float s) {
+        return tf_lookup(tab, P, s).v;
+    }
+};
+
 template <bool SLOPE>
 struct TFCache {
     int i = -1;

@@ -11,6 +11,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "dpv_internal.cuh"
 #include "launch.h"
@@ -429,7 +430,7 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                 float fx, fy, fz;
                 wk.at(m, 0, ix, iy, iz, fx, fy, fz);
                 raw.fetch(b, ix, iy, iz);
-                TFCache<GL == GATHER_QUAD> tfc;
+                typename std::conditional<GL == GATHER_QUAD, TFNoCache, TFCache<false>>::type tfc;
                 for (; k < n; ++k) {
                     float v[8];
                     raw.decode(v);
@@ -578,11 +579,16 @@ __device__ __forceinline__ unsigned long long march_any(const FrameParams& P, co
 // The march over the cell layout is held to 48 registers, 5 CTAs per SM;
 // its plain form keeps the next sample's cell in flight (software
 // pipelining): more loads in flight per SM, measured 5 % faster than 4 CTAs
-// at 52 registers.  The others at 64 registers, 4 CTAs per SM (the quad
-// march with its kept TF entries: 7 % faster than at 67 registers, 3 CTAs).
+// at 52 registers.  The pipelined quad march (plain and pair-wide forms)
+// looks its TF entries up from shared memory every sample and fits 48
+// registers with no spill, 5 CTAs per SM; keeping the last interval's
+// entries in registers instead needs 60 and holds it to 4 (measured: 2048^3
+// bf16 193.8 against 194.1 ms, fp8 175.2 against 177.2, 512^3 bf16 2.938
+// against 3.007; the lookup without the kept entries at 4 CTAs: 202.5,
+// 181.3, 2.954).  The others at 64 registers, 4 CTAs per SM.
 template <int GL, int MODE>
 constexpr int fwd_min_ctas() {
-    return GL == GATHER_CELL ? 5 : 4;
+    return GL == GATHER_CELL || (GL == GATHER_QUAD && (MODE == 0 || MODE == 3)) ? 5 : 4;
 }
 
 template <typename T, int GL, int MODE>
