@@ -430,7 +430,10 @@ __device__ __forceinline__ unsigned long long march_item(const FrameParams& P, c
                 float fx, fy, fz;
                 wk.at(m, 0, ix, iy, iz, fx, fy, fz);
                 raw.fetch(b, ix, iy, iz);
-                typename std::conditional<GL == GATHER_QUAD, TFNoCache, TFCache<false>>::type tfc;
+                // the float32 cell march keeps the TF interval's entries in
+                // registers; the others look them up every sample (fewer
+                // registers: no spills, 5 CTAs per SM for the quad march)
+                typename std::conditional<GL == GATHER_QUAD || sizeof(T) <= 2, TFNoCache, TFCache<false>>::type tfc;
                 for (; k < n; ++k) {
                     float v[8];
                     raw.decode(v);
@@ -585,7 +588,10 @@ __device__ __forceinline__ unsigned long long march_any(const FrameParams& P, co
 // entries in registers instead needs 60 and holds it to 4 (measured: 2048^3
 // bf16 193.8 against 194.1 ms, fp8 175.2 against 177.2, 512^3 bf16 2.938
 // against 3.007; the lookup without the kept entries at 4 CTAs: 202.5,
-// 181.3, 2.954).  The others at 64 registers, 4 CTAs per SM.
+// 181.3, 2.954).  The cell march of 16- and 8-bit storage also looks them
+// up every sample (its spills at 48 registers go: 2048^3 fp8 181.3 -> 175.7
+// ms, 512^3 f16 +1 %); the float32 one keeps them (1.894 against 1.99 ms at
+// 512^3).  The others at 64 registers, 4 CTAs per SM.
 template <int GL, int MODE>
 constexpr int fwd_min_ctas() {
     return GL == GATHER_CELL || (GL == GATHER_QUAD && (MODE == 0 || MODE == 3)) ? 5 : 4;
