@@ -53,23 +53,23 @@ BYTES_PER_VOXEL = {"f32": 4, "f16": 2, "bf16": 2, "fp8": 1}
 TRAFFIC = {
     # one-pass captures (time, DRAM read, DRAM write) of the bench's own
     # timed steps at full size: 3 steps, 4.7465e10 samples each
-    "large_bf16_fwd": {"bytes_per_sample": 12.629, "l1_hit": None, "l2_hit": None,
+    "large_bf16_fwd": {"bytes_per_sample": 14.248, "l1_hit": None, "l2_hit": None,
                        "capture": "profiles/bench_large_bf16_launch_list.md",
                        "case": "2048^3 bf16, 64 bricks, 8 x 3840x2160, quad layout with pair-wide loads, persistent, "
                                "8x32 tiles (the bench's timed steps)",
-                       "source": "f85c52622c8fc759"},
-    "large_bf16_bwd": {"bytes_per_sample": 54.376, "l1_hit": None, "l2_hit": None,
+                       "source": "e4384e70632415e5"},
+    "large_bf16_bwd": {"bytes_per_sample": 54.426, "l1_hit": None, "l2_hit": None,
                        "capture": "profiles/bench_large_bf16_launch_list.md",
                        "case": "2048^3 bf16, the same steps; two replay launches per step (face-buffer groups)",
-                       "source": "f85c52622c8fc759"},
+                       "source": "e4384e70632415e5"},
     # mid: the bench's timed steps (3 steps, 3.7027e8 samples each)
-    "mid_fwd": {"bytes_per_sample": 13.315, "l1_hit": None, "l2_hit": None,
+    "mid_fwd": {"bytes_per_sample": 14.341, "l1_hit": None, "l2_hit": None,
                 "capture": "profiles/bench_mid_launch_list.md",
                 "case": "512^3 f32, 8 bricks, 1920x1080, cell layout, persistent, 16x16 tiles (the bench's timed steps)",
-                "source": "f85c52622c8fc759"},
-    "mid_bwd": {"bytes_per_sample": 25.872, "l1_hit": None, "l2_hit": None,
+                "source": "e4384e70632415e5"},
+    "mid_bwd": {"bytes_per_sample": 29.936, "l1_hit": None, "l2_hit": None,
                 "capture": "profiles/bench_mid_launch_list.md",
-                "case": "512^3 f32, the same steps", "source": "f85c52622c8fc759"},
+                "case": "512^3 f32, the same steps", "source": "e4384e70632415e5"},
 }
 
 # the capture whose per-sample traffic stands for each (workload, kernel)
