@@ -69,7 +69,7 @@ typedef enum {
     DPV_ERR_OUT_OF_MEMORY = 3, /* a device or host allocation failed */
     DPV_ERR_CUDA = 4,          /* a CUDA call failed; the device is poisoned */
     DPV_ERR_TIMEOUT = 5,       /* a bounded wait expired */
-    DPV_ERR_UNSUPPORTED = 6    /* valid request this build does not handle */
+    DPV_ERR_UNSUPPORTED = 6    /* valid request the library does not handle */
 } dpv_status;
 
 typedef enum {
