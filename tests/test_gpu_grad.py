@@ -292,6 +292,45 @@ def test_face_buffer_in_brick_groups(monkeypatch, split):
     dev.release()
 
 
+@pytest.mark.parametrize("split", ["regular", "kd"])
+def test_adjoint_overwrites_every_output(monkeypatch, split):
+    """dpvBackward overwrites its outputs: caller buffers filled with NaN
+    come back finite, equal to the one-buffer pass, whether the face buffer
+    holds every brick or the bricks go in groups (where the first group to
+    reach a node stores it and later groups add: no node may be missed, on
+    the owned boxes' surfaces least of all), and on the scalar-atomic
+    path."""
+    dims = (40, 36, 32)
+    cams = inputs.sphere_cameras(dims, 2, seed=5)
+    kw = dict(splits=(2, 2, 2)) if split == "regular" else dict(kd=7)
+    sc = scenes.make(dims, nblobs=10, cams=cams, width=48, height=40, **kw)
+    dev = scenes.gpu_device(sc, order=False)
+    dev.render()
+    g = torch.from_numpy(inputs.rng(3, inputs.STREAM_GRAD).normal(size=(len(sc.cams), sc.height, sc.width, 4))
+                         .astype(np.float32)).cuda()
+    lib = dpv.load()
+
+    def run():
+        dtf = torch.full((dev.ntf, 4), float("nan"), dtype=torch.float64, device="cuda")
+        dvol = torch.full((dims[2], dims[1], dims[0]), float("nan"), dtype=torch.float32, device="cuda")
+        assert lib.dpvBackward(dev._h, g.data_ptr(), dtf.data_ptr(), dvol.data_ptr()) == 0
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(dtf).all()) and bool(torch.isfinite(dvol).all())
+        return dtf, dvol
+
+    monkeypatch.delenv("DPV_FACE_GRAD", raising=False)
+    monkeypatch.delenv("DPV_FACE_GROUP", raising=False)
+    dtf0, dvol0 = run()
+    assert float(dvol0.abs().max()) > 0
+    for env in (("DPV_FACE_GROUP", "1"), ("DPV_FACE_GROUP", "3"), ("DPV_FACE_GRAD", "0")):
+        monkeypatch.setenv(*env)
+        dtf, dvol = run()
+        monkeypatch.delenv(env[0])
+        assert torch.allclose(dvol, dvol0, rtol=1e-5, atol=1e-6 * float(dvol0.abs().max())), env
+        assert torch.allclose(dtf, dtf0, rtol=0, atol=1e-9 * float(dtf0.abs().max())), env
+    dev.release()
+
+
 def test_adjoint_run_to_run_spread():
     """The forward has no atomics and is bit-deterministic (test_gpu_parity);
     the adjoint sums with atomics in whatever order the hardware takes, so
